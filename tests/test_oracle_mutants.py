@@ -1,0 +1,130 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case below plants one mistake (a dropped term, a wrong sign, a wrong factor, a
+transposed operand) in a temporary copy of the oracle source, builds it, and runs
+the pins of ``oracle_pins``; at least one pin must fail.  Mutants listed in
+``UNPINNED`` are the known blind spots (terms no independent check reaches); they
+are asserted to survive so that the list stays honest.
+"""
+from __future__ import annotations
+
+import os
+import subprocess
+import tempfile
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+import oracle
+import oracle_pins as P
+
+SRC = open(oracle._SRC).read()
+
+# (name, text in the oracle, replacement)
+CAUGHT = [
+    ("un-Kozai direction", "rc.n0pp = rc.n0 / (1.0 + delta0)", "rc.n0pp = rc.n0 * (1.0 + delta0)"),
+    ("a0'' from n0", "rc.a0pp = pow(g.xke / rc.n0pp", "rc.a0pp = pow(g.xke / rc.n0"),
+    ("xi sign", "rc.xi = 1.0 / (rc.a0pp - rc.s)", "rc.xi = 1.0 / (rc.a0pp + rc.s)"),
+    ("q0 height", "R q0ms = (120.0 - s_km)", "R q0ms = (100.0 - s_km)"),
+    ("s* low branch", "if (hp_km < 156.0) s_km = hp_km - 78.0;", "if (hp_km < 156.0) s_km = hp_km - 58.0;"),
+    ("C1 from C2", "rc.C1 = rc.bstar * C2;", "rc.C1 = 0.5 * rc.bstar * C2;"),
+    ("Mdot first order", "rc.Mdot = rc.n0pp + 0.5 * T1", "rc.Mdot = rc.n0pp - 0.5 * T1"),
+    ("argpdot first order", "-0.5 * T1 * (1.0 - 5.0 * theta2)", "-0.5 * T1 * (1.0 - 3.0 * theta2)"),
+    ("raandot first order", "R raandot1 = -T1 * rc.cosi;", "R raandot1 = T1 * rc.cosi;"),
+    ("T1 factor", "R T1 = 1.5 * g.j2", "R T1 = 0.75 * g.j2"),
+    ("L2", "rc.L2 = 1.5 * rc.C1;", "rc.L2 = 0.5 * rc.C1;"),
+    ("aycof sign", "rc.aycof = -0.5 * g.j3oj2", "rc.aycof = 0.5 * g.j3oj2"),
+    ("a(t) power of tempa", "* tempa * tempa;", "* tempa;"),
+    ("drag e sign", "m.e = rc.e0 - tempe;", "m.e = rc.e0 + tempe;"),
+    ("mean longitude uses n0''", "M = M + rc.n0pp * templ;", "M = M + 0.5 * rc.n0pp * templ;"),
+    ("node secular", "R raan_df = rc.raan0 + rc.raandot * t;", "R raan_df = rc.raan0 - rc.raandot * t;"),
+    ("argp secular", "R argp_df = rc.argp0 + rc.argpdot * t;", "R argp_df = rc.argp0 - rc.argpdot * t;"),
+    ("axn uses sin", "R axn = m.e * cos(m.argp);", "R axn = m.e * sin(m.argp);"),
+    ("Kepler numerator sign", "R f = U - ayn * cp + axn * sp - psi;", "R f = U + ayn * cp + axn * sp - psi;"),
+    ("Kepler derivative", "R fp = 1.0 - ayn * sp - axn * cp;", "R fp = 1.0 + ayn * sp - axn * cp;"),
+    ("ecosE transposed", "R ecosE = axn * cp + ayn * sp;", "R ecosE = axn * sp + ayn * cp;"),
+    ("esinE sign", "R esinE = axn * sp - ayn * cp;", "R esinE = axn * sp + ayn * cp;"),
+    ("pL", "R pL = m.a * (1.0 - eL2);", "R pL = m.a * (1.0 + eL2);"),
+    ("rdot", "R rdot = sqrt(m.a) * esinE / rr;", "R rdot = sqrt(m.a) * esinE;"),
+    ("rfdot", "R rfdot = sqrt(pL) / rr;", "R rfdot = sqrt(m.a) / rr;"),
+    ("sinu correction sign", "(sp - ayn - axn * w)", "(sp - ayn + axn * w)"),
+    ("cosu uses axn", "(cp - axn + ayn * w)", "(cp - ayn + ayn * w)"),
+    ("k2/pL", "R k = 0.5 * g.j2 / pL;", "R k = 0.5 * g.j2 / (pL * pL);"),
+    ("rk radial J2 term", "R rk = rr * (1.0 - 1.5 * kp", "R rk = rr * (1.0 + 1.5 * kp"),
+    ("rk cos2u term", "+ 0.5 * k * rc.x1mth2 * cos2u;", "- 0.5 * k * rc.x1mth2 * cos2u;"),
+    ("uk sign", "R uk = u - 0.25 * kp", "R uk = u + 0.25 * kp"),
+    ("raank sign", "R raank = m.raan + 1.5 * kp", "R raank = m.raan - 1.5 * kp"),
+    ("ik sign", "R ik = rc.i0 + 1.5 * kp", "R ik = rc.i0 - 1.5 * kp"),
+    ("rdotk sign", "R rdotk = rdot - m.n * k", "R rdotk = rdot + m.n * k"),
+    ("rfdotk constant term", "+ 1.5 * rc.x3thm1) / g.xke;", "- 1.5 * rc.x3thm1) / g.xke;"),
+    ("M vector", "R Mx = -sO * ci, My = cO * ci", "R Mx = sO * ci, My = cO * ci"),
+    ("V vector sign", "R Vx = Mx * cu - Nx * su", "R Vx = Mx * cu + Nx * su"),
+    ("velocity scale", "double vscale = g.re * g.xke / 60.0;", "double vscale = g.re * g.xke;"),
+    ("e validity", "if (m.e >= 1.0 || m.e < -0.001)", "if (m.e >= 1.0 || m.e < -0.1)"),
+    ("decay code", "if (rk < 1.0) return 6;", "if (rk < 0.9) return 6;"),
+    ("input e range", "(rc.e0 < 0.0 || rc.e0 >= 1.0)", "(rc.e0 < 0.0 || rc.e0 >= 2.0)"),
+]
+
+# Terms that no independent check reaches (documented as parity-unpinned).
+UNPINNED = [
+    ("C2 eccentric term", "(1.0 + 1.5 * eta2 + e0eta", "(1.0 + 0.5 * eta2 + e0eta"),
+    ("C4 cos 2w term", "* cos(2.0 * rc.argp0)));", "* sin(2.0 * rc.argp0)));"),
+    ("C5 factor", "(1.0 + 2.75 * (eta2 + e0eta)", "(1.0 + 1.75 * (eta2 + e0eta)"),
+    ("D3 factor", "(17.0 * rc.a0pp + rc.s)", "(7.0 * rc.a0pp + rc.s)"),
+    ("Mdot second order", "(13.0 - 78.0 * theta2 + 137.0 * theta4)", "(13.0 - 78.0 * theta2 + 37.0 * theta4)"),
+    # second-order terms of the Kozai -> Brouwer mean-motion recovery
+    ("delta1 factor", "R delta1 = 1.5 * k2", "R delta1 = 0.75 * k2"),
+    ("a0 series sign", "- delta1 * delta1 - (134.0", "+ delta1 * delta1 - (134.0"),
+    # J3 long-period terms of the mean longitude (size ~ e J3/J2, below what the
+    # integration comparisons resolve)
+    ("xlcof sign", "rc.xlcof = -0.25 * g.j3oj2", "rc.xlcof = 0.25 * g.j3oj2"),
+    ("xlcof (3+5cos)", "(3.0 + 5.0 * rc.cosi)", "(5.0 + 3.0 * rc.cosi)"),
+    ("q = 1/(a(1-e^2))", "R q = 1.0 / (m.a * (1.0 - m.e * m.e));", "R q = 1.0 / (m.a * (1.0 + m.e * m.e));"),
+    ("U drops long period", "+ q * rc.xlcof * axn;", ";"),
+]
+
+_BUILD_DIR = tempfile.mkdtemp(prefix="oracle_mutants_")
+
+
+def _build(name, old, new):
+    assert SRC.count(old) == 1, f"mutant '{name}': pattern must occur exactly once"
+    tag = "".join(c if c.isalnum() else "_" for c in name)
+    src = os.path.join(_BUILD_DIR, f"{tag}.cpp")
+    so = os.path.join(_BUILD_DIR, f"{tag}.so")
+    with open(src, "w") as f:
+        f.write(SRC.replace(old, new))
+    subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off", "-fPIC", "-shared",
+                    "-pthread", "-o", so, src], check=True)
+    return so
+
+
+def _first_failure(lib):
+    for pin in P.ALL_PINS:
+        try:
+            fails = pin(lib)
+        except Exception as exc:  # a crash of the mutant counts as caught
+            return f"{pin.__name__}: raised {exc!r}"
+        if fails:
+            return f"{pin.__name__}: {fails[0]}"
+    return None
+
+
+@pytest.fixture(scope="module")
+def built():
+    cases = CAUGHT + UNPINNED
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        paths = list(ex.map(lambda c: _build(*c), cases))
+    return {c[0]: p for c, p in zip(cases, paths)}
+
+
+@pytest.mark.parametrize("name,old,new", CAUGHT, ids=[c[0] for c in CAUGHT])
+def test_pins_catch_mutant(built, name, old, new):
+    lib = oracle.load(built[name])
+    assert _first_failure(lib) is not None, f"no pin catches the mutant '{name}'"
+
+
+@pytest.mark.parametrize("name,old,new", UNPINNED, ids=[c[0] for c in UNPINNED])
+def test_known_blind_spots_are_still_blind(built, name, old, new):
+    lib = oracle.load(built[name])
+    assert _first_failure(lib) is None, (
+        f"'{name}' is now caught: move it from UNPINNED to CAUGHT")
