@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the SGP4 hot path: propagated states/s.
+
+One step = sgp4_init (record build) + sgp4_propagate (secular update, long-period
+terms, Kepler, short-period terms, TEME output) of the Starlink-shaped workload,
+9,341 satellites x 1,000 times over one day, on the FP32 mixed-precision path;
+the plain FP64 GPU path is timed beside it.  Inputs are resident in HBM when the
+timed region starts; L2 is flushed (256 MB write) between timed steps.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (the
+only reference this project has: the paper ships no runnable code here).
+Under torchrun each rank propagates its own copy of the workload (independent
+problems, no collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "propagated states/s (sat x time) FP32 vs FP64 at stated max |dr| km; % roofline"
+UNIT = "states/s"
+
+# Per-state algorithmic output bytes (r, v as float32 x3 + int32 status; FP64: doubles).
+BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1].split()[0]), float(parts[2].split()[0]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, _, flags in rows for k, f in enumerate(flags)
+                          if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": rows[0][1],
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle_rate(elements, tsince, n_sats: int, threads: int):
+    """Time the FP64 oracle (as it stands) on the first n_sats satellites."""
+    import oracle
+    el = elements[:n_sats]
+    oracle.load()
+    t0 = time.perf_counter()
+    oracle.propagate(el, tsince, threads=threads)
+    dt = time.perf_counter() - t0
+    return el.shape[0] * tsince.shape[-1] / dt, dt
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    from paper_2603_27830_b300 import workloads as W
+    w = W.config2()
+    threads = os.cpu_count() or 1
+    n_sample = args.ref_sats
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w.elements, w.tsince, max(1, n_sample // 10), threads)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt = cpu_oracle_rate(w.elements, w.tsince, n_sample, threads)
+        rates.append(r)
+        times.append(dt)
+    total_states = n_sample * w.t_count * args.steps
+    value = total_states / sum(times)
+    sample = f"first {n_sample} of {w.n} satellites x {w.t_count} times per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "n_sats": w.n, "t_count": w.t_count,
+                   "precision": "fp64 (CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2603_27830_b300 import sgp4_init, sgp4_propagate
+    from paper_2603_27830_b300 import workloads as W
+
+    rank, world, local = _dist()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peak_kind = _peaks()
+
+    w = W.config2()
+    n, T = w.n, w.t_count
+    states = n * T
+    el_h = torch.from_numpy(w.elements).pin_memory()
+    ts_h = torch.from_numpy(w.tsince).pin_memory()
+    el = el_h.to(dev)
+    ts = ts_h.to(dev)
+    recs, ist = sgp4_init(el)
+    out32 = (torch.empty((n, T, 3), dtype=torch.float32, device=dev),
+             torch.empty((n, T, 3), dtype=torch.float32, device=dev),
+             torch.empty((n, T), dtype=torch.int32, device=dev))
+    out64 = (torch.empty((n, T, 3), dtype=torch.float64, device=dev),
+             torch.empty((n, T, 3), dtype=torch.float64, device=dev),
+             torch.empty((n, T), dtype=torch.int32, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(prec, out):
+        sgp4_init(el, records=recs, init_status=ist)
+        sgp4_propagate(recs, ts, prec, out=out)
+
+    def timed(prec, out, steps, warmup, kernel_only=False):
+        for _ in range(warmup):
+            step(prec, out)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        tot = 0.0
+        per = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            if kernel_only:
+                sgp4_init(el, records=recs, init_status=ist)
+                a.record(stream)
+                sgp4_propagate(recs, ts, prec, out=out)
+                b.record(stream)
+            else:
+                a.record(stream)
+                step(prec, out)
+                b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            per.append(ms)
+            tot += ms
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+            t = torch.tensor([tot], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        return tot, per
+
+    # correctness spot check against the oracle (rank 0, before timing)
+    max_dr_km = None
+    if rank == 0:
+        import oracle
+        step("fp32", out32)
+        torch.cuda.synchronize()
+        k = 200
+        rr, _, sr, _ = oracle.propagate(w.elements[:k], w.tsince)
+        r32 = out32[0][:k].double().cpu().numpy()
+        ok = sr == 0
+        max_dr_km = float(np.linalg.norm(r32[ok] - rr[ok], axis=-1).max())
+
+    with ClockSampler(local) as clk:
+        ms32, per32 = timed("fp32", out32, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms32_k, per32_k = timed("fp32", out32, args.steps, 1, kernel_only=True)
+    ms64, _ = timed("fp64", out64, max(1, min(args.steps, 5)), 1)
+    ms64_k, per64_k = timed("fp64", out64, max(1, min(args.steps, 5)), 1, kernel_only=True)
+
+    value = world * states * args.steps / (ms32 * 1e-3)
+    fp64_value = world * states * max(1, min(args.steps, 5)) / (ms64 * 1e-3)
+
+    # end to end through the public API with pinned host buffers
+    r_h = torch.empty((n, T, 3), dtype=torch.float32).pin_memory()
+    v_h = torch.empty((n, T, 3), dtype=torch.float32).pin_memory()
+    s_h = torch.empty((n, T), dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+
+    def e2e_step():
+        el_d = el_h.to(dev, non_blocking=True)
+        ts_d = ts_h.to(dev, non_blocking=True)
+        sgp4_init(el_d, records=recs, init_status=ist)
+        sgp4_propagate(recs, ts_d, "fp32", out=out32)
+        r_h.copy_(out32[0], non_blocking=True)
+        v_h.copy_(out32[1], non_blocking=True)
+        s_h.copy_(out32[2], non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    b.synchronize()
+    e2e_ms = a.elapsed_time(b)
+    e2e_value = world * states * e2e_steps / (e2e_ms * 1e-3)
+    h2d = el_h.numel() * 8 + ts_h.numel() * 8
+    d2h = (r_h.numel() + v_h.numel()) * 4 + s_h.numel() * 4
+
+    # roofline of the dominant kernel (the FP32 propagate), per launch
+    kern_ms = statistics.mean(per32_k)
+    bytes_per_launch = BYTES_PER_STATE["fp32"] * states
+    achieved_gbs = bytes_per_launch / (kern_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "propagate_kernel<fp32>", "peak_kind": peak_kind,
+                "kernel_ms": kern_ms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        rate, dt = cpu_oracle_rate(w.elements, w.tsince, args.cpu_sats, threads)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {args.cpu_sats} of {n} satellites x {T} times, "
+                         f"{dt:.1f} s wall on {threads} threads"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 (f64/double-float n*t phase)",
+            "data": "synthetic",
+            "config": {"workload": w.name, "n_sats": n, "t_count": T, "precision": "fp32",
+                       "step": "sgp4_init + sgp4_propagate", "l2": "flushed between steps "
+                       "(256 MB write)", "parallelism": f"replicas x{world}"},
+            "fp32_max_dr_km_sample": max_dr_km,
+            "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / max(1, min(args.steps, 5)),
+                     "kernel_ms": statistics.mean(per64_k)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-sats", type=int, default=2000)
+    ap.add_argument("--ref-sats", type=int, default=1000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

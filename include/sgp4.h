@@ -1,0 +1,148 @@
+/*
+ * sgp4.h -- C ABI of the B300 (sm_103a) near-Earth SGP4 propagation library.
+ *
+ * The problem is the paper's f(s, t) -> (r, v), batched over satellites s and
+ * times t (Priestley & Handley, "jaxsgp4", Sec. 2.2 "Vectorisation"): near-Earth
+ * SGP4 (Spacetrack Report #3 equations as revised in 2006, WGS-72 constants,
+ * Sec. 2.1), with invalid physical states flagged by integer codes instead of
+ * aborting (Sec. 2.2 "Control Flow").
+ *
+ * Conventions for every entry point:
+ *  - All array arguments are DEVICE pointers unless stated otherwise, owned by the
+ *    caller, and must stay valid until the work queued on `stream` has finished.
+ *    The library never allocates device memory in these calls.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    All calls are asynchronous with respect to the host.
+ *  - Return value: SGP4_OK, or a negative sgp4_result.  Argument errors are
+ *    detected on the host before any launch and leave all outputs untouched.
+ *    SGP4_ERR_CUDA reports a failed launch (cudaGetLastError after the launch).
+ *    Physical validity is never an API error: it is reported per record and per
+ *    state in the int32 status arrays.
+ *  - Units: mean motion in rad/min (Kozai, as in a TLE), angles in rad, B* in
+ *    1/Earth radii, tsince in minutes from the record's epoch, r in km, v in km/s,
+ *    TEME frame.
+ *
+ * Status codes (per record and per state):
+ *   0  ok
+ *   1  eccentricity out of range: input e0 outside [0,1) or a non-finite input
+ *      element (fatal for the record), or mean e(t) >= 1 or < -0.001 after drag
+ *   2  mean motion <= 0 (input n0 fatal for the record, or n0'' <= 0)
+ *   4  semi-latus rectum p_L < 0
+ *   6  decayed: osculating radius below one Earth radius (r, v are still written)
+ * Codes 1, 2 and 4 write NaN to r and v.  The first failing check in this order
+ * wins: 2, 1, 4, 6.  3 and 5 are reserved (deep-space codes, not implemented).
+ */
+#ifndef SGP4_B300_SGP4_H
+#define SGP4_B300_SGP4_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sgp4_result {
+  SGP4_OK = 0,
+  SGP4_ERR_ARG = -1,     /* bad size, NULL or misaligned pointer, bad enum        */
+  SGP4_ERR_CUDA = -2,    /* a CUDA launch or runtime call failed                  */
+  SGP4_ERR_OOM = -3,     /* a caller-provided buffer is too small                 */
+  SGP4_ERR_TIMEOUT = -4  /* reserved for bounded device-side waits                */
+} sgp4_result;
+
+typedef enum sgp4_precision {
+  SGP4_FP64 = 0,  /* every step in FP64; outputs double                            */
+  SGP4_FP32 = 1   /* FP32 arithmetic with the n*t angle accumulation in double-float
+                     and an FP64 recomputation of states near a status threshold;
+                     outputs float                                                  */
+} sgp4_precision;
+
+enum {
+  SGP4_STATUS_OK = 0,
+  SGP4_STATUS_ECCENTRICITY = 1,
+  SGP4_STATUS_MEAN_MOTION = 2,
+  SGP4_STATUS_SEMI_LATUS = 4,
+  SGP4_STATUS_DECAYED = 6
+};
+
+/* Earth model (paper Sec. 2.1: WGS-72).  ke is derived as 60/sqrt(R^3/mu). */
+typedef struct sgp4_consts {
+  double mu_km3s2;   /* gravitational parameter, km^3/s^2  */
+  double radius_km;  /* equatorial radius, km              */
+  double j2, j3, j4; /* zonal harmonics                    */
+} sgp4_consts;
+
+/* WGS-72: mu 398600.8, R 6378.135, J2 0.001082616, J3 -0.00000253881, J4 -0.00000165597. */
+sgp4_consts sgp4_wgs72(void);
+
+/*
+ * Per-satellite records (the "initialisation" constants of Sec. 2.1 / Sec. 3.1:
+ * un-Kozai'd mean motion, drag coefficients C1..C5, D2..D4, secular rates,
+ * long-period coefficients).  Structure of arrays: one FP64 plane per field, one
+ * FP32/double-float plane per field of the FP32 path, one int32 flag plane, each
+ * padded to `stride` entries.  The struct is a plain value: `arena` is caller-owned
+ * device memory of sgp4_records_bytes(n) bytes, 256-byte aligned.
+ */
+typedef struct sgp4_records {
+  void* arena;        /* device memory written by sgp4_init                          */
+  int64_t n;          /* number of satellites                                        */
+  int64_t stride;     /* padded plane length (entries)                               */
+  sgp4_consts consts; /* Earth model used by sgp4_init; propagation uses the same one */
+} sgp4_records;
+
+/* Bytes of arena needed for n satellites (0 if n < 0). */
+size_t sgp4_records_bytes(int64_t n);
+
+/*
+ * Bind an arena to a record set.  Errors: SGP4_ERR_ARG if out is NULL, n < 0,
+ * arena is NULL (n > 0) or not 256-byte aligned; SGP4_ERR_OOM if bytes is below
+ * sgp4_records_bytes(n).  `consts` NULL selects WGS-72.
+ */
+sgp4_result sgp4_records_bind(void* arena, size_t bytes, int64_t n, const sgp4_consts* consts,
+                              sgp4_records* out);
+
+/*
+ * sgp4_init: build the records from mean elements (paper Sec. 2.1, the
+ * initialisation phase; Sec. 3.1 notes it is separate from propagation in the
+ * C++ baseline).  One thread per satellite, FP64.
+ *   elements     [n][7] double, row-major: n0 (rad/min, Kozai), e0, i0, RAAN0,
+ *                argp0, M0 (rad), B* (1/Earth radii)
+ *   epoch_day    [n] int32 and epoch_frac [n] double: epoch as integer day plus
+ *                fraction (paper Sec. 6: a split epoch avoids the FP32 epoch
+ *                rounding).  Both may be NULL; they are stored, not used by
+ *                tsince-based propagation.
+ *   init_status  [n] int32 out: 1/2 for unusable input (fatal for the record),
+ *                otherwise the status of the state at tsince = 0.
+ * Errors: SGP4_ERR_ARG for NULL elements/records/init_status with n > 0, a record
+ * set whose n differs from `n`, or elements not 8-byte aligned.
+ */
+sgp4_result sgp4_init(const double* elements, const int32_t* epoch_day, const double* epoch_frac,
+                      int64_t n, const sgp4_records* records, int32_t* init_status,
+                      void* stream);
+
+/*
+ * sgp4_propagate: r, v and status of every (satellite, time) state (paper
+ * Sec. 2.2: f(s, t) -> (r, v) under vmap over satellites and times).
+ *   tsince       [t_count] double (grid_per_sat == 0: one grid for all satellites)
+ *                or [n][t_count] (grid_per_sat != 0), minutes since epoch
+ *   precision    SGP4_FP64: r, v are double; SGP4_FP32: r, v are float
+ *   r, v         [n][t_count][3], 16-byte aligned
+ *   status       [n][t_count] int32, 16-byte aligned
+ *   fixups       optional device counter (may be NULL): SGP4_FP32 adds the number
+ *                of states recomputed in FP64 because a status threshold was
+ *                within the FP32 guard band.  Ignored for SGP4_FP64.
+ * Errors: SGP4_ERR_ARG for a bad precision, t_count < 0, NULL or misaligned
+ * arrays when n * t_count > 0, or n * t_count * 3 overflowing int64.
+ */
+sgp4_result sgp4_propagate(const sgp4_records* records, const double* tsince, int64_t t_count,
+                           int grid_per_sat, sgp4_precision precision, void* r, void* v,
+                           int32_t* status, unsigned long long* fixups, void* stream);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int sgp4_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SGP4_B300_SGP4_H */

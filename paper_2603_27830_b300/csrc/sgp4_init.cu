@@ -1,0 +1,217 @@
+// Record builder: one thread per satellite computes the initialisation constants of
+// near-Earth SGP4 (paper Sec. 2.1; Spacetrack Report #3 "initialization", 2006
+// revision) in FP64 and writes them as structure-of-arrays planes, plus the FP32 /
+// double-float planes of the mixed-precision path and the init status.
+#include <cmath>
+
+#include "sgp4_device.cuh"
+#include "sgp4_kernels.cuh"
+
+namespace sgp4 {
+
+namespace {
+
+__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
+__global__ void __launch_bounds__(128) init_kernel(const double* __restrict__ el,
+                                                   const int32_t* __restrict__ epoch_day,
+                                                   const double* __restrict__ epoch_frac,
+                                                   RecordPtrs rp, Geo g,
+                                                   int32_t* __restrict__ init_status) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= rp.n) return;
+  const int64_t s = rp.stride;
+  double* f = rp.f64;
+  float* h = rp.f32;
+
+  const double n0 = el[j * 7 + 0], e0 = el[j * 7 + 1], i0 = el[j * 7 + 2];
+  const double raan0 = el[j * 7 + 3], argp0 = el[j * 7 + 4], m0 = el[j * 7 + 5];
+  const double bstar = el[j * 7 + 6];
+  rp.epoch_day[j] = epoch_day ? epoch_day[j] : 0;
+  f[kEpochFrac * s + j] = epoch_frac ? epoch_frac[j] : 0.0;
+
+  // Input validity (fatal for the record): non-finite or e0 outside [0,1) -> 1,
+  // n0 <= 0 -> 2.
+  int fatal = 0;
+  bool finite = isfinite(n0) && isfinite(e0) && isfinite(i0) && isfinite(raan0) &&
+                isfinite(argp0) && isfinite(m0) && isfinite(bstar);
+  if (!finite || e0 < 0.0 || e0 >= 1.0) fatal = 1;
+  else if (n0 <= 0.0) fatal = 2;
+  if (fatal) {
+    const double nan = __longlong_as_double(0x7ff8000000000000LL);
+    for (int k = 0; k < kEpochFrac; ++k) f[k * s + j] = nan;
+    for (int k = 0; k < kNumF32; ++k) h[k * s + j] = __int_as_float(0x7fc00000);
+    rp.flags[j] = fatal << kFatalShift;
+    init_status[j] = fatal;
+    return;
+  }
+
+  const double k2 = 0.5 * g.j2;
+  const double cosi = cos(i0), sini = sin(i0);
+  const double th2 = cosi * cosi;
+  const double x3thm1 = 3.0 * th2 - 1.0;
+  const double x1mth2 = 1.0 - th2;
+  const double x7thm1 = 7.0 * th2 - 1.0;
+  const double b2 = 1.0 - e0 * e0;
+  const double b = sqrt(b2);
+  const double b3 = b2 * b;
+
+  // Kozai -> Brouwer mean motion and semi-major axis.
+  const double a1 = pow(g.xke / n0, 2.0 / 3.0);
+  const double d1 = 1.5 * k2 * x3thm1 / (a1 * a1 * b3);
+  const double a0 = a1 * (1.0 - d1 / 3.0 - d1 * d1 - (134.0 / 81.0) * d1 * d1 * d1);
+  const double d0 = 1.5 * k2 * x3thm1 / (a0 * a0 * b3);
+  const double n0pp = n0 / (1.0 + d0);
+  const double a0pp = pow(g.xke / n0pp, 2.0 / 3.0);
+
+  // Atmosphere: s and (q0 - s)^4 by perigee height.
+  const double rp_er = a0pp * (1.0 - e0);
+  const double hp = (rp_er - 1.0) * g.re;
+  const bool isimp = rp_er < 1.0 + 220.0 / g.re;
+  double s_km = 78.0;
+  if (hp < 156.0) s_km = hp - 78.0;
+  if (hp < 98.0) s_km = 20.0;
+  const double qs = (120.0 - s_km) / g.re;
+  const double qs4 = qs * qs * qs * qs;
+  const double ss = 1.0 + s_km / g.re;
+
+  const double xi = 1.0 / (a0pp - ss);
+  const double eta = a0pp * e0 * xi;
+  const double eta2 = eta * eta;
+  const double eeta = e0 * eta;
+  const double psi2 = fabs(1.0 - eta2);
+  const double xi4 = xi * xi * xi * xi;
+  const double coef = qs4 * xi4;
+  const double coef1 = coef / pow(psi2, 3.5);
+
+  const double C2 = coef1 * n0pp *
+                    (a0pp * (1.0 + 1.5 * eta2 + eeta * (4.0 + eta2)) +
+                     0.375 * g.j2 * xi / psi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
+  const double C1 = bstar * C2;
+  double C3 = 0.0;
+  if (e0 > 1.0e-4) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sini / e0;
+  const double C4 = 2.0 * n0pp * coef1 * a0pp * b2 *
+                    (eta * (2.0 + 0.5 * eta2) + e0 * (0.5 + 2.0 * eta2) -
+                     g.j2 * xi / (a0pp * psi2) *
+                         (-3.0 * x3thm1 * (1.0 - 2.0 * eeta + eta2 * (1.5 - 0.5 * eeta)) +
+                          0.75 * x1mth2 * (2.0 * eta2 - eeta * (1.0 + eta2)) * cos(2.0 * argp0)));
+  const double C5 = 2.0 * coef1 * a0pp * b2 * (1.0 + 2.75 * (eta2 + eeta) + eeta * eta2);
+
+  // Secular rates.
+  const double p0 = a0pp * b2;
+  const double pinv2 = 1.0 / (p0 * p0);
+  const double T1 = 1.5 * g.j2 * pinv2 * n0pp;
+  const double T2 = 0.5 * T1 * g.j2 * pinv2;
+  const double T3 = -0.46875 * g.j4 * pinv2 * pinv2 * n0pp;
+  const double th4 = th2 * th2;
+  const double mdot = n0pp + 0.5 * T1 * b * x3thm1 + 0.0625 * T2 * b * (13.0 - 78.0 * th2 + 137.0 * th4);
+  const double argpdot = -0.5 * T1 * (1.0 - 5.0 * th2) + 0.0625 * T2 * (7.0 - 114.0 * th2 + 395.0 * th4) +
+                         T3 * (3.0 - 36.0 * th2 + 49.0 * th4);
+  const double raandot1 = -T1 * cosi;
+  const double raandot = raandot1 + (0.5 * T2 * (4.0 - 19.0 * th2) + 2.0 * T3 * (3.0 - 7.0 * th2)) * cosi;
+
+  const double raan_cf = 3.5 * b2 * raandot1 * C1;
+  const double argp_cf = bstar * C3 * cos(argp0);
+  double m_cf = 0.0;
+  if (e0 > 1.0e-4) m_cf = -(2.0 / 3.0) * coef * bstar / eeta;
+  const double L2 = 1.5 * C1;
+
+  double opc = 1.0 + cosi;
+  if (fabs(opc) <= 1.5e-12) opc = 1.5e-12;
+  const double xlcof = -0.25 * g.j3oj2 * sini * (3.0 + 5.0 * cosi) / opc;
+  const double aycof = -0.5 * g.j3oj2 * sini;
+  const double cm = 1.0 + eta * cos(m0);
+  const double delm0 = cm * cm * cm;
+  const double sinm0 = sin(m0);
+
+  double D2 = 0.0, D3 = 0.0, D4 = 0.0, L3 = 0.0, L4 = 0.0, L5 = 0.0;
+  if (!isimp) {
+    const double c1sq = C1 * C1;
+    D2 = 4.0 * a0pp * xi * c1sq;
+    D3 = (4.0 / 3.0) * a0pp * xi * xi * (17.0 * a0pp + ss) * c1sq * C1;
+    D4 = (2.0 / 3.0) * a0pp * a0pp * xi * xi * xi * (221.0 * a0pp + 31.0 * ss) * c1sq * c1sq;
+    L3 = D2 + 2.0 * c1sq;
+    L4 = 0.25 * (3.0 * D3 + 12.0 * C1 * D2 + 10.0 * c1sq * C1);
+    L5 = 0.2 * (3.0 * D4 + 12.0 * C1 * D3 + 6.0 * D2 * D2 + 30.0 * c1sq * D2 + 15.0 * c1sq * c1sq);
+  }
+  const double bc4 = bstar * C4, bc5 = bstar * C5;
+
+  // FP64 planes.
+  f[kN0pp * s + j] = n0pp;     f[kA0pp * s + j] = a0pp;     f[kE0 * s + j] = e0;
+  f[kI0 * s + j] = i0;         f[kRaan0 * s + j] = raan0;   f[kArgp0 * s + j] = argp0;
+  f[kM0 * s + j] = m0;         f[kBstar * s + j] = bstar;   f[kMdot * s + j] = mdot;
+  f[kArgpdot * s + j] = argpdot; f[kRaandot * s + j] = raandot; f[kRaanCf * s + j] = raan_cf;
+  f[kArgpCf * s + j] = argp_cf;  f[kMCf * s + j] = m_cf;     f[kC1 * s + j] = C1;
+  f[kBC4 * s + j] = bc4;       f[kBC5 * s + j] = bc5;       f[kD2 * s + j] = D2;
+  f[kD3 * s + j] = D3;         f[kD4 * s + j] = D4;         f[kL2 * s + j] = L2;
+  f[kL3 * s + j] = L3;         f[kL4 * s + j] = L4;         f[kL5 * s + j] = L5;
+  f[kEta * s + j] = eta;       f[kDelM0 * s + j] = delm0;   f[kSinM0 * s + j] = sinm0;
+  f[kXlcof * s + j] = xlcof;   f[kAycof * s + j] = aycof;   f[kCosi * s + j] = cosi;
+  f[kSini * s + j] = sini;     f[kX3thm1 * s + j] = x3thm1; f[kX1mth2 * s + j] = x1mth2;
+  f[kX7thm1 * s + j] = x7thm1;
+
+  // FP32 planes: angles in revolutions, the argument-of-latitude phase as double-float.
+  const double inv2pi = 1.0 / kTwoPi;
+  double phi0 = (m0 + argp0) * inv2pi;
+  phi0 -= floor(phi0);
+  float hi, lo;
+  split_df(phi0, hi, lo);
+  h[fPhi0H * s + j] = hi; h[fPhi0L * s + j] = lo;
+  split_df((mdot + argpdot) * inv2pi, hi, lo);
+  h[fPhiDH * s + j] = hi; h[fPhiDL * s + j] = lo;
+  double m0r = m0 * inv2pi;       m0r -= floor(m0r);
+  double argp0r = argp0 * inv2pi; argp0r -= floor(argp0r);
+  double raan0r = raan0 * inv2pi; raan0r -= floor(raan0r);
+  h[fM0r * s + j] = (float)m0r;
+  h[fMdr * s + j] = (float)(mdot * inv2pi);
+  h[fArgp0r * s + j] = (float)argp0r;
+  h[fArgpdr * s + j] = (float)(argpdot * inv2pi);
+  h[fRaan0r * s + j] = (float)raan0r;
+  h[fRaandr * s + j] = (float)(raandot * inv2pi);
+  h[fRaanCfr * s + j] = (float)(raan_cf * inv2pi);
+  h[fN0ppr * s + j] = (float)(n0pp * inv2pi);
+  h[fA0pp * s + j] = (float)a0pp;   h[fE0 * s + j] = (float)e0;     h[fC1 * s + j] = (float)C1;
+  h[fBC4 * s + j] = (float)bc4;     h[fBC5 * s + j] = (float)bc5;   h[fD2 * s + j] = (float)D2;
+  h[fD3 * s + j] = (float)D3;       h[fD4 * s + j] = (float)D4;     h[fL2 * s + j] = (float)L2;
+  h[fL3 * s + j] = (float)L3;       h[fL4 * s + j] = (float)L4;     h[fL5 * s + j] = (float)L5;
+  h[fEta * s + j] = (float)eta;     h[fDelM0 * s + j] = (float)delm0; h[fSinM0 * s + j] = (float)sinm0;
+  h[fArgpCf * s + j] = (float)argp_cf; h[fMCf * s + j] = (float)m_cf;
+  h[fXlcof * s + j] = (float)xlcof; h[fAycof * s + j] = (float)aycof;
+  h[fCosi * s + j] = (float)cosi;   h[fSini * s + j] = (float)sini;
+  h[fX3thm1 * s + j] = (float)x3thm1; h[fX1mth2 * s + j] = (float)x1mth2;
+  h[fX7thm1 * s + j] = (float)x7thm1;
+
+  int flags = 0;
+  if (isimp) flags |= kFlagIsimp;
+  if (n0pp <= 0.0) flags |= kFlagN0ppNonPos;
+  rp.flags[j] = flags;
+
+  // Init status: the status of the state at tsince = 0.
+  Rec64 rc;
+  rc.n0pp = n0pp; rc.a0pp = a0pp; rc.e0 = e0; rc.i0 = i0; rc.raan0 = raan0; rc.argp0 = argp0;
+  rc.m0 = m0; rc.mdot = mdot; rc.argpdot = argpdot; rc.raandot = raandot; rc.raan_cf = raan_cf;
+  rc.argp_cf = argp_cf; rc.m_cf = m_cf; rc.c1 = C1; rc.bc4 = bc4; rc.bc5 = bc5; rc.d2 = D2;
+  rc.d3 = D3; rc.d4 = D4; rc.l2 = L2; rc.l3 = L3; rc.l4 = L4; rc.l5 = L5; rc.eta = eta;
+  rc.delm0 = delm0; rc.sinm0 = sinm0; rc.xlcof = xlcof; rc.aycof = aycof; rc.cosi = cosi;
+  rc.sini = sini; rc.x3thm1 = x3thm1; rc.x1mth2 = x1mth2; rc.x7thm1 = x7thm1; rc.flags = flags;
+  double r[3], v[3];
+  init_status[j] = state64(rc, g, 0.0, r, v);
+}
+
+}  // namespace
+
+cudaError_t launch_init(const double* el, const int32_t* epoch_day, const double* epoch_frac,
+                        const RecordPtrs& rp, const Geo& g, int32_t* init_status,
+                        cudaStream_t stream) {
+  if (rp.n == 0) return cudaSuccess;
+  const int threads = 128;
+  const int64_t blocks = (rp.n + threads - 1) / threads;
+  init_kernel<<<(unsigned)blocks, threads, 0, stream>>>(el, epoch_day, epoch_frac, rp, g,
+                                                        init_status);
+  return cudaGetLastError();
+}
+
+}  // namespace sgp4

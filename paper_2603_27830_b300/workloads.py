@@ -104,7 +104,8 @@ def config2(seed: int = 0, n: int = 9341, t_count: int = 1000) -> Workload:
 
 
 def catalogue_elements(rng: np.random.Generator, n: int, invalid_frac: float = 0.01,
-                       bstar_range=(1e-6, 1e-2), e_max: float = 0.2) -> np.ndarray:
+                       bstar_range=(1e-6, 1e-2), e_max: float = 0.2,
+                       return_invalid: bool = False):
     """Near-Earth catalogue draw: period < 225 min, e U[0, e_max] with perigee above
     6,578 km, B* log-uniform; a fraction of deliberately invalid records (half with
     e0 in [1, 1.5], half with a perigee below the Earth's surface)."""
@@ -132,17 +133,21 @@ def catalogue_elements(rng: np.random.Generator, n: int, invalid_frac: float = 0
         low = bad[half:]
         a = _semi_major_km(out[low, 0])
         out[low, 1] = 1.0 - _RE_KM * rng.uniform(0.85, 0.995, low.size) / a
+    else:
+        bad = np.zeros(0, dtype=np.int64)
+    if return_invalid:
+        return out, np.sort(bad)
     return out
 
 
 def config3(seed: int = 0, n: int = 1_000_000, t_count: int = 100) -> Workload:
     """Catalogue scale: 1,000,000 satellites x 100 times over 7 days, ~1% invalid."""
     rng = np.random.default_rng(3000 + seed)
-    el = catalogue_elements(rng, n)
+    el, bad = catalogue_elements(rng, n, return_invalid=True)
     return Workload("catalogue-1Mx100", el, np.linspace(0.0, 10080.0, t_count),
                     "n U[6.45,16.5] rev/day (period < 225 min), e U[0,0.2] with perigee > "
                     "6578 km, i U[0,180) deg, B* log-U[1e-6,1e-2], 1% invalid, "
-                    "tsince 0..10080 min")
+                    "tsince 0..10080 min", meta={"invalid": bad})
 
 
 def config4(seed: int = 0, n_requests: int = 256, n_range=(100, 50_000),

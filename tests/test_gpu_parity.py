@@ -1,0 +1,202 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Status codes must match bit-exactly; FP64 states agree to |dr| <= 1e-6 km and
+|dv| <= 1e-9 km/s; the FP32 path's error is bounded per workload (one-day grids:
+max |dr| <= 0.1 km).
+"""
+from __future__ import annotations
+
+import json
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import (FP64_TOL_R_KM, FP64_TOL_V_KMS, assert_status_and_nan, error_summary,
+                      gpu_propagate, state_errors)
+from paper_2603_27830_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+REV = W.REV_PER_DAY
+
+
+def _check_fp64(el, t):
+    r, v, st, ist = gpu_propagate(el, t, "fp64")
+    rr, vr, sr, isr = oracle.propagate(el, t)
+    assert_status_and_nan(st, sr, r, v, ist, isr)
+    dr, dv = state_errors(r, v, rr, vr, sr)
+    if dr.size:
+        assert dr.max() <= FP64_TOL_R_KM, error_summary(dr, dv)
+        assert dv.max() <= FP64_TOL_V_KMS, error_summary(dr, dv)
+    return error_summary(dr, dv)
+
+
+def _check_fp32(el, t, max_dr_km, max_dv_kms):
+    r, v, st, ist, nfix = gpu_propagate(el, t, "fp32", fixups=True)
+    rr, vr, sr, isr = oracle.propagate(el, t)
+    assert_status_and_nan(st, sr, r, v, ist, isr)
+    dr, dv = state_errors(r, v, rr, vr, sr)
+    summ = error_summary(dr, dv)
+    summ["fp64_fixups"] = nfix
+    print(json.dumps(summ))
+    if dr.size:
+        assert dr.max() <= max_dr_km, summ
+        assert dv.max() <= max_dv_kms, summ
+    return summ
+
+
+# ------------------------------------------------------------------ workloads
+def test_near_earth_64x100_fp64():
+    w = W.config1()
+    _check_fp64(w.elements, w.tsince)
+
+
+def test_near_earth_64x100_fp32():
+    w = W.config1()
+    _check_fp32(w.elements, w.tsince, 0.1, 1e-4)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_starlink_9341x1000_fp64(seed):
+    w = W.config2(seed)
+    _check_fp64(w.elements, w.tsince)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_starlink_9341x1000_fp32(seed):
+    w = W.config2(seed)
+    _check_fp32(w.elements, w.tsince, 0.1, 1e-4)
+
+
+def test_catalogue_small_fp64():
+    """Catalogue draws (1% invalid) over 7 days, small n spanning many tiles."""
+    w = W.config3(seed=7, n=20_000)
+    _check_fp64(w.elements, w.tsince)
+
+
+def test_catalogue_small_fp32():
+    w = W.config3(seed=7, n=20_000)
+    # seven days and B* up to 1e-2: bounded but looser than the one-day target
+    _check_fp32(w.elements, w.tsince, 2.0, 2e-3)
+
+
+def test_catalogue_full_size_sampled():
+    """1,000,000 x 100 in the launch configuration of the benchmark; the oracle checks
+    every invalid record and a random sample of the rest."""
+    import torch
+
+    from paper_2603_27830_b300 import sgp4_init, sgp4_propagate
+    w = W.config3(seed=0)
+    el = torch.as_tensor(w.elements, device="cuda")
+    ts = torch.as_tensor(w.tsince, device="cuda")
+    recs, ist = sgp4_init(el)
+    rng = np.random.default_rng(0)
+    invalid = w.meta["invalid"]
+    sample = np.unique(np.concatenate([invalid, rng.choice(w.n, 3000, replace=False)]))
+    rr, vr, sr, isr = oracle.propagate(w.elements[sample], w.tsince)
+    for prec, tol in (("fp64", FP64_TOL_R_KM), ("fp32", 2.0)):
+        r, v, st = sgp4_propagate(recs, ts, prec)
+        torch.cuda.synchronize()
+        idx = torch.as_tensor(sample, device="cuda")
+        rs = r[idx].double().cpu().numpy()
+        vs = v[idx].double().cpu().numpy()
+        ss = st[idx].cpu().numpy()
+        assert_status_and_nan(ss, sr, rs, vs, ist[idx].cpu().numpy(), isr)
+        dr, dv = state_errors(rs, vs, rr, vr, sr)
+        assert dr.max() <= tol, (prec, error_summary(dr, dv))
+        # every status of the full run is a valid code
+        u = torch.unique(st).cpu().numpy()
+        assert set(u.tolist()) <= {0, 1, 2, 4, 6}
+        del r, v, st
+
+
+# ------------------------------------------------------------------ edge cases
+def _edge_elements():
+    n = 15.2 * REV
+    rows = [
+        [n, 0.0, 0.9, 0.1, 0.2, 0.3, 1e-4],               # e0 = 0
+        [n, 0.001, 0.0, 0.1, 0.2, 0.3, 1e-4],             # equatorial
+        [n, 0.001, math.pi, 0.1, 0.2, 0.3, 1e-4],         # retrograde pole guard
+        [n, 0.001, 1.2, 0.1, 0.2, 0.3, 0.0],              # no drag
+        [n, 0.001, 1.2, 0.1, 0.2, 0.3, -2e-4],            # negative B* (valid)
+        [16.3 * REV, 0.001, 1.0, 0.1, 0.2, 0.3, 5e-3],    # low perigee, truncated drag
+        [15.8 * REV, 0.01, 0.9, 0.0, 0.5, 0.0, 0.5],      # enormous drag -> code 1 later
+        [n, 1.0, 0.9, 0, 0, 0, 1e-4],                     # e0 = 1 -> fatal 1
+        [n, -0.1, 0.9, 0, 0, 0, 1e-4],                    # e0 < 0 -> fatal 1
+        [0.0, 0.01, 0.9, 0, 0, 0, 1e-4],                  # n0 = 0 -> fatal 2
+        [n, float("nan"), 0.9, 0, 0, 0, 1e-4],            # NaN -> fatal 1
+        [n, 0.01, float("inf"), 0, 0, 0, 1e-4],           # inf -> fatal 1
+        [15.0 * REV, 1 - 0.97 / (0.0743669161 / (15.0 * REV)) ** (2 / 3), 0.9, 0, 0, 0, 0.0],
+        [6.5 * REV, 0.6, 1.1, 0.3, 0.4, 0.5, 1e-4],       # eccentric, long period
+    ]
+    return np.array(rows)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_edge_elements(prec):
+    el = _edge_elements()
+    t = np.concatenate([np.linspace(-720, 2880, 97), [0.0, 1e-9, 1e5]])
+    if prec == "fp64":
+        _check_fp64(el, t)
+    else:
+        r, v, st, ist = gpu_propagate(el, t, "fp32")
+        rr, vr, sr, isr = oracle.propagate(el, t)
+        assert_status_and_nan(st, sr, r, v, ist, isr)
+
+
+@pytest.mark.parametrize("n,T", [(1, 1), (1, 127), (3, 1), (7, 13), (129, 1), (33, 129),
+                                 (5, 1000), (1000, 3)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_ragged_shapes(n, T, prec):
+    rng = np.random.default_rng(n * 1000 + T)
+    el = W.catalogue_elements(rng, n, invalid_frac=0.0)
+    t = np.sort(rng.uniform(-100, 2000, T))
+    if prec == "fp64":
+        _check_fp64(el, t)
+    else:
+        _check_fp32(el, t, 1.0, 1e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_per_satellite_grid(prec):
+    rng = np.random.default_rng(3)
+    el = W.catalogue_elements(rng, 300, invalid_frac=0.02)
+    t = np.sort(rng.uniform(-720, 2880, (300, 77)), axis=1)
+    if prec == "fp64":
+        _check_fp64(el, t)
+    else:
+        _check_fp32(el, t, 1.0, 1e-3)
+
+
+def test_empty_inputs():
+    import torch
+
+    from paper_2603_27830_b300 import sgp4_init, sgp4_propagate
+    el = torch.zeros((0, 7), dtype=torch.float64, device="cuda")
+    recs, ist = sgp4_init(el)
+    r, v, st = sgp4_propagate(recs, torch.zeros(5, dtype=torch.float64, device="cuda"))
+    assert r.shape == (0, 5, 3) and st.shape == (0, 5)
+    el1 = torch.as_tensor(W.config1().elements[:4], device="cuda")
+    recs1, _ = sgp4_init(el1)
+    r, v, st = sgp4_propagate(recs1, torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert r.shape == (4, 0, 3)
+
+
+def test_argument_errors_leave_outputs_untouched():
+    import torch
+
+    from paper_2603_27830_b300 import _lib, sgp4_init, sgp4_propagate
+    el = torch.as_tensor(W.config1().elements[:8], device="cuda")
+    recs, _ = sgp4_init(el)
+    ts = torch.linspace(0, 100, 16, dtype=torch.float64, device="cuda")
+    buf = torch.full((8 * 16 * 3 + 4,), 7.0, dtype=torch.float32, device="cuda")
+    st = torch.full((8 * 16 + 4,), 99, dtype=torch.int32, device="cuda")
+    mis_r = buf[1:1 + 8 * 16 * 3].view(8, 16, 3)     # 4-byte offset: not 16-byte aligned
+    ok_v = torch.empty((8, 16, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(_lib.Sgp4Error) as ei:
+        sgp4_propagate(recs, ts, "fp32", out=(mis_r, ok_v, st[:8 * 16].view(8, 16)))
+    assert ei.value.code == _lib.SGP4_ERR_ARG
+    torch.cuda.synchronize()
+    assert torch.all(buf == 7.0) and torch.all(st == 99)
