@@ -15,8 +15,8 @@ namespace sgp4 {
 
 // ---------------------------------------------------------------- record layout
 // Structure of arrays inside one caller-owned arena:
-//   [kNumF64 planes of double][kNumF32 planes of float][flags int32][epoch_day int32]
-// each plane `stride` entries long, stride a multiple of 64 (256-byte planes).
+//   [kNumF64 planes of double][stride rows of kF32Row floats][flags int32][epoch_day int32]
+// planes are `stride` entries long, stride a multiple of 64 (256-byte planes).
 enum F64Field {
   kN0pp, kA0pp, kE0, kI0, kRaan0, kArgp0, kM0, kBstar,
   kMdot, kArgpdot, kRaandot, kRaanCf, kArgpCf, kMCf,
@@ -27,18 +27,23 @@ enum F64Field {
   kNumF64
 };
 
-// FP32-path planes.  Angles and their rates are stored in revolutions (x / 2 pi) so
-// that the reduction mod one revolution is a subtraction of rint(x).  The mean
-// argument of latitude phase (M0 + argp0) and its rate (Mdot + argpdot) are kept as
-// unevaluated float sums hi + lo ("double-float").
+// FP32-path record: one 160-byte row of 40 floats per satellite (array of
+// structures), read with ten 16-byte loads per state.  Angles and their rates are
+// in revolutions (x / 2 pi) so that the reduction mod one revolution is a
+// subtraction of rint(x).  The mean argument of latitude phase (M0 + argp0) and
+// its rate (Mdot + argpdot) are unevaluated float sums hi + lo ("double-float").
+// Slot fFlags holds the int32 flags word as raw bits.
 enum F32Field {
   fPhi0H, fPhi0L, fPhiDH, fPhiDL,
   fM0r, fMdr, fArgp0r, fArgpdr, fRaan0r, fRaandr, fRaanCfr, fN0ppr,
   fA0pp, fE0, fC1, fBC4, fBC5, fD2, fD3, fD4, fL2, fL3, fL4, fL5,
   fEta, fDelM0, fSinM0, fArgpCf, fMCf, fXlcof, fAycof,
   fCosi, fSini, fX3thm1, fX1mth2, fX7thm1,
-  kNumF32
+  fFlags,
+  kNumF32Used
 };
+constexpr int kF32Row = 40;   // floats per satellite row (16-byte multiple)
+static_assert(kNumF32Used <= kF32Row, "FP32 record row too small");
 
 // flags word
 constexpr int kFlagIsimp = 1;        // perigee below 220 km: truncated drag terms
@@ -49,12 +54,12 @@ __host__ __device__ inline int64_t record_stride(int64_t n) { return ((n + 63) /
 
 __host__ __device__ inline size_t record_bytes(int64_t n) {
   const int64_t s = record_stride(n);
-  return (size_t)s * (sizeof(double) * kNumF64 + sizeof(float) * kNumF32 + 2 * sizeof(int32_t));
+  return (size_t)s * (sizeof(double) * kNumF64 + sizeof(float) * kF32Row + 2 * sizeof(int32_t));
 }
 
 struct RecordPtrs {
   double* f64;      // [kNumF64][stride]
-  float* f32;       // [kNumF32][stride]
+  float* f32;       // [stride][kF32Row]
   int32_t* flags;   // [stride]
   int32_t* epoch_day;
   int64_t stride;
@@ -69,7 +74,7 @@ __host__ __device__ inline RecordPtrs record_ptrs(void* arena, int64_t n) {
   p.f64 = reinterpret_cast<double*>(base);
   base += sizeof(double) * kNumF64 * p.stride;
   p.f32 = reinterpret_cast<float*>(base);
-  base += sizeof(float) * kNumF32 * p.stride;
+  base += sizeof(float) * kF32Row * p.stride;
   p.flags = reinterpret_cast<int32_t*>(base);
   base += sizeof(int32_t) * p.stride;
   p.epoch_day = reinterpret_cast<int32_t*>(base);
@@ -277,33 +282,81 @@ struct Rec32 {
 };
 
 __device__ __forceinline__ Rec32 load_rec32(const RecordPtrs& rp, int64_t j) {
-  const float* __restrict__ f = rp.f32;
-  const int64_t s = rp.stride;
+  const float4* __restrict__ row = reinterpret_cast<const float4*>(rp.f32 + j * kF32Row);
+  const float4 q0 = __ldg(row + 0), q1 = __ldg(row + 1), q2 = __ldg(row + 2), q3 = __ldg(row + 3);
+  const float4 q4 = __ldg(row + 4), q5 = __ldg(row + 5), q6 = __ldg(row + 6), q7 = __ldg(row + 7);
+  const float4 q8 = __ldg(row + 8), q9 = __ldg(row + 9);
   Rec32 r;
-#define SGP4_LD32(dst, fld) r.dst = __ldg(f + (fld) * s + j)
-  SGP4_LD32(phi0h, fPhi0H); SGP4_LD32(phi0l, fPhi0L); SGP4_LD32(phidh, fPhiDH);
-  SGP4_LD32(phidl, fPhiDL); SGP4_LD32(m0r, fM0r); SGP4_LD32(mdr, fMdr);
-  SGP4_LD32(argp0r, fArgp0r); SGP4_LD32(argpdr, fArgpdr); SGP4_LD32(raan0r, fRaan0r);
-  SGP4_LD32(raandr, fRaandr); SGP4_LD32(raancfr, fRaanCfr); SGP4_LD32(n0ppr, fN0ppr);
-  SGP4_LD32(a0pp, fA0pp); SGP4_LD32(e0, fE0); SGP4_LD32(c1, fC1); SGP4_LD32(bc4, fBC4);
-  SGP4_LD32(bc5, fBC5); SGP4_LD32(d2, fD2); SGP4_LD32(d3, fD3); SGP4_LD32(d4, fD4);
-  SGP4_LD32(l2, fL2); SGP4_LD32(l3, fL3); SGP4_LD32(l4, fL4); SGP4_LD32(l5, fL5);
-  SGP4_LD32(eta, fEta); SGP4_LD32(delm0, fDelM0); SGP4_LD32(sinm0, fSinM0);
-  SGP4_LD32(argpcf, fArgpCf); SGP4_LD32(mcf, fMCf); SGP4_LD32(xlcof, fXlcof);
-  SGP4_LD32(aycof, fAycof); SGP4_LD32(cosi, fCosi); SGP4_LD32(sini, fSini);
-  SGP4_LD32(x3thm1, fX3thm1); SGP4_LD32(x1mth2, fX1mth2); SGP4_LD32(x7thm1, fX7thm1);
-#undef SGP4_LD32
-  r.flags = __ldg(rp.flags + j);
+  r.phi0h = q0.x; r.phi0l = q0.y; r.phidh = q0.z; r.phidl = q0.w;
+  r.m0r = q1.x; r.mdr = q1.y; r.argp0r = q1.z; r.argpdr = q1.w;
+  r.raan0r = q2.x; r.raandr = q2.y; r.raancfr = q2.z; r.n0ppr = q2.w;
+  r.a0pp = q3.x; r.e0 = q3.y; r.c1 = q3.z; r.bc4 = q3.w;
+  r.bc5 = q4.x; r.d2 = q4.y; r.d3 = q4.z; r.d4 = q4.w;
+  r.l2 = q5.x; r.l3 = q5.y; r.l4 = q5.z; r.l5 = q5.w;
+  r.eta = q6.x; r.delm0 = q6.y; r.sinm0 = q6.z; r.argpcf = q6.w;
+  r.mcf = q7.x; r.xlcof = q7.y; r.aycof = q7.z; r.cosi = q7.w;
+  r.sini = q8.x; r.x3thm1 = q8.y; r.x1mth2 = q8.z; r.x7thm1 = q8.w;
+  r.flags = __float_as_int(q9.x);
   return r;
 }
 
 // Reduce an angle in revolutions to [-1/2, 1/2].  Exact for |x| < 2^23.
 __device__ __forceinline__ float wrap_rev(float x) { return x - rintf(x); }
 
+// Split a double into float hi + lo with hi = t rounded to float and lo = the
+// remainder rounded to float (so hi + lo carries ~48 significant bits), using only
+// integer operations: B300's FP64 unit is a small fraction of the FP32 rate, and a
+// conversion through it per state would be the kernel's busiest pipe.  IEEE 754
+// binary64: hi keeps the top 24 bits of the 53-bit significand (round to nearest,
+// ties to even), lo is the signed 29-bit remainder times 2^(exponent - 52).
+// |t| < 2^-74 min (3e-21 s) is taken as zero; |t| >= 2^128 gives hi = +-inf.
+__device__ __forceinline__ void split_double(double t, float& hi, float& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(t);
+  const unsigned w1 = (unsigned)(b >> 32), w0 = (unsigned)b;
+  const int e = (int)((w1 >> 20) & 0x7ffu);
+  const unsigned sign = w1 & 0x80000000u;
+  if (e < 949) { hi = 0.0f; lo = 0.0f; return; }
+  if (e > 1150) { hi = __uint_as_float(sign | 0x7f800000u); lo = 0.0f; return; }
+  unsigned hs = (((w1 & 0xfffffu) | 0x100000u) << 3) | (w0 >> 29);   // 24-bit significand
+  const unsigned rem = w0 & 0x1fffffffu;                                // low 29 bits
+  const unsigned up = (rem > 0x10000000u || (rem == 0x10000000u && (hs & 1u))) ? 1u : 0u;
+  hs += up;   // a carry to 2^24 propagates into the exponent field below
+  hi = __uint_as_float((sign | ((unsigned)(e - 896) << 23)) + (hs - 0x800000u));
+  const int d = (int)rem - (up ? 0x20000000 : 0);                       // |d| <= 2^28
+  const float l = (float)d * __uint_as_float((unsigned)(e - 948) << 23);  // d * 2^(e-1075)
+  lo = sign ? -l : l;
+}
+
+// sin and cos of x, |x| <= 2^12, to ~1e-7 absolute: Cody-Waite reduction by pi/2
+// with a two-part constant applied by FMA, then the Taylor series of sin (degree 9)
+// and cos (degree 10) on [-pi/4, pi/4] (truncation below 2e-9), and the quadrant
+// swap.  Used where an angle's error goes straight into the position (the final
+// Kepler iterate and the node); elsewhere the SFU's __sincosf is accurate enough.
+__device__ __forceinline__ void sincos_acc(float x, float* sp, float* cp) {
+  const float k = rintf(x * 0.636619772367581343f);
+  float r = fmaf(k, -1.57079637050628662f, x);
+  r = fmaf(k, 4.37113900018624284e-8f, r);
+  const float r2 = r * r;
+  float ps = fmaf(r2, 2.75573192239858907e-6f, -1.98412698412698413e-4f);
+  ps = fmaf(r2, ps, 8.33333333333333333e-3f);
+  ps = fmaf(r2, ps, -1.66666666666666667e-1f);
+  const float sn = fmaf(r * r2, ps, r);
+  float pc = fmaf(r2, -2.75573192239858907e-7f, 2.48015873015873016e-5f);
+  pc = fmaf(r2, pc, -1.38888888888888889e-3f);
+  pc = fmaf(r2, pc, 4.16666666666666667e-2f);
+  pc = fmaf(r2, pc, -0.5f);
+  const float cs = fmaf(r2, pc, 1.0f);
+  const int q = (int)k;
+  const float s0 = (q & 1) ? cs : sn;
+  const float c0 = (q & 1) ? sn : cs;
+  *sp = (q & 2) ? -s0 : s0;
+  *cp = ((q + 1) & 2) ? -c0 : c0;
+}
+
 // Rotate the unit vector (s, c) = (sin a, cos a) to (sin(a+d), cos(a+d)).  The
 // corrections d of the short-period terms are O(J2/p_L^2) ~ 1e-3 rad, where a
 // 5th/4th-order Taylor pair is exact to float precision; larger d (only for
-// nearly degenerate orbits) takes the full sincosf.
+// nearly degenerate orbits) takes the full sincos.
 __device__ __forceinline__ void rotate_small(float& s, float& c, float d) {
   float sd, cd;
   if (fabsf(d) < 0.05f) {
@@ -311,12 +364,21 @@ __device__ __forceinline__ void rotate_small(float& s, float& c, float d) {
     sd = d * (1.0f - d2 * (1.0f / 6.0f) * (1.0f - d2 * 0.05f));
     cd = 1.0f - 0.5f * d2 * (1.0f - d2 * (1.0f / 12.0f));
   } else {
-    sincosf(d, &sd, &cd);
+    sincos_acc(d, &sd, &cd);
   }
   const float s2 = s * cd + c * sd;
   const float c2 = c * cd - s * sd;
   s = s2;
   c = c2;
+}
+
+// Newton steps needed for Kepler's equation from psi0 = U: with |psi0 - psi*| <= e_L,
+// f' >= 1 - e_L and |f''| <= e_L the error obeys err' <= e_L/(2(1-e_L)) err^2, which
+// reaches 1e-8 rad after 1 step for e_L <= 0.0027, 2 for <= 0.093, 3 for <= 0.33 and
+// 4 for <= 0.5; beyond that the theory's cap of 10 steps is used.
+// The thresholds below are on e_L^2.
+__device__ __forceinline__ int newton_steps(float eL2) {
+  return eL2 <= 6.25e-6f ? 1 : eL2 <= 0.0081f ? 2 : eL2 <= 0.1089f ? 3 : eL2 <= 0.25f ? 4 : 10;
 }
 
 // Guard bands: a state whose FP32 value of e, p_L or r_k lies this close to a status
@@ -330,7 +392,6 @@ constexpr int kRecomputeFP64 = -1;
 // One state in FP32 with the n*t phase in double-float.  (th, tl) is tsince split as
 // th + tl.  Returns the status code, or kRecomputeFP64 when the state must be
 // recomputed by state64.
-template <int K>
 __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th, float tl,
                                        float r[3], float v[3]) {
   const int fatal = (rc.flags >> kFatalShift) & 0xff;
@@ -348,21 +409,23 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   if (!isimp) {
     const float dargp = rc.argpcf * t;
     const float mdf = wrap_rev(fmaf(rc.mdr, t, rc.m0r)) * kTwoPiF;
-    const float c = 1.0f + rc.eta * cosf(mdf);
+    const float c = 1.0f + rc.eta * __cosf(mdf);
     const float dm = rc.mcf * (c * c * c - rc.delm0);
     dd = dargp + dm;
     const float t3 = t2 * t, t4 = t3 * t;
     tempa = tempa - rc.d2 * t2 - rc.d3 * t3 - rc.d4 * t4;
-    tempe = tempe + rc.bc5 * (sinf(mdf + dd) - rc.sinm0);
+    tempe = tempe + rc.bc5 * (__sinf(mdf + dd) - rc.sinm0);
     templ = templ + rc.l3 * t3 + t4 * (rc.l4 + t * rc.l5);
   }
   const float a = rc.a0pp * tempa * tempa;
-  const float sa = sqrtf(a);
-  const float n = g.xke / (a * sa);
   float e = rc.e0 - tempe;
-  if (!(fabsf(e - 1.0f) >= kGuardE && fabsf(e + 0.001f) >= kGuardE)) return kRecomputeFP64;
+  if (!(fabsf(e - 1.0f) >= kGuardE && fabsf(e + 0.001f) >= kGuardE && a > 1.0e-3f))
+    return kRecomputeFP64;
   if (e >= 1.0f || e < -0.001f) return 1;
   if (e < 1.0e-6f) e = 1.0e-6f;
+  const float ra = rsqrtf(a);
+  const float sa = a * ra;
+  const float n = g.xke * ra * ra * ra;
 
   // Phase of the mean argument of latitude, M + argp = M_DF + argp_DF + n0'' templ
   // (the drag corrections of M and argp cancel), in revolutions.  The n*t product is
@@ -380,38 +443,40 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
 
   // Long-period periodics (J3).
   float sw, cw;
-  sincosf(argp, &sw, &cw);
+  __sincosf(argp, &sw, &cw);
   const float axn = e * cw;
-  const float q = 1.0f / (a * (1.0f - e * e));
+  const float q = __fdividef(1.0f, a * (1.0f - e * e));
   const float ayn = fmaf(e, sw, q * rc.aycof);
   const float U = wrap_rev(y + q * rc.xlcof * axn * kInvTwoPiF) * kTwoPiF;
+  const float eL2 = axn * axn + ayn * ayn;
 
-  // Kepler: K Newton steps from psi = U, clamped to +-0.95.
+  // Kepler: Newton from psi = U, clamped to +-0.95, step count from the e_L bound.
   float psi = U;
-#pragma unroll
+  const int K = newton_steps(eL2);
   for (int k = 0; k < K; ++k) {
     float sp, cp;
-    sincosf(psi, &sp, &cp);
+    __sincosf(psi, &sp, &cp);
     const float f = U - ayn * cp + axn * sp - psi;
     const float fp = 1.0f - ayn * sp - axn * cp;
     psi += fminf(fmaxf(__fdividef(f, fp), -0.95f), 0.95f);
   }
   float sp, cp;
-  sincosf(psi, &sp, &cp);
+  sincos_acc(psi, &sp, &cp);
 
   // Short-period preliminaries.
   const float ecosE = axn * cp + ayn * sp;
   const float esinE = axn * sp - ayn * cp;
-  const float eL2 = axn * axn + ayn * ayn;
   const float pL = a * (1.0f - eL2);
   if (!(fabsf(pL) >= kGuardP)) return kRecomputeFP64;
   if (pL < 0.0f) return 4;
   const float rl = a * (1.0f - ecosE);
-  const float invr = 1.0f / rl;
+  const float invr = __fdividef(1.0f, rl);
   const float rdotl = sa * esinE * invr;
-  const float rfdotl = sqrtf(pL) * invr;
-  const float betal = sqrtf(1.0f - eL2);
-  const float w = esinE / (1.0f + betal);
+  const float rpl = rsqrtf(pL);
+  const float rfdotl = pL * rpl * invr;
+  const float omel = 1.0f - eL2;
+  const float betal = omel * rsqrtf(omel);
+  const float w = __fdividef(esinE, 1.0f + betal);
   const float aor = a * invr;
   const float sinu = aor * (sp - ayn - axn * w);
   const float cosu = aor * (cp - axn + ayn * w);
@@ -419,7 +484,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   const float cos2u = 1.0f - 2.0f * sinu * sinu;
 
   // Short-period periodics (J2).
-  const float invp = 1.0f / pL;
+  const float invp = rpl * rpl;
   const float k = 0.5f * g.j2 * invp;
   const float kp = k * invp;
   const float rk = rl * (1.0f - 1.5f * kp * betal * rc.x3thm1) + 0.5f * k * rc.x1mth2 * cos2u;
@@ -433,7 +498,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   float su = sinu * nrm, cu = cosu * nrm;
   rotate_small(su, cu, -0.25f * kp * rc.x7thm1 * sin2u);
   float sO, cO;
-  sincosf(raan, &sO, &cO);
+  sincos_acc(raan, &sO, &cO);
   rotate_small(sO, cO, 1.5f * kp * rc.cosi * sin2u);
   float si = rc.sini, ci = rc.cosi;
   rotate_small(si, ci, 1.5f * kp * rc.cosi * rc.sini * cos2u);

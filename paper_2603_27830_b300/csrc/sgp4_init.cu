@@ -1,7 +1,7 @@
 // Record builder: one thread per satellite computes the initialisation constants of
 // near-Earth SGP4 (paper Sec. 2.1; Spacetrack Report #3 "initialization", 2006
 // revision) in FP64 and writes them as structure-of-arrays planes, plus the FP32 /
-// double-float planes of the mixed-precision path and the init status.
+// double-float row of the mixed-precision path and the init status.
 #include <cmath>
 
 #include "sgp4_device.cuh"
@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(128) init_kernel(const double* __restrict__ el
   if (j >= rp.n) return;
   const int64_t s = rp.stride;
   double* f = rp.f64;
-  float* h = rp.f32;
+  float* h = rp.f32 + j * kF32Row;   // this satellite's FP32 row
 
   const double n0 = el[j * 7 + 0], e0 = el[j * 7 + 1], i0 = el[j * 7 + 2];
   const double raan0 = el[j * 7 + 3], argp0 = el[j * 7 + 4], m0 = el[j * 7 + 5];
@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(128) init_kernel(const double* __restrict__ el
   if (fatal) {
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
     for (int k = 0; k < kEpochFrac; ++k) f[k * s + j] = nan;
-    for (int k = 0; k < kNumF32; ++k) h[k * s + j] = __int_as_float(0x7fc00000);
+    for (int k = 0; k < kF32Row; ++k) h[k] = __int_as_float(0x7fc00000);
+    h[fFlags] = __int_as_float(fatal << kFatalShift);
     rp.flags[j] = fatal << kFatalShift;
     init_status[j] = fatal;
     return;
@@ -153,41 +154,43 @@ __global__ void __launch_bounds__(128) init_kernel(const double* __restrict__ el
   f[kSini * s + j] = sini;     f[kX3thm1 * s + j] = x3thm1; f[kX1mth2 * s + j] = x1mth2;
   f[kX7thm1 * s + j] = x7thm1;
 
-  // FP32 planes: angles in revolutions, the argument-of-latitude phase as double-float.
+  // FP32 row: angles in revolutions, the argument-of-latitude phase as double-float.
   const double inv2pi = 1.0 / kTwoPi;
   double phi0 = (m0 + argp0) * inv2pi;
   phi0 -= floor(phi0);
   float hi, lo;
   split_df(phi0, hi, lo);
-  h[fPhi0H * s + j] = hi; h[fPhi0L * s + j] = lo;
+  h[fPhi0H] = hi; h[fPhi0L] = lo;
   split_df((mdot + argpdot) * inv2pi, hi, lo);
-  h[fPhiDH * s + j] = hi; h[fPhiDL * s + j] = lo;
+  h[fPhiDH] = hi; h[fPhiDL] = lo;
   double m0r = m0 * inv2pi;       m0r -= floor(m0r);
   double argp0r = argp0 * inv2pi; argp0r -= floor(argp0r);
   double raan0r = raan0 * inv2pi; raan0r -= floor(raan0r);
-  h[fM0r * s + j] = (float)m0r;
-  h[fMdr * s + j] = (float)(mdot * inv2pi);
-  h[fArgp0r * s + j] = (float)argp0r;
-  h[fArgpdr * s + j] = (float)(argpdot * inv2pi);
-  h[fRaan0r * s + j] = (float)raan0r;
-  h[fRaandr * s + j] = (float)(raandot * inv2pi);
-  h[fRaanCfr * s + j] = (float)(raan_cf * inv2pi);
-  h[fN0ppr * s + j] = (float)(n0pp * inv2pi);
-  h[fA0pp * s + j] = (float)a0pp;   h[fE0 * s + j] = (float)e0;     h[fC1 * s + j] = (float)C1;
-  h[fBC4 * s + j] = (float)bc4;     h[fBC5 * s + j] = (float)bc5;   h[fD2 * s + j] = (float)D2;
-  h[fD3 * s + j] = (float)D3;       h[fD4 * s + j] = (float)D4;     h[fL2 * s + j] = (float)L2;
-  h[fL3 * s + j] = (float)L3;       h[fL4 * s + j] = (float)L4;     h[fL5 * s + j] = (float)L5;
-  h[fEta * s + j] = (float)eta;     h[fDelM0 * s + j] = (float)delm0; h[fSinM0 * s + j] = (float)sinm0;
-  h[fArgpCf * s + j] = (float)argp_cf; h[fMCf * s + j] = (float)m_cf;
-  h[fXlcof * s + j] = (float)xlcof; h[fAycof * s + j] = (float)aycof;
-  h[fCosi * s + j] = (float)cosi;   h[fSini * s + j] = (float)sini;
-  h[fX3thm1 * s + j] = (float)x3thm1; h[fX1mth2 * s + j] = (float)x1mth2;
-  h[fX7thm1 * s + j] = (float)x7thm1;
+  h[fM0r] = (float)m0r;
+  h[fMdr] = (float)(mdot * inv2pi);
+  h[fArgp0r] = (float)argp0r;
+  h[fArgpdr] = (float)(argpdot * inv2pi);
+  h[fRaan0r] = (float)raan0r;
+  h[fRaandr] = (float)(raandot * inv2pi);
+  h[fRaanCfr] = (float)(raan_cf * inv2pi);
+  h[fN0ppr] = (float)(n0pp * inv2pi);
+  h[fA0pp] = (float)a0pp;   h[fE0] = (float)e0;     h[fC1] = (float)C1;
+  h[fBC4] = (float)bc4;     h[fBC5] = (float)bc5;   h[fD2] = (float)D2;
+  h[fD3] = (float)D3;       h[fD4] = (float)D4;     h[fL2] = (float)L2;
+  h[fL3] = (float)L3;       h[fL4] = (float)L4;     h[fL5] = (float)L5;
+  h[fEta] = (float)eta;     h[fDelM0] = (float)delm0; h[fSinM0] = (float)sinm0;
+  h[fArgpCf] = (float)argp_cf; h[fMCf] = (float)m_cf;
+  h[fXlcof] = (float)xlcof; h[fAycof] = (float)aycof;
+  h[fCosi] = (float)cosi;   h[fSini] = (float)sini;
+  h[fX3thm1] = (float)x3thm1; h[fX1mth2] = (float)x1mth2;
+  h[fX7thm1] = (float)x7thm1;
 
   int flags = 0;
   if (isimp) flags |= kFlagIsimp;
   if (n0pp <= 0.0) flags |= kFlagN0ppNonPos;
   rp.flags[j] = flags;
+  h[fFlags] = __int_as_float(flags);
+  for (int k = kNumF32Used; k < kF32Row; ++k) h[k] = 0.0f;
 
   // Init status: the status of the state at tsince = 0.
   Rec64 rc;

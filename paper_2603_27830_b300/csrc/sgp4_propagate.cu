@@ -3,7 +3,8 @@
 // satellites), with
 //   * a persistent grid of one wave, each block owning one contiguous range of the
 //     flattened [n][T] state space, so consecutive iterations of a thread walk along
-//     the time axis of the same satellite and its record stays in registers;
+//     the time axis of the same satellite and its record stays in L1 (FP32) or in
+//     registers (FP64);
 //   * outputs staged in shared memory and written back with 16-byte streaming
 //     stores ([n][T][3] is AoS per state, so a block's 128 states are 1.5 KB (FP32)
 //     or 3 KB (FP64) of contiguous r, the same of v, and 512 B of status).
@@ -17,7 +18,6 @@ namespace sgp4 {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kNewtonFP32 = 5;
 
 template <typename OutT>
 __device__ __forceinline__ void nan_fill(OutT x[3]) {
@@ -43,7 +43,6 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(PropArgs a, int64_t
   int64_t i = (beg + tid) - j * T;
   int64_t cur = -1;
   Rec64 rc64;
-  Rec32 rc32;
   GeoF gf;
   if (kFP32) {
     gf.xke = (float)a.g.xke;
@@ -59,17 +58,19 @@ __global__ void __launch_bounds__(kThreads) propagate_kernel(PropArgs a, int64_t
     OutT rr[3], vv[3];
     int code = 0;
     if (idx < end) {
-      if (j != cur) {
-        if (kFP32) rc32 = load_rec32(a.rp, j);
-        else rc64 = load_rec64(a.rp, j);
+      if (!kFP32 && j != cur) {
+        rc64 = load_rec64(a.rp, j);
         cur = j;
       }
       const double t = a.grid_per_sat ? __ldg(a.tsince + j * T + i) : __ldg(a.tsince + i);
       if (kFP32) {
-        const float th = __double2float_rn(t);
-        const float tl = __double2float_rn(t - (double)th);
+        // The 160-byte FP32 row is re-read every state (ten 16-byte loads that L1
+        // serves as broadcasts) instead of being held in registers across states.
+        const Rec32 rc32 = load_rec32(a.rp, j);
+        float th, tl;
+        split_double(t, th, tl);
         float r32[3], v32[3];
-        code = state32<kNewtonFP32>(rc32, gf, th, tl, r32, v32);
+        code = state32(rc32, gf, th, tl, r32, v32);
         if (code == kRecomputeFP64) {
           code = state64_fallback(a.rp, a.g, j, t, r32, v32);
           ++nfix;

@@ -200,3 +200,18 @@ def test_argument_errors_leave_outputs_untouched():
     assert ei.value.code == _lib.SGP4_ERR_ARG
     torch.cuda.synchronize()
     assert torch.all(buf == 7.0) and torch.all(st == 99)
+
+
+def test_fp32_time_split_keeps_minute_fractions():
+    """tsince far from zero with a fractional part: the double -> float hi + lo split
+    must carry the low bits (without them the phase error at 5e4 min is ~1 km)."""
+    el = np.array([[15.2 * REV, 0.001, math.radians(53.0), 0.3, 0.4, 0.5, 0.0],
+                   [14.1 * REV, 0.01, math.radians(97.6), 2.3, 1.4, 4.5, 0.0]])
+    rng = np.random.default_rng(9)
+    t = np.sort(np.concatenate([10000.0 + rng.uniform(0, 1, 40), -5000.0 - rng.uniform(0, 1, 20),
+                                50000.0 + rng.uniform(0, 1, 40), [1e-30, 2.0 ** -80, 0.1]]))
+    r, v, st, ist = gpu_propagate(el, t, "fp32")
+    rr, vr, sr, isr = oracle.propagate(el, t)
+    assert_status_and_nan(st, sr, r, v, ist, isr)
+    dr, dv = state_errors(r, v, rr, vr, sr)
+    assert dr.max() < 0.02, error_summary(dr, dv)
