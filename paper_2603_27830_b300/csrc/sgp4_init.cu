@@ -16,7 +16,7 @@ __device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
   lo = __double2float_rn(x - (double)hi);
 }
 
-__global__ void __launch_bounds__(128) init_kernel(const double* __restrict__ el,
+__global__ void __launch_bounds__(64) init_kernel(const double* __restrict__ el,
                                                    const int32_t* __restrict__ epoch_day,
                                                    const double* __restrict__ epoch_frac,
                                                    RecordPtrs rp, Geo g,
@@ -192,7 +192,23 @@ __global__ void __launch_bounds__(128) init_kernel(const double* __restrict__ el
   h[fFlags] = __int_as_float(flags);
   for (int k = kNumF32Used; k < kF32Row; ++k) h[k] = 0.0f;
 
-  // Init status: the status of the state at tsince = 0.
+  // Init status: the status of the state at tsince = 0, from the FP32 state with
+  // its FP64 recomputation inside the guard bands (so it equals the FP64 decision).
+  {
+    const Rec32 r32 = load_rec32(rp, j);
+    GeoF gf;
+    gf.xke = (float)g.xke;
+    gf.inv_xke = (float)(1.0 / g.xke);
+    gf.j2 = (float)g.j2;
+    gf.re = (float)g.re;
+    gf.vkmps = (float)g.vkmps;
+    float r[3], v[3];
+    const int code = state32(r32, gf, 0.0f, 0.0f, r, v);
+    if (code != kRecomputeFP64) {
+      init_status[j] = code;
+      return;
+    }
+  }
   Rec64 rc;
   rc.n0pp = n0pp; rc.a0pp = a0pp; rc.e0 = e0; rc.i0 = i0; rc.raan0 = raan0; rc.argp0 = argp0;
   rc.m0 = m0; rc.mdot = mdot; rc.argpdot = argpdot; rc.raandot = raandot; rc.raan_cf = raan_cf;
@@ -210,7 +226,8 @@ cudaError_t launch_init(const double* el, const int32_t* epoch_day, const double
                         const RecordPtrs& rp, const Geo& g, int32_t* init_status,
                         cudaStream_t stream) {
   if (rp.n == 0) return cudaSuccess;
-  const int threads = 128;
+  // 64-thread blocks: a Starlink-sized catalogue (9,341) then spans all 148 SMs.
+  const int threads = 64;
   const int64_t blocks = (rp.n + threads - 1) / threads;
   init_kernel<<<(unsigned)blocks, threads, 0, stream>>>(el, epoch_day, epoch_frac, rp, g,
                                                         init_status);
