@@ -32,6 +32,9 @@ UNIT = "states/s"
 
 # Per-state algorithmic output bytes (r, v as float32 x3 + int32 status; FP64: doubles).
 BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
+# FP32 arithmetic operations per state of the FP32 formulation on the Starlink-shaped
+# workload's branch (add/mul/FMA/compare = 1, each SFU op = 1); itemised in the design doc.
+ALG_OPS_FP32 = 285
 
 
 def _peaks():
@@ -50,6 +53,47 @@ def _dist():
     return rank, world, local
 
 
+class _Nvml:
+    """Minimal ctypes binding of the NVML calls the clock sampler needs (the driver's
+    libnvidia-ml.so.1; no Python package required)."""
+
+    def __init__(self):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit_v2 failed")
+        self.reason_fn = None
+        for name in ("nvmlDeviceGetCurrentClocksEventReasons",
+                     "nvmlDeviceGetCurrentClocksThrottleReasons"):
+            if hasattr(self.lib, name):
+                self.reason_fn = getattr(self.lib, name)
+                break
+
+    def handle(self, pci_bus_id: str | None, index: int):
+        h = self.c.c_void_p()
+        if pci_bus_id:
+            if self.lib.nvmlDeviceGetHandleByPciBusId_v2(pci_bus_id.encode(),
+                                                         self.c.byref(h)) == 0:
+                return h
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(index, self.c.byref(h)) != 0:
+            raise RuntimeError("no NVML handle")
+        return h
+
+    def sm_clock(self, h, max_clock=False):
+        v = self.c.c_uint()
+        fn = self.lib.nvmlDeviceGetMaxClockInfo if max_clock else self.lib.nvmlDeviceGetClockInfo
+        if fn(h, 1, self.c.byref(v)) != 0:      # NVML_CLOCK_SM = 1
+            raise RuntimeError("clock query failed")
+        return v.value
+
+    def reasons(self, h):
+        v = self.c.c_ulonglong()
+        if self.reason_fn is None or self.reason_fn(h, self.c.byref(v)) != 0:
+            return 0
+        return v.value
+
+
 class ClockSampler:
     """SM clock and throttle reasons sampled through NVML every 2 ms while the timed
     region runs (the region is only milliseconds long)."""
@@ -57,8 +101,9 @@ class ClockSampler:
     REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    def __init__(self, gpu_index: int):
-        self.idx = gpu_index
+    def __init__(self, pci_bus_id: str | None, index: int):
+        self.pci = pci_bus_id
+        self.idx = index
         self.samples = []
         self.max_mhz = None
         self._stop = None
@@ -68,12 +113,9 @@ class ClockSampler:
     def __enter__(self):
         import threading
         try:
-            import pynvml
-            pynvml.nvmlInit()
-            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-            phys = int(vis.split(",")[self.idx]) if vis and vis.split(",")[0].isdigit() else self.idx
-            h = pynvml.nvmlDeviceGetHandleByIndex(phys)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+            nv = _Nvml()
+            h = nv.handle(self.pci, self.idx)
+            self.max_mhz = nv.sm_clock(h, max_clock=True)
         except Exception as exc:  # no NVML: report it instead of clocks
             self.error = f"nvml unavailable: {exc}"
             return self
@@ -82,9 +124,7 @@ class ClockSampler:
         def poll():
             while not self._stop.is_set():
                 try:
-                    mhz = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
-                    rs = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
-                    self.samples.append((mhz, rs))
+                    self.samples.append((nv.sm_clock(h), nv.reasons(h)))
                 except Exception as exc:
                     self.error = str(exc)
                     return
@@ -234,7 +274,11 @@ def run_ours(args):
         ok = sr == 0
         max_dr_km = float(np.linalg.norm(r32[ok] - rr[ok], axis=-1).max())
 
-    with ClockSampler(local) as clk:
+    props = torch.cuda.get_device_properties(dev)
+    pci = None
+    if hasattr(props, "pci_bus_id"):
+        pci = f"{props.pci_domain_id:08X}:{props.pci_bus_id:02X}:{props.pci_device_id:02X}.0"
+    with ClockSampler(pci, local) as clk:
         ms32, per32 = timed("fp32", out32, args.steps, args.warmup)
     clocks = clk.summary()
     ms32_k, per32_k = timed("fp32", out32, args.steps, 1, kernel_only=True)
@@ -273,22 +317,35 @@ def run_ours(args):
     h2d = el_h.numel() * 8 + ts_h.numel() * 8
     d2h = (r_h.numel() + v_h.numel()) * 4 + s_h.numel() * 4
 
-    # roofline of the dominant kernel (the FP32 propagate), per launch
+    # Roofline of the dominant kernel (the FP32 propagate), per launch.  It is bound by
+    # FP32 arithmetic: ALG_OPS_FP32 operations per state (hand count of the FP32
+    # formulation on this workload's branch: drag with D terms, one Newton step)
+    # against the FP32 lanes (148 SMs x 128 lanes x SM clock).  Its HBM side (28 B
+    # per state of output) is reported beside it.
     kern_ms = statistics.mean(per32_k)
+    sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = n_sm * 128 * sm_mhz * 1e6 / 1e9          # Gop/s
+    achieved_gops = ALG_OPS_FP32 * states / (kern_ms * 1e-3) / 1e9
     bytes_per_launch = BYTES_PER_STATE["fp32"] * states
     achieved_gbs = bytes_per_launch / (kern_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved_gbs / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "propagate_kernel<fp32>", "peak_kind": peak_kind,
-                "kernel_ms": kern_ms}
+    roofline = {"bound": "alu", "achieved": achieved_gops, "peak": alu_peak, "unit": "Gop/s",
+                "frac": achieved_gops / alu_peak, "traffic": None,
+                "kernel": "propagate_kernel<fp32>", "kernel_ms": kern_ms,
+                "ops_per_state": ALG_OPS_FP32,
+                "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
+                "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind,
+                        "bytes_per_state": BYTES_PER_STATE["fp32"]}}
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        rate, dt = cpu_oracle_rate(w.elements, w.tsince, args.cpu_sats, threads)
+        rate, dt = cpu_oracle_rate(w.elements, w.tsince, min(args.cpu_sats, n), threads)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {args.cpu_sats} of {n} satellites x {T} times, "
-                         f"{dt:.1f} s wall on {threads} threads"}
+               "sample": f"first {min(args.cpu_sats, n)} of {n} satellites x {T} times, "
+                         f"{dt:.2f} s wall on {threads} threads "
+                         f"({dt * threads:.0f} core-s)"}
 
     if rank == 0:
         line = {
@@ -321,7 +378,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sats", type=int, default=2000)
+    ap.add_argument("--cpu-sats", type=int, default=9341)
     ap.add_argument("--ref-sats", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
