@@ -138,6 +138,93 @@ sgp4_result sgp4_propagate(const sgp4_records* records, const double* tsince, in
                            int grid_per_sat, sgp4_precision precision, void* r, void* v,
                            int32_t* status, unsigned long long* fixups, void* stream);
 
+/*
+ * Batched propagation of many uneven problems in one persistent launch.  The paper
+ * batches by composing vmaps over satellites and times (Sec. 2.2); a service
+ * receives many such problems at once, each with its own satellites and grid.
+ *
+ * A request covers satellites [sat_offset, sat_offset + n) of one record set, the
+ * grid tsince[t_offset, t_offset + t_count) (shared by its satellites), and writes
+ * its n * t_count states, satellite-major, to the states
+ * [out_offset, out_offset + n * t_count) of r, v ([states][3]) and status.
+ * Output ranges of different requests must not overlap.
+ */
+typedef struct sgp4_request {
+  int64_t sat_offset;
+  int64_t n;
+  int64_t t_offset;
+  int64_t t_count;
+  int64_t out_offset;
+} sgp4_request;
+
+/*
+ * A prepared batch: host-side value whose tables live in the caller's workspace.
+ * Fields are filled by sgp4_batch_plan_init; the *_needed fields are the minimum
+ * sizes of records, tsince and outputs that sgp4_propagate_batched checks.
+ */
+typedef struct sgp4_batch_plan {
+  void* workspace;        /* device, caller-owned, sgp4_batch_workspace_bytes(n) */
+  int32_t n_requests;
+  int32_t tile_states;    /* states per work tile, a multiple of 128 */
+  int32_t grid_blocks;    /* persistent grid size; 0 = one full wave on the device */
+  int32_t reserved;
+  int64_t total_tiles;
+  int64_t total_states;
+  int64_t sats_needed;    /* max over requests of sat_offset + n */
+  int64_t tsince_needed;  /* max of t_offset + t_count */
+  int64_t out_needed;     /* max of out_offset + n * t_count (states) */
+} sgp4_batch_plan;
+
+/* Device workspace bytes for a batch of n_requests (0 if n_requests < 0). */
+size_t sgp4_batch_workspace_bytes(int32_t n_requests);
+
+/*
+ * Validate a HOST request table, derive the tiling and copy the tables to the
+ * workspace (stream-ordered; `requests` may be reused when the call returns).
+ *   tile_states  states per tile, a positive multiple of 128 (chosen by the
+ *                autotuner of the Python layer, e.g. 1024)
+ *   grid_blocks  persistent grid size, 0 for one full wave
+ * Errors: SGP4_ERR_ARG for a NULL plan/workspace/requests (n_requests > 0), a
+ * negative size or offset, a bad tile_states, overlapping output ranges, or
+ * overflow; SGP4_ERR_OOM if workspace_bytes is too small; SGP4_ERR_CUDA if the copy
+ * fails.
+ */
+sgp4_result sgp4_batch_plan_init(const sgp4_request* requests, int32_t n_requests,
+                                 int32_t tile_states, int32_t grid_blocks, void* workspace,
+                                 size_t workspace_bytes, sgp4_batch_plan* plan, void* stream);
+
+/*
+ * Propagate every request of the plan in one persistent kernel launch (preceded by
+ * an 8-byte reset of the tile counter in the workspace).  Arguments as in
+ * sgp4_propagate; tsince_len and out_len (states) are the sizes of tsince and of
+ * r/v/status, checked against the plan.  Plans sharing a workspace must not run
+ * concurrently.  Errors: SGP4_ERR_ARG as in sgp4_propagate, or a record set, grid
+ * or output smaller than the plan needs.
+ */
+sgp4_result sgp4_propagate_batched(const sgp4_batch_plan* plan, const sgp4_records* records,
+                                   const double* tsince, int64_t tsince_len,
+                                   sgp4_precision precision, void* r, void* v, int32_t* status,
+                                   int64_t out_len, unsigned long long* fixups, void* stream);
+
+/*
+ * Capture sgp4_propagate_batched with these arguments into a CUDA graph and
+ * instantiate it; *graph receives an opaque handle.  `stream` must be a non-NULL
+ * stream; it is used only for the capture.  Replaying the graph re-runs the batch
+ * on the buffers given here.  Errors: those of sgp4_propagate_batched, SGP4_ERR_ARG
+ * for a NULL stream or graph, SGP4_ERR_CUDA if capture or instantiation fails.
+ */
+sgp4_result sgp4_batch_graph_create(const sgp4_batch_plan* plan, const sgp4_records* records,
+                                    const double* tsince, int64_t tsince_len,
+                                    sgp4_precision precision, void* r, void* v, int32_t* status,
+                                    int64_t out_len, unsigned long long* fixups, void* stream,
+                                    void** graph);
+
+/* Launch a graph made by sgp4_batch_graph_create on `stream`. */
+sgp4_result sgp4_batch_graph_launch(void* graph, void* stream);
+
+/* Destroy a graph made by sgp4_batch_graph_create (NULL is a no-op). */
+sgp4_result sgp4_batch_graph_destroy(void* graph);
+
 /* Library version (major*10000 + minor*100 + patch). */
 int sgp4_version(void);
 

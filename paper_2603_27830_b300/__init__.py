@@ -4,7 +4,10 @@ The C ABI is declared in include/sgp4.h and implemented by the CUDA kernels unde
 csrc/, built in-tree into libsgp4_b300.so.  The Python layer (api.py) only
 marshals torch tensors to that ABI; there is no CPU fallback.
 """
-from .api import (Records, alloc_records, propagate_host, sgp4_init,  # noqa: F401
-                  sgp4_propagate)
+from .api import (Batch, BatchGraph, BatchPlan, Records, alloc_records,  # noqa: F401
+                  make_batch, plan_batch, propagate_host, sgp4_init, sgp4_propagate,
+                  sgp4_propagate_batched)
 
-__all__ = ["Records", "alloc_records", "propagate_host", "sgp4_init", "sgp4_propagate"]
+__all__ = ["Batch", "BatchGraph", "BatchPlan", "Records", "alloc_records", "make_batch",
+           "plan_batch", "propagate_host", "sgp4_init", "sgp4_propagate",
+           "sgp4_propagate_batched"]

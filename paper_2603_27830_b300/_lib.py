@@ -26,7 +26,9 @@ RESULT_NAMES = {0: "SGP4_OK", -1: "SGP4_ERR_ARG", -2: "SGP4_ERR_CUDA", -3: "SGP4
 # Every symbol include/sgp4.h declares (checked by the CPU tests).
 EXPORTS = (
     "sgp4_version", "sgp4_wgs72", "sgp4_records_bytes", "sgp4_records_bind", "sgp4_init",
-    "sgp4_propagate",
+    "sgp4_propagate", "sgp4_batch_workspace_bytes", "sgp4_batch_plan_init",
+    "sgp4_propagate_batched", "sgp4_batch_graph_create", "sgp4_batch_graph_launch",
+    "sgp4_batch_graph_destroy",
 )
 
 
@@ -38,6 +40,20 @@ class Sgp4Consts(ctypes.Structure):
 class Sgp4Records(ctypes.Structure):
     _fields_ = [("arena", ctypes.c_void_p), ("n", ctypes.c_int64), ("stride", ctypes.c_int64),
                 ("consts", Sgp4Consts)]
+
+
+class Sgp4Request(ctypes.Structure):
+    _fields_ = [("sat_offset", ctypes.c_int64), ("n", ctypes.c_int64),
+                ("t_offset", ctypes.c_int64), ("t_count", ctypes.c_int64),
+                ("out_offset", ctypes.c_int64)]
+
+
+class Sgp4BatchPlan(ctypes.Structure):
+    _fields_ = [("workspace", ctypes.c_void_p), ("n_requests", ctypes.c_int32),
+                ("tile_states", ctypes.c_int32), ("grid_blocks", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("total_tiles", ctypes.c_int64),
+                ("total_states", ctypes.c_int64), ("sats_needed", ctypes.c_int64),
+                ("tsince_needed", ctypes.c_int64), ("out_needed", ctypes.c_int64)]
 
 
 class Sgp4Error(RuntimeError):
@@ -63,6 +79,21 @@ def _declare(lib):
     lib.sgp4_init.restype = I32
     lib.sgp4_propagate.argtypes = [R, P, I64, I32, I32, P, P, P, P, P]
     lib.sgp4_propagate.restype = I32
+    BP = ctypes.POINTER(Sgp4BatchPlan)
+    lib.sgp4_batch_workspace_bytes.argtypes = [ctypes.c_int32]
+    lib.sgp4_batch_workspace_bytes.restype = ctypes.c_size_t
+    lib.sgp4_batch_plan_init.argtypes = [P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P,
+                                         ctypes.c_size_t, BP, P]
+    lib.sgp4_batch_plan_init.restype = I32
+    lib.sgp4_propagate_batched.argtypes = [BP, R, P, I64, I32, P, P, P, I64, P, P]
+    lib.sgp4_propagate_batched.restype = I32
+    lib.sgp4_batch_graph_create.argtypes = [BP, R, P, I64, I32, P, P, P, I64, P, P,
+                                            ctypes.POINTER(ctypes.c_void_p)]
+    lib.sgp4_batch_graph_create.restype = I32
+    lib.sgp4_batch_graph_launch.argtypes = [P, P]
+    lib.sgp4_batch_graph_launch.restype = I32
+    lib.sgp4_batch_graph_destroy.argtypes = [P]
+    lib.sgp4_batch_graph_destroy.restype = I32
     return lib
 
 

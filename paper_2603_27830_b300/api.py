@@ -13,6 +13,7 @@ from __future__ import annotations
 import ctypes
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _lib
@@ -130,3 +131,134 @@ def propagate_host(elements, tsince, precision: str = "fp32", device="cuda"):
     recs, ist = sgp4_init(el_d)
     r, v, st = sgp4_propagate(recs, ts_d, precision)
     return r.cpu().numpy(), v.cpu().numpy(), st.cpu().numpy(), ist.cpu().numpy()
+
+
+# ------------------------------------------------------------------------ batching
+@dataclass
+class BatchPlan:
+    """A prepared batch of requests: device workspace plus the ABI plan struct."""
+    workspace: torch.Tensor
+    c: _lib.Sgp4BatchPlan
+    requests: np.ndarray          # [n_req, 5] int64: sat_offset, n, t_offset, t_count, out_offset
+
+    @property
+    def total_states(self) -> int:
+        return int(self.c.total_states)
+
+
+@dataclass
+class Batch:
+    """Concatenated inputs of many requests (see ``make_batch``)."""
+    elements: np.ndarray          # [sum n_i, 7]
+    tsince: np.ndarray            # [sum T_i]
+    requests: np.ndarray          # [n_req, 5] int64, outputs contiguous in request order
+
+
+def make_batch(problems) -> Batch:
+    """Concatenate (elements [n_i, 7], tsince [T_i]) pairs into one record set, one
+    grid array and a request table whose outputs follow each other."""
+    els, ts, rows = [], [], []
+    sat = tof = out = 0
+    for el, t in problems:
+        el = np.asarray(el, dtype=np.float64).reshape(-1, 7)
+        t = np.asarray(t, dtype=np.float64).reshape(-1)
+        rows.append((sat, el.shape[0], tof, t.shape[0], out))
+        els.append(el)
+        ts.append(t)
+        sat += el.shape[0]
+        tof += t.shape[0]
+        out += el.shape[0] * t.shape[0]
+    return Batch(np.concatenate(els) if els else np.zeros((0, 7)),
+                 np.concatenate(ts) if ts else np.zeros(0),
+                 np.asarray(rows, dtype=np.int64).reshape(-1, 5))
+
+
+def plan_batch(requests, tile_states: int = 1024, grid_blocks: int = 0, device=None,
+               stream=None) -> BatchPlan:
+    """Validate a request table ([n_req, 5] int64) and place it in a device workspace."""
+    req = np.ascontiguousarray(np.asarray(requests, dtype=np.int64).reshape(-1, 5))
+    n = req.shape[0]
+    lib = _lib.load()
+    nbytes = int(lib.sgp4_batch_workspace_bytes(n))
+    ws = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device or "cuda")
+    plan = _lib.Sgp4BatchPlan()
+    table = (_lib.Sgp4Request * max(n, 1))()
+    for k in range(n):
+        table[k] = _lib.Sgp4Request(*[int(x) for x in req[k]])
+    _lib.check("sgp4_batch_plan_init",
+               lib.sgp4_batch_plan_init(ctypes.cast(table, ctypes.c_void_p), n, int(tile_states),
+                                        int(grid_blocks), _ptr(ws), nbytes, ctypes.byref(plan),
+                                        _stream_handle(stream)))
+    return BatchPlan(ws, plan, req)
+
+
+def _batch_out(plan: BatchPlan, precision: str, device, out):
+    if out is not None:
+        return out
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    S = int(plan.c.out_needed)
+    return (torch.empty((S, 3), dtype=dt, device=device),
+            torch.empty((S, 3), dtype=dt, device=device),
+            torch.empty((S,), dtype=torch.int32, device=device))
+
+
+def sgp4_propagate_batched(plan: BatchPlan, records: Records, tsince: torch.Tensor,
+                           precision: str = "fp32", out: tuple | None = None,
+                           fixups: torch.Tensor | None = None, stream=None):
+    """All requests of a plan in one persistent launch.  Returns r, v [S, 3] and
+    status [S] over the concatenated output states (request k at its out_offset)."""
+    _require_cuda("tsince", tsince, torch.float64)
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    r, v, st = _batch_out(plan, precision, tsince.device, out)
+    if fixups is not None:
+        _require_cuda("fixups", fixups, torch.int64)
+    lib = _lib.load()
+    _lib.check("sgp4_propagate_batched",
+               lib.sgp4_propagate_batched(ctypes.byref(plan.c), ctypes.byref(records.c),
+                                          _ptr(tsince), tsince.numel(), PRECISIONS[precision],
+                                          _ptr(r), _ptr(v), _ptr(st), st.numel(), _ptr(fixups),
+                                          _stream_handle(stream)))
+    return r, v, st
+
+
+class BatchGraph:
+    """The batched launch captured once in a CUDA graph; ``replay()`` re-runs it on
+    the same buffers (stream-ordered)."""
+
+    def __init__(self, plan: BatchPlan, records: Records, tsince: torch.Tensor,
+                 precision: str = "fp32", out: tuple | None = None, stream=None):
+        _require_cuda("tsince", tsince, torch.float64)
+        self.plan, self.records, self.tsince = plan, records, tsince
+        self.out = _batch_out(plan, precision, tsince.device, out)
+        self._capture_stream = torch.cuda.Stream(device=tsince.device)
+        self._capture_stream.wait_stream(torch.cuda.current_stream(tsince.device))
+        r, v, st = self.out
+        handle = ctypes.c_void_p()
+        lib = _lib.load()
+        _lib.check("sgp4_batch_graph_create",
+                   lib.sgp4_batch_graph_create(ctypes.byref(plan.c), ctypes.byref(records.c),
+                                               _ptr(tsince), tsince.numel(),
+                                               PRECISIONS[precision], _ptr(r), _ptr(v), _ptr(st),
+                                               st.numel(), None,
+                                               _stream_handle(self._capture_stream),
+                                               ctypes.byref(handle)))
+        self.handle = handle
+        self._stream = stream
+
+    def replay(self, stream=None):
+        lib = _lib.load()
+        _lib.check("sgp4_batch_graph_launch",
+                   lib.sgp4_batch_graph_launch(self.handle, _stream_handle(stream or self._stream)))
+        return self.out
+
+    def close(self):
+        if self.handle:
+            _lib.load().sgp4_batch_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "sgp4.h"
 #include "sgp4_device.cuh"
 
 namespace sgp4 {
@@ -27,7 +28,31 @@ struct PropArgs {
 cudaError_t launch_propagate64(const PropArgs& a, cudaStream_t stream);
 cudaError_t launch_propagate32(const PropArgs& a, cudaStream_t stream);
 
-// SM count and resident blocks per SM for a kernel, cached per device.
+struct BatchArgs {
+  RecordPtrs rp;
+  Geo g;
+  const double* tsince;          // all requests' grids, concatenated
+  const sgp4_request* reqs;      // [n_req], device
+  const int64_t* tile_start;     // [n_req + 1], device: exclusive prefix of tile counts
+  int32_t n_req;
+  int64_t tile_states;
+  unsigned long long* counter;   // next tile index (reset before every launch)
+  void* r;
+  void* v;
+  int32_t* status;
+  unsigned long long* fixups;
+};
+
+// Persistent grid of the batched kernel: grid_blocks if positive, else one full wave
+// (SMs x resident blocks), at most one block per tile.  Queries the device: call it
+// outside stream capture.
+int64_t batched_grid(bool fp32, int64_t total_tiles, int grid_blocks);
+
+// Resets the tile counter, then launches the persistent batched kernel on `grid` blocks.
+cudaError_t launch_batched(const BatchArgs& a, bool fp32, int64_t total_tiles, int64_t grid,
+                           cudaStream_t stream);
+
+// SM count of the current device.
 int device_sm_count();
 
 }  // namespace sgp4

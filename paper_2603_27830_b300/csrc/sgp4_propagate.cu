@@ -1,14 +1,19 @@
 // Propagation kernels: one (satellite, time) state per thread (paper Sec. 2.2,
 // "Vectorisation": f(s, t) under a vmap over times composed with a vmap over
-// satellites), with
-//   * a persistent grid of one wave, each block owning one contiguous range of the
-//     flattened [n][T] state space, so consecutive iterations of a thread walk along
-//     the time axis of the same satellite and its record stays in L1 (FP32) or in
+// satellites).  Both kernels run the same range loop, run_range():
+//   * a block walks a contiguous range of the flattened [n][T] state space of one
+//     problem, 128 states per step, so consecutive steps of a thread walk along the
+//     time axis of the same satellite and its record stays in L1 (FP32) or in
 //     registers (FP64);
-//   * outputs staged in shared memory and written back with 16-byte streaming
-//     stores ([n][T][3] is AoS per state, so a block's 128 states are 1.5 KB (FP32)
-//     or 3 KB (FP64) of contiguous r, the same of v, and 512 B of status).
+//   * outputs are staged in shared memory and written back with 16-byte streaming
+//     stores ([n][T][3] is AoS per state, so 128 states are 1.5 KB (FP32) or 3 KB
+//     (FP64) of contiguous r, the same of v, and 512 B of status).
+// propagate_kernel: one problem, a persistent grid of one wave, each block owning
+// one contiguous range.  batched_kernel: many problems ("requests") of uneven size
+// in one persistent launch; blocks take fixed-size tiles of states from a global
+// atomic counter, so uneven requests and uneven per-state cost balance themselves.
 #include <algorithm>
+#include <cstdint>
 
 #include "sgp4_device.cuh"
 #include "sgp4_kernels.cuh"
@@ -35,88 +40,105 @@ __device__ __forceinline__ void nan_fill(OutT x[3]) {
 }
 
 template <bool kFP32>
-__global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
-    propagate_kernel(PropArgs a, int64_t chunk) {
+struct Stage {
   using OutT = typename std::conditional<kFP32, float, double>::type;
-  __shared__ __align__(16) OutT s_r[3 * kThreads];
-  __shared__ __align__(16) OutT s_v[3 * kThreads];
-  __shared__ __align__(16) int32_t s_st[kThreads];
+  __align__(16) OutT r[3 * kThreads];
+  __align__(16) OutT v[3 * kThreads];
+  __align__(16) int32_t st[kThreads];
+};
 
+// One problem's view: its time grid, its first record and its output base.
+struct Range {
+  const double* tsince;   // [T], or [n][T] when per_sat
+  int64_t T;
+  int per_sat;
+  int64_t sat0;           // record index of the problem's satellite 0
+  void* r;                // output of the problem's state 0
+  void* v;
+  int32_t* status;
+};
+
+__device__ __forceinline__ GeoF make_geof(const Geo& g) {
+  GeoF gf;
+  gf.xke = (float)g.xke;
+  gf.inv_xke = (float)(1.0 / g.xke);
+  gf.j2 = (float)g.j2;
+  gf.re = (float)g.re;
+  gf.vkmps = (float)g.vkmps;
+  return gf;
+}
+
+// States [beg, end) of one problem (local flattened index j * T + i).  Every thread
+// of the block calls it with the same arguments (it contains block barriers).
+template <bool kFP32>
+__device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
+                                          const Range& rg, int64_t beg, int64_t end,
+                                          Stage<kFP32>& sm, unsigned long long& nfix) {
+  using OutT = typename Stage<kFP32>::OutT;
   const int tid = threadIdx.x;
-  const int64_t T = a.t_count;
-  const int64_t total = a.rp.n * T;
-  const int64_t beg = (int64_t)blockIdx.x * chunk;
-  const int64_t end = min(total, beg + chunk);
-  if (beg >= end) return;
-
-  // (j, i) of this thread's first state; advanced incrementally afterwards.
+  const int64_t T = rg.T;
   int64_t j = (beg + tid) / T;
   int64_t i = (beg + tid) - j * T;
   int64_t cur = -1;
   Rec64 rc64;
-  GeoF gf;
-  if (kFP32) {
-    gf.xke = (float)a.g.xke;
-    gf.inv_xke = (float)(1.0 / a.g.xke);
-    gf.j2 = (float)a.g.j2;
-    gf.re = (float)a.g.re;
-    gf.vkmps = (float)a.g.vkmps;
-  }
-  unsigned long long nfix = 0;
 
   for (int64_t base = beg; base < end; base += kThreads) {
     const int64_t idx = base + tid;
     OutT rr[3], vv[3];
     int code = 0;
     if (idx < end) {
+      const int64_t rec = rg.sat0 + j;
       if (!kFP32 && j != cur) {
-        rc64 = load_rec64(a.rp, j);
+        rc64 = load_rec64(rp, rec);
         cur = j;
       }
-      const double t = a.grid_per_sat ? __ldg(a.tsince + j * T + i) : __ldg(a.tsince + i);
+      const double t = rg.per_sat ? __ldg(rg.tsince + j * T + i) : __ldg(rg.tsince + i);
       if (kFP32) {
         // The 160-byte FP32 row is re-read every state (ten 16-byte loads that L1
         // serves as broadcasts) instead of being held in registers across states.
-        const Rec32 rc32 = load_rec32(a.rp, j);
+        const Rec32 rc32 = load_rec32(rp, rec);
         float th, tl;
         split_double(t, th, tl);
         float r32[3], v32[3];
         code = state32(rc32, gf, th, tl, r32, v32);
         if (code == kRecomputeFP64) {
-          code = state64_fallback(a.rp, a.g, j, t, r32, v32);
+          code = state64_fallback(rp, g, rec, t, r32, v32);
           ++nfix;
         }
         for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r32[c]; vv[c] = (OutT)v32[c]; }
       } else {
         double r64[3], v64[3];
-        code = state64(rc64, a.g, t, r64, v64);
+        code = state64(rc64, g, t, r64, v64);
         for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r64[c]; vv[c] = (OutT)v64[c]; }
       }
       if (code != 0 && code != 6) { nan_fill(rr); nan_fill(vv); }
     }
-    s_r[3 * tid + 0] = rr[0]; s_r[3 * tid + 1] = rr[1]; s_r[3 * tid + 2] = rr[2];
-    s_v[3 * tid + 0] = vv[0]; s_v[3 * tid + 1] = vv[1]; s_v[3 * tid + 2] = vv[2];
-    s_st[tid] = code;
+    sm.r[3 * tid + 0] = rr[0]; sm.r[3 * tid + 1] = rr[1]; sm.r[3 * tid + 2] = rr[2];
+    sm.v[3 * tid + 0] = vv[0]; sm.v[3 * tid + 1] = vv[1]; sm.v[3 * tid + 2] = vv[2];
+    sm.st[tid] = code;
     __syncthreads();
 
-    OutT* gr = static_cast<OutT*>(a.r) + base * 3;
-    OutT* gv = static_cast<OutT*>(a.v) + base * 3;
-    int32_t* gs = a.status + base;
+    OutT* gr = static_cast<OutT*>(rg.r) + base * 3;
+    OutT* gv = static_cast<OutT*>(rg.v) + base * 3;
+    int32_t* gs = rg.status + base;
     const int64_t cnt = min((int64_t)kThreads, end - base);
-    if (cnt == kThreads) {
+    const bool vec = cnt == kThreads &&
+                     ((reinterpret_cast<uintptr_t>(gr) | reinterpret_cast<uintptr_t>(gv) |
+                       reinterpret_cast<uintptr_t>(gs)) & 15) == 0;
+    if (vec) {
       constexpr int kVec = 3 * kThreads * (int)sizeof(OutT) / 16;
       constexpr int kVecSt = kThreads * 4 / 16;
-      const int4* sr = reinterpret_cast<const int4*>(s_r);
-      const int4* sv = reinterpret_cast<const int4*>(s_v);
-      const int4* ss = reinterpret_cast<const int4*>(s_st);
+      const int4* sr = reinterpret_cast<const int4*>(sm.r);
+      const int4* sv = reinterpret_cast<const int4*>(sm.v);
+      const int4* ss = reinterpret_cast<const int4*>(sm.st);
       for (int k = tid; k < kVec; k += kThreads) {
         __stcs(reinterpret_cast<int4*>(gr) + k, sr[k]);
         __stcs(reinterpret_cast<int4*>(gv) + k, sv[k]);
       }
       if (tid < kVecSt) __stcs(reinterpret_cast<int4*>(gs) + tid, ss[tid]);
     } else {
-      for (int k = tid; k < 3 * cnt; k += kThreads) { gr[k] = s_r[k]; gv[k] = s_v[k]; }
-      if (tid < cnt) gs[tid] = s_st[tid];
+      for (int k = tid; k < 3 * cnt; k += kThreads) { gr[k] = sm.r[k]; gv[k] = sm.v[k]; }
+      if (tid < cnt) gs[tid] = sm.st[tid];
     }
     __syncthreads();
 
@@ -127,27 +149,105 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
       i -= q * T;
     }
   }
+}
+
+template <bool kFP32>
+__global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
+    propagate_kernel(PropArgs a, int64_t chunk) {
+  __shared__ Stage<kFP32> sm;
+  const int64_t total = a.rp.n * a.t_count;
+  const int64_t beg = (int64_t)blockIdx.x * chunk;
+  const int64_t end = min(total, beg + chunk);
+  if (beg >= end) return;
+  const GeoF gf = make_geof(a.g);
+  Range rg;
+  rg.tsince = a.tsince;
+  rg.T = a.t_count;
+  rg.per_sat = a.grid_per_sat;
+  rg.sat0 = 0;
+  rg.r = a.r;
+  rg.v = a.v;
+  rg.status = a.status;
+  unsigned long long nfix = 0;
+  run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, sm, nfix);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
+}
+
+// Persistent batched kernel: tiles of `tile_states` consecutive states of one
+// request, numbered request by request (tile_start is the exclusive prefix sum of
+// the tile counts); a block takes the next tile index from the counter until the
+// tiles run out.  The counter is only incremented: no block ever waits on another.
+template <bool kFP32>
+__global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
+    batched_kernel(BatchArgs a) {
+  __shared__ Stage<kFP32> sm;
+  __shared__ unsigned long long s_tile;
+  const GeoF gf = make_geof(a.g);
+  const int64_t total_tiles = a.tile_start[a.n_req];
+  unsigned long long nfix = 0;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1ULL);
+    __syncthreads();
+    const int64_t tile = (int64_t)s_tile;
+    __syncthreads();
+    if (tile >= total_tiles) break;
+    // Request owning the tile: the last q with tile_start[q] <= tile (requests with
+    // no states have no tiles and are skipped by this rule).
+    int lo = 0, hi = a.n_req - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(a.tile_start + mid) <= tile) lo = mid; else hi = mid - 1;
+    }
+    const sgp4_request q = a.reqs[lo];
+    const int64_t states = q.n * q.t_count;
+    const int64_t beg = (tile - __ldg(a.tile_start + lo)) * a.tile_states;
+    const int64_t end = min(states, beg + a.tile_states);
+    Range rg;
+    rg.tsince = a.tsince + q.t_offset;
+    rg.T = q.t_count;
+    rg.per_sat = 0;
+    rg.sat0 = q.sat_offset;
+    if (kFP32) {
+      rg.r = static_cast<float*>(a.r) + q.out_offset * 3;
+      rg.v = static_cast<float*>(a.v) + q.out_offset * 3;
+    } else {
+      rg.r = static_cast<double*>(a.r) + q.out_offset * 3;
+      rg.v = static_cast<double*>(a.v) + q.out_offset * 3;
+    }
+    rg.status = a.status + q.out_offset;
+    run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, sm, nfix);
+  }
+  if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
+}
+
+template <typename K>
+int blocks_per_sm_of(K kernel) {
+  int bps = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kThreads, 0) != cudaSuccess)
+    return 1;
+  return bps > 0 ? bps : 1;
 }
 
 template <bool kFP32>
 cudaError_t launch(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * a.t_count;
   if (total == 0) return cudaSuccess;
-  static int blocks_per_sm[2] = {0, 0};   // per precision; same kernel on every device
-  int& bps = blocks_per_sm[kFP32 ? 1 : 0];
-  if (bps == 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, propagate_kernel<kFP32>,
-                                                                  kThreads, 0);
-    if (e != cudaSuccess) return e;
-    if (bps < 1) bps = 1;
-  }
+  static int bps = 0;   // resident blocks per SM of this kernel (same on every B300)
+  if (bps == 0) bps = blocks_per_sm_of(propagate_kernel<kFP32>);
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
   const int64_t blocks = (total + chunk - 1) / chunk;
   propagate_kernel<kFP32><<<(unsigned)blocks, kThreads, 0, stream>>>(a, chunk);
   return cudaGetLastError();
+}
+
+template <bool kFP32>
+int64_t grid_b(int64_t total_tiles, int grid_blocks) {
+  static int bps = 0;
+  if (bps == 0) bps = blocks_per_sm_of(batched_kernel<kFP32>);
+  int64_t grid = grid_blocks > 0 ? grid_blocks : (int64_t)device_sm_count() * bps;
+  return std::max<int64_t>(1, std::min<int64_t>(grid, total_tiles));
 }
 
 }  // namespace
@@ -165,6 +265,20 @@ cudaError_t launch_propagate64(const PropArgs& a, cudaStream_t stream) {
 
 cudaError_t launch_propagate32(const PropArgs& a, cudaStream_t stream) {
   return launch<true>(a, stream);
+}
+
+int64_t batched_grid(bool fp32, int64_t total_tiles, int grid_blocks) {
+  return fp32 ? grid_b<true>(total_tiles, grid_blocks) : grid_b<false>(total_tiles, grid_blocks);
+}
+
+cudaError_t launch_batched(const BatchArgs& a, bool fp32, int64_t total_tiles, int64_t grid,
+                           cudaStream_t stream) {
+  if (total_tiles == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  if (fp32) batched_kernel<true><<<(unsigned)grid, kThreads, 0, stream>>>(a);
+  else batched_kernel<false><<<(unsigned)grid, kThreads, 0, stream>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace sgp4
