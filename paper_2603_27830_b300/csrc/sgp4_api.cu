@@ -171,7 +171,8 @@ sgp4_result sgp4_batch_plan_init(const sgp4_request* requests, int32_t n_request
   if (!plan || n_requests < 0 || grid_blocks < 0) return SGP4_ERR_ARG;
   if (tile_states <= 0 || tile_states % 128 != 0) return SGP4_ERR_ARG;
   if (n_requests > 0 && (!requests || !workspace || !aligned(workspace, 256))) return SGP4_ERR_ARG;
-  if (workspace_bytes < sgp4_batch_workspace_bytes(n_requests)) return SGP4_ERR_OOM;
+  if (n_requests > 0 && workspace_bytes < sgp4_batch_workspace_bytes(n_requests))
+    return SGP4_ERR_OOM;
   const int64_t kLimit = INT64_MAX / 4;
   std::vector<int64_t> tile_start((size_t)n_requests + 1, 0);
   std::vector<std::pair<int64_t, int64_t>> spans;

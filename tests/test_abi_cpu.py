@@ -110,3 +110,29 @@ def test_python_api_refuses_cpu_tensors():
     from paper_2603_27830_b300 import sgp4_init
     with pytest.raises(ValueError, match="CUDA"):
         sgp4_init(torch.zeros((3, 7), dtype=torch.float64))
+
+
+def test_batch_plan_rejects_bad_tables_before_any_copy():
+    lib = _lib.load()
+    assert lib.sgp4_batch_workspace_bytes(-1) == 0
+    assert lib.sgp4_batch_workspace_bytes(3) >= 256 + 3 * 40
+    plan = _lib.Sgp4BatchPlan()
+    ws = ctypes.c_void_p(1 << 20)
+    nb = lib.sgp4_batch_workspace_bytes(2)
+
+    def call(rows, tile=1024, grid=0, nbytes=None):
+        table = (_lib.Sgp4Request * len(rows))(*[_lib.Sgp4Request(*r) for r in rows])
+        return lib.sgp4_batch_plan_init(ctypes.cast(table, ctypes.c_void_p), len(rows), tile,
+                                        grid, ws, nb if nbytes is None else nbytes,
+                                        ctypes.byref(plan), None)
+
+    ok = [(0, 10, 0, 5, 0), (10, 4, 5, 3, 50)]
+    assert call(ok, tile=100) == _lib.SGP4_ERR_ARG          # not a multiple of 128
+    assert call(ok, tile=0) == _lib.SGP4_ERR_ARG
+    assert call(ok, grid=-1) == _lib.SGP4_ERR_ARG
+    assert call(ok, nbytes=16) == _lib.SGP4_ERR_OOM
+    assert call([(0, -1, 0, 5, 0), ok[1]]) == _lib.SGP4_ERR_ARG
+    assert call([(0, 10, 0, 5, 0), (10, 4, 5, 3, 49)]) == _lib.SGP4_ERR_ARG   # outputs overlap
+    assert call([(0, 1 << 40, 0, 1 << 40, 0), ok[1]]) == _lib.SGP4_ERR_ARG    # overflow
+    assert lib.sgp4_batch_plan_init(None, 0, 1024, 0, None, 0, ctypes.byref(plan), None) == 0
+    assert plan.n_requests == 0 and plan.total_tiles == 0

@@ -1,0 +1,190 @@
+"""Batched persistent propagation: many uneven requests in one launch.
+
+The batched kernel runs the same per-state code as sgp4_propagate, so its outputs
+must equal the per-request launches bit for bit, for every tile size; against the
+oracle the same bars hold as for single problems (status bit-exact, FP64 within
+1e-6 km)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import FP64_TOL_R_KM, assert_status_and_nan, error_summary, state_errors
+from paper_2603_27830_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _small_batch(seed=0, n_req=30):
+    from paper_2603_27830_b300 import make_batch
+    rng = np.random.default_rng(seed)
+    probs = []
+    for k in range(n_req):
+        n = int(rng.integers(0, 300)) if k % 7 else 0          # some empty requests
+        T = int(rng.integers(0, 200)) if k % 11 else 0
+        el = W.catalogue_elements(rng, max(n, 1), invalid_frac=0.03)[:n]
+        probs.append((el, np.sort(rng.uniform(-720.0, 2880.0, T))))
+    return make_batch(probs)
+
+
+def _run_batched(b, precision, tile=1024, records=None):
+    import torch
+
+    from paper_2603_27830_b300 import plan_batch, sgp4_init, sgp4_propagate_batched
+    el = torch.as_tensor(b.elements, device="cuda")
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    recs = records or sgp4_init(el)[0]
+    plan = plan_batch(b.requests, tile)
+    r, v, st = sgp4_propagate_batched(plan, recs, ts, precision)
+    torch.cuda.synchronize()
+    return r, v, st, recs
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batched_equals_per_request_launches(precision):
+    import torch
+
+    from paper_2603_27830_b300 import sgp4_init, sgp4_propagate
+    b = _small_batch()
+    r, v, st, _ = _run_batched(b, precision)
+    for sat0, n, t0, T, out0 in b.requests:
+        if n * T == 0:
+            continue
+        el = torch.as_tensor(b.elements[sat0:sat0 + n], device="cuda")
+        ts = torch.as_tensor(b.tsince[t0:t0 + T], device="cuda")
+        recs, _ = sgp4_init(el)
+        r1, v1, s1 = sgp4_propagate(recs, ts, precision)
+        sl = slice(out0, out0 + n * T)
+        assert torch.equal(st[sl], s1.reshape(-1))
+        assert torch.equal(r[sl].nan_to_num(7.0), r1.reshape(-1, 3).nan_to_num(7.0))
+        assert torch.equal(v[sl].nan_to_num(7.0), v1.reshape(-1, 3).nan_to_num(7.0))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_batched_against_oracle(precision):
+    b = _small_batch(seed=1)
+    r, v, st, _ = _run_batched(b, precision)
+    r, v, st = r.double().cpu().numpy(), v.double().cpu().numpy(), st.cpu().numpy()
+    for sat0, n, t0, T, out0 in b.requests:
+        if n * T == 0:
+            continue
+        rr, vr, sr, _ = oracle.propagate(b.elements[sat0:sat0 + n], b.tsince[t0:t0 + T])
+        sl = slice(out0, out0 + n * T)
+        rg, vg, sg = r[sl].reshape(n, T, 3), v[sl].reshape(n, T, 3), st[sl].reshape(n, T)
+        assert_status_and_nan(sg, sr, rg, vg)
+        dr, dv = state_errors(rg, vg, rr, vr, sr)
+        tol = FP64_TOL_R_KM if precision == "fp64" else 1.0
+        if dr.size:
+            assert dr.max() <= tol, error_summary(dr, dv)
+
+
+def test_tile_size_does_not_change_results():
+    import torch
+    b = _small_batch(seed=2)
+    ref = _run_batched(b, "fp32", tile=1024)
+    for tile in (128, 384, 4096):
+        out = _run_batched(b, "fp32", tile=tile, records=ref[3])
+        for x, y in zip(out[:3], ref[:3]):
+            assert torch.equal(x.nan_to_num(7.0), y.nan_to_num(7.0))
+
+
+def test_reversed_outputs_with_gaps():
+    """Outputs may be placed in any order with gaps: the gaps stay untouched."""
+    import torch
+
+    from paper_2603_27830_b300 import plan_batch, sgp4_init, sgp4_propagate_batched
+    b = _small_batch(seed=3, n_req=8)
+    req = b.requests.copy()
+    off = 5
+    for k in reversed(range(len(req))):
+        req[k, 4] = off
+        off += req[k, 1] * req[k, 3] + 3           # 3-state gap after each request
+    el = torch.as_tensor(b.elements, device="cuda")
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    recs, _ = sgp4_init(el)
+    S = off
+    r = torch.full((S, 3), 123.0, device="cuda")
+    v = torch.full((S, 3), 123.0, device="cuda")
+    st = torch.full((S,), 77, dtype=torch.int32, device="cuda")
+    sgp4_propagate_batched(plan_batch(req, 256), recs, ts, "fp32", out=(r, v, st))
+    ref_r, _, ref_st, _ = _run_batched(b, "fp32")
+    written = torch.zeros(S, dtype=torch.bool, device="cuda")
+    for (sat0, n, t0, T, o_new), o_ref in zip(req, b.requests[:, 4]):
+        m = n * T
+        written[o_new:o_new + m] = True
+        assert torch.equal(st[o_new:o_new + m], ref_st[o_ref:o_ref + m])
+        assert torch.equal(r[o_new:o_new + m].nan_to_num(7.0),
+                           ref_r[o_ref:o_ref + m].nan_to_num(7.0))
+    assert torch.all(st[~written] == 77) and torch.all(r[~written] == 123.0)
+
+
+def test_graph_replay_equals_direct_launch():
+    import torch
+
+    from paper_2603_27830_b300 import BatchGraph, plan_batch, sgp4_init
+    b = _small_batch(seed=4)
+    ref = _run_batched(b, "fp32")
+    el = torch.as_tensor(b.elements, device="cuda")
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    recs, _ = sgp4_init(el)
+    g = BatchGraph(plan_batch(b.requests, 1024), recs, ts, "fp32")
+    for _ in range(2):
+        for x in g.out:
+            x.fill_(0)
+        out = g.replay()
+        torch.cuda.synchronize()
+        for x, y in zip(out, ref[:3]):
+            assert torch.equal(x.nan_to_num(7.0), y.nan_to_num(7.0))
+    g.close()
+
+
+def test_plan_larger_than_buffers_is_rejected():
+    import torch
+
+    from paper_2603_27830_b300 import _lib, plan_batch, sgp4_init, sgp4_propagate_batched
+    b = _small_batch(seed=5, n_req=4)
+    el = torch.as_tensor(b.elements[:-1], device="cuda")      # one satellite short
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    recs, _ = sgp4_init(el)
+    with pytest.raises(_lib.Sgp4Error) as ei:
+        sgp4_propagate_batched(plan_batch(b.requests), recs, ts, "fp32")
+    assert ei.value.code == _lib.SGP4_ERR_ARG
+
+
+def test_uneven_requests_full_size_autotuned():
+    """256 uneven requests (N log-U[100, 5e4], T log-U[10, 5e3], grids U[-720, 2880])
+    in one autotuned persistent launch, FP32; every invalid record and a sample of
+    each of 16 requests checked against the oracle."""
+    import torch
+
+    from paper_2603_27830_b300 import autotune, make_batch, sgp4_init, sgp4_propagate_batched
+    reqs = W.config4(seed=0)
+    b = make_batch([(q.elements, q.tsince) for q in reqs])
+    el = torch.as_tensor(b.elements, device="cuda")
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    recs, ist = sgp4_init(el)
+    S = int((b.requests[:, 1] * b.requests[:, 3]).sum())
+    out = (torch.empty((S, 3), dtype=torch.float32, device="cuda"),
+           torch.empty((S, 3), dtype=torch.float32, device="cuda"),
+           torch.empty((S,), dtype=torch.int32, device="cuda"))
+    plan, entry = autotune.tune_batch(b.requests, recs, ts, "fp32", out=out, reps=2,
+                                      use_cache=False)
+    r, v, st = sgp4_propagate_batched(plan, recs, ts, "fp32", out=out)
+    torch.cuda.synchronize()
+    assert set(torch.unique(st).cpu().tolist()) <= {0, 1, 2, 4, 6}
+    rng = np.random.default_rng(0)
+    for k in rng.choice(len(reqs), 16, replace=False):
+        sat0, n, t0, T, out0 = b.requests[k]
+        pick = np.unique(np.concatenate([rng.choice(n, min(n, 40), replace=False),
+                                         np.flatnonzero(reqs[k].elements[:, 1] >= 1.0)]))
+        rr, vr, sr, _ = oracle.propagate(reqs[k].elements[pick], reqs[k].tsince)
+        idx = torch.as_tensor((out0 + pick[:, None] * T + np.arange(T)[None, :]).reshape(-1),
+                              device="cuda")
+        rg = r[idx].double().cpu().numpy().reshape(len(pick), T, 3)
+        vg = v[idx].double().cpu().numpy().reshape(len(pick), T, 3)
+        sg = st[idx].cpu().numpy().reshape(len(pick), T)
+        assert_status_and_nan(sg, sr, rg, vg)
+        dr, dv = state_errors(rg, vg, rr, vr, sr)
+        if dr.size:
+            assert dr.max() <= 1.0, (k, error_summary(dr, dv))
