@@ -281,11 +281,31 @@ struct Rec32 {
   int flags;
 };
 
+// Unpack ten float4 of one FP32 row.
+__device__ __forceinline__ Rec32 unpack_rec32(const float4 q0, const float4 q1, const float4 q2,
+                                              const float4 q3, const float4 q4, const float4 q5,
+                                              const float4 q6, const float4 q7, const float4 q8,
+                                              const float4 q9);
+
+// Read-only path (__ldg): only for rows that no thread of the running kernel writes.
 __device__ __forceinline__ Rec32 load_rec32(const RecordPtrs& rp, int64_t j) {
   const float4* __restrict__ row = reinterpret_cast<const float4*>(rp.f32 + j * kF32Row);
-  const float4 q0 = __ldg(row + 0), q1 = __ldg(row + 1), q2 = __ldg(row + 2), q3 = __ldg(row + 3);
-  const float4 q4 = __ldg(row + 4), q5 = __ldg(row + 5), q6 = __ldg(row + 6), q7 = __ldg(row + 7);
-  const float4 q8 = __ldg(row + 8), q9 = __ldg(row + 9);
+  return unpack_rec32(__ldg(row + 0), __ldg(row + 1), __ldg(row + 2), __ldg(row + 3),
+                      __ldg(row + 4), __ldg(row + 5), __ldg(row + 6), __ldg(row + 7),
+                      __ldg(row + 8), __ldg(row + 9));
+}
+
+// Coherent path: for a row the calling thread has just written (the record builder).
+__device__ __forceinline__ Rec32 read_own_rec32(const float* row_f) {
+  const float4* row = reinterpret_cast<const float4*>(row_f);
+  return unpack_rec32(row[0], row[1], row[2], row[3], row[4], row[5], row[6], row[7], row[8],
+                      row[9]);
+}
+
+__device__ __forceinline__ Rec32 unpack_rec32(const float4 q0, const float4 q1, const float4 q2,
+                                              const float4 q3, const float4 q4, const float4 q5,
+                                              const float4 q6, const float4 q7, const float4 q8,
+                                              const float4 q9) {
   Rec32 r;
   r.phi0h = q0.x; r.phi0l = q0.y; r.phidh = q0.z; r.phidl = q0.w;
   r.m0r = q1.x; r.mdr = q1.y; r.argp0r = q1.z; r.argpdr = q1.w;

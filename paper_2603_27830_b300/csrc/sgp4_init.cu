@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(64) init_kernel(const double* __restrict__ el,
   // Init status: the status of the state at tsince = 0, from the FP32 state with
   // its FP64 recomputation inside the guard bands (so it equals the FP64 decision).
   {
-    const Rec32 r32 = load_rec32(rp, j);
+    const Rec32 r32 = read_own_rec32(h);
     GeoF gf;
     gf.xke = (float)g.xke;
     gf.inv_xke = (float)(1.0 / g.xke);

@@ -50,3 +50,16 @@ def error_summary(dr, dv):
     return {"n": int(dr.size), "max_dr_km": float(dr.max()),
             "p99_dr_km": float(np.percentile(dr, 99)), "median_dr_km": float(np.median(dr)),
             "max_dv_kms": float(dv.max()), "p99_dv_kms": float(np.percentile(dv, 99))}
+
+
+def valid_codes_only(st) -> bool:
+    """Every entry of a (possibly > 2^31-element) device status array is 0, 1, 2, 4 or 6."""
+    import torch
+    flat = st.reshape(-1)
+    step = 1 << 28
+    for k in range(0, flat.numel(), step):
+        c = flat[k:k + step]
+        ok = (c == 0) | (c == 1) | (c == 2) | (c == 4) | (c == 6)
+        if not bool(torch.all(ok)):
+            return False
+    return True

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import FP64_TOL_R_KM, assert_status_and_nan, error_summary, state_errors
+from gpu_util import valid_codes_only, FP64_TOL_R_KM, assert_status_and_nan, error_summary, state_errors
 from paper_2603_27830_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -172,7 +172,7 @@ def test_uneven_requests_full_size_autotuned():
                                       use_cache=False)
     r, v, st = sgp4_propagate_batched(plan, recs, ts, "fp32", out=out)
     torch.cuda.synchronize()
-    assert set(torch.unique(st).cpu().tolist()) <= {0, 1, 2, 4, 6}
+    assert valid_codes_only(st)
     rng = np.random.default_rng(0)
     for k in rng.choice(len(reqs), 16, replace=False):
         sat0, n, t0, T, out0 = b.requests[k]
