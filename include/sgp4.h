@@ -225,6 +225,36 @@ sgp4_result sgp4_batch_graph_launch(void* graph, void* stream);
 /* Destroy a graph made by sgp4_batch_graph_create (NULL is a no-op). */
 sgp4_result sgp4_batch_graph_destroy(void* graph);
 
+/*
+ * Batched propagation without any device allocation by the caller.  The paper has
+ * no counterpart; this serves callers that cannot allocate device memory (a host
+ * application that owns the allocator and hands out only fixed buffers, real-time
+ * or flight software whose device memory is budgeted once at start-up, a plug-in
+ * that must not grow its footprint after initialisation).  It runs the batched
+ * kernel of sgp4_propagate_batched, with the tile counter, the tile prefix sums and
+ * the request table in a fixed array inside the library: about 48 KB held on every
+ * GPU that loads the library, until the process exits.
+ *   requests     HOST table of n_requests <= SGP4_STATIC_MAX_REQUESTS requests
+ *                (same meaning as for sgp4_batch_plan_init; may be reused on return)
+ *   tile_states  states per work tile, a positive multiple of 128
+ *   other arguments as in sgp4_propagate_batched (no fixup counter)
+ * The first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  All calls on a device
+ * share the array: two calls whose work overlaps on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.  Each call
+ * rewrites the table and prefix sums and resets the counter before its launch.
+ * Errors: SGP4_ERR_OOM if n_requests exceeds SGP4_STATIC_MAX_REQUESTS; SGP4_ERR_ARG
+ * for bad sizes, offsets outside records / tsince / outputs, overlapping outputs,
+ * a bad precision or tile size, NULL or misaligned arrays; SGP4_ERR_CUDA if the
+ * address lookup, the copy or a launch fails.  Calls no allocation routine.
+ */
+#define SGP4_STATIC_MAX_REQUESTS 1024
+sgp4_result sgp4_propagate_batched_static(const sgp4_request* requests, int32_t n_requests,
+                                          int32_t tile_states, const sgp4_records* records,
+                                          const double* tsince, int64_t tsince_len,
+                                          sgp4_precision precision, void* r, void* v,
+                                          int32_t* status, int64_t out_len, void* stream);
+
 /* Library version (major*10000 + minor*100 + patch). */
 int sgp4_version(void);
 

@@ -28,8 +28,9 @@ EXPORTS = (
     "sgp4_version", "sgp4_wgs72", "sgp4_records_bytes", "sgp4_records_bind", "sgp4_init",
     "sgp4_propagate", "sgp4_batch_workspace_bytes", "sgp4_batch_plan_init",
     "sgp4_propagate_batched", "sgp4_batch_graph_create", "sgp4_batch_graph_launch",
-    "sgp4_batch_graph_destroy",
+    "sgp4_batch_graph_destroy", "sgp4_propagate_batched_static",
 )
+STATIC_MAX_REQUESTS = 1024
 
 
 class Sgp4Consts(ctypes.Structure):
@@ -94,6 +95,9 @@ def _declare(lib):
     lib.sgp4_batch_graph_launch.restype = I32
     lib.sgp4_batch_graph_destroy.argtypes = [P]
     lib.sgp4_batch_graph_destroy.restype = I32
+    lib.sgp4_propagate_batched_static.argtypes = [P, ctypes.c_int32, ctypes.c_int32, R, P, I64,
+                                                  I32, P, P, P, I64, P]
+    lib.sgp4_propagate_batched_static.restype = I32
     return lib
 
 
