@@ -5,6 +5,7 @@
 #include <cmath>
 
 #include "sgp4_device.cuh"
+#include "sgp4_init_math.cuh"
 #include "sgp4_kernels.cuh"
 
 namespace sgp4 {
@@ -50,95 +51,18 @@ __global__ void __launch_bounds__(64) init_kernel(const double* __restrict__ el,
     return;
   }
 
-  const double k2 = 0.5 * g.j2;
-  const double cosi = cos(i0), sini = sin(i0);
-  const double th2 = cosi * cosi;
-  const double x3thm1 = 3.0 * th2 - 1.0;
-  const double x1mth2 = 1.0 - th2;
-  const double x7thm1 = 7.0 * th2 - 1.0;
-  const double b2 = 1.0 - e0 * e0;
-  const double b = sqrt(b2);
-  const double b3 = b2 * b;
-
-  // Kozai -> Brouwer mean motion and semi-major axis.
-  const double a1 = pow(g.xke / n0, 2.0 / 3.0);
-  const double d1 = 1.5 * k2 * x3thm1 / (a1 * a1 * b3);
-  const double a0 = a1 * (1.0 - d1 / 3.0 - d1 * d1 - (134.0 / 81.0) * d1 * d1 * d1);
-  const double d0 = 1.5 * k2 * x3thm1 / (a0 * a0 * b3);
-  const double n0pp = n0 / (1.0 + d0);
-  const double a0pp = pow(g.xke / n0pp, 2.0 / 3.0);
-
-  // Atmosphere: s and (q0 - s)^4 by perigee height.
-  const double rp_er = a0pp * (1.0 - e0);
-  const double hp = (rp_er - 1.0) * g.re;
-  const bool isimp = rp_er < 1.0 + 220.0 / g.re;
-  double s_km = 78.0;
-  if (hp < 156.0) s_km = hp - 78.0;
-  if (hp < 98.0) s_km = 20.0;
-  const double qs = (120.0 - s_km) / g.re;
-  const double qs4 = qs * qs * qs * qs;
-  const double ss = 1.0 + s_km / g.re;
-
-  const double xi = 1.0 / (a0pp - ss);
-  const double eta = a0pp * e0 * xi;
-  const double eta2 = eta * eta;
-  const double eeta = e0 * eta;
-  const double psi2 = fabs(1.0 - eta2);
-  const double xi4 = xi * xi * xi * xi;
-  const double coef = qs4 * xi4;
-  const double coef1 = coef / pow(psi2, 3.5);
-
-  const double C2 = coef1 * n0pp *
-                    (a0pp * (1.0 + 1.5 * eta2 + eeta * (4.0 + eta2)) +
-                     0.375 * g.j2 * xi / psi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
-  const double C1 = bstar * C2;
-  double C3 = 0.0;
-  if (e0 > 1.0e-4) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sini / e0;
-  const double C4 = 2.0 * n0pp * coef1 * a0pp * b2 *
-                    (eta * (2.0 + 0.5 * eta2) + e0 * (0.5 + 2.0 * eta2) -
-                     g.j2 * xi / (a0pp * psi2) *
-                         (-3.0 * x3thm1 * (1.0 - 2.0 * eeta + eta2 * (1.5 - 0.5 * eeta)) +
-                          0.75 * x1mth2 * (2.0 * eta2 - eeta * (1.0 + eta2)) * cos(2.0 * argp0)));
-  const double C5 = 2.0 * coef1 * a0pp * b2 * (1.0 + 2.75 * (eta2 + eeta) + eeta * eta2);
-
-  // Secular rates.
-  const double p0 = a0pp * b2;
-  const double pinv2 = 1.0 / (p0 * p0);
-  const double T1 = 1.5 * g.j2 * pinv2 * n0pp;
-  const double T2 = 0.5 * T1 * g.j2 * pinv2;
-  const double T3 = -0.46875 * g.j4 * pinv2 * pinv2 * n0pp;
-  const double th4 = th2 * th2;
-  const double mdot = n0pp + 0.5 * T1 * b * x3thm1 + 0.0625 * T2 * b * (13.0 - 78.0 * th2 + 137.0 * th4);
-  const double argpdot = -0.5 * T1 * (1.0 - 5.0 * th2) + 0.0625 * T2 * (7.0 - 114.0 * th2 + 395.0 * th4) +
-                         T3 * (3.0 - 36.0 * th2 + 49.0 * th4);
-  const double raandot1 = -T1 * cosi;
-  const double raandot = raandot1 + (0.5 * T2 * (4.0 - 19.0 * th2) + 2.0 * T3 * (3.0 - 7.0 * th2)) * cosi;
-
-  const double raan_cf = 3.5 * b2 * raandot1 * C1;
-  const double argp_cf = bstar * C3 * cos(argp0);
-  double m_cf = 0.0;
-  if (e0 > 1.0e-4) m_cf = -(2.0 / 3.0) * coef * bstar / eeta;
-  const double L2 = 1.5 * C1;
-
-  double opc = 1.0 + cosi;
-  if (fabs(opc) <= 1.5e-12) opc = 1.5e-12;
-  const double xlcof = -0.25 * g.j3oj2 * sini * (3.0 + 5.0 * cosi) / opc;
-  const double aycof = -0.5 * g.j3oj2 * sini;
-  const double cm = 1.0 + eta * cos(m0);
-  const double delm0 = cm * cm * cm;
-  const double sinm0 = sin(m0);
-
-  double D2 = 0.0, D3 = 0.0, D4 = 0.0, L3 = 0.0, L4 = 0.0, L5 = 0.0;
-  if (!isimp) {
-    const double c1sq = C1 * C1;
-    D2 = 4.0 * a0pp * xi * c1sq;
-    D3 = (4.0 / 3.0) * a0pp * xi * xi * (17.0 * a0pp + ss) * c1sq * C1;
-    D4 = (2.0 / 3.0) * a0pp * a0pp * xi * xi * xi * (221.0 * a0pp + 31.0 * ss) * c1sq * c1sq;
-    L3 = D2 + 2.0 * c1sq;
-    L4 = 0.25 * (3.0 * D3 + 12.0 * C1 * D2 + 10.0 * c1sq * C1);
-    L5 = 0.2 * (3.0 * D4 + 12.0 * C1 * D3 + 6.0 * D2 * D2 + 30.0 * c1sq * D2 + 15.0 * c1sq * c1sq);
+  InitFields<double> o;
+  {
+    const double e7[7] = {n0, e0, i0, raan0, argp0, m0, bstar};
+    init_fields(e7, g, o);
   }
-  const double bc4 = bstar * C4, bc5 = bstar * C5;
+  const double n0pp = o.n0pp, a0pp = o.a0pp, mdot = o.mdot, argpdot = o.argpdot;
+  const double raandot = o.raandot, raan_cf = o.raan_cf, argp_cf = o.argp_cf, m_cf = o.m_cf;
+  const double C1 = o.c1, bc4 = o.bc4, bc5 = o.bc5, D2 = o.d2, D3 = o.d3, D4 = o.d4;
+  const double L2 = o.l2, L3 = o.l3, L4 = o.l4, L5 = o.l5, eta = o.eta, delm0 = o.delm0;
+  const double sinm0 = o.sinm0, xlcof = o.xlcof, aycof = o.aycof, cosi = o.cosi, sini = o.sini;
+  const double x3thm1 = o.x3thm1, x1mth2 = o.x1mth2, x7thm1 = o.x7thm1;
+  const bool isimp = o.isimp;
 
   // FP64 planes.
   f[kN0pp * s + j] = n0pp;     f[kA0pp * s + j] = a0pp;     f[kE0 * s + j] = e0;

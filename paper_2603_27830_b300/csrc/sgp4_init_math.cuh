@@ -1,0 +1,211 @@
+// Initialisation constants of near-Earth SGP4 as a function of the mean elements,
+// templated on the scalar: double for the record builder, D7 (value + derivatives
+// with respect to the 7 elements) for the Jacobian the adjoint needs.  Equations of
+// Spacetrack Report #3 as revised in 2006 (paper Sec. 2.1); readings: a0'' from
+// n0'' by Kepler's third law, D4 with a0''^2.
+#pragma once
+
+#include <cmath>
+
+#include "sgp4_device.cuh"
+
+namespace sgp4 {
+
+// Forward-mode dual number with 7 tangent directions (n0, e0, i0, RAAN0, argp0, M0, B*).
+struct D7 {
+  double v;
+  double d[7];
+};
+
+__device__ __forceinline__ D7 d7c(double x) {
+  D7 r;
+  r.v = x;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) r.d[k] = 0.0;
+  return r;
+}
+__device__ __forceinline__ D7 d7var(double x, int k) {
+  D7 r = d7c(x);
+  r.d[k] = 1.0;
+  return r;
+}
+__device__ __forceinline__ D7 d7chain(const D7& a, double val, double dfda) {
+  D7 r;
+  r.v = val;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) r.d[k] = dfda * a.d[k];
+  return r;
+}
+__device__ __forceinline__ D7 operator+(const D7& a, const D7& b) {
+  D7 r; r.v = a.v + b.v;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+__device__ __forceinline__ D7 operator-(const D7& a, const D7& b) {
+  D7 r; r.v = a.v - b.v;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+__device__ __forceinline__ D7 operator-(const D7& a) {
+  D7 r; r.v = -a.v;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+__device__ __forceinline__ D7 operator*(const D7& a, const D7& b) {
+  D7 r; r.v = a.v * b.v;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+__device__ __forceinline__ D7 operator/(const D7& a, const D7& b) {
+  D7 r; r.v = a.v / b.v;
+  const double ib = 1.0 / b.v;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+  return r;
+}
+__device__ __forceinline__ D7 operator+(const D7& a, double b) { D7 r = a; r.v += b; return r; }
+__device__ __forceinline__ D7 operator+(double a, const D7& b) { return b + a; }
+__device__ __forceinline__ D7 operator-(const D7& a, double b) { D7 r = a; r.v -= b; return r; }
+__device__ __forceinline__ D7 operator-(double a, const D7& b) { return -b + a; }
+__device__ __forceinline__ D7 operator*(const D7& a, double b) { return d7chain(a, a.v * b, b); }
+__device__ __forceinline__ D7 operator*(double a, const D7& b) { return b * a; }
+__device__ __forceinline__ D7 operator/(const D7& a, double b) { return a * (1.0 / b); }
+__device__ __forceinline__ D7 operator/(double a, const D7& b) {
+  const double q = a / b.v;
+  return d7chain(b, q, -q / b.v);
+}
+__device__ __forceinline__ D7 sin(const D7& a) { return d7chain(a, ::sin(a.v), ::cos(a.v)); }
+__device__ __forceinline__ D7 cos(const D7& a) { return d7chain(a, ::cos(a.v), -::sin(a.v)); }
+__device__ __forceinline__ D7 sqrt(const D7& a) {
+  const double s = ::sqrt(a.v);
+  return d7chain(a, s, 0.5 / s);
+}
+__device__ __forceinline__ D7 pow(const D7& a, double p) {
+  const double y = ::pow(a.v, p);
+  return d7chain(a, y, p * y / a.v);
+}
+__device__ __forceinline__ D7 fabs(const D7& a) { return a.v < 0.0 ? -a : a; }
+__device__ __forceinline__ double val(const D7& a) { return a.v; }
+__device__ __forceinline__ double val(double a) { return a; }
+// Keep the double versions visible next to the D7 overloads in this namespace.
+using ::cos;
+using ::fabs;
+using ::pow;
+using ::sin;
+using ::sqrt;
+
+// The 33 record fields the propagation reads, plus C1 for the FP32 row.
+template <class S>
+struct InitFields {
+  S n0pp, a0pp, e0, i0, raan0, argp0, m0;
+  S mdot, argpdot, raandot, raan_cf, argp_cf, m_cf;
+  S c1, bc4, bc5, d2, d3, d4, l2, l3, l4, l5;
+  S eta, delm0, sinm0, xlcof, aycof;
+  S cosi, sini, x3thm1, x1mth2, x7thm1;
+  bool isimp;
+};
+
+// Valid elements only (the caller screens non-finite input, e0 outside [0,1), n0 <= 0).
+template <class S>
+__device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFields<S>& o) {
+  const S n0 = el[0], e0 = el[1], i0 = el[2], raan0 = el[3], argp0 = el[4], m0 = el[5];
+  const S bstar = el[6];
+  const double k2 = 0.5 * g.j2;
+  const S cosi = cos(i0), sini = sin(i0);
+  const S th2 = cosi * cosi;
+  const S x3thm1 = 3.0 * th2 - 1.0;
+  const S x1mth2 = 1.0 - th2;
+  const S x7thm1 = 7.0 * th2 - 1.0;
+  const S b2 = 1.0 - e0 * e0;
+  const S b = sqrt(b2);
+  const S b3 = b2 * b;
+
+  // Kozai -> Brouwer mean motion and semi-major axis.
+  const S a1 = pow(g.xke / n0, 2.0 / 3.0);
+  const S d1 = 1.5 * k2 * x3thm1 / (a1 * a1 * b3);
+  const S a0 = a1 * (1.0 - d1 / 3.0 - d1 * d1 - (134.0 / 81.0) * d1 * d1 * d1);
+  const S d0 = 1.5 * k2 * x3thm1 / (a0 * a0 * b3);
+  const S n0pp = n0 / (1.0 + d0);
+  const S a0pp = pow(g.xke / n0pp, 2.0 / 3.0);
+
+  // Atmosphere: s and (q0 - s)^4 by perigee height.
+  const S rp_er = a0pp * (1.0 - e0);
+  const S hp = (rp_er - 1.0) * g.re;
+  o.isimp = val(rp_er) < 1.0 + 220.0 / g.re;
+  S s_km = 0.0 * hp + 78.0;
+  if (val(hp) < 156.0) s_km = hp - 78.0;
+  if (val(hp) < 98.0) s_km = 0.0 * hp + 20.0;
+  const S qs = (120.0 - s_km) / g.re;
+  const S qs4 = qs * qs * qs * qs;
+  const S ss = 1.0 + s_km / g.re;
+
+  const S xi = 1.0 / (a0pp - ss);
+  const S eta = a0pp * e0 * xi;
+  const S eta2 = eta * eta;
+  const S eeta = e0 * eta;
+  const S psi2 = fabs(1.0 - eta2);
+  const S xi4 = xi * xi * xi * xi;
+  const S coef = qs4 * xi4;
+  const S coef1 = coef / pow(psi2, 3.5);
+
+  const S C2 = coef1 * n0pp *
+               (a0pp * (1.0 + 1.5 * eta2 + eeta * (4.0 + eta2)) +
+                0.375 * g.j2 * xi / psi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
+  const S C1 = bstar * C2;
+  S C3 = 0.0 * C1;
+  if (val(e0) > 1.0e-4) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sini / e0;
+  const S C4 = 2.0 * n0pp * coef1 * a0pp * b2 *
+               (eta * (2.0 + 0.5 * eta2) + e0 * (0.5 + 2.0 * eta2) -
+                g.j2 * xi / (a0pp * psi2) *
+                    (-3.0 * x3thm1 * (1.0 - 2.0 * eeta + eta2 * (1.5 - 0.5 * eeta)) +
+                     0.75 * x1mth2 * (2.0 * eta2 - eeta * (1.0 + eta2)) * cos(2.0 * argp0)));
+  const S C5 = 2.0 * coef1 * a0pp * b2 * (1.0 + 2.75 * (eta2 + eeta) + eeta * eta2);
+
+  // Secular rates.
+  const S p0 = a0pp * b2;
+  const S pinv2 = 1.0 / (p0 * p0);
+  const S T1 = 1.5 * g.j2 * pinv2 * n0pp;
+  const S T2 = 0.5 * T1 * g.j2 * pinv2;
+  const S T3 = -0.46875 * g.j4 * pinv2 * pinv2 * n0pp;
+  const S th4 = th2 * th2;
+  o.mdot = n0pp + 0.5 * T1 * b * x3thm1 + 0.0625 * T2 * b * (13.0 - 78.0 * th2 + 137.0 * th4);
+  o.argpdot = -0.5 * T1 * (1.0 - 5.0 * th2) + 0.0625 * T2 * (7.0 - 114.0 * th2 + 395.0 * th4) +
+              T3 * (3.0 - 36.0 * th2 + 49.0 * th4);
+  const S raandot1 = -T1 * cosi;
+  o.raandot = raandot1 + (0.5 * T2 * (4.0 - 19.0 * th2) + 2.0 * T3 * (3.0 - 7.0 * th2)) * cosi;
+
+  o.raan_cf = 3.5 * b2 * raandot1 * C1;
+  o.argp_cf = bstar * C3 * cos(argp0);
+  o.m_cf = 0.0 * C1;
+  if (val(e0) > 1.0e-4) o.m_cf = -(2.0 / 3.0) * coef * bstar / eeta;
+  o.l2 = 1.5 * C1;
+
+  S opc = 1.0 + cosi;
+  if (::fabs(val(opc)) <= 1.5e-12) opc = 0.0 * opc + 1.5e-12;
+  o.xlcof = -0.25 * g.j3oj2 * sini * (3.0 + 5.0 * cosi) / opc;
+  o.aycof = -0.5 * g.j3oj2 * sini;
+  const S cm = 1.0 + eta * cos(m0);
+  o.delm0 = cm * cm * cm;
+  o.sinm0 = sin(m0);
+
+  o.d2 = 0.0 * C1; o.d3 = o.d2; o.d4 = o.d2; o.l3 = o.d2; o.l4 = o.d2; o.l5 = o.d2;
+  if (!o.isimp) {
+    const S c1sq = C1 * C1;
+    o.d2 = 4.0 * a0pp * xi * c1sq;
+    o.d3 = (4.0 / 3.0) * a0pp * xi * xi * (17.0 * a0pp + ss) * c1sq * C1;
+    o.d4 = (2.0 / 3.0) * a0pp * a0pp * xi * xi * xi * (221.0 * a0pp + 31.0 * ss) * c1sq * c1sq;
+    o.l3 = o.d2 + 2.0 * c1sq;
+    o.l4 = 0.25 * (3.0 * o.d3 + 12.0 * C1 * o.d2 + 10.0 * c1sq * C1);
+    o.l5 = 0.2 * (3.0 * o.d4 + 12.0 * C1 * o.d3 + 6.0 * o.d2 * o.d2 + 30.0 * c1sq * o.d2 +
+                  15.0 * c1sq * c1sq);
+  }
+  o.n0pp = n0pp; o.a0pp = a0pp; o.e0 = e0; o.i0 = i0; o.raan0 = raan0; o.argp0 = argp0;
+  o.m0 = m0; o.c1 = C1; o.bc4 = bstar * C4; o.bc5 = bstar * C5; o.eta = eta;
+  o.cosi = cosi; o.sini = sini; o.x3thm1 = x3thm1; o.x1mth2 = x1mth2; o.x7thm1 = x7thm1;
+}
+
+}  // namespace sgp4
