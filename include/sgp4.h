@@ -226,6 +226,33 @@ sgp4_result sgp4_batch_graph_launch(void* graph, void* stream);
 sgp4_result sgp4_batch_graph_destroy(void* graph);
 
 /*
+ * Adjoint of the propagation (paper Sec. 5, "Differentiable Orbital Mechanics":
+ * gradients of the state vectors with respect to the mean elements through the
+ * initialisation and the propagation).  For upstream gradients g_r, g_v of every
+ * state it returns, per satellite j and element k of (n0, e0, i0, RAAN0, argp0, M0,
+ * B*):  grad[j][k] = sum_t dr_jt/del_jk . g_r[j][t] + dv_jt/del_jk . g_v[j][t].
+ *   elements   [n][7] double, the elements the records were built from
+ *   records    the record set built by sgp4_init from those elements
+ *   tsince     as in sgp4_propagate ([t_count] or [n][t_count] with grid_per_sat)
+ *   precision  SGP4_FP64: grad_r / grad_v are double and the sweep runs in FP64;
+ *              SGP4_FP32: they are float and the sweep runs in FP32 (angle sums in
+ *              FP64), accumulated in FP64
+ *   grad_r     [n][t_count][3] (may be NULL: zero); grad_v likewise
+ *   grad_elements  [n][7] double out
+ *   workspace  device, sgp4_adjoint_workspace_bytes(n) bytes, 8-byte aligned
+ * States with status 1, 2 or 4 contribute nothing; records with unusable elements
+ * get a zero gradient.  Errors: SGP4_ERR_ARG for NULL / misaligned arrays, a record
+ * set of another size, bad precision or t_count < 0; SGP4_ERR_OOM for a small
+ * workspace; SGP4_ERR_CUDA for a failed launch.
+ */
+size_t sgp4_adjoint_workspace_bytes(int64_t n);
+sgp4_result sgp4_adjoint(const double* elements, const sgp4_records* records,
+                         const double* tsince, int64_t t_count, int grid_per_sat,
+                         sgp4_precision precision, const void* grad_r, const void* grad_v,
+                         double* grad_elements, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/*
  * Batched propagation without any device allocation by the caller.  The paper has
  * no counterpart; this serves callers that cannot allocate device memory (a host
  * application that owns the allocator and hands out only fixed buffers, real-time

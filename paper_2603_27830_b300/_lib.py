@@ -28,7 +28,8 @@ EXPORTS = (
     "sgp4_version", "sgp4_wgs72", "sgp4_records_bytes", "sgp4_records_bind", "sgp4_init",
     "sgp4_propagate", "sgp4_batch_workspace_bytes", "sgp4_batch_plan_init",
     "sgp4_propagate_batched", "sgp4_batch_graph_create", "sgp4_batch_graph_launch",
-    "sgp4_batch_graph_destroy", "sgp4_propagate_batched_static",
+    "sgp4_batch_graph_destroy", "sgp4_propagate_batched_static", "sgp4_adjoint_workspace_bytes",
+    "sgp4_adjoint",
 )
 STATIC_MAX_REQUESTS = 1024
 
@@ -98,6 +99,10 @@ def _declare(lib):
     lib.sgp4_propagate_batched_static.argtypes = [P, ctypes.c_int32, ctypes.c_int32, R, P, I64,
                                                   I32, P, P, P, I64, P]
     lib.sgp4_propagate_batched_static.restype = I32
+    lib.sgp4_adjoint_workspace_bytes.argtypes = [I64]
+    lib.sgp4_adjoint_workspace_bytes.restype = ctypes.c_size_t
+    lib.sgp4_adjoint.argtypes = [P, R, P, I64, I32, I32, P, P, P, P, ctypes.c_size_t, P]
+    lib.sgp4_adjoint.restype = I32
     return lib
 
 

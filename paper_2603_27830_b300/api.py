@@ -262,3 +262,72 @@ class BatchGraph:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------------- adjoint
+def sgp4_adjoint(elements: torch.Tensor, records: Records, tsince: torch.Tensor,
+                 grad_r: torch.Tensor | None, grad_v: torch.Tensor | None,
+                 precision: str = "fp64", out: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """d(sum g_r . r + g_v . v)/d(elements) [n, 7] through init and propagation."""
+    _require_cuda("elements", elements, torch.float64)
+    _require_cuda("tsince", tsince, torch.float64)
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    n = records.n
+    if elements.shape != (n, 7):
+        raise ValueError("elements must be [n, 7] and match the records")
+    per_sat = tsince.dim() == 2
+    T = tsince.shape[-1]
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    for name, g in (("grad_r", grad_r), ("grad_v", grad_v)):
+        if g is not None:
+            _require_cuda(name, g, dt)
+            if g.shape != (n, T, 3):
+                raise ValueError(f"{name} must be [n, T, 3]")
+    lib = _lib.load()
+    if workspace is None:
+        workspace = torch.empty(max(int(lib.sgp4_adjoint_workspace_bytes(n)), 8),
+                                dtype=torch.uint8, device=elements.device)
+    if out is None:
+        out = torch.empty((n, 7), dtype=torch.float64, device=elements.device)
+    _lib.check("sgp4_adjoint",
+               lib.sgp4_adjoint(_ptr(elements), ctypes.byref(records.c), _ptr(tsince), T,
+                                1 if per_sat else 0, PRECISIONS[precision], _ptr(grad_r),
+                                _ptr(grad_v), _ptr(out), _ptr(workspace), workspace.numel(),
+                                _stream_handle(stream)))
+    return out
+
+
+class SGP4Function(torch.autograd.Function):
+    """(r, v) = SGP4(elements, tsince) with a hand-written adjoint for backward.
+
+    elements [n, 7] float64 CUDA (n0 rad/min, e0, i0, RAAN0, argp0, M0, B*); tsince
+    [T] or [n, T] float64.  r, v are [n, T, 3] in the precision's dtype; states with
+    status 1, 2, 4 are NaN and get no gradient.
+    """
+
+    @staticmethod
+    def forward(ctx, elements, tsince, precision="fp64"):
+        recs, _ = sgp4_init(elements.detach().contiguous())
+        r, v, st = sgp4_propagate(recs, tsince, precision)
+        ctx.save_for_backward(elements, tsince)
+        ctx.records = recs
+        ctx.precision = precision
+        ctx.mark_non_differentiable(st)
+        return r, v, st
+
+    @staticmethod
+    def backward(ctx, grad_r, grad_v, _grad_st):
+        elements, tsince = ctx.saved_tensors
+        dt = torch.float32 if ctx.precision == "fp32" else torch.float64
+        gr = None if grad_r is None else grad_r.to(dt).nan_to_num(0.0).contiguous()
+        gv = None if grad_v is None else grad_v.to(dt).nan_to_num(0.0).contiguous()
+        g = sgp4_adjoint(elements.detach().contiguous(), ctx.records, tsince, gr, gv,
+                         ctx.precision)
+        return g, None, None
+
+
+def sgp4_differentiable(elements: torch.Tensor, tsince: torch.Tensor, precision: str = "fp64"):
+    """Differentiable propagation: returns (r, v, status); backward runs the adjoint."""
+    return SGP4Function.apply(elements, tsince, precision)

@@ -267,6 +267,35 @@ sgp4_result sgp4_batch_graph_create(const sgp4_batch_plan* plan, const sgp4_reco
   return SGP4_OK;
 }
 
+size_t sgp4_adjoint_workspace_bytes(int64_t n) { return sgp4::adjoint_workspace_bytes(n); }
+
+sgp4_result sgp4_adjoint(const double* elements, const sgp4_records* records,
+                         const double* tsince, int64_t t_count, int grid_per_sat,
+                         sgp4_precision precision, const void* grad_r, const void* grad_v,
+                         double* grad_elements, void* workspace, size_t workspace_bytes,
+                         void* stream) {
+  if (!records_ok(records) || t_count < 0) return SGP4_ERR_ARG;
+  if (precision != SGP4_FP64 && precision != SGP4_FP32) return SGP4_ERR_ARG;
+  const int64_t n = records->n;
+  if (n == 0) return SGP4_OK;
+  if (!elements || !grad_elements || !aligned(elements, 8) || !aligned(grad_elements, 8))
+    return SGP4_ERR_ARG;
+  if (t_count > 0 && (!tsince || !aligned(tsince, 8))) return SGP4_ERR_ARG;
+  if (n > INT64_MAX / 3 / (t_count > 0 ? t_count : 1)) return SGP4_ERR_ARG;
+  const size_t esz = precision == SGP4_FP32 ? 4 : 8;
+  if ((grad_r && !aligned(grad_r, esz)) || (grad_v && !aligned(grad_v, esz)))
+    return SGP4_ERR_ARG;
+  if (!workspace || !aligned(workspace, 8)) return SGP4_ERR_ARG;
+  if (workspace_bytes < sgp4::adjoint_workspace_bytes(n)) return SGP4_ERR_OOM;
+  if (n > 0x7fffffffLL) return SGP4_ERR_ARG;   // one block per satellite
+  cudaError_t e = sgp4::launch_adjoint(
+      sgp4::record_ptrs(records->arena, n), make_geo(records->consts), elements, tsince, t_count,
+      grid_per_sat ? 1 : 0, precision == SGP4_FP32, t_count > 0 ? grad_r : nullptr,
+      t_count > 0 ? grad_v : nullptr, grad_elements, static_cast<double*>(workspace),
+      static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
+}
+
 sgp4_result sgp4_batch_graph_launch(void* graph, void* stream) {
   if (!graph) return SGP4_ERR_ARG;
   BatchGraph* bg = static_cast<BatchGraph*>(graph);

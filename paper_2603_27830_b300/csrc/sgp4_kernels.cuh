@@ -52,6 +52,13 @@ int64_t batched_grid(bool fp32, int64_t total_tiles, int grid_blocks);
 cudaError_t launch_batched(const BatchArgs& a, bool fp32, int64_t total_tiles, int64_t grid,
                            cudaStream_t stream);
 
+// Adjoint: field-adjoint workspace bytes and the two-kernel launch.
+size_t adjoint_workspace_bytes(int64_t n);
+cudaError_t launch_adjoint(const RecordPtrs& rp, const Geo& g, const double* el,
+                           const double* tsince, int64_t T, int per_sat, bool fp32,
+                           const void* grad_r, const void* grad_v, double* grad_el,
+                           double* workspace, cudaStream_t stream);
+
 // SM count of the current device.
 int device_sm_count();
 
