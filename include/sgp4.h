@@ -253,6 +253,26 @@ sgp4_result sgp4_adjoint(const double* elements, const sgp4_records* records,
                          void* stream);
 
 /*
+ * One batch-least-squares step per satellite, fitting the mean elements to observed
+ * positions with the gradients of sgp4_adjoint (paper Sec. 5 names gradient-based
+ * orbit determination as the use of a differentiable SGP4).  For the states with
+ * finite output, res_t = r_t(elements) - r_obs_t, J_t = dr_t/d(elements) (three
+ * reverse sweeps per state), A = sum J^T J, b = sum J^T res; the step solves
+ * (A' + lambda diag A') x = -b' on the Jacobi-scaled system (Cholesky) and returns
+ * elements_out = elements + step (Levenberg-Marquardt with damping lambda[j]).
+ *   elements      [n][7] double, the elements the records were built from
+ *   r_obs         [n][t_count][3] double, observed TEME positions, km
+ *   lambda        [n] double, damping (>= 0)
+ *   elements_out  [n][7] double (may not alias elements)
+ *   sse           [n] double out: sum of squared residuals at `elements`, km^2
+ * Unusable records keep their elements and get sse 0.  Errors as sgp4_adjoint.
+ */
+sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
+                          const double* tsince, int64_t t_count, int grid_per_sat,
+                          sgp4_precision precision, const double* r_obs, const double* lambda,
+                          double* elements_out, double* sse, void* stream);
+
+/*
  * Batched propagation without any device allocation by the caller.  The paper has
  * no counterpart; this serves callers that cannot allocate device memory (a host
  * application that owns the allocator and hands out only fixed buffers, real-time

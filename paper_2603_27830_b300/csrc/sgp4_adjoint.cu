@@ -44,7 +44,7 @@ __device__ __forceinline__ void sc(float x, float& s, float& c) { sincosf(x, &s,
 // adjoint of every record field into acc[f * kAdjThreads].  Returns the status.
 template <class T>
 __device__ int adjoint_state(const Rec64& rc, const Geo& g, double t, const T gr[3],
-                             const T gv[3], double* acc) {
+                             const T gv[3], double* acc, T* r_out = nullptr) {
   const int fatal = (rc.flags >> kFatalShift) & 0xff;
   if (fatal) return fatal;
   if (rc.flags & kFlagN0ppNonPos) return 2;
@@ -153,6 +153,11 @@ __device__ int adjoint_state(const Rec64& rc, const Geo& g, double t, const T gr
   const T Ux = mx * su + cO * cu, Uy = my * su + sO * cu, Uz = mz * su;
   const T Vx = mx * cu - cO * su, Vy = my * cu - sO * su, Vz = mz * cu;
   const int code = rk < one ? 6 : 0;
+  if (r_out) {
+    r_out[0] = rk * T(g.re) * Ux;
+    r_out[1] = rk * T(g.re) * Uy;
+    r_out[2] = rk * T(g.re) * Uz;
+  }
 
   // ------------------------------------------------------------------ reverse
   const T re = T(g.re), vk = T(g.vkmps);
@@ -408,7 +413,176 @@ __global__ void __launch_bounds__(64) adjoint_init_kernel(const double* __restri
   for (int k = 0; k < 7; ++k) grad[j * 7 + k] = out[k];
 }
 
+// Record-field Jacobian of sgp4init, d(field)/d(element), [kNumAdj][7], by dual
+// numbers (false for unusable elements).
+__device__ bool init_jacobian(const double e7[7], const Geo& g, double J[kNumAdj][7]) {
+  bool ok = true;
+  for (int k = 0; k < 7; ++k) ok = ok && isfinite(e7[k]);
+  ok = ok && e7[1] >= 0.0 && e7[1] < 1.0 && e7[0] > 0.0;
+  if (!ok) return false;
+  D7 x[7];
+  for (int k = 0; k < 7; ++k) x[k] = d7var(e7[k], k);
+  InitFields<D7> o;
+  init_fields(x, g, o);
+  const D7* f[kNumAdj] = {&o.n0pp, &o.a0pp, &o.e0, &o.i0, &o.raan0, &o.argp0, &o.m0,
+                          &o.mdot, &o.argpdot, &o.raandot, &o.raan_cf, &o.argp_cf, &o.m_cf,
+                          &o.c1, &o.bc4, &o.bc5, &o.d2, &o.d3, &o.d4, &o.l2, &o.l3, &o.l4,
+                          &o.l5, &o.eta, &o.delm0, &o.sinm0, &o.xlcof, &o.aycof, &o.cosi,
+                          &o.sini, &o.x3thm1, &o.x1mth2, &o.x7thm1};
+  for (int q = 0; q < kNumAdj; ++q)
+    for (int k = 0; k < 7; ++k) J[q][k] = f[q]->d[k];
+  return true;
+}
+
+struct FitArgs {
+  RecordPtrs rp;
+  Geo g;
+  const double* el;      // [n][7]
+  const double* tsince;
+  int64_t T;
+  int per_sat;
+  const double* r_obs;   // [n][T][3]
+  const double* lambda;  // [n] Levenberg-Marquardt damping
+  double* el_out;        // [n][7]
+  double* sse;           // [n] sum of squared position residuals at el (km^2)
+};
+
+// One Gauss-Newton / Levenberg-Marquardt step of batch least squares per satellite:
+// residuals res_t = r_t(el) - r_obs_t over the states with finite output, the
+// position Jacobian J_t = dr_t/del (three reverse sweeps per state, contracted with
+// the init Jacobian), A = sum J_t^T J_t, b = sum J_t^T res_t, and the step
+// delta = -(A + lambda diag A)^-1 b solved by Cholesky on the Jacobi-scaled matrix.
+template <class T>
+__global__ void __launch_bounds__(kAdjThreads) fit_step_kernel(FitArgs a) {
+  __shared__ double acc[kNumAdj * kAdjThreads];
+  __shared__ double Ji[kNumAdj][7];
+  __shared__ double red[36][kAdjThreads / 32];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x;
+  const int64_t j = blockIdx.x;
+  double e7[7];
+  for (int k = 0; k < 7; ++k) e7[k] = a.el[j * 7 + k];
+  if (tid == 0) s_ok = init_jacobian(e7, a.g, Ji) ? 1 : 0;
+  __syncthreads();
+  if (!s_ok) {
+    if (tid < 7) a.el_out[j * 7 + tid] = e7[tid];
+    if (tid == 0) a.sse[j] = 0.0;
+    return;
+  }
+  const Rec64 rc = load_rec64(a.rp, j);
+  double A[28], b[7], sse = 0.0;
+  for (int k = 0; k < 28; ++k) A[k] = 0.0;
+  for (int k = 0; k < 7; ++k) b[k] = 0.0;
+  const T zero3[3] = {T(0), T(0), T(0)};
+  for (int64_t i = tid; i < a.T; i += kAdjThreads) {
+    const int64_t s = j * a.T + i;
+    const double t = a.per_sat ? a.tsince[s] : a.tsince[i];
+    double Jt[3][7];
+    T r[3];
+    int code = 0;
+    for (int c = 0; c < 3; ++c) {
+      for (int f = 0; f < kNumAdj; ++f) acc[f * kAdjThreads + tid] = 0.0;
+      T seed[3] = {T(0), T(0), T(0)};
+      seed[c] = T(1);
+      code = adjoint_state<T>(rc, a.g, t, seed, zero3, acc + tid, r);
+      for (int k = 0; k < 7; ++k) {
+        double v = 0.0;
+        for (int f = 0; f < kNumAdj; ++f) v += acc[f * kAdjThreads + tid] * Ji[f][k];
+        Jt[c][k] = v;
+      }
+    }
+    if (code != 0 && code != 6) continue;
+    double res[3];
+    for (int c = 0; c < 3; ++c) res[c] = (double)r[c] - a.r_obs[s * 3 + c];
+    if (!(isfinite(res[0]) && isfinite(res[1]) && isfinite(res[2]))) continue;
+    sse += res[0] * res[0] + res[1] * res[1] + res[2] * res[2];
+    int q = 0;
+    for (int k = 0; k < 7; ++k) {
+      b[k] += Jt[0][k] * res[0] + Jt[1][k] * res[1] + Jt[2][k] * res[2];
+      for (int m = 0; m <= k; ++m, ++q)
+        A[q] += Jt[0][k] * Jt[0][m] + Jt[1][k] * Jt[1][m] + Jt[2][k] * Jt[2][m];
+    }
+  }
+  // Block reduction of the 28 + 7 + 1 sums (warp shuffles, then one value per warp).
+  double vals[36];
+  for (int k = 0; k < 28; ++k) vals[k] = A[k];
+  for (int k = 0; k < 7; ++k) vals[28 + k] = b[k];
+  vals[35] = sse;
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int k = 0; k < 36; ++k) {
+    double v = vals[k];
+    for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[k][warp] = v;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  double S[36];
+  for (int k = 0; k < 36; ++k) {
+    double v = 0.0;
+    for (int w = 0; w < kAdjThreads / 32; ++w) v += red[k][w];
+    S[k] = v;
+  }
+  // Unpack A (lower triangle), Jacobi scaling, damping, Cholesky.
+  double M[7][7], rhs[7], d[7];
+  int q = 0;
+  for (int k = 0; k < 7; ++k)
+    for (int m = 0; m <= k; ++m, ++q) M[k][m] = M[m][k] = S[q];
+  for (int k = 0; k < 7; ++k) d[k] = M[k][k] > 0.0 ? 1.0 / sqrt(M[k][k]) : 0.0;
+  const double lam = a.lambda[j];
+  for (int k = 0; k < 7; ++k) {
+    for (int m = 0; m < 7; ++m) M[k][m] *= d[k] * d[m];
+    M[k][k] = (d[k] > 0.0 ? M[k][k] : 1.0) * (1.0 + lam);
+    rhs[k] = -S[28 + k] * d[k];
+  }
+  bool spd = true;
+  for (int k = 0; k < 7 && spd; ++k) {
+    for (int m = 0; m < k; ++m) M[k][k] -= M[k][m] * M[k][m];
+    if (!(M[k][k] > 0.0)) { spd = false; break; }
+    M[k][k] = sqrt(M[k][k]);
+    for (int r2 = k + 1; r2 < 7; ++r2) {
+      for (int m = 0; m < k; ++m) M[r2][k] -= M[r2][m] * M[k][m];
+      M[r2][k] /= M[k][k];
+    }
+  }
+  double x[7] = {0, 0, 0, 0, 0, 0, 0};
+  if (spd) {
+    for (int k = 0; k < 7; ++k) {            // forward substitution L y = rhs
+      double v = rhs[k];
+      for (int m = 0; m < k; ++m) v -= M[k][m] * x[m];
+      x[k] = v / M[k][k];
+    }
+    for (int k = 6; k >= 0; --k) {           // back substitution L^T x = y
+      double v = x[k];
+      for (int m = k + 1; m < 7; ++m) v -= M[m][k] * x[m];
+      x[k] = v / M[k][k];
+    }
+  }
+  for (int k = 0; k < 7; ++k) a.el_out[j * 7 + k] = e7[k] + x[k] * d[k];
+  a.sse[j] = S[35];
+}
+
 }  // namespace
+
+cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el,
+                            const double* tsince, int64_t T, int per_sat, bool fp32,
+                            const double* r_obs, const double* lambda, double* el_out,
+                            double* sse, cudaStream_t stream) {
+  if (rp.n == 0) return cudaSuccess;
+  FitArgs a;
+  a.rp = rp;
+  a.g = g;
+  a.el = el;
+  a.tsince = tsince;
+  a.T = T;
+  a.per_sat = per_sat;
+  a.r_obs = r_obs;
+  a.lambda = lambda;
+  a.el_out = el_out;
+  a.sse = sse;
+  if (fp32) fit_step_kernel<float><<<(unsigned)rp.n, kAdjThreads, 0, stream>>>(a);
+  else fit_step_kernel<double><<<(unsigned)rp.n, kAdjThreads, 0, stream>>>(a);
+  return cudaGetLastError();
+}
 
 size_t adjoint_workspace_bytes(int64_t n) {
   return n <= 0 ? 0 : (size_t)n * kNumAdj * sizeof(double);

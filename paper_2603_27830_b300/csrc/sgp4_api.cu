@@ -296,6 +296,29 @@ sgp4_result sgp4_adjoint(const double* elements, const sgp4_records* records,
   return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
 }
 
+sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
+                          const double* tsince, int64_t t_count, int grid_per_sat,
+                          sgp4_precision precision, const double* r_obs, const double* lambda,
+                          double* elements_out, double* sse, void* stream) {
+  if (!records_ok(records) || t_count < 0) return SGP4_ERR_ARG;
+  if (precision != SGP4_FP64 && precision != SGP4_FP32) return SGP4_ERR_ARG;
+  const int64_t n = records->n;
+  if (n == 0) return SGP4_OK;
+  if (n > 0x7fffffffLL) return SGP4_ERR_ARG;
+  if (n > INT64_MAX / 3 / (t_count > 0 ? t_count : 1)) return SGP4_ERR_ARG;
+  const void* ptrs[] = {elements, lambda, elements_out, sse};
+  for (const void* p : ptrs)
+    if (!p || !aligned(p, 8)) return SGP4_ERR_ARG;
+  if (elements_out == elements) return SGP4_ERR_ARG;
+  if (t_count > 0 && (!tsince || !r_obs || !aligned(tsince, 8) || !aligned(r_obs, 8)))
+    return SGP4_ERR_ARG;
+  cudaError_t e = sgp4::launch_fit_step(
+      sgp4::record_ptrs(records->arena, n), make_geo(records->consts), elements, tsince, t_count,
+      grid_per_sat ? 1 : 0, precision == SGP4_FP32, r_obs, lambda, elements_out, sse,
+      static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
+}
+
 sgp4_result sgp4_batch_graph_launch(void* graph, void* stream) {
   if (!graph) return SGP4_ERR_ARG;
   BatchGraph* bg = static_cast<BatchGraph*>(graph);

@@ -59,6 +59,12 @@ cudaError_t launch_adjoint(const RecordPtrs& rp, const Geo& g, const double* el,
                            const void* grad_r, const void* grad_v, double* grad_el,
                            double* workspace, cudaStream_t stream);
 
+// One batch-least-squares (Levenberg-Marquardt) step per satellite.
+cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el,
+                            const double* tsince, int64_t T, int per_sat, bool fp32,
+                            const double* r_obs, const double* lambda, double* el_out,
+                            double* sse, cudaStream_t stream);
+
 // SM count of the current device.
 int device_sm_count();
 
