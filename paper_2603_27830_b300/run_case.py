@@ -3,7 +3,9 @@
     python -m paper_2603_27830_b300.run_case --workload starlink --precision fp32 --reps 2
 
 Workloads: near-earth (64 x 100), starlink (9,341 x 1,000), catalogue (1,000,000 x
-100; ``--n`` shrinks it).  Prints the wall time of each repetition.
+100; ``--n`` shrinks it), batch (64 uneven requests, N_i log-U[100,5e3], T_i
+log-U[10,500]: the batched persistent launch), adjoint (the fitting workload,
+10,000 x 500: one sgp4_adjoint call).  Prints the wall time of each repetition.
 """
 from __future__ import annotations
 
@@ -16,14 +18,57 @@ from . import sgp4_init, sgp4_propagate
 from . import workloads as W
 
 
+def _timed(label, fn, reps):
+    for k in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        print(f"{label} rep {k}: {1e3 * (time.perf_counter() - t0):.3f} ms")
+
+
+def run_batch(args):
+    from . import make_batch, plan_batch, sgp4_propagate_batched
+    reqs = W.config4(seed=0, n_requests=64, n_range=(100, 5000), t_range=(10, 500))
+    b = make_batch([(q.elements, q.tsince) for q in reqs])
+    el = torch.as_tensor(b.elements, device="cuda")
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    recs, _ = sgp4_init(el)
+    plan = plan_batch(b.requests, 2048)
+    precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
+    for prec in precs:
+        out = sgp4_propagate_batched(plan, recs, ts, prec)
+        _timed(f"batch {plan.total_states} states {prec}",
+               lambda: sgp4_propagate_batched(plan, recs, ts, prec, out=out), args.reps)
+
+
+def run_adjoint(args):
+    from . import sgp4_adjoint
+    w = W.config5(n=args.n or 10_000)
+    el = torch.as_tensor(w.elements, device="cuda")
+    ts = torch.as_tensor(w.tsince, device="cuda")
+    recs, _ = sgp4_init(el)
+    precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
+    for prec in precs:
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        g = torch.randn((w.n, w.t_count, 3), dtype=dt, device="cuda")
+        _timed(f"adjoint {w.states} states {prec}",
+               lambda: sgp4_adjoint(el, recs, ts, g, g, prec), args.reps)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["near-earth", "starlink", "catalogue"],
+    ap.add_argument("--workload", choices=["near-earth", "starlink", "catalogue", "batch",
+                                           "adjoint"],
                     default="starlink")
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="fp32")
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--n", type=int, default=None)
     args = ap.parse_args()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     if args.workload == "near-earth":
         w = W.config1()
     elif args.workload == "starlink":
