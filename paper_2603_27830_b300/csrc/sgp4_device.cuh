@@ -38,8 +38,10 @@ enum F32Field {
   fM0r, fMdr, fArgp0r, fArgpdr, fRaan0r, fRaandr, fRaanCfr, fN0ppr,
   fA0pp, fE0, fC1, fBC4, fBC5, fD2, fD3, fD4, fL2, fL3, fL4, fL5,
   fEta, fDelM0, fSinM0, fArgpCf, fMCf, fXlcof, fAycof,
-  fCosi, fSini, fX3thm1, fX1mth2, fX7thm1,
+  fCosi, fSini, fX3thm1, fX1mth2, fX7thm1,   // fX3thm1 holds 1.5 (3 th^2 - 1), fX7thm1 holds
+                                              // -0.25 (7 th^2 - 1): the factors they appear with
   fFlags,
+  fHalfX1mth2, fC15Cosi, fC15CosiSini,        // 0.5 (1 - th^2), 1.5 cos i, 1.5 cos i sin i
   kNumF32Used
 };
 constexpr int kF32Row = 40;   // floats per satellite row (16-byte multiple)
@@ -270,6 +272,7 @@ static __device__ __noinline__ int state64_fallback(RecordPtrs rp, Geo g, int64_
 // ============================================================== FP32 state
 struct GeoF {
   float xke, inv_xke, j2, re, vkmps;
+  float half_j2;
 };
 
 struct Rec32 {
@@ -277,7 +280,8 @@ struct Rec32 {
   float m0r, mdr, argp0r, argpdr, raan0r, raandr, raancfr, n0ppr;
   float a0pp, e0, c1, bc4, bc5, d2, d3, d4, l2, l3, l4, l5;
   float eta, delm0, sinm0, argpcf, mcf, xlcof, aycof;
-  float cosi, sini, x3thm1, x1mth2, x7thm1;
+  float cosi, sini, x3thm1_15, x1mth2, x7thm1_m025;
+  float half_x1mth2, c15cosi, c15cosisini;
   int flags;
 };
 
@@ -315,8 +319,9 @@ __device__ __forceinline__ Rec32 unpack_rec32(const float4 q0, const float4 q1, 
   r.l2 = q5.x; r.l3 = q5.y; r.l4 = q5.z; r.l5 = q5.w;
   r.eta = q6.x; r.delm0 = q6.y; r.sinm0 = q6.z; r.argpcf = q6.w;
   r.mcf = q7.x; r.xlcof = q7.y; r.aycof = q7.z; r.cosi = q7.w;
-  r.sini = q8.x; r.x3thm1 = q8.y; r.x1mth2 = q8.z; r.x7thm1 = q8.w;
+  r.sini = q8.x; r.x3thm1_15 = q8.y; r.x1mth2 = q8.z; r.x7thm1_m025 = q8.w;
   r.flags = __float_as_int(q9.x);
+  r.half_x1mth2 = q9.y; r.c15cosi = q9.z; r.c15cosisini = q9.w;
   return r;
 }
 
@@ -337,6 +342,14 @@ __device__ __forceinline__ float round_magic_int(float x, int& q) {
 // Exact float of an integer with |i| < 2^22 (same trick in reverse).
 __device__ __forceinline__ float int_to_float_small(int i) {
   return __fsub_rn(__int_as_float(__float_as_int(kRoundMagic) + i), kRoundMagic);
+}
+
+// 1 / y for y > 0 as rsqrt(y)^2 (one SFU operation and a multiply, ~2 ulp).  On B300
+// the fast-divide intrinsic puts an instruction on the small FP64 unit (4 per state
+// kept that unit 36% busy); every denominator of the FP32 path is positive.
+__device__ __forceinline__ float rcp_pos(float y) {
+  const float r = rsqrtf(y);
+  return r * r;
 }
 
 // Reduce an angle in revolutions to [-1/2, 1/2].  Exact for |x| < 2^22.
@@ -395,12 +408,17 @@ __device__ __forceinline__ void sincos_acc(float x, float* sp, float* cp) {
 }
 
 // Rotate the unit vector (s, c) = (sin a, cos a) to (sin(a+d), cos(a+d)).  The
-// corrections d of the short-period terms are O(J2/p_L^2) ~ 1e-3 rad, where a
-// 5th/4th-order Taylor pair is exact to float precision; larger d (only for
-// nearly degenerate orbits) takes the full sincos.
+// corrections d of the short-period terms are O(J2/p_L^2), below ~1e-3 rad for
+// near-Earth orbits, where a 3rd/2nd-order Taylor pair is exact to float precision;
+// larger d (nearly degenerate orbits) takes longer series or the full sincos.
 __device__ __forceinline__ void rotate_small(float& s, float& c, float d) {
   float sd, cd;
-  if (fabsf(d) < 0.05f) {
+  if (fabsf(d) < 4.0e-3f) {
+    // truncation d^5/120 and d^4/24 stay below 1e-11 here
+    const float d2 = d * d;
+    sd = fmaf(d2 * (-1.0f / 6.0f), d, d);
+    cd = fmaf(-0.5f, d2, 1.0f);
+  } else if (fabsf(d) < 0.05f) {
     const float d2 = d * d;
     sd = d * (1.0f - d2 * (1.0f / 6.0f) * (1.0f - d2 * 0.05f));
     cd = 1.0f - 0.5f * d2 * (1.0f - d2 * (1.0f / 12.0f));
@@ -466,7 +484,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   if (e < 1.0e-6f) e = 1.0e-6f;
   const float ra = rsqrtf(a);
   const float sa = a * ra;
-  const float n = g.xke * ra * ra * ra;
+  const float ra3 = ra * ra * ra;           // n / ke = a^-1.5
 
   // Phase of the mean argument of latitude, M + argp = M_DF + argp_DF + n0'' templ
   // (the drag corrections of M and argp cancel), in revolutions.  The n*t product is
@@ -486,7 +504,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   float sw, cw;
   __sincosf(argp, &sw, &cw);
   const float axn = e * cw;
-  const float q = __fdividef(1.0f, a * (1.0f - e * e));
+  const float q = rcp_pos(a * (1.0f - e * e));
   const float ayn = fmaf(e, sw, q * rc.aycof);
   const float U = wrap_rev(y + q * rc.xlcof * axn * kInvTwoPiF) * kTwoPiF;
   const float eL2 = axn * axn + ayn * ayn;
@@ -499,7 +517,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
     __sincosf(psi, &sp, &cp);
     const float f = U - ayn * cp + axn * sp - psi;
     const float fp = 1.0f - ayn * sp - axn * cp;
-    psi += fminf(fmaxf(__fdividef(f, fp), -0.95f), 0.95f);
+    psi += fminf(fmaxf(f * rcp_pos(fp), -0.95f), 0.95f);
   }
   float sp, cp;
   sincos_acc(psi, &sp, &cp);
@@ -511,13 +529,13 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   if (!(fabsf(pL) >= kGuardP)) return kRecomputeFP64;
   if (pL < 0.0f) return 4;
   const float rl = a * (1.0f - ecosE);
-  const float invr = __fdividef(1.0f, rl);
+  const float invr = rcp_pos(rl);
   const float rdotl = sa * esinE * invr;
   const float rpl = rsqrtf(pL);
   const float rfdotl = pL * rpl * invr;
   const float omel = 1.0f - eL2;
   const float betal = omel * rsqrtf(omel);
-  const float w = __fdividef(esinE, 1.0f + betal);
+  const float w = esinE * rcp_pos(1.0f + betal);
   const float aor = a * invr;
   const float sinu = aor * (sp - ayn - axn * w);
   const float cosu = aor * (cp - axn + ayn * w);
@@ -526,23 +544,23 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
 
   // Short-period periodics (J2).
   const float invp = rpl * rpl;
-  const float k = 0.5f * g.j2 * invp;
+  const float k = g.half_j2 * invp;
   const float kp = k * invp;
-  const float rk = rl * (1.0f - 1.5f * kp * betal * rc.x3thm1) + 0.5f * k * rc.x1mth2 * cos2u;
+  const float rk = rl * fmaf(-kp * betal, rc.x3thm1_15, 1.0f) + k * rc.half_x1mth2 * cos2u;
   if (!(fabsf(rk - 1.0f) >= kGuardR)) return kRecomputeFP64;
-  const float nk = n * k * g.inv_xke;
+  const float nk = ra3 * k;                 // n k / ke
   const float rdotk = rdotl - nk * rc.x1mth2 * sin2u;
-  const float rfdotk = rfdotl + nk * (rc.x1mth2 * cos2u + 1.5f * rc.x3thm1);
+  const float rfdotk = fmaf(nk, fmaf(rc.x1mth2, cos2u, rc.x3thm1_15), rfdotl);
 
   // u_k, RAAN_k and i_k as small rotations of (sin, cos) pairs.
   const float nrm = rsqrtf(sinu * sinu + cosu * cosu);
   float su = sinu * nrm, cu = cosu * nrm;
-  rotate_small(su, cu, -0.25f * kp * rc.x7thm1 * sin2u);
+  rotate_small(su, cu, kp * rc.x7thm1_m025 * sin2u);
   float sO, cO;
   sincos_acc(raan, &sO, &cO);
-  rotate_small(sO, cO, 1.5f * kp * rc.cosi * sin2u);
+  rotate_small(sO, cO, kp * rc.c15cosi * sin2u);
   float si = rc.sini, ci = rc.cosi;
-  rotate_small(si, ci, 1.5f * kp * rc.cosi * rc.sini * cos2u);
+  rotate_small(si, ci, kp * rc.c15cosisini * cos2u);
 
   const float mx = -sO * ci, my = cO * ci, mz = si;
   const float ux = mx * su + cO * cu, uy = my * su + sO * cu, uz = mz * su;

@@ -106,8 +106,11 @@ __global__ void __launch_bounds__(64) init_kernel(const double* __restrict__ el,
   h[fArgpCf] = (float)argp_cf; h[fMCf] = (float)m_cf;
   h[fXlcof] = (float)xlcof; h[fAycof] = (float)aycof;
   h[fCosi] = (float)cosi;   h[fSini] = (float)sini;
-  h[fX3thm1] = (float)x3thm1; h[fX1mth2] = (float)x1mth2;
-  h[fX7thm1] = (float)x7thm1;
+  h[fX3thm1] = (float)(1.5 * x3thm1); h[fX1mth2] = (float)x1mth2;
+  h[fX7thm1] = (float)(-0.25 * x7thm1);
+  h[fHalfX1mth2] = (float)(0.5 * x1mth2);
+  h[fC15Cosi] = (float)(1.5 * cosi);
+  h[fC15CosiSini] = (float)(1.5 * cosi * sini);
 
   int flags = 0;
   if (isimp) flags |= kFlagIsimp;
@@ -126,6 +129,7 @@ __global__ void __launch_bounds__(64) init_kernel(const double* __restrict__ el,
     gf.j2 = (float)g.j2;
     gf.re = (float)g.re;
     gf.vkmps = (float)g.vkmps;
+    gf.half_j2 = (float)(0.5 * g.j2);
     float r[3], v[3];
     const int code = state32(r32, gf, 0.0f, 0.0f, r, v);
     if (code != kRecomputeFP64) {

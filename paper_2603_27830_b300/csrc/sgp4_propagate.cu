@@ -65,6 +65,7 @@ __device__ __forceinline__ GeoF make_geof(const Geo& g) {
   gf.j2 = (float)g.j2;
   gf.re = (float)g.re;
   gf.vkmps = (float)g.vkmps;
+  gf.half_j2 = (float)(0.5 * g.j2);
   return gf;
 }
 
