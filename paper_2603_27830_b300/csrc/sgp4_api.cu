@@ -65,6 +65,7 @@ sgp4_result batch_args(const sgp4_batch_plan* plan, const sgp4_records* records,
   char* ws = static_cast<char*>(plan->workspace);
   a->rp = sgp4::record_ptrs(records->arena, records->n);
   a->g = make_geo(records->consts);
+  a->gf = sgp4::geo_float(a->g);
   a->tsince = tsince;
   a->reqs = reinterpret_cast<const sgp4_request*>(ws + ws_reqs_off(plan->n_requests));
   a->tile_start = reinterpret_cast<const int64_t*>(ws + ws_tile_start_off());
@@ -147,6 +148,7 @@ sgp4_result sgp4_propagate(const sgp4_records* records, const double* tsince, in
   sgp4::PropArgs a;
   a.rp = sgp4::record_ptrs(records->arena, n);
   a.g = make_geo(records->consts);
+  a.gf = sgp4::geo_float(a.g);
   a.tsince = tsince;
   a.t_count = t_count;
   a.grid_per_sat = grid_per_sat ? 1 : 0;

@@ -1,4 +1,6 @@
 // Initialisation constants of near-Earth SGP4 as a function of the mean elements,
+// (x^(2/3) as cbrt(x^2), x^3.5 as x^3 sqrt(x), one sincos per angle: the record
+// build runs on B300's small FP64 unit, so its operation count is its cost),
 // templated on the scalar: double for the record builder, D7 (value + derivatives
 // with respect to the 7 elements) for the Jacobian the adjoint needs.  Equations of
 // Spacetrack Report #3 as revised in 2006 (paper Sec. 2.1); readings: a0'' from
@@ -89,13 +91,25 @@ __device__ __forceinline__ D7 pow(const D7& a, double p) {
   return d7chain(a, y, p * y / a.v);
 }
 __device__ __forceinline__ D7 fabs(const D7& a) { return a.v < 0.0 ? -a : a; }
+__device__ __forceinline__ D7 cbrt(const D7& a) {
+  const double y = ::cbrt(a.v);
+  return d7chain(a, y, y / (3.0 * a.v));
+}
+__device__ __forceinline__ void sincos(const D7& a, D7* s, D7* c) {
+  double sv, cv;
+  ::sincos(a.v, &sv, &cv);
+  *s = d7chain(a, sv, cv);
+  *c = d7chain(a, cv, -sv);
+}
 __device__ __forceinline__ double val(const D7& a) { return a.v; }
 __device__ __forceinline__ double val(double a) { return a; }
 // Keep the double versions visible next to the D7 overloads in this namespace.
+using ::cbrt;
 using ::cos;
 using ::fabs;
 using ::pow;
 using ::sin;
+using ::sincos;
 using ::sqrt;
 
 // The 33 record fields the propagation reads, plus C1 for the FP32 row.
@@ -115,7 +129,8 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
   const S n0 = el[0], e0 = el[1], i0 = el[2], raan0 = el[3], argp0 = el[4], m0 = el[5];
   const S bstar = el[6];
   const double k2 = 0.5 * g.j2;
-  const S cosi = cos(i0), sini = sin(i0);
+  S cosi, sini;
+  sincos(i0, &sini, &cosi);
   const S th2 = cosi * cosi;
   const S x3thm1 = 3.0 * th2 - 1.0;
   const S x1mth2 = 1.0 - th2;
@@ -125,12 +140,14 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
   const S b3 = b2 * b;
 
   // Kozai -> Brouwer mean motion and semi-major axis.
-  const S a1 = pow(g.xke / n0, 2.0 / 3.0);
+  const S x1 = g.xke / n0;
+  const S a1 = cbrt(x1 * x1);                 // (ke / n0)^(2/3)
   const S d1 = 1.5 * k2 * x3thm1 / (a1 * a1 * b3);
   const S a0 = a1 * (1.0 - d1 / 3.0 - d1 * d1 - (134.0 / 81.0) * d1 * d1 * d1);
   const S d0 = 1.5 * k2 * x3thm1 / (a0 * a0 * b3);
   const S n0pp = n0 / (1.0 + d0);
-  const S a0pp = pow(g.xke / n0pp, 2.0 / 3.0);
+  const S xpp = g.xke / n0pp;
+  const S a0pp = cbrt(xpp * xpp);             // (ke / n0'')^(2/3)
 
   // Atmosphere: s and (q0 - s)^4 by perigee height.
   const S rp_er = a0pp * (1.0 - e0);
@@ -150,19 +167,22 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
   const S psi2 = fabs(1.0 - eta2);
   const S xi4 = xi * xi * xi * xi;
   const S coef = qs4 * xi4;
-  const S coef1 = coef / pow(psi2, 3.5);
+  const S coef1 = coef / (psi2 * psi2 * psi2 * sqrt(psi2));   // coef / psi2^3.5
 
   const S C2 = coef1 * n0pp *
                (a0pp * (1.0 + 1.5 * eta2 + eeta * (4.0 + eta2)) +
                 0.375 * g.j2 * xi / psi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
   const S C1 = bstar * C2;
+  S sinw, cosw;
+  sincos(argp0, &sinw, &cosw);
+  const S cos2w = 2.0 * cosw * cosw - 1.0;
   S C3 = 0.0 * C1;
   if (val(e0) > 1.0e-4) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sini / e0;
   const S C4 = 2.0 * n0pp * coef1 * a0pp * b2 *
                (eta * (2.0 + 0.5 * eta2) + e0 * (0.5 + 2.0 * eta2) -
                 g.j2 * xi / (a0pp * psi2) *
                     (-3.0 * x3thm1 * (1.0 - 2.0 * eeta + eta2 * (1.5 - 0.5 * eeta)) +
-                     0.75 * x1mth2 * (2.0 * eta2 - eeta * (1.0 + eta2)) * cos(2.0 * argp0)));
+                     0.75 * x1mth2 * (2.0 * eta2 - eeta * (1.0 + eta2)) * cos2w));
   const S C5 = 2.0 * coef1 * a0pp * b2 * (1.0 + 2.75 * (eta2 + eeta) + eeta * eta2);
 
   // Secular rates.
@@ -179,7 +199,7 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
   o.raandot = raandot1 + (0.5 * T2 * (4.0 - 19.0 * th2) + 2.0 * T3 * (3.0 - 7.0 * th2)) * cosi;
 
   o.raan_cf = 3.5 * b2 * raandot1 * C1;
-  o.argp_cf = bstar * C3 * cos(argp0);
+  o.argp_cf = bstar * C3 * cosw;
   o.m_cf = 0.0 * C1;
   if (val(e0) > 1.0e-4) o.m_cf = -(2.0 / 3.0) * coef * bstar / eeta;
   o.l2 = 1.5 * C1;
@@ -188,9 +208,11 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
   if (::fabs(val(opc)) <= 1.5e-12) opc = 0.0 * opc + 1.5e-12;
   o.xlcof = -0.25 * g.j3oj2 * sini * (3.0 + 5.0 * cosi) / opc;
   o.aycof = -0.5 * g.j3oj2 * sini;
-  const S cm = 1.0 + eta * cos(m0);
+  S sinm, cosm;
+  sincos(m0, &sinm, &cosm);
+  const S cm = 1.0 + eta * cosm;
   o.delm0 = cm * cm * cm;
-  o.sinm0 = sin(m0);
+  o.sinm0 = sinm;
 
   o.d2 = 0.0 * C1; o.d3 = o.d2; o.d4 = o.d2; o.l3 = o.d2; o.l4 = o.d2; o.l5 = o.d2;
   if (!o.isimp) {

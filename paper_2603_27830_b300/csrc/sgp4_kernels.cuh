@@ -16,6 +16,7 @@ cudaError_t launch_init(const double* el, const int32_t* epoch_day, const double
 struct PropArgs {
   RecordPtrs rp;
   Geo g;
+  GeoF gf;        // float copy of g, made on the host
   const double* tsince;
   int64_t t_count;
   int grid_per_sat;
@@ -31,6 +32,7 @@ cudaError_t launch_propagate32(const PropArgs& a, cudaStream_t stream);
 struct BatchArgs {
   RecordPtrs rp;
   Geo g;
+  GeoF gf;
   const double* tsince;          // all requests' grids, concatenated
   const sgp4_request* reqs;      // [n_req], device
   const int64_t* tile_start;     // [n_req + 1], device: exclusive prefix of tile counts
@@ -64,6 +66,18 @@ cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el
                             const double* tsince, int64_t T, int per_sat, bool fp32,
                             const double* r_obs, const double* lambda, double* el_out,
                             double* sse, cudaStream_t stream);
+
+// Float copy of the Earth model for the FP32 path (host side, once per call).
+inline GeoF geo_float(const Geo& g) {
+  GeoF gf;
+  gf.xke = (float)g.xke;
+  gf.inv_xke = (float)(1.0 / g.xke);
+  gf.j2 = (float)g.j2;
+  gf.re = (float)g.re;
+  gf.vkmps = (float)g.vkmps;
+  gf.half_j2 = (float)(0.5 * g.j2);
+  return gf;
+}
 
 // SM count of the current device.
 int device_sm_count();

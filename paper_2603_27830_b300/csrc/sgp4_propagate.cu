@@ -58,16 +58,6 @@ struct Range {
   int32_t* status;
 };
 
-__device__ __forceinline__ GeoF make_geof(const Geo& g) {
-  GeoF gf;
-  gf.xke = (float)g.xke;
-  gf.inv_xke = (float)(1.0 / g.xke);
-  gf.j2 = (float)g.j2;
-  gf.re = (float)g.re;
-  gf.vkmps = (float)g.vkmps;
-  gf.half_j2 = (float)(0.5 * g.j2);
-  return gf;
-}
 
 // States [beg, end) of one problem (local flattened index j * T + i).  Every thread
 // of the block calls it with the same arguments (it contains block barriers).
@@ -160,7 +150,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
-  const GeoF gf = make_geof(a.g);
+  const GeoF gf = a.gf;
   Range rg;
   rg.tsince = a.tsince;
   rg.T = a.t_count;
@@ -183,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
     batched_kernel(BatchArgs a) {
   __shared__ Stage<kFP32> sm;
   __shared__ unsigned long long s_tile;
-  const GeoF gf = make_geof(a.g);
+  const GeoF gf = a.gf;
   const int64_t total_tiles = a.tile_start[a.n_req];
   unsigned long long nfix = 0;
   for (;;) {

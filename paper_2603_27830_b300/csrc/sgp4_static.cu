@@ -145,6 +145,7 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
   sgp4::BatchArgs a;
   a.rp = sgp4::record_ptrs(records->arena, records->n);
   a.g = make_geo(records->consts);
+  a.gf = sgp4::geo_float(a.g);
   a.tsince = tsince;
   a.reqs = reinterpret_cast<const sgp4_request*>(scratch + kCounterBytes + kTileStartBytes);
   a.tile_start = reinterpret_cast<const int64_t*>(scratch + kCounterBytes);
