@@ -17,12 +17,21 @@ __device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
   lo = __double2float_rn(x - (double)hi);
 }
 
-__global__ void __launch_bounds__(64) init_kernel(const double* __restrict__ el,
+// Satellites per 32-lane warp.  The record build is bound by B300's small FP64 unit,
+// which works through the active lanes of a warp instruction; a Starlink-sized set
+// (9,341) fills only half of the SM sub-partitions at 32 per warp, so fewer
+// satellites per warp spread the same FP64 work over all of them.
+#ifndef SGP4_INIT_LANES
+#define SGP4_INIT_LANES 32
+#endif
+
+__global__ void __launch_bounds__(32) init_kernel(const double* __restrict__ el,
                                                    const int32_t* __restrict__ epoch_day,
                                                    const double* __restrict__ epoch_frac,
                                                    RecordPtrs rp, Geo g,
                                                    int32_t* __restrict__ init_status) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (threadIdx.x >= SGP4_INIT_LANES) return;
+  const int64_t j = (int64_t)blockIdx.x * SGP4_INIT_LANES + threadIdx.x;
   if (j >= rp.n) return;
   const int64_t s = rp.stride;
   double* f = rp.f64;
@@ -154,9 +163,8 @@ cudaError_t launch_init(const double* el, const int32_t* epoch_day, const double
                         const RecordPtrs& rp, const Geo& g, int32_t* init_status,
                         cudaStream_t stream) {
   if (rp.n == 0) return cudaSuccess;
-  // 64-thread blocks: a Starlink-sized catalogue (9,341) then spans all 148 SMs.
-  const int threads = 64;
-  const int64_t blocks = (rp.n + threads - 1) / threads;
+  const int threads = 32;
+  const int64_t blocks = (rp.n + SGP4_INIT_LANES - 1) / SGP4_INIT_LANES;
   init_kernel<<<(unsigned)blocks, threads, 0, stream>>>(el, epoch_day, epoch_frac, rp, g,
                                                         init_status);
   return cudaGetLastError();
