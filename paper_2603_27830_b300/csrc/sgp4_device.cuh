@@ -148,8 +148,42 @@ __device__ __forceinline__ Rec64 load_rec64(const RecordPtrs& rp, int64_t j) {
   return r;
 }
 
+// Angle reduction like C fmod(x, 2 pi) (sign kept), as x - 2 pi trunc(x / 2 pi): the
+// same value to rounding, without fmod's iterative remainder on the FP64 unit.
+__device__ __forceinline__ double wrap_2pi(double x) {
+  return fma(-kTwoPi, trunc(x * (1.0 / kTwoPi)), x);
+}
+
+// Rotate (s, c) = (sin a, cos a) to (sin(a+d), cos(a+d)) in FP64: 7th/6th-order Taylor
+// pair for |d| < 1e-2 (truncation below 3e-18), the full sincos beyond.
+__device__ __forceinline__ void rotate64(double& s, double& c, double d) {
+  double sd, cd;
+  if (fabs(d) < 1.0e-2) {
+    const double d2 = d * d;
+    sd = d * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0))));
+    cd = 1.0 - 0.5 * d2 * (1.0 - d2 * (1.0 / 12.0) * (1.0 - d2 * (1.0 / 30.0)));
+  } else {
+    sincos(d, &sd, &cd);
+  }
+  const double s2 = s * cd + c * sd;
+  const double c2 = c * cd - s * sd;
+  s = s2;
+  c = c2;
+}
+
+// Newton steps for Kepler's equation in FP64 from psi0 = U (same bound as the FP32
+// path, target 1e-15 rad), thresholds on e_L^2: 1 step for e_L <= 1.26e-5, 2 for
+// <= 0.0096, 3 for <= 0.129, 4 for <= 0.367, 5 for <= 0.5; beyond that the theory's
+// rule (stop when a step is below 1e-12, at most 10 steps).
+__device__ __forceinline__ int newton_steps64(double eL2) {
+  return eL2 <= 1.5876e-10 ? 1 : eL2 <= 9.3e-5 ? 2 : eL2 <= 0.01664 ? 3 : eL2 <= 0.1347 ? 4
+       : eL2 <= 0.25 ? 5 : 10;
+}
+
 // One state in FP64.  Returns the status code; r (km) and v (km/s) are written
-// for codes 0 and 6 only.
+// for codes 0 and 6 only.  Same theory and status decisions as the FP32 path and the
+// textbook form: atan2 and the sin/cos of u_k, RAAN_k, i_k are replaced by small
+// rotations of (sin, cos) pairs by the short-period corrections.
 __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, double r[3],
                                        double v[3]) {
   const int fatal = (rc.flags >> kFatalShift) & 0xff;
@@ -162,33 +196,36 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   const double raandf = rc.raan0 + rc.raandot * t;
   const double t2 = t * t;
   double raan = raandf + rc.raan_cf * t2;
-  double mm = mdf, argp = argpdf;
+  double argp = argpdf;
   double tempa = 1.0 - rc.c1 * t;
   double tempe = rc.bc4 * t;
   double templ = rc.l2 * t2;
   if (!isimp) {
     const double dargp = rc.argp_cf * t;
-    const double c = 1.0 + rc.eta * cos(mdf);
+    double sm, cm;
+    sincos(wrap_2pi(mdf), &sm, &cm);
+    const double c = 1.0 + rc.eta * cm;
     const double dm = rc.m_cf * (c * c * c - rc.delm0);
-    mm = mdf + dargp + dm;
-    argp = argpdf - dargp - dm;
+    const double dd = dargp + dm;
+    argp = argpdf - dd;
     const double t3 = t2 * t, t4 = t3 * t;
     tempa = tempa - rc.d2 * t2 - rc.d3 * t3 - rc.d4 * t4;
-    tempe = tempe + rc.bc5 * (sin(mm) - rc.sinm0);
+    double sdd, cdd;
+    sincos(dd, &sdd, &cdd);
+    tempe = tempe + rc.bc5 * (sm * cdd + cm * sdd - rc.sinm0);   // sin(M_DF + dd)
     templ = templ + rc.l3 * t3 + t4 * (rc.l4 + t * rc.l5);
   }
   if (rc.flags & kFlagN0ppNonPos) return 2;
   const double a = rc.a0pp * tempa * tempa;
-  const double n = g.xke / (a * sqrt(a));
+  const double sa = sqrt(a);
+  const double ia15 = 1.0 / (a * sa);                  // n / ke
   double e = rc.e0 - tempe;
   if (e >= 1.0 || e < -0.001) return 1;
   if (e < 1.0e-6) e = 1.0e-6;
-  mm = mm + rc.n0pp * templ;
-  double L = mm + argp + raan;
-  raan = fmod(raan, kTwoPi);
-  argp = fmod(argp, kTwoPi);
-  L = fmod(L, kTwoPi);
-  mm = fmod(L - argp - raan, kTwoPi);
+  raan = wrap_2pi(raan);
+  argp = wrap_2pi(argp);
+  // M + argp: the drag corrections of M and argp cancel.
+  const double mpa = mdf + argpdf + rc.n0pp * templ;
 
   // Long-period periodics (J3).
   double sw, cw;
@@ -196,54 +233,58 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   const double axn = e * cw;
   const double q = 1.0 / (a * (1.0 - e * e));
   const double ayn = e * sw + q * rc.aycof;
-  const double xl = mm + argp + raan + q * rc.xlcof * axn;
-  const double U = fmod(xl - raan, kTwoPi);
+  const double U = wrap_2pi(mpa + q * rc.xlcof * axn);
+  const double eL2 = axn * axn + ayn * ayn;
 
-  // Kepler's equation, Newton with clamped steps; same stopping rule as the theory.
-  double psi = U;
-  for (int k = 0; k < 10; ++k) {
-    double sp, cp;
+  // Kepler's equation: Newton with clamped steps, count from the e_L bound.
+  double psi = U, sp = 0.0, cp = 1.0, step = 0.0;
+  const int K = newton_steps64(eL2);
+  for (int k = 0; k < K; ++k) {
     sincos(psi, &sp, &cp);
-    double step = (U - ayn * cp + axn * sp - psi) / (1.0 - ayn * sp - axn * cp);
+    step = (U - ayn * cp + axn * sp - psi) / (1.0 - ayn * sp - axn * cp);
     step = fmin(fmax(step, -0.95), 0.95);
     psi += step;
-    if (fabs(step) < 1.0e-12) break;
+    if (K == 10 && fabs(step) < 1.0e-12) break;
   }
-  double sp, cp;
-  sincos(psi, &sp, &cp);
+  rotate64(sp, cp, step);      // sin, cos at the final iterate
 
   // Short-period preliminaries.
   const double ecosE = axn * cp + ayn * sp;
   const double esinE = axn * sp - ayn * cp;
-  const double eL2 = axn * axn + ayn * ayn;
   const double pL = a * (1.0 - eL2);
   if (pL < 0.0) return 4;
   const double rl = a * (1.0 - ecosE);
-  const double rdotl = sqrt(a) * esinE / rl;
-  const double rfdotl = sqrt(pL) / rl;
+  const double invr = 1.0 / rl;
+  const double rdotl = sa * esinE * invr;
+  const double spl = sqrt(pL);
+  const double rfdotl = spl * invr;
   const double betal = sqrt(1.0 - eL2);
   const double w = esinE / (1.0 + betal);
-  const double sinu = a / rl * (sp - ayn - axn * w);
-  const double cosu = a / rl * (cp - axn + ayn * w);
-  const double u = atan2(sinu, cosu);
+  const double aor = a * invr;
+  const double sinu = aor * (sp - ayn - axn * w);
+  const double cosu = aor * (cp - axn + ayn * w);
   const double sin2u = 2.0 * cosu * sinu;
   const double cos2u = 1.0 - 2.0 * sinu * sinu;
 
   // Short-period periodics (J2).
-  const double k = 0.5 * g.j2 / pL;
-  const double kp = k / pL;
+  const double invp = 1.0 / pL;
+  const double k = 0.5 * g.j2 * invp;
+  const double kp = k * invp;
   const double rk = rl * (1.0 - 1.5 * kp * betal * rc.x3thm1) + 0.5 * k * rc.x1mth2 * cos2u;
-  const double uk = u - 0.25 * kp * rc.x7thm1 * sin2u;
-  const double raank = raan + 1.5 * kp * rc.cosi * sin2u;
-  const double ik = rc.i0 + 1.5 * kp * rc.cosi * rc.sini * cos2u;
-  const double rdotk = rdotl - n * k * rc.x1mth2 * sin2u / g.xke;
-  const double rfdotk = rfdotl + n * k * (rc.x1mth2 * cos2u + 1.5 * rc.x3thm1) / g.xke;
+  const double nk = ia15 * k;          // n k / ke
+  const double rdotk = rdotl - nk * rc.x1mth2 * sin2u;
+  const double rfdotk = rfdotl + nk * (rc.x1mth2 * cos2u + 1.5 * rc.x3thm1);
 
-  // Orientation and TEME output.
-  double su, cu, sO, cO, si, ci;
-  sincos(uk, &su, &cu);
-  sincos(raank, &sO, &cO);
-  sincos(ik, &si, &ci);
+  // u_k, RAAN_k and i_k as rotations of (sin, cos) pairs.
+  const double nrm = 1.0 / sqrt(sinu * sinu + cosu * cosu);
+  double su = sinu * nrm, cu = cosu * nrm;
+  rotate64(su, cu, -0.25 * kp * rc.x7thm1 * sin2u);
+  double sO, cO;
+  sincos(raan, &sO, &cO);
+  rotate64(sO, cO, 1.5 * kp * rc.cosi * sin2u);
+  double si = rc.sini, ci = rc.cosi;
+  rotate64(si, ci, 1.5 * kp * rc.cosi * rc.sini * cos2u);
+
   const double mx = -sO * ci, my = cO * ci, mz = si;
   const double ux = mx * su + cO * cu, uy = my * su + sO * cu, uz = mz * su;
   const double vx = mx * cu - cO * su, vy = my * cu - sO * su, vz = mz * cu;
