@@ -449,23 +449,15 @@ __device__ __forceinline__ void sincos_acc(float x, float* sp, float* cp) {
 }
 
 // Rotate the unit vector (s, c) = (sin a, cos a) to (sin(a+d), cos(a+d)).  The
-// corrections d of the short-period terms are O(J2/p_L^2), below ~1e-3 rad for
-// near-Earth orbits, where a 3rd/2nd-order Taylor pair is exact to float precision;
-// larger d (nearly degenerate orbits) takes longer series or the full sincos.
+// corrections d of the short-period terms are O(J2/p_L^2): below ~1e-3 rad for
+// near-Earth orbits, where a 3rd/2nd-order Taylor pair is exact to float precision.
+// |d| >= 4e-3 needs p_L < ~0.45 Earth radii (a perigee deep inside the Earth); the
+// FP32 path hands such states to the FP64 recomputation instead.
 __device__ __forceinline__ void rotate_small(float& s, float& c, float d) {
-  float sd, cd;
-  if (fabsf(d) < 4.0e-3f) {
-    // truncation d^5/120 and d^4/24 stay below 1e-11 here
-    const float d2 = d * d;
-    sd = fmaf(d2 * (-1.0f / 6.0f), d, d);
-    cd = fmaf(-0.5f, d2, 1.0f);
-  } else if (fabsf(d) < 0.05f) {
-    const float d2 = d * d;
-    sd = d * (1.0f - d2 * (1.0f / 6.0f) * (1.0f - d2 * 0.05f));
-    cd = 1.0f - 0.5f * d2 * (1.0f - d2 * (1.0f / 12.0f));
-  } else {
-    sincos_acc(d, &sd, &cd);
-  }
+  // truncation d^5/120 and d^4/24 stay below 1e-11 for |d| < 4e-3 (callers check)
+  const float d2 = d * d;
+  const float sd = fmaf(d2 * (-1.0f / 6.0f), d, d);
+  const float cd = fmaf(-0.5f, d2, 1.0f);
   const float s2 = s * cd + c * sd;
   const float c2 = c * cd - s * sd;
   s = s2;
@@ -594,14 +586,18 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   const float rfdotk = fmaf(nk, fmaf(rc.x1mth2, cos2u, rc.x3thm1_15), rfdotl);
 
   // u_k, RAAN_k and i_k as small rotations of (sin, cos) pairs.
+  const float du = kp * rc.x7thm1_m025 * sin2u;
+  const float dO = kp * rc.c15cosi * sin2u;
+  const float di = kp * rc.c15cosisini * cos2u;
+  if (!(fmaxf(fabsf(du), fmaxf(fabsf(dO), fabsf(di))) < 4.0e-3f)) return kRecomputeFP64;
   const float nrm = rsqrtf(sinu * sinu + cosu * cosu);
   float su = sinu * nrm, cu = cosu * nrm;
-  rotate_small(su, cu, kp * rc.x7thm1_m025 * sin2u);
+  rotate_small(su, cu, du);
   float sO, cO;
-  sincos_acc(raan, &sO, &cO);
-  rotate_small(sO, cO, kp * rc.c15cosi * sin2u);
+  __sincosf(raan, &sO, &cO);   // SFU: <= 3.6e-7 rad, a few metres at LEO radius
+  rotate_small(sO, cO, dO);
   float si = rc.sini, ci = rc.cosi;
-  rotate_small(si, ci, kp * rc.c15cosisini * cos2u);
+  rotate_small(si, ci, di);
 
   const float mx = -sO * ci, my = cO * ci, mz = si;
   const float ux = mx * su + cO * cu, uy = my * su + sO * cu, uz = mz * su;
