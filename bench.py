@@ -32,9 +32,10 @@ UNIT = "states/s"
 
 # Per-state algorithmic output bytes (r, v as float32 x3 + int32 status; FP64: doubles).
 BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
-# FP32 arithmetic operations per state of the FP32 formulation on the Starlink-shaped
-# workload's branch (add/mul/FMA/compare = 1, each SFU op = 1); itemised in the design doc.
-ALG_OPS_FP32 = 285
+# FP32 arithmetic + SFU operations per state of the FP32 formulation on the
+# Starlink-shaped workload (FADD 45 + FFMA 68 + FMUL 104 + SFU 16.5 thread instructions,
+# counted with ncu; the command is in the design doc and profiles/).
+ALG_OPS_FP32 = 234
 
 
 def _peaks():
@@ -357,10 +358,9 @@ def run_ours(args):
     d2h = (r_h.numel() + v_h.numel()) * 4 + s_h.numel() * 4
 
     # Roofline of the dominant kernel (the FP32 propagate), per launch.  It is bound by
-    # FP32 arithmetic: ALG_OPS_FP32 operations per state (hand count of the FP32
-    # formulation on this workload's branch: drag with D terms, one Newton step)
-    # against the FP32 lanes (148 SMs x 128 lanes x SM clock).  Its HBM side (28 B
-    # per state of output) is reported beside it.
+    # FP32 arithmetic: ALG_OPS_FP32 operations per state (the formulation's FP32 and
+    # SFU operations on this workload) against the FP32 lanes (148 SMs x 128 lanes x
+    # SM clock).  Its HBM side (28 B per state of output) is reported beside it.
     kern_ms = statistics.mean(per32_k)
     sm_mhz = float(peaks.get("sm_max_mhz", 2032.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
