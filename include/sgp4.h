@@ -131,8 +131,8 @@ sgp4_result sgp4_init(const double* elements, const int32_t* epoch_day, const do
  *   fixups       optional device counter (may be NULL): SGP4_FP32 adds the number
  *                of states recomputed in FP64 because a status threshold was
  *                within the FP32 guard band.  Ignored for SGP4_FP64.
- * Errors: SGP4_ERR_ARG for a bad precision, t_count < 0, NULL or misaligned
- * arrays when n * t_count > 0, or n * t_count * 3 overflowing int64.
+ * Errors: SGP4_ERR_ARG for a bad precision, t_count < 0 or > INT32_MAX, NULL or
+ * misaligned arrays when n * t_count > 0, or n * t_count * 3 overflowing int64.
  */
 sgp4_result sgp4_propagate(const sgp4_records* records, const double* tsince, int64_t t_count,
                            int grid_per_sat, sgp4_precision precision, void* r, void* v,
@@ -185,8 +185,8 @@ size_t sgp4_batch_workspace_bytes(int32_t n_requests);
  *                autotuner of the Python layer, e.g. 1024)
  *   grid_blocks  persistent grid size, 0 for one full wave
  * Errors: SGP4_ERR_ARG for a NULL plan/workspace/requests (n_requests > 0), a
- * negative size or offset, a bad tile_states, overlapping output ranges, or
- * overflow; SGP4_ERR_OOM if workspace_bytes is too small; SGP4_ERR_CUDA if the copy
+ * negative size or offset, a t_count above INT32_MAX, a bad tile_states, overlapping
+ * output ranges, or overflow; SGP4_ERR_OOM if workspace_bytes is too small; SGP4_ERR_CUDA if the copy
  * fails.
  */
 sgp4_result sgp4_batch_plan_init(const sgp4_request* requests, int32_t n_requests,

@@ -136,7 +136,7 @@ sgp4_result sgp4_init(const double* elements, const int32_t* epoch_day, const do
 sgp4_result sgp4_propagate(const sgp4_records* records, const double* tsince, int64_t t_count,
                            int grid_per_sat, sgp4_precision precision, void* r, void* v,
                            int32_t* status, unsigned long long* fixups, void* stream) {
-  if (!records_ok(records) || t_count < 0) return SGP4_ERR_ARG;
+  if (!records_ok(records) || t_count < 0 || t_count > INT32_MAX) return SGP4_ERR_ARG;
   if (precision != SGP4_FP64 && precision != SGP4_FP32) return SGP4_ERR_ARG;
   const int64_t n = records->n;
   if (n == 0 || t_count == 0) return SGP4_OK;
@@ -184,6 +184,7 @@ sgp4_result sgp4_batch_plan_init(const sgp4_request* requests, int32_t n_request
     const sgp4_request& q = requests[k];
     if (q.n < 0 || q.t_count < 0 || q.sat_offset < 0 || q.t_offset < 0 || q.out_offset < 0)
       return SGP4_ERR_ARG;
+    if (q.t_count > INT32_MAX) return SGP4_ERR_ARG;
     if (q.sat_offset > kLimit - q.n || q.t_offset > kLimit - q.t_count) return SGP4_ERR_ARG;
     if (!mul_ok(q.n, q.t_count, kLimit / 3)) return SGP4_ERR_ARG;
     const int64_t st = q.n * q.t_count;

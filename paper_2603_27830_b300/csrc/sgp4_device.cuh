@@ -483,12 +483,14 @@ constexpr int kRecomputeFP64 = -1;
 
 // One state in FP32 with the n*t phase in double-float.  (th, tl) is tsince split as
 // th + tl.  Returns the status code, or kRecomputeFP64 when the state must be
-// recomputed by state64.
+// recomputed by state64.  The status checks of the theory are evaluated as flags with a
+// single exit at the end (states with a nonzero code compute on and are discarded):
+// early returns cost every state divergence bookkeeping.
 __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th, float tl,
                                        float r[3], float v[3]) {
   const int fatal = (rc.flags >> kFatalShift) & 0xff;
-  if (fatal) return fatal;
-  if (rc.flags & kFlagN0ppNonPos) return 2;
+  int code = fatal ? fatal : ((rc.flags & kFlagN0ppNonPos) ? 2 : 0);
+  bool need64 = false;
   const bool isimp = rc.flags & kFlagIsimp;
   const float t = th;
   const float t2 = t * t;
@@ -511,10 +513,10 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   }
   const float a = rc.a0pp * tempa * tempa;
   float e = rc.e0 - tempe;
-  if (!(fabsf(e - 1.0f) >= kGuardE && fabsf(e + 0.001f) >= kGuardE && a > 1.0e-3f))
-    return kRecomputeFP64;
-  if (e >= 1.0f || e < -0.001f) return 1;
-  if (e < 1.0e-6f) e = 1.0e-6f;
+  const bool near_e = !(fabsf(e - 1.0f) >= kGuardE && fabsf(e + 0.001f) >= kGuardE && a > 1.0e-3f);
+  need64 = need64 || (code == 0 && near_e);
+  if (code == 0 && !need64 && (e >= 1.0f || e < -0.001f)) code = 1;
+  e = fmaxf(e, 1.0e-6f);
   const float ra = rsqrtf(a);
   const float sa = a * ra;
   const float ra3 = ra * ra * ra;           // n / ke = a^-1.5
@@ -559,8 +561,8 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   const float ecosE = axn * cp + ayn * sp;
   const float esinE = axn * sp - ayn * cp;
   const float pL = a * (1.0f - eL2);
-  if (!(fabsf(pL) >= kGuardP)) return kRecomputeFP64;
-  if (pL < 0.0f) return 4;
+  need64 = need64 || (code == 0 && !(fabsf(pL) >= kGuardP));
+  if (code == 0 && !need64 && pL < 0.0f) code = 4;
   const float rl = a * (1.0f - ecosE);
   const float invr = rcp_pos(rl);
   const float rdotl = sa * esinE * invr;
@@ -580,7 +582,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   const float k = g.half_j2 * invp;
   const float kp = k * invp;
   const float rk = rl * fmaf(-kp * betal, rc.x3thm1_15, 1.0f) + k * rc.half_x1mth2 * cos2u;
-  if (!(fabsf(rk - 1.0f) >= kGuardR)) return kRecomputeFP64;
+  need64 = need64 || (code == 0 && !(fabsf(rk - 1.0f) >= kGuardR));
   const float nk = ra3 * k;                 // n k / ke
   const float rdotk = rdotl - nk * rc.x1mth2 * sin2u;
   const float rfdotk = fmaf(nk, fmaf(rc.x1mth2, cos2u, rc.x3thm1_15), rfdotl);
@@ -589,7 +591,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   const float du = kp * rc.x7thm1_m025 * sin2u;
   const float dO = kp * rc.c15cosi * sin2u;
   const float di = kp * rc.c15cosisini * cos2u;
-  if (!(fmaxf(fabsf(du), fmaxf(fabsf(dO), fabsf(di))) < 4.0e-3f)) return kRecomputeFP64;
+  need64 = need64 || (code == 0 && !(fmaxf(fabsf(du), fmaxf(fabsf(dO), fabsf(di))) < 4.0e-3f));
   const float nrm = rsqrtf(sinu * sinu + cosu * cosu);
   float su = sinu * nrm, cu = cosu * nrm;
   rotate_small(su, cu, du);
@@ -607,7 +609,8 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   v[0] = (rdotk * ux + rfdotk * vx) * g.vkmps;
   v[1] = (rdotk * uy + rfdotk * vy) * g.vkmps;
   v[2] = (rdotk * uz + rfdotk * vz) * g.vkmps;
-  return rk < 1.0f ? 6 : 0;
+  if (need64) return kRecomputeFP64;
+  return code != 0 ? code : (rk < 1.0f ? 6 : 0);
 }
 
 }  // namespace sgp4

@@ -67,9 +67,10 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
                                           Stage<kFP32>& sm, unsigned long long& nfix) {
   using OutT = typename Stage<kFP32>::OutT;
   const int tid = threadIdx.x;
-  const int64_t T = rg.T;
+  const int64_t T = rg.T;            // <= INT32_MAX (checked by the API)
+  const int T32 = (int)T;
   int64_t j = (beg + tid) / T;
-  int64_t i = (beg + tid) - j * T;
+  int i = (int)((beg + tid) - j * T);
   int64_t cur = -1;
   Rec64 rc64;
 
@@ -134,10 +135,10 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
     __syncthreads();
 
     i += kThreads;
-    if (i >= T) {
-      const int64_t q = i / T;
+    if (i >= T32) {
+      const int q = i / T32;
       j += q;
-      i -= q * T;
+      i -= q * T32;
     }
   }
 }

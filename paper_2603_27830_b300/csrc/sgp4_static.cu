@@ -94,6 +94,7 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
     const sgp4_request& q = requests[k];
     if (q.n < 0 || q.t_count < 0 || q.sat_offset < 0 || q.t_offset < 0 || q.out_offset < 0)
       return SGP4_ERR_ARG;
+    if (q.t_count > INT32_MAX) return SGP4_ERR_ARG;
     if (q.n > 0 && q.t_count > kLimit / 3 / q.n) return SGP4_ERR_ARG;
     const int64_t st = q.n * q.t_count;
     if (q.sat_offset > records->n - q.n || q.t_offset > tsince_len - q.t_count ||
