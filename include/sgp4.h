@@ -235,8 +235,10 @@ sgp4_result sgp4_batch_graph_destroy(void* graph);
  *   records    the record set built by sgp4_init from those elements
  *   tsince     as in sgp4_propagate ([t_count] or [n][t_count] with grid_per_sat)
  *   precision  SGP4_FP64: grad_r / grad_v are double and the sweep runs in FP64;
- *              SGP4_FP32: they are float and the sweep runs in FP32 (angle sums in
- *              FP64), accumulated in FP64
+ *              SGP4_FP32: they are float and the sweep runs in FP32 (the n*t phase
+ *              in double-float, states near a status threshold in FP64, as in
+ *              sgp4_propagate); per-thread and per-warp sums in FP32, the sum over
+ *              warps in FP64
  *   grad_r     [n][t_count][3] (may be NULL: zero); grad_v likewise
  *   grad_elements  [n][7] double out
  *   workspace  device, sgp4_adjoint_workspace_bytes(n) bytes, 8-byte aligned
@@ -265,12 +267,18 @@ sgp4_result sgp4_adjoint(const double* elements, const sgp4_records* records,
  *   lambda        [n] double, damping (>= 0)
  *   elements_out  [n][7] double (may not alias elements)
  *   sse           [n] double out: sum of squared residuals at `elements`, km^2
+ *   workspace     device, sgp4_fit_workspace_bytes(n) bytes, 8-byte aligned (holds
+ *                 the Jacobian of sgp4init per satellite during the call)
+ * SGP4_FP32 runs the sweeps in FP32 as sgp4_adjoint does and forms A and b per thread
+ * in FP32 (sums over warps in FP64); the Cholesky solve is FP64 in both precisions.
  * Unusable records keep their elements and get sse 0.  Errors as sgp4_adjoint.
  */
+size_t sgp4_fit_workspace_bytes(int64_t n);
 sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
                           const double* tsince, int64_t t_count, int grid_per_sat,
                           sgp4_precision precision, const double* r_obs, const double* lambda,
-                          double* elements_out, double* sse, void* stream);
+                          double* elements_out, double* sse, void* workspace,
+                          size_t workspace_bytes, void* stream);
 
 /*
  * Batched propagation without any device allocation by the caller.  The paper has

@@ -29,7 +29,7 @@ EXPORTS = (
     "sgp4_propagate", "sgp4_batch_workspace_bytes", "sgp4_batch_plan_init",
     "sgp4_propagate_batched", "sgp4_batch_graph_create", "sgp4_batch_graph_launch",
     "sgp4_batch_graph_destroy", "sgp4_propagate_batched_static", "sgp4_adjoint_workspace_bytes",
-    "sgp4_adjoint", "sgp4_fit_step",
+    "sgp4_adjoint", "sgp4_fit_workspace_bytes", "sgp4_fit_step",
 )
 STATIC_MAX_REQUESTS = 1024
 
@@ -103,7 +103,9 @@ def _declare(lib):
     lib.sgp4_adjoint_workspace_bytes.restype = ctypes.c_size_t
     lib.sgp4_adjoint.argtypes = [P, R, P, I64, I32, I32, P, P, P, P, ctypes.c_size_t, P]
     lib.sgp4_adjoint.restype = I32
-    lib.sgp4_fit_step.argtypes = [P, R, P, I64, I32, I32, P, P, P, P, P]
+    lib.sgp4_fit_workspace_bytes.argtypes = [I64]
+    lib.sgp4_fit_workspace_bytes.restype = ctypes.c_size_t
+    lib.sgp4_fit_step.argtypes = [P, R, P, I64, I32, I32, P, P, P, P, P, ctypes.c_size_t, P]
     lib.sgp4_fit_step.restype = I32
     return lib
 

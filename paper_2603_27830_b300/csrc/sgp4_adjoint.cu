@@ -4,18 +4,27 @@
 // for el = (n0, e0, i0, RAAN0, argp0, M0, B*), through propagation and sgp4init
 // (the paper's differentiable propagator, Sec. 5).
 //
-// Two kernels:
-//  * adjoint_prop_kernel: one block per satellite; each thread recomputes its
-//    states forward and runs the hand-written reverse sweep of the propagation,
-//    accumulating the adjoints of the 33 record fields the propagation reads (per
-//    thread columns in shared memory, then a column sum).  The Kepler solve is
-//    differentiated at its root (implicit function theorem), the clamps and
-//    threshold decisions are constants of the sweep.
+// Kernels:
+//  * adjoint_prop_kernel: one block per satellite; each thread recomputes its states
+//    forward (forward64 / forward32, the same formulations as the propagation
+//    kernels) and runs the hand-written reverse sweep of the propagation, giving the
+//    adjoints of the 33 record fields the propagation reads.  A thread sums them over
+//    its states in registers, a warp in a shuffle tree, and the warps' partial sums
+//    are added in FP64.  The Kepler solve is differentiated at its root (implicit
+//    function theorem); the clamps and threshold decisions are constants of the sweep.
 //  * adjoint_init_kernel: one thread per satellite pushes the 7 element directions
 //    through sgp4init with dual numbers (the record build is per satellite, so
 //    forward mode costs nothing next to the per-state sweep) and contracts the
 //    record-field Jacobian with the accumulated field adjoints.
+//  * fit_jacobian_kernel + fit_step_kernel: one Levenberg-Marquardt step of batch
+//    least squares per satellite (three reverse sweeps per state after one forward).
 // States whose status is 1, 2 or 4 (NaN output) contribute nothing.
+//
+// The FP32 variants run every per-state operation in FP32 (with the double-float
+// n*t phase of the FP32 propagation) and use FP64 only to add the warps' partial sums
+// and for states inside the FP32 path's guard bands, which go through the FP64 sweep
+// as in the propagation.  On B300 the FP64 unit retires a warp instruction per tens of
+// cycles, so a handful of FP64 operations per state would bound the whole kernel.
 #include <cmath>
 #include <cstdint>
 
@@ -36,314 +45,487 @@ enum AdjField {
 };
 
 constexpr int kAdjThreads = 128;
+constexpr int kAdjWarps = kAdjThreads / 32;
 
-__device__ __forceinline__ void sc(double x, double& s, double& c) { sincos(x, &s, &c); }
-__device__ __forceinline__ void sc(float x, float& s, float& c) { sincosf(x, &s, &c); }
-
-// Forward recomputation and reverse sweep of one state in precision T.  Adds the
-// adjoint of every record field into acc[f * kAdjThreads].  Returns the status.
+// Values of the forward pass of one state that the reverse sweep reads (names as in
+// the propagation: a, e, a_xN, a_yN, E, p_L, r, u and the short-period terms).
 template <class T>
-__device__ int adjoint_state(const Rec64& rc, const Geo& g, double t, const T gr[3],
-                             const T gv[3], double* acc, T* r_out = nullptr) {
+struct Fwd {
+  T tt, t2, t3, t4;
+  T sMdf, cMdf, c, sMM, cMM;   // sin/cos M_DF, 1 + eta cos M_DF, sin/cos(M_DF + dd)
+  T tempa, templ, a, sqa, n, e, om, q, sw, cw, axn, ayn;
+  bool clamped;                // e was raised to 1e-6
+  T sp, cp, ecosE, esinE, eL2, pL, rl, rdotl, sqp, rfdotl, betal, opb, w, aor, As, Ac;
+  T sinu, cosu, sin2u, cos2u, k, kp, fac, rk, nk, rdotk, rfdotk;
+  T su, cu, sO, cO, si, ci, mx, my, mz, Ux, Uy, Uz, Vx, Vy, Vz;
+};
+
+// Per-satellite constants of the reverse sweep.
+template <class T>
+struct RevC {
+  T bc5, sinm0, mcf, delm0, eta, a0pp, xke, n0pp, xlcof, aycof;
+  T x3thm1, x1mth2, x7thm1, cosi, sini, re, vk;
+  bool isimp;
+};
+
+__device__ __forceinline__ RevC<double> rev_consts(const Rec64& rc, const Geo& g) {
+  RevC<double> k;
+  k.bc5 = rc.bc5; k.sinm0 = rc.sinm0; k.mcf = rc.m_cf; k.delm0 = rc.delm0; k.eta = rc.eta;
+  k.a0pp = rc.a0pp; k.xke = g.xke; k.n0pp = rc.n0pp; k.xlcof = rc.xlcof; k.aycof = rc.aycof;
+  k.x3thm1 = rc.x3thm1; k.x1mth2 = rc.x1mth2; k.x7thm1 = rc.x7thm1;
+  k.cosi = rc.cosi; k.sini = rc.sini; k.re = g.re; k.vk = g.vkmps;
+  k.isimp = rc.flags & kFlagIsimp;
+  return k;
+}
+
+__device__ __forceinline__ RevC<float> rev_consts(const Rec32& rc, const GeoF& g) {
+  RevC<float> k;
+  k.bc5 = rc.bc5; k.sinm0 = rc.sinm0; k.mcf = rc.mcf; k.delm0 = rc.delm0; k.eta = rc.eta;
+  k.a0pp = rc.a0pp; k.xke = g.xke; k.n0pp = rc.n0ppr * kTwoPiF; k.xlcof = rc.xlcof;
+  k.aycof = rc.aycof; k.x3thm1 = rc.x3thm1_15 * (1.0f / 1.5f); k.x1mth2 = rc.x1mth2;
+  k.x7thm1 = rc.x7thm1_m025 * -4.0f; k.cosi = rc.cosi; k.sini = rc.sini; k.re = g.re;
+  k.vk = g.vkmps;
+  k.isimp = rc.flags & kFlagIsimp;
+  return k;
+}
+
+// The position and velocity unit vectors U, V and the rest of the output frame.
+template <class T>
+__device__ __forceinline__ void frame(Fwd<T>& f) {
+  f.mx = -f.sO * f.ci; f.my = f.cO * f.ci; f.mz = f.si;
+  f.Ux = f.mx * f.su + f.cO * f.cu; f.Uy = f.my * f.su + f.sO * f.cu; f.Uz = f.mz * f.su;
+  f.Vx = f.mx * f.cu - f.cO * f.su; f.Vy = f.my * f.cu - f.sO * f.su; f.Vz = f.mz * f.cu;
+}
+
+// Forward pass of one state in FP64: the formulation of state64 (angle reduction by
+// trunc, small rotations instead of atan2 and three sincos), keeping what the reverse
+// sweep reads.  Returns the status code.
+__device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t,
+                                         Fwd<double>& f) {
   const int fatal = (rc.flags >> kFatalShift) & 0xff;
   if (fatal) return fatal;
   if (rc.flags & kFlagN0ppNonPos) return 2;
   const bool isimp = rc.flags & kFlagIsimp;
-  const T one = T(1), two = T(2), half = T(0.5);
-
-  // ------------------------------------------------------------------ forward
-  // The angle sums (which grow as n t) in FP64; everything else in T.
-  const double mdf_d = rc.m0 + rc.mdot * t;
-  const double argpdf_d = rc.argp0 + rc.argpdot * t;
-  const double t2d = t * t;
-  const double raan1_d = rc.raan0 + rc.raandot * t + rc.raan_cf * t2d;
-  const T tt = T(t), t2 = T(t2d), t3 = t2 * tt, t4 = t3 * tt;
-  const T c1 = T(rc.c1), bc4 = T(rc.bc4), l2 = T(rc.l2);
-  T tempa = one - c1 * tt;
-  T tempe = bc4 * tt;
-  T templ = l2 * t2;
-  T sMdf = T(0), cMdf = T(0), c = one, dm = T(0), sMM = T(0), cMM = T(0);
-  double mm1_d = mdf_d, argp1_d = argpdf_d;
-  const T eta = T(rc.eta), mcf = T(rc.m_cf), delm0 = T(rc.delm0), bc5 = T(rc.bc5);
-  const T d2 = T(rc.d2), d3 = T(rc.d3), d4 = T(rc.d4), l3 = T(rc.l3), l4 = T(rc.l4);
-  const T l5 = T(rc.l5), sinm0 = T(rc.sinm0), argpcf = T(rc.argp_cf);
+  const double mdf = rc.m0 + rc.mdot * t;
+  const double argpdf = rc.argp0 + rc.argpdot * t;
+  f.tt = t; f.t2 = t * t; f.t3 = f.t2 * t; f.t4 = f.t3 * t;
+  double raan = rc.raan0 + rc.raandot * t + rc.raan_cf * f.t2;
+  double argp = argpdf;
+  double tempa = 1.0 - rc.c1 * t;
+  double tempe = rc.bc4 * t;
+  double templ = rc.l2 * f.t2;
+  f.sMdf = 0.0; f.cMdf = 0.0; f.c = 1.0; f.sMM = 0.0; f.cMM = 0.0;
   if (!isimp) {
-    const T dargp = argpcf * tt;
-    sc(T(fmod(mdf_d, kTwoPi)), sMdf, cMdf);
-    c = one + eta * cMdf;
-    dm = mcf * (c * c * c - delm0);
-    mm1_d = mdf_d + (double)dargp + (double)dm;
-    argp1_d = argpdf_d - (double)dargp - (double)dm;
-    tempa = tempa - d2 * t2 - d3 * t3 - d4 * t4;
-    sc(T(fmod(mm1_d, kTwoPi)), sMM, cMM);
-    tempe = tempe + bc5 * (sMM - sinm0);
-    templ = templ + l3 * t3 + t4 * (l4 + tt * l5);
+    const double dargp = rc.argp_cf * t;
+    sincos(wrap_2pi(mdf), &f.sMdf, &f.cMdf);
+    f.c = 1.0 + rc.eta * f.cMdf;
+    const double dd = dargp + rc.m_cf * (f.c * f.c * f.c - rc.delm0);
+    argp = argpdf - dd;
+    tempa = tempa - rc.d2 * f.t2 - rc.d3 * f.t3 - rc.d4 * f.t4;
+    double sdd, cdd;
+    sincos(dd, &sdd, &cdd);
+    f.sMM = f.sMdf * cdd + f.cMdf * sdd;
+    f.cMM = f.cMdf * cdd - f.sMdf * sdd;
+    tempe = tempe + rc.bc5 * (f.sMM - rc.sinm0);
+    templ = templ + rc.l3 * f.t3 + f.t4 * (rc.l4 + t * rc.l5);
   }
-  const T a0pp = T(rc.a0pp), e0 = T(rc.e0);
-  const T a = a0pp * tempa * tempa;
-  const T sqa = sqrt(a);
-  const T xke = T(g.xke);
-  const T n = xke / (a * sqa);
-  const T e1 = e0 - tempe;
-  if (e1 >= one || e1 < T(-0.001)) return 1;
-  const bool clamped = e1 < T(1.0e-6);
-  const T e = clamped ? T(1.0e-6) : e1;
-  const double mm2_d = mm1_d + rc.n0pp * (double)templ;
-  const T raan = T(fmod(raan1_d, kTwoPi));
-  const T argp = T(fmod(argp1_d, kTwoPi));
-  const T mpa = T(fmod(mm2_d + argp1_d, kTwoPi));   // M + argp (the node cancels in U)
-  T sw, cw;
-  sc(argp, sw, cw);
-  const T axn = e * cw;
-  const T om = one - e * e;
-  const T qa = a * om;
-  const T q = one / qa;
-  const T aycof = T(rc.aycof), xlcof = T(rc.xlcof);
-  const T ayn = e * sw + q * aycof;
-  const T U = mpa + q * xlcof * axn;
-  T psi = U;
-  const T tol = sizeof(T) == 8 ? T(1.0e-12) : T(1.0e-6);
-  for (int k = 0; k < 10; ++k) {
-    T sp, cp;
-    sc(psi, sp, cp);
-    T step = (U - ayn * cp + axn * sp - psi) / (one - ayn * sp - axn * cp);
-    step = fmin(fmax(step, T(-0.95)), T(0.95));
+  f.tempa = tempa;
+  f.templ = templ;
+  f.a = rc.a0pp * tempa * tempa;
+  f.sqa = sqrt(f.a);
+  const double ia15 = 1.0 / (f.a * f.sqa);
+  f.n = g.xke * ia15;
+  const double e1 = rc.e0 - tempe;
+  if (e1 >= 1.0 || e1 < -0.001) return 1;
+  f.clamped = e1 < 1.0e-6;
+  f.e = f.clamped ? 1.0e-6 : e1;
+  raan = wrap_2pi(raan);
+  argp = wrap_2pi(argp);
+  const double mpa = mdf + argpdf + rc.n0pp * templ;   // M + argp (drag terms cancel)
+  sincos(argp, &f.sw, &f.cw);
+  f.axn = f.e * f.cw;
+  f.om = 1.0 - f.e * f.e;
+  f.q = 1.0 / (f.a * f.om);
+  f.ayn = f.e * f.sw + f.q * rc.aycof;
+  const double U = wrap_2pi(mpa + f.q * rc.xlcof * f.axn);
+  f.eL2 = f.axn * f.axn + f.ayn * f.ayn;
+  double psi = U, sp = 0.0, cp = 1.0, step = 0.0;
+  const int K = newton_steps64(f.eL2);
+  for (int k = 0; k < K; ++k) {
+    sincos(psi, &sp, &cp);
+    step = (U - f.ayn * cp + f.axn * sp - psi) / (1.0 - f.ayn * sp - f.axn * cp);
+    step = fmin(fmax(step, -0.95), 0.95);
     psi += step;
-    if (fabs(step) < tol) break;
+    if (K == 10 && fabs(step) < 1.0e-12) break;
   }
-  T sp, cp;
-  sc(psi, sp, cp);
-  const T ecosE = axn * cp + ayn * sp;
-  const T esinE = axn * sp - ayn * cp;
-  const T eL2 = axn * axn + ayn * ayn;
-  const T pL = a * (one - eL2);
-  if (pL < T(0)) return 4;
-  const T rl = a * (one - ecosE);
-  const T rdotl = sqa * esinE / rl;
-  const T sqp = sqrt(pL);
-  const T rfdotl = sqp / rl;
-  const T betal = sqrt(one - eL2);
-  const T opb = one + betal;
-  const T w = esinE / opb;
-  const T aor = a / rl;
-  const T As = sp - ayn - axn * w;
-  const T Ac = cp - axn + ayn * w;
-  const T sinu = aor * As, cosu = aor * Ac;
-  const T u = atan2(sinu, cosu);
-  const T sin2u = two * cosu * sinu;
-  const T cos2u = one - two * sinu * sinu;
-  const T j2 = T(g.j2);
-  const T k = half * j2 / pL;
-  const T kp = k / pL;
-  const T x3thm1 = T(rc.x3thm1), x1mth2 = T(rc.x1mth2), x7thm1 = T(rc.x7thm1);
-  const T cosi = T(rc.cosi), sini = T(rc.sini), i0 = T(rc.i0);
-  const T fac = one - T(1.5) * kp * betal * x3thm1;
-  const T rk = rl * fac + half * k * x1mth2 * cos2u;
-  const T uk = u - T(0.25) * kp * x7thm1 * sin2u;
-  const T raank = raan + T(1.5) * kp * cosi * sin2u;
-  const T ik = i0 + T(1.5) * kp * cosi * sini * cos2u;
-  const T nk = n * k / xke;
-  const T rdotk = rdotl - nk * x1mth2 * sin2u;
-  const T rfdotk = rfdotl + nk * (x1mth2 * cos2u + T(1.5) * x3thm1);
-  T su, cu, sO, cO, si, ci;
-  sc(uk, su, cu);
-  sc(raank, sO, cO);
-  sc(ik, si, ci);
-  const T mx = -sO * ci, my = cO * ci, mz = si;
-  const T Ux = mx * su + cO * cu, Uy = my * su + sO * cu, Uz = mz * su;
-  const T Vx = mx * cu - cO * su, Vy = my * cu - sO * su, Vz = mz * cu;
-  const int code = rk < one ? 6 : 0;
-  if (r_out) {
-    r_out[0] = rk * T(g.re) * Ux;
-    r_out[1] = rk * T(g.re) * Uy;
-    r_out[2] = rk * T(g.re) * Uz;
-  }
+  rotate64(sp, cp, step);
+  f.sp = sp; f.cp = cp;
+  f.ecosE = f.axn * cp + f.ayn * sp;
+  f.esinE = f.axn * sp - f.ayn * cp;
+  f.pL = f.a * (1.0 - f.eL2);
+  if (f.pL < 0.0) return 4;
+  f.rl = f.a * (1.0 - f.ecosE);
+  const double invr = 1.0 / f.rl;
+  f.rdotl = f.sqa * f.esinE * invr;
+  f.sqp = sqrt(f.pL);
+  f.rfdotl = f.sqp * invr;
+  f.betal = sqrt(1.0 - f.eL2);
+  f.opb = 1.0 + f.betal;
+  f.w = f.esinE / f.opb;
+  f.aor = f.a * invr;
+  f.As = sp - f.ayn - f.axn * f.w;
+  f.Ac = cp - f.axn + f.ayn * f.w;
+  f.sinu = f.aor * f.As;
+  f.cosu = f.aor * f.Ac;
+  f.sin2u = 2.0 * f.cosu * f.sinu;
+  f.cos2u = 1.0 - 2.0 * f.sinu * f.sinu;
+  const double invp = 1.0 / f.pL;
+  f.k = 0.5 * g.j2 * invp;
+  f.kp = f.k * invp;
+  f.fac = 1.0 - 1.5 * f.kp * f.betal * rc.x3thm1;
+  f.rk = f.rl * f.fac + 0.5 * f.k * rc.x1mth2 * f.cos2u;
+  f.nk = ia15 * f.k;
+  f.rdotk = f.rdotl - f.nk * rc.x1mth2 * f.sin2u;
+  f.rfdotk = f.rfdotl + f.nk * (rc.x1mth2 * f.cos2u + 1.5 * rc.x3thm1);
+  const double nrm = 1.0 / sqrt(f.sinu * f.sinu + f.cosu * f.cosu);
+  f.su = f.sinu * nrm; f.cu = f.cosu * nrm;
+  rotate64(f.su, f.cu, -0.25 * f.kp * rc.x7thm1 * f.sin2u);
+  sincos(raan, &f.sO, &f.cO);
+  rotate64(f.sO, f.cO, 1.5 * f.kp * rc.cosi * f.sin2u);
+  f.si = rc.sini; f.ci = rc.cosi;
+  rotate64(f.si, f.ci, 1.5 * f.kp * rc.cosi * rc.sini * f.cos2u);
+  frame(f);
+  return f.rk < 1.0 ? 6 : 0;
+}
 
-  // ------------------------------------------------------------------ reverse
-  const T re = T(g.re), vk = T(g.vkmps);
-  const T Ubx = rk * re * gr[0] + vk * rdotk * gv[0];
-  const T Uby = rk * re * gr[1] + vk * rdotk * gv[1];
-  const T Ubz = rk * re * gr[2] + vk * rdotk * gv[2];
-  const T Vbx = vk * rfdotk * gv[0], Vby = vk * rfdotk * gv[1], Vbz = vk * rfdotk * gv[2];
-  const T rkb = re * (gr[0] * Ux + gr[1] * Uy + gr[2] * Uz);
-  const T rdotkb = vk * (gv[0] * Ux + gv[1] * Uy + gv[2] * Uz);
-  const T rfdotkb = vk * (gv[0] * Vx + gv[1] * Vy + gv[2] * Vz);
-  // U = M su + N cu, V = M cu - N su, M = (mx, my, mz), N = (cO, sO, 0)
-  const T Mbx = Ubx * su + Vbx * cu, Mby = Uby * su + Vby * cu, Mbz = Ubz * su + Vbz * cu;
-  const T Nbx = Ubx * cu - Vbx * su, Nby = Uby * cu - Vby * su;
-  const T sub = Ubx * mx + Uby * my + Ubz * mz - (Vbx * cO + Vby * sO);
-  const T cub = Ubx * cO + Uby * sO + (Vbx * mx + Vby * my + Vbz * mz);
-  const T sOb = -Mbx * ci + Nby;
-  const T cOb = Mby * ci + Nbx;
-  const T cib = -Mbx * sO + Mby * cO;
-  const T sib = Mbz;
-  const T ukb = sub * cu - cub * su;
-  const T raankb = sOb * cO - cOb * sO;
-  const T ikb = sib * ci - cib * si;
-  // rdot_k, rfdot_k
-  const T rdotlb = rdotkb, rfdotlb = rfdotkb;
-  const T nkb = -rdotkb * x1mth2 * sin2u + rfdotkb * (x1mth2 * cos2u + T(1.5) * x3thm1);
-  T x1mth2b = -rdotkb * nk * sin2u + rfdotkb * nk * cos2u;
-  T sin2ub = -rdotkb * nk * x1mth2;
-  T cos2ub = rfdotkb * nk * x1mth2;
-  T x3thm1b = rfdotkb * nk * T(1.5);
-  const T nb = nkb * k / xke;
-  T kb = nkb * n / xke;
-  // i_k, RAAN_k, u_k
-  const T i0b = ikb;
-  T kpb = ikb * T(1.5) * cosi * sini * cos2u;
-  T cosib = ikb * T(1.5) * kp * sini * cos2u;
-  const T sinib = ikb * T(1.5) * kp * cosi * cos2u;
-  cos2ub += ikb * T(1.5) * kp * cosi * sini;
-  const T raanb = raankb;
-  kpb += raankb * T(1.5) * cosi * sin2u;
-  cosib += raankb * T(1.5) * kp * sin2u;
-  sin2ub += raankb * T(1.5) * kp * cosi;
-  const T ub = ukb;
-  kpb += -ukb * T(0.25) * x7thm1 * sin2u;
-  const T x7thm1b = -ukb * T(0.25) * kp * sin2u;
-  sin2ub += -ukb * T(0.25) * kp * x7thm1;
-  // r_k
-  T rlb = rkb * fac;
-  kpb += -rkb * rl * T(1.5) * betal * x3thm1;
-  T betalb = -rkb * rl * T(1.5) * kp * x3thm1;
-  x3thm1b += -rkb * rl * T(1.5) * kp * betal;
-  kb += rkb * half * x1mth2 * cos2u;
-  x1mth2b += rkb * half * k * cos2u;
-  cos2ub += rkb * half * k * x1mth2;
-  // kp = k / pL, k = j2 / (2 pL)
-  kb += kpb / pL;
-  T pLb = -kpb * kp / pL;
-  pLb += -kb * k / pL;
-  // sin 2u, cos 2u, u = atan2(sin u, cos u)
-  T sinub = two * cosu * sin2ub - T(4) * sinu * cos2ub;
-  T cosub = two * sinu * sin2ub;
-  const T den = sinu * sinu + cosu * cosu;
-  sinub += ub * cosu / den;
-  cosub += -ub * sinu / den;
-  // sin u = aor As, cos u = aor Ac
-  const T aorb = sinub * As + cosub * Ac;
-  const T Asb = sinub * aor, Acb = cosub * aor;
-  T spb = Asb, cpb = Acb;
-  T aynb = -Asb + Acb * w;
-  T axnb = -Asb * w - Acb;
-  const T wb = -Asb * axn + Acb * ayn;
-  T ab = aorb / rl;
-  rlb += -aorb * aor / rl;
-  T esinEb = wb / opb;
-  betalb += -wb * w / opb;
-  T eL2b = -betalb * half / betal;
-  const T sqpb = rfdotlb / rl;
-  rlb += -rfdotlb * rfdotl / rl;
-  pLb += sqpb * half / sqp;
-  T sqab = rdotlb * esinE / rl;
-  esinEb += rdotlb * sqa / rl;
-  rlb += -rdotlb * rdotl / rl;
-  ab += rlb * (one - ecosE);
-  const T ecosEb = -rlb * a;
-  ab += pLb * (one - eL2);
-  eL2b += -pLb * a;
-  axnb += two * axn * eL2b;
-  aynb += two * ayn * eL2b;
-  axnb += esinEb * sp;
-  spb += esinEb * axn;
-  aynb += -esinEb * cp;
-  cpb += -esinEb * ayn;
-  axnb += ecosEb * cp;
-  cpb += ecosEb * axn;
-  aynb += ecosEb * sp;
-  spb += ecosEb * ayn;
-  // Kepler at its root: psi - axn sin psi + ayn cos psi = U
-  const T psib = spb * cp - cpb * sp;
-  const T D = one - axn * cp - ayn * sp;
-  const T Ub = psib / D;
-  axnb += psib * sp / D;
-  aynb += -psib * cp / D;
-  // U = (M + argp) + q xlcof axn
-  const T mpab = Ub;
-  T qb = Ub * xlcof * axn;
-  const T xlcofb = Ub * q * axn;
-  axnb += Ub * q * xlcof;
-  // a_yN = e sin argp + q aycof
-  T eb = aynb * sw;
-  const T swb = aynb * e;
-  qb += aynb * aycof;
-  const T aycofb = aynb * q;
-  // q = 1 / (a (1 - e^2))
-  const T qab = -qb * q * q;
-  ab += qab * om;
-  eb += -two * e * (qab * a);
-  // a_xN = e cos argp
-  eb += axnb * cw;
-  const T cwb = axnb * e;
-  const T argpb = swb * cw - cwb * sw;
-  // angles: mpa = mm2 + argp1, argp = argp1, raan = raan1 (mod 2 pi)
-  const T mm2b = mpab;
-  const T argp1b = mpab + argpb;
-  const T raan1b = raanb;
-  T mm1b = mm2b;
-  const T n0ppb = mm2b * templ;
-  const T templb = mm2b * T(rc.n0pp);
-  const T e1b = clamped ? T(0) : eb;
-  const T e0b = e1b;
-  const T tempeb = -e1b;
-  ab += nb * T(-1.5) * n / a;
-  ab += sqab * half / sqa;
-  const T a0ppb = ab * tempa * tempa;
-  const T tempab = ab * a0pp * two * tempa;
-  T mdfb, argpdfb;
+// Forward pass of one state in FP32: the formulation and guard bands of state32
+// (double-float n*t phase, bound-based Newton count, small rotations).  Returns the
+// status code, or kRecomputeFP64 for a state inside a guard band.
+__device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float th, float tl,
+                                         Fwd<float>& f) {
+  const int fatal = (rc.flags >> kFatalShift) & 0xff;
+  if (fatal) return fatal;
+  if (rc.flags & kFlagN0ppNonPos) return 2;
+  const bool isimp = rc.flags & kFlagIsimp;
+  const float t = th;
+  f.tt = t; f.t2 = t * t; f.t3 = f.t2 * t; f.t4 = f.t3 * t;
+  float tempa = 1.0f - rc.c1 * t;
+  float tempe = rc.bc4 * t;
+  float templ = rc.l2 * f.t2;
+  float dd = 0.0f;
+  f.sMdf = 0.0f; f.cMdf = 0.0f; f.c = 1.0f; f.sMM = 0.0f; f.cMM = 0.0f;
   if (!isimp) {
-    acc[aL3 * kAdjThreads] += (double)(templb * t3);
-    acc[aL4 * kAdjThreads] += (double)(templb * t4);
-    acc[aL5 * kAdjThreads] += (double)(templb * t4 * tt);
-    acc[aBC5 * kAdjThreads] += (double)(tempeb * (sMM - sinm0));
-    const T sMMb = tempeb * bc5;
-    acc[aSinM0 * kAdjThreads] += (double)(-tempeb * bc5);
-    acc[aD2 * kAdjThreads] += (double)(-tempab * t2);
-    acc[aD3 * kAdjThreads] += (double)(-tempab * t3);
-    acc[aD4 * kAdjThreads] += (double)(-tempab * t4);
-    mm1b += sMMb * cMM;
-    mdfb = mm1b;
-    argpdfb = argp1b;
-    const T dargpb = mm1b - argp1b;
-    const T dmb = mm1b - argp1b;
-    acc[aMCf * kAdjThreads] += (double)(dmb * (c * c * c - delm0));
-    const T cb = dmb * mcf * T(3) * c * c;
-    acc[aDelM0 * kAdjThreads] += (double)(-dmb * mcf);
-    acc[aEta * kAdjThreads] += (double)(cb * cMdf);
-    mdfb += -(cb * eta) * sMdf;
-    acc[aArgpCf * kAdjThreads] += (double)(dargpb * tt);
-  } else {
-    mdfb = mm1b;
-    argpdfb = argp1b;
+    const float dargp = rc.argpcf * t;
+    const float mdf = wrap_rev(fmaf(rc.mdr, t, rc.m0r)) * kTwoPiF;
+    __sincosf(mdf, &f.sMdf, &f.cMdf);
+    f.c = 1.0f + rc.eta * f.cMdf;
+    dd = dargp + rc.mcf * (f.c * f.c * f.c - rc.delm0);
+    tempa = tempa - rc.d2 * f.t2 - rc.d3 * f.t3 - rc.d4 * f.t4;
+    __sincosf(mdf + dd, &f.sMM, &f.cMM);
+    tempe = tempe + rc.bc5 * (f.sMM - rc.sinm0);
+    templ = templ + rc.l3 * f.t3 + f.t4 * (rc.l4 + t * rc.l5);
   }
-  acc[aL2 * kAdjThreads] += (double)(templb * t2);
-  acc[aBC4 * kAdjThreads] += (double)(tempeb * tt);
-  acc[aC1 * kAdjThreads] += (double)(-tempab * tt);
-  acc[aRaan0 * kAdjThreads] += (double)raan1b;
-  acc[aRaandot * kAdjThreads] += (double)raan1b * t;
-  acc[aRaanCf * kAdjThreads] += (double)raan1b * t2d;
-  acc[aArgp0 * kAdjThreads] += (double)argpdfb;
-  acc[aArgpdot * kAdjThreads] += (double)argpdfb * t;
-  acc[aM0 * kAdjThreads] += (double)mdfb;
-  acc[aMdot * kAdjThreads] += (double)mdfb * t;
-  acc[aN0pp * kAdjThreads] += (double)n0ppb;
-  acc[aA0pp * kAdjThreads] += (double)a0ppb;
-  acc[aE0 * kAdjThreads] += (double)e0b;
-  acc[aI0 * kAdjThreads] += (double)i0b;
-  acc[aXlcof * kAdjThreads] += (double)xlcofb;
-  acc[aAycof * kAdjThreads] += (double)aycofb;
-  acc[aCosi * kAdjThreads] += (double)cosib;
-  acc[aSini * kAdjThreads] += (double)sinib;
-  acc[aX3thm1 * kAdjThreads] += (double)x3thm1b;
-  acc[aX1mth2 * kAdjThreads] += (double)x1mth2b;
-  acc[aX7thm1 * kAdjThreads] += (double)x7thm1b;
+  f.tempa = tempa;
+  f.templ = templ;
+  f.a = rc.a0pp * tempa * tempa;
+  const float e1 = rc.e0 - tempe;
+  if (!(fabsf(e1 - 1.0f) >= kGuardE && fabsf(e1 + 0.001f) >= kGuardE && f.a > 1.0e-3f))
+    return kRecomputeFP64;
+  if (e1 >= 1.0f || e1 < -0.001f) return 1;
+  f.clamped = e1 < 1.0e-6f;
+  f.e = fmaxf(e1, 1.0e-6f);
+  const float ra = rsqrtf(f.a);
+  f.sqa = f.a * ra;
+  const float ra3 = ra * ra * ra;
+  f.n = g.xke * ra3;
+
+  float p = rc.phidh * th;
+  const float pe = fmaf(rc.phidh, th, -p);
+  const float s = fmaf(rc.phidh, tl, fmaf(rc.phidl, th, pe));
+  p = p - round_magic(p);
+  float y = wrap_rev(p + rc.phi0h);
+  y += s + rc.phi0l;
+  y += wrap_rev(rc.n0ppr * templ);
+  const float argp = wrap_rev(fmaf(rc.argpdr, t, rc.argp0r) - dd * kInvTwoPiF) * kTwoPiF;
+  const float raan = wrap_rev(fmaf(rc.raancfr, f.t2, fmaf(rc.raandr, t, rc.raan0r))) * kTwoPiF;
+
+  __sincosf(argp, &f.sw, &f.cw);
+  f.axn = f.e * f.cw;
+  f.om = 1.0f - f.e * f.e;
+  f.q = rcp_pos(f.a * f.om);
+  f.ayn = fmaf(f.e, f.sw, f.q * rc.aycof);
+  const float U = wrap_rev(y + f.q * rc.xlcof * f.axn * kInvTwoPiF) * kTwoPiF;
+  f.eL2 = f.axn * f.axn + f.ayn * f.ayn;
+  float psi = U;
+  const int K = newton_steps(f.eL2);
+  for (int k = 0; k < K; ++k) {
+    float sp, cp;
+    __sincosf(psi, &sp, &cp);
+    const float fv = U - f.ayn * cp + f.axn * sp - psi;
+    const float fp = 1.0f - f.ayn * sp - f.axn * cp;
+    psi += fminf(fmaxf(fv * rcp_pos(fp), -0.95f), 0.95f);
+  }
+  sincos_acc(psi, &f.sp, &f.cp);
+  f.ecosE = f.axn * f.cp + f.ayn * f.sp;
+  f.esinE = f.axn * f.sp - f.ayn * f.cp;
+  f.pL = f.a * (1.0f - f.eL2);
+  if (!(fabsf(f.pL) >= kGuardP)) return kRecomputeFP64;
+  if (f.pL < 0.0f) return 4;
+  f.rl = f.a * (1.0f - f.ecosE);
+  const float invr = rcp_pos(f.rl);
+  f.rdotl = f.sqa * f.esinE * invr;
+  const float rpl = rsqrtf(f.pL);
+  f.sqp = f.pL * rpl;
+  f.rfdotl = f.sqp * invr;
+  const float omel = 1.0f - f.eL2;
+  f.betal = omel * rsqrtf(omel);
+  f.opb = 1.0f + f.betal;
+  f.w = f.esinE * rcp_pos(f.opb);
+  f.aor = f.a * invr;
+  f.As = f.sp - f.ayn - f.axn * f.w;
+  f.Ac = f.cp - f.axn + f.ayn * f.w;
+  f.sinu = f.aor * f.As;
+  f.cosu = f.aor * f.Ac;
+  f.sin2u = 2.0f * f.cosu * f.sinu;
+  f.cos2u = 1.0f - 2.0f * f.sinu * f.sinu;
+  const float invp = rpl * rpl;
+  f.k = g.half_j2 * invp;
+  f.kp = f.k * invp;
+  f.fac = fmaf(-f.kp * f.betal, rc.x3thm1_15, 1.0f);
+  f.rk = f.rl * f.fac + f.k * rc.half_x1mth2 * f.cos2u;
+  if (!(fabsf(f.rk - 1.0f) >= kGuardR)) return kRecomputeFP64;
+  f.nk = ra3 * f.k;
+  f.rdotk = f.rdotl - f.nk * rc.x1mth2 * f.sin2u;
+  f.rfdotk = fmaf(f.nk, fmaf(rc.x1mth2, f.cos2u, rc.x3thm1_15), f.rfdotl);
+  const float du = f.kp * rc.x7thm1_m025 * f.sin2u;
+  const float dO = f.kp * rc.c15cosi * f.sin2u;
+  const float di = f.kp * rc.c15cosisini * f.cos2u;
+  if (!(fmaxf(fabsf(du), fmaxf(fabsf(dO), fabsf(di))) < 4.0e-3f)) return kRecomputeFP64;
+  const float nrm = rsqrtf(f.sinu * f.sinu + f.cosu * f.cosu);
+  f.su = f.sinu * nrm; f.cu = f.cosu * nrm;
+  rotate_small(f.su, f.cu, du);
+  __sincosf(raan, &f.sO, &f.cO);
+  rotate_small(f.sO, f.cO, dO);
+  f.si = rc.sini; f.ci = rc.cosi;
+  rotate_small(f.si, f.ci, di);
+  frame(f);
+  return f.rk < 1.0f ? 6 : 0;
+}
+
+// Reverse sweep of one state: the adjoints of the 33 record fields, given the forward
+// values f and the output adjoints gr (of r, km) and gv (of v, km/s).  Each field's
+// adjoint goes to sink(field, value) as soon as it is final (fields that do not
+// depend on the state, such as the drag terms of a simplified-drag record, are not
+// passed), so that no array of 33 adjoints has to stay live through the sweep.
+template <class T, class Sink>
+__device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, const T gr[3],
+                                        const T gv[3], Sink&& sink) {
+  const T one = T(1), two = T(2), half = T(0.5), c15 = T(1.5);
+  const T re = rc.re, vk = rc.vk;
+  // r = rk re U, v = vk (rdotk U + rfdotk V)
+  const T Ubx = f.rk * re * gr[0] + vk * f.rdotk * gv[0];
+  const T Uby = f.rk * re * gr[1] + vk * f.rdotk * gv[1];
+  const T Ubz = f.rk * re * gr[2] + vk * f.rdotk * gv[2];
+  const T Vbx = vk * f.rfdotk * gv[0], Vby = vk * f.rfdotk * gv[1], Vbz = vk * f.rfdotk * gv[2];
+  const T rkb = re * (gr[0] * f.Ux + gr[1] * f.Uy + gr[2] * f.Uz);
+  const T rdotkb = vk * (gv[0] * f.Ux + gv[1] * f.Uy + gv[2] * f.Uz);
+  const T rfdotkb = vk * (gv[0] * f.Vx + gv[1] * f.Vy + gv[2] * f.Vz);
+  // U = M su + N cu, V = M cu - N su, M = (mx, my, mz), N = (cO, sO, 0)
+  const T Mbx = Ubx * f.su + Vbx * f.cu, Mby = Uby * f.su + Vby * f.cu;
+  const T Mbz = Ubz * f.su + Vbz * f.cu;
+  const T Nbx = Ubx * f.cu - Vbx * f.su, Nby = Uby * f.cu - Vby * f.su;
+  const T sub = Ubx * f.mx + Uby * f.my + Ubz * f.mz - (Vbx * f.cO + Vby * f.sO);
+  const T cub = Ubx * f.cO + Uby * f.sO + (Vbx * f.mx + Vby * f.my + Vbz * f.mz);
+  const T sOb = -Mbx * f.ci + Nby;
+  const T cOb = Mby * f.ci + Nbx;
+  const T cib = -Mbx * f.sO + Mby * f.cO;
+  const T sib = Mbz;
+  const T ukb = sub * f.cu - cub * f.su;       // (su, cu) = (sin u_k, cos u_k)
+  const T raankb = sOb * f.cO - cOb * f.sO;
+  const T ikb = sib * f.ci - cib * f.si;
+  // rdot_k, rfdot_k
+  const T nkb = -rdotkb * rc.x1mth2 * f.sin2u +
+                rfdotkb * (rc.x1mth2 * f.cos2u + c15 * rc.x3thm1);
+  T x1mth2b = -rdotkb * f.nk * f.sin2u + rfdotkb * f.nk * f.cos2u;
+  T sin2ub = -rdotkb * f.nk * rc.x1mth2;
+  T cos2ub = rfdotkb * f.nk * rc.x1mth2;
+  T x3thm1b = rfdotkb * f.nk * c15;
+  const T nb = nkb * f.k / rc.xke;
+  T kb = nkb * f.n / rc.xke;
+  // i_k = i0 + 1.5 kp cosi sini cos2u, RAAN_k = RAAN + 1.5 kp cosi sin2u,
+  // u_k = u - 0.25 kp x7thm1 sin2u
+  T kpb = ikb * c15 * rc.cosi * rc.sini * f.cos2u;
+  T cosib = ikb * c15 * f.kp * rc.sini * f.cos2u;
+  const T sinib = ikb * c15 * f.kp * rc.cosi * f.cos2u;
+  cos2ub += ikb * c15 * f.kp * rc.cosi * rc.sini;
+  kpb += raankb * c15 * rc.cosi * f.sin2u;
+  cosib += raankb * c15 * f.kp * f.sin2u;
+  sin2ub += raankb * c15 * f.kp * rc.cosi;
+  kpb += -ukb * T(0.25) * rc.x7thm1 * f.sin2u;
+  const T x7thm1b = -ukb * T(0.25) * f.kp * f.sin2u;
+  sin2ub += -ukb * T(0.25) * f.kp * rc.x7thm1;
+  // r_k = rl (1 - 1.5 kp betal x3thm1) + 0.5 k x1mth2 cos2u
+  T rlb = rkb * f.fac;
+  kpb += -rkb * f.rl * c15 * f.betal * rc.x3thm1;
+  T betalb = -rkb * f.rl * c15 * f.kp * rc.x3thm1;
+  x3thm1b += -rkb * f.rl * c15 * f.kp * f.betal;
+  kb += rkb * half * rc.x1mth2 * f.cos2u;
+  x1mth2b += rkb * half * f.k * f.cos2u;
+  cos2ub += rkb * half * f.k * rc.x1mth2;
+  // kp = k / pL, k = j2 / (2 pL)
+  kb += kpb / f.pL;
+  T pLb = -kpb * f.kp / f.pL;
+  pLb += -kb * f.k / f.pL;
+  // sin 2u, cos 2u, u = atan2(sin u, cos u)
+  T sinub = two * f.cosu * sin2ub - T(4) * f.sinu * cos2ub;
+  T cosub = two * f.sinu * sin2ub;
+  const T den = f.sinu * f.sinu + f.cosu * f.cosu;
+  sinub += ukb * f.cosu / den;
+  cosub += -ukb * f.sinu / den;
+  // sin u = aor As, cos u = aor Ac
+  const T aorb = sinub * f.As + cosub * f.Ac;
+  const T Asb = sinub * f.aor, Acb = cosub * f.aor;
+  T spb = Asb, cpb = Acb;
+  T aynb = -Asb + Acb * f.w;
+  T axnb = -Asb * f.w - Acb;
+  const T wb = -Asb * f.axn + Acb * f.ayn;
+  T ab = aorb / f.rl;
+  rlb += -aorb * f.aor / f.rl;
+  T esinEb = wb / f.opb;
+  betalb += -wb * f.w / f.opb;
+  T eL2b = -betalb * half / f.betal;
+  const T sqpb = rfdotkb / f.rl;
+  rlb += -rfdotkb * f.rfdotl / f.rl;
+  pLb += sqpb * half / f.sqp;
+  const T sqab = rdotkb * f.esinE / f.rl;
+  esinEb += rdotkb * f.sqa / f.rl;
+  rlb += -rdotkb * f.rdotl / f.rl;
+  ab += rlb * (one - f.ecosE);
+  const T ecosEb = -rlb * f.a;
+  ab += pLb * (one - f.eL2);
+  eL2b += -pLb * f.a;
+  axnb += two * f.axn * eL2b;
+  aynb += two * f.ayn * eL2b;
+  axnb += esinEb * f.sp;
+  spb += esinEb * f.axn;
+  aynb += -esinEb * f.cp;
+  cpb += -esinEb * f.ayn;
+  axnb += ecosEb * f.cp;
+  cpb += ecosEb * f.axn;
+  aynb += ecosEb * f.sp;
+  spb += ecosEb * f.ayn;
+  // Kepler at its root: psi - axn sin psi + ayn cos psi = U
+  const T psib = spb * f.cp - cpb * f.sp;
+  const T D = one - f.axn * f.cp - f.ayn * f.sp;
+  const T Ub = psib / D;
+  axnb += psib * f.sp / D;
+  aynb += -psib * f.cp / D;
+  // U = (M + argp) + q xlcof axn
+  T qb = Ub * rc.xlcof * f.axn;
+  sink(aXlcof, Ub * f.q * f.axn);
+  axnb += Ub * f.q * rc.xlcof;
+  // a_yN = e sin argp + q aycof
+  T eb = aynb * f.sw;
+  const T swb = aynb * f.e;
+  qb += aynb * rc.aycof;
+  sink(aAycof, aynb * f.q);
+  // q = 1 / (a (1 - e^2))
+  const T qab = -qb * f.q * f.q;
+  ab += qab * f.om;
+  eb += -two * f.e * (qab * f.a);
+  // a_xN = e cos argp
+  eb += axnb * f.cw;
+  const T cwb = axnb * f.e;
+  const T argpb = swb * f.cw - cwb * f.sw;
+  // mpa = M_DF + argp_DF + n0'' templ, argp = argp_DF - dd, RAAN = RAAN_DF + raan_cf t^2
+  const T mm2b = Ub;
+  const T argp1b = Ub + argpb;
+  sink(aN0pp, mm2b * f.templ);
+  const T templb = mm2b * rc.n0pp;
+  const T e1b = f.clamped ? T(0) : eb;
+  sink(aE0, e1b);
+  const T tempeb = -e1b;
+  ab += nb * T(-1.5) * f.n / f.a;
+  ab += sqab * half / f.sqa;
+  sink(aA0pp, ab * f.tempa * f.tempa);
+  const T tempab = ab * rc.a0pp * two * f.tempa;
+  T mdfb = mm2b, argpdfb = argp1b;
+  if (!rc.isimp) {
+    sink(aL3, templb * f.t3);
+    sink(aL4, templb * f.t4);
+    sink(aL5, templb * f.t4 * f.tt);
+    sink(aBC5, tempeb * (f.sMM - rc.sinm0));
+    const T sMMb = tempeb * rc.bc5;
+    sink(aSinM0, -tempeb * rc.bc5);
+    sink(aD2, -tempab * f.t2);
+    sink(aD3, -tempab * f.t3);
+    sink(aD4, -tempab * f.t4);
+    // mm1 = M_DF + dd carries sin(mm1); argp = argp_DF - dd; dd = argp_cf t + dm
+    const T mm1b = mm2b + sMMb * f.cMM;
+    mdfb = mm1b;
+    const T ddb = mm1b - argp1b;
+    sink(aMCf, ddb * (f.c * f.c * f.c - rc.delm0));
+    const T cb = ddb * rc.mcf * T(3) * f.c * f.c;
+    sink(aDelM0, -ddb * rc.mcf);
+    sink(aEta, cb * f.cMdf);
+    mdfb += -(cb * rc.eta) * f.sMdf;
+    sink(aArgpCf, ddb * f.tt);
+  }
+  sink(aL2, templb * f.t2);
+  sink(aBC4, tempeb * f.tt);
+  sink(aC1, -tempab * f.tt);
+  sink(aRaan0, raankb);
+  sink(aRaandot, raankb * f.tt);
+  sink(aRaanCf, raankb * f.t2);
+  sink(aArgp0, argpdfb);
+  sink(aArgpdot, argpdfb * f.tt);
+  sink(aM0, mdfb);
+  sink(aMdot, mdfb * f.tt);
+  sink(aI0, ikb);
+  sink(aCosi, cosib);
+  sink(aSini, sinib);
+  sink(aX3thm1, x3thm1b);
+  sink(aX1mth2, x1mth2b);
+  sink(aX7thm1, x7thm1b);
+}
+
+__device__ __forceinline__ bool usable(int code) { return code == 0 || code == 6; }
+
+// FP64 forward and reverse sweeps of one state for the FP32 kernels (guard-band
+// states).  nseed seeds (g_r, g_v) of 6 values each in `seeds`; writes nseed x 33
+// field adjoints to bar and the position (km) to r.  Out of line: rarely taken.
+static __device__ __noinline__ int adjoint_fallback(RecordPtrs rp, Geo g, int64_t j, double t,
+                                                    const float* seeds, int nseed, float* bar,
+                                                    float* r) {
+  const Rec64 rc = load_rec64(rp, j);
+  Fwd<double> f;
+  const int code = forward64(rc, g, t, f);
+  if (!usable(code)) return code;
+  const RevC<double> k = rev_consts(rc, g);
+  for (int s = 0; s < nseed; ++s) {
+    const double gr[3] = {seeds[6 * s + 0], seeds[6 * s + 1], seeds[6 * s + 2]};
+    const double gv[3] = {seeds[6 * s + 3], seeds[6 * s + 4], seeds[6 * s + 5]};
+    float* out = bar + s * kNumAdj;
+    for (int q = 0; q < kNumAdj; ++q) out[q] = 0.0f;
+    reverse(f, k, gr, gv, [&](int q, double v) { out[q] = (float)v; });
+  }
+  r[0] = (float)(f.rk * g.re * f.Ux);
+  r[1] = (float)(f.rk * g.re * f.Uy);
+  r[2] = (float)(f.rk * g.re * f.Uz);
   return code;
+}
+
+// Warp sum of v by a shuffle tree in T; lane 0 stores it to part[idx][warp].
+template <class T>
+__device__ __forceinline__ void warp_partial(T v, int idx, T (*part)[kAdjWarps]) {
+  for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) part[idx][threadIdx.x >> 5] = v;
 }
 
 struct AdjArgs {
   RecordPtrs rp;
   Geo g;
+  GeoF gf;
   const double* tsince;
   int64_t T;
   int per_sat;
@@ -354,29 +536,85 @@ struct AdjArgs {
 
 template <class T>
 __global__ void __launch_bounds__(kAdjThreads) adjoint_prop_kernel(AdjArgs a) {
-  __shared__ double acc[kNumAdj * kAdjThreads];
+  __shared__ T part[kNumAdj][kAdjWarps];
+  constexpr bool kFP32 = sizeof(T) == 4;
   const int tid = threadIdx.x;
-  for (int f = 0; f < kNumAdj; ++f) acc[f * kAdjThreads + tid] = 0.0;
   const int64_t j = blockIdx.x;
-  const Rec64 rc = load_rec64(a.rp, j);
   const T* gr = static_cast<const T*>(a.grad_r);
   const T* gv = static_cast<const T*>(a.grad_v);
+  T acc[kNumAdj];
+#pragma unroll
+  for (int q = 0; q < kNumAdj; ++q) acc[q] = T(0);
+  Rec64 rc64;
+  Rec32 rc32;
+  RevC<T> k;
+  if constexpr (kFP32) {
+    rc32 = load_rec32(a.rp, j);
+    k = rev_consts(rc32, a.gf);
+  } else {
+    rc64 = load_rec64(a.rp, j);
+    k = rev_consts(rc64, a.g);
+  }
   for (int64_t i = tid; i < a.T; i += kAdjThreads) {
     const int64_t s = j * a.T + i;
-    const double t = a.per_sat ? a.tsince[s] : a.tsince[i];
+    const double t = a.per_sat ? __ldg(a.tsince + s) : __ldg(a.tsince + i);
     T g_r[3], g_v[3];
     for (int c = 0; c < 3; ++c) {
       g_r[c] = gr ? gr[s * 3 + c] : T(0);
       g_v[c] = gv ? gv[s * 3 + c] : T(0);
     }
-    adjoint_state<T>(rc, a.g, t, g_r, g_v, acc + tid);
+    auto add = [&](int q, T v) { acc[q] += v; };
+    Fwd<T> f;
+    if constexpr (kFP32) {
+      float th, tl;
+      split_double(t, th, tl);
+      const int code = forward32(rc32, a.gf, th, tl, f);
+      if (code == kRecomputeFP64) {
+        const float seed[6] = {g_r[0], g_r[1], g_r[2], g_v[0], g_v[1], g_v[2]};
+        float bar[kNumAdj], r[3];
+        if (usable(adjoint_fallback(a.rp, a.g, j, t, seed, 1, bar, r))) {
+#pragma unroll
+          for (int q = 0; q < kNumAdj; ++q) acc[q] += bar[q];
+        }
+      } else if (usable(code)) {
+        reverse(f, k, g_r, g_v, add);
+      }
+    } else {
+      if (usable(forward64(rc64, a.g, t, f))) reverse(f, k, g_r, g_v, add);
+    }
   }
+#pragma unroll
+  for (int q = 0; q < kNumAdj; ++q) warp_partial(acc[q], q, part);
   __syncthreads();
   if (tid < kNumAdj) {
     double sum = 0.0;
-    for (int k = 0; k < kAdjThreads; ++k) sum += acc[tid * kAdjThreads + k];
+    for (int w = 0; w < kAdjWarps; ++w) sum += (double)part[tid][w];
     a.field_bar[j * kNumAdj + tid] = sum;
   }
+}
+
+__device__ __forceinline__ bool elements_usable(const double e7[7]) {
+  bool ok = true;
+  for (int k = 0; k < 7; ++k) ok = ok && isfinite(e7[k]);
+  return ok && e7[1] >= 0.0 && e7[1] < 1.0 && e7[0] > 0.0;
+}
+
+// Record-field Jacobian of sgp4init, d(field)/d(element), [kNumAdj][7] row-major, by
+// dual numbers (false for unusable elements).
+__device__ bool init_jacobian(const double e7[7], const Geo& g, double* J) {
+  if (!elements_usable(e7)) return false;
+  D7 x[7];
+  for (int k = 0; k < 7; ++k) x[k] = d7var(e7[k], k);
+  InitFields<D7> o;
+  init_fields(x, g, o);
+  const D7* f[kNumAdj] = {&o.n0pp, &o.a0pp, &o.e0, &o.i0, &o.raan0, &o.argp0, &o.m0,
+                          &o.mdot, &o.argpdot, &o.raandot, &o.raan_cf, &o.argp_cf, &o.m_cf,
+                          &o.c1, &o.bc4, &o.bc5, &o.d2, &o.d3, &o.d4, &o.l2, &o.l3, &o.l4,
+                          &o.l5, &o.eta, &o.delm0, &o.sinm0, &o.xlcof, &o.aycof, &o.cosi,
+                          &o.sini, &o.x3thm1, &o.x1mth2, &o.x7thm1};
+  for (int q = 0; q < kNumAdj; ++q)
+    for (int k = 0; k < 7; ++k) J[q * 7 + k] = f[q]->d[k];
+  return true;
 }
 
 __global__ void __launch_bounds__(64) adjoint_init_kernel(const double* __restrict__ el,
@@ -386,13 +624,8 @@ __global__ void __launch_bounds__(64) adjoint_init_kernel(const double* __restri
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double e7[7];
-  bool ok = true;
-  for (int k = 0; k < 7; ++k) {
-    e7[k] = el[j * 7 + k];
-    ok = ok && isfinite(e7[k]);
-  }
-  ok = ok && e7[1] >= 0.0 && e7[1] < 1.0 && e7[0] > 0.0;
-  if (!ok) {
+  for (int k = 0; k < 7; ++k) e7[k] = el[j * 7 + k];
+  if (!elements_usable(e7)) {
     for (int k = 0; k < 7; ++k) grad[j * 7 + k] = 0.0;
     return;
   }
@@ -413,31 +646,24 @@ __global__ void __launch_bounds__(64) adjoint_init_kernel(const double* __restri
   for (int k = 0; k < 7; ++k) grad[j * 7 + k] = out[k];
 }
 
-// Record-field Jacobian of sgp4init, d(field)/d(element), [kNumAdj][7], by dual
-// numbers (false for unusable elements).
-__device__ bool init_jacobian(const double e7[7], const Geo& g, double J[kNumAdj][7]) {
-  bool ok = true;
-  for (int k = 0; k < 7; ++k) ok = ok && isfinite(e7[k]);
-  ok = ok && e7[1] >= 0.0 && e7[1] < 1.0 && e7[0] > 0.0;
-  if (!ok) return false;
-  D7 x[7];
-  for (int k = 0; k < 7; ++k) x[k] = d7var(e7[k], k);
-  InitFields<D7> o;
-  init_fields(x, g, o);
-  const D7* f[kNumAdj] = {&o.n0pp, &o.a0pp, &o.e0, &o.i0, &o.raan0, &o.argp0, &o.m0,
-                          &o.mdot, &o.argpdot, &o.raandot, &o.raan_cf, &o.argp_cf, &o.m_cf,
-                          &o.c1, &o.bc4, &o.bc5, &o.d2, &o.d3, &o.d4, &o.l2, &o.l3, &o.l4,
-                          &o.l5, &o.eta, &o.delm0, &o.sinm0, &o.xlcof, &o.aycof, &o.cosi,
-                          &o.sini, &o.x3thm1, &o.x1mth2, &o.x7thm1};
-  for (int q = 0; q < kNumAdj; ++q)
-    for (int k = 0; k < 7; ++k) J[q][k] = f[q]->d[k];
-  return true;
+// One thread per satellite: the init Jacobian of the fit step into the workspace.
+__global__ void __launch_bounds__(64) fit_jacobian_kernel(const double* __restrict__ el,
+                                                          int64_t n, Geo g,
+                                                          double* __restrict__ jac) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double e7[7];
+  for (int k = 0; k < 7; ++k) e7[k] = el[j * 7 + k];
+  if (!init_jacobian(e7, g, jac + j * kNumAdj * 7))
+    for (int q = 0; q < kNumAdj * 7; ++q) jac[j * kNumAdj * 7 + q] = 0.0;
 }
 
 struct FitArgs {
   RecordPtrs rp;
   Geo g;
+  GeoF gf;
   const double* el;      // [n][7]
+  const double* jac;     // [n][kNumAdj][7], fit_jacobian_kernel
   const double* tsince;
   int64_t T;
   int per_sat;
@@ -449,129 +675,177 @@ struct FitArgs {
 
 // One Gauss-Newton / Levenberg-Marquardt step of batch least squares per satellite:
 // residuals res_t = r_t(el) - r_obs_t over the states with finite output, the
-// position Jacobian J_t = dr_t/del (three reverse sweeps per state, contracted with
-// the init Jacobian), A = sum J_t^T J_t, b = sum J_t^T res_t, and the step
-// delta = -(A + lambda diag A)^-1 b solved by Cholesky on the Jacobi-scaled matrix.
+// position Jacobian J_t = dr_t/del (one forward and three reverse sweeps per state,
+// contracted with the init Jacobian), A = sum J_t^T J_t, b = sum J_t^T res_t, and the
+// step delta = -(A + lambda diag A)^-1 b solved by Cholesky on the Jacobi-scaled
+// matrix.  Per-thread sums in T, warp sums by shuffles, the warps' sums in FP64.
 template <class T>
 __global__ void __launch_bounds__(kAdjThreads) fit_step_kernel(FitArgs a) {
-  __shared__ double acc[kNumAdj * kAdjThreads];
-  __shared__ double Ji[kNumAdj][7];
-  __shared__ double red[36][kAdjThreads / 32];
+  constexpr bool kFP32 = sizeof(T) == 4;
+  __shared__ T Ji[kNumAdj][7];
+  __shared__ T part[36][kAdjWarps];
+  __shared__ double S[36];
   __shared__ int s_ok;
   const int tid = threadIdx.x;
   const int64_t j = blockIdx.x;
-  double e7[7];
-  for (int k = 0; k < 7; ++k) e7[k] = a.el[j * 7 + k];
-  if (tid == 0) s_ok = init_jacobian(e7, a.g, Ji) ? 1 : 0;
+  if (tid == 0) {
+    double e7[7];
+    for (int k = 0; k < 7; ++k) e7[k] = a.el[j * 7 + k];
+    s_ok = elements_usable(e7) ? 1 : 0;
+  }
+  for (int q = tid; q < kNumAdj * 7; q += kAdjThreads)
+    (&Ji[0][0])[q] = T(a.jac[j * kNumAdj * 7 + q]);
   __syncthreads();
   if (!s_ok) {
-    if (tid < 7) a.el_out[j * 7 + tid] = e7[tid];
+    if (tid < 7) a.el_out[j * 7 + tid] = a.el[j * 7 + tid];
     if (tid == 0) a.sse[j] = 0.0;
     return;
   }
-  const Rec64 rc = load_rec64(a.rp, j);
-  double A[28], b[7], sse = 0.0;
-  for (int k = 0; k < 28; ++k) A[k] = 0.0;
-  for (int k = 0; k < 7; ++k) b[k] = 0.0;
-  const T zero3[3] = {T(0), T(0), T(0)};
+  Rec64 rc64;
+  Rec32 rc32;
+  RevC<T> k;
+  if constexpr (kFP32) {
+    rc32 = load_rec32(a.rp, j);
+    k = rev_consts(rc32, a.gf);
+  } else {
+    rc64 = load_rec64(a.rp, j);
+    k = rev_consts(rc64, a.g);
+  }
+  T A[28], b[7], sse = T(0);
+#pragma unroll
+  for (int q = 0; q < 28; ++q) A[q] = T(0);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) b[q] = T(0);
   for (int64_t i = tid; i < a.T; i += kAdjThreads) {
     const int64_t s = j * a.T + i;
-    const double t = a.per_sat ? a.tsince[s] : a.tsince[i];
-    double Jt[3][7];
-    T r[3];
-    int code = 0;
-    for (int c = 0; c < 3; ++c) {
-      for (int f = 0; f < kNumAdj; ++f) acc[f * kAdjThreads + tid] = 0.0;
-      T seed[3] = {T(0), T(0), T(0)};
-      seed[c] = T(1);
-      code = adjoint_state<T>(rc, a.g, t, seed, zero3, acc + tid, r);
-      for (int k = 0; k < 7; ++k) {
-        double v = 0.0;
-        for (int f = 0; f < kNumAdj; ++f) v += acc[f * kAdjThreads + tid] * Ji[f][k];
-        Jt[c][k] = v;
+    const double t = a.per_sat ? __ldg(a.tsince + s) : __ldg(a.tsince + i);
+    Fwd<T> f;
+    int code;
+    bool fell_back = false;
+    float fb_bar[3 * kNumAdj], fb_r[3] = {0.0f, 0.0f, 0.0f};
+    if constexpr (kFP32) {
+      float th, tl;
+      split_double(t, th, tl);
+      code = forward32(rc32, a.gf, th, tl, f);
+      if (code == kRecomputeFP64) {
+        const float seeds[18] = {1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0};
+        code = adjoint_fallback(a.rp, a.g, j, t, seeds, 3, fb_bar, fb_r);
+        fell_back = true;
       }
+    } else {
+      code = forward64(rc64, a.g, t, f);
     }
-    if (code != 0 && code != 6) continue;
-    double res[3];
-    for (int c = 0; c < 3; ++c) res[c] = (double)r[c] - a.r_obs[s * 3 + c];
+    if (!usable(code)) continue;
+    T r[3];
+    if (fell_back) {
+      r[0] = T(fb_r[0]); r[1] = T(fb_r[1]); r[2] = T(fb_r[2]);
+    } else {
+      const T rs = f.rk * k.re;
+      r[0] = rs * f.Ux; r[1] = rs * f.Uy; r[2] = rs * f.Uz;
+    }
+    T res[3];
+    for (int c = 0; c < 3; ++c) res[c] = r[c] - T(a.r_obs[s * 3 + c]);
     if (!(isfinite(res[0]) && isfinite(res[1]) && isfinite(res[2]))) continue;
     sse += res[0] * res[0] + res[1] * res[1] + res[2] * res[2];
-    int q = 0;
-    for (int k = 0; k < 7; ++k) {
-      b[k] += Jt[0][k] * res[0] + Jt[1][k] * res[1] + Jt[2][k] * res[2];
-      for (int m = 0; m <= k; ++m, ++q)
-        A[q] += Jt[0][k] * Jt[0][m] + Jt[1][k] * Jt[1][m] + Jt[2][k] * Jt[2][m];
+    // Row c of dr/del: J_c = (field adjoints of seed e_c) . Ji; then A += J_c^T J_c and
+    // b += J_c^T res_c.
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T Jc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+      auto contract = [&](int q, T v) {
+#pragma unroll
+        for (int m = 0; m < 7; ++m) Jc[m] += v * Ji[q][m];
+      };
+      if (fell_back) {
+        for (int q = 0; q < kNumAdj; ++q) contract(q, T(fb_bar[c * kNumAdj + q]));
+      } else {
+        const T zero3[3] = {T(0), T(0), T(0)};
+        const T seed[3] = {T(c == 0), T(c == 1), T(c == 2)};
+        reverse(f, k, seed, zero3, contract);
+      }
+      int idx = 0;
+#pragma unroll
+      for (int m = 0; m < 7; ++m) {
+        b[m] += Jc[m] * res[c];
+#pragma unroll
+        for (int l = 0; l <= m; ++l, ++idx) A[idx] += Jc[m] * Jc[l];
+      }
     }
   }
-  // Block reduction of the 28 + 7 + 1 sums (warp shuffles, then one value per warp).
-  double vals[36];
-  for (int k = 0; k < 28; ++k) vals[k] = A[k];
-  for (int k = 0; k < 7; ++k) vals[28 + k] = b[k];
-  vals[35] = sse;
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int k = 0; k < 36; ++k) {
-    double v = vals[k];
-    for (int off = 16; off; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0) red[k][warp] = v;
+#pragma unroll
+  for (int q = 0; q < 28; ++q) warp_partial(A[q], q, part);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) warp_partial(b[q], 28 + q, part);
+  warp_partial(sse, 35, part);
+  __syncthreads();
+  if (tid < 36) {
+    double v = 0.0;
+    for (int w = 0; w < kAdjWarps; ++w) v += (double)part[tid][w];
+    S[tid] = v;
   }
   __syncthreads();
   if (tid != 0) return;
-  double S[36];
-  for (int k = 0; k < 36; ++k) {
-    double v = 0.0;
-    for (int w = 0; w < kAdjThreads / 32; ++w) v += red[k][w];
-    S[k] = v;
-  }
   // Unpack A (lower triangle), Jacobi scaling, damping, Cholesky.
   double M[7][7], rhs[7], d[7];
   int q = 0;
-  for (int k = 0; k < 7; ++k)
-    for (int m = 0; m <= k; ++m, ++q) M[k][m] = M[m][k] = S[q];
-  for (int k = 0; k < 7; ++k) d[k] = M[k][k] > 0.0 ? 1.0 / sqrt(M[k][k]) : 0.0;
+  for (int m = 0; m < 7; ++m)
+    for (int l = 0; l <= m; ++l, ++q) M[m][l] = M[l][m] = S[q];
+  for (int m = 0; m < 7; ++m) d[m] = M[m][m] > 0.0 ? 1.0 / sqrt(M[m][m]) : 0.0;
   const double lam = a.lambda[j];
-  for (int k = 0; k < 7; ++k) {
-    for (int m = 0; m < 7; ++m) M[k][m] *= d[k] * d[m];
-    M[k][k] = (d[k] > 0.0 ? M[k][k] : 1.0) * (1.0 + lam);
-    rhs[k] = -S[28 + k] * d[k];
+  for (int m = 0; m < 7; ++m) {
+    for (int l = 0; l < 7; ++l) M[m][l] *= d[m] * d[l];
+    M[m][m] = (d[m] > 0.0 ? M[m][m] : 1.0) * (1.0 + lam);
+    rhs[m] = -S[28 + m] * d[m];
   }
   bool spd = true;
-  for (int k = 0; k < 7 && spd; ++k) {
-    for (int m = 0; m < k; ++m) M[k][k] -= M[k][m] * M[k][m];
-    if (!(M[k][k] > 0.0)) { spd = false; break; }
-    M[k][k] = sqrt(M[k][k]);
-    for (int r2 = k + 1; r2 < 7; ++r2) {
-      for (int m = 0; m < k; ++m) M[r2][k] -= M[r2][m] * M[k][m];
-      M[r2][k] /= M[k][k];
+  for (int m = 0; m < 7 && spd; ++m) {
+    for (int l = 0; l < m; ++l) M[m][m] -= M[m][l] * M[m][l];
+    if (!(M[m][m] > 0.0)) { spd = false; break; }
+    M[m][m] = sqrt(M[m][m]);
+    for (int r2 = m + 1; r2 < 7; ++r2) {
+      for (int l = 0; l < m; ++l) M[r2][m] -= M[r2][l] * M[m][l];
+      M[r2][m] /= M[m][m];
     }
   }
   double x[7] = {0, 0, 0, 0, 0, 0, 0};
   if (spd) {
-    for (int k = 0; k < 7; ++k) {            // forward substitution L y = rhs
-      double v = rhs[k];
-      for (int m = 0; m < k; ++m) v -= M[k][m] * x[m];
-      x[k] = v / M[k][k];
+    for (int m = 0; m < 7; ++m) {            // forward substitution L y = rhs
+      double v = rhs[m];
+      for (int l = 0; l < m; ++l) v -= M[m][l] * x[l];
+      x[m] = v / M[m][m];
     }
-    for (int k = 6; k >= 0; --k) {           // back substitution L^T x = y
-      double v = x[k];
-      for (int m = k + 1; m < 7; ++m) v -= M[m][k] * x[m];
-      x[k] = v / M[k][k];
+    for (int m = 6; m >= 0; --m) {           // back substitution L^T x = y
+      double v = x[m];
+      for (int l = m + 1; l < 7; ++l) v -= M[l][m] * x[l];
+      x[m] = v / M[m][m];
     }
   }
-  for (int k = 0; k < 7; ++k) a.el_out[j * 7 + k] = e7[k] + x[k] * d[k];
+  for (int m = 0; m < 7; ++m) a.el_out[j * 7 + m] = a.el[j * 7 + m] + x[m] * d[m];
   a.sse[j] = S[35];
 }
 
 }  // namespace
 
+size_t fit_workspace_bytes(int64_t n) {
+  return n <= 0 ? 0 : (size_t)n * kNumAdj * 7 * sizeof(double);
+}
+
 cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el,
                             const double* tsince, int64_t T, int per_sat, bool fp32,
                             const double* r_obs, const double* lambda, double* el_out,
-                            double* sse, cudaStream_t stream) {
+                            double* sse, double* workspace, cudaStream_t stream) {
   if (rp.n == 0) return cudaSuccess;
+  const int threads = 64;
+  fit_jacobian_kernel<<<(unsigned)((rp.n + threads - 1) / threads), threads, 0, stream>>>(
+      el, rp.n, g, workspace);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   FitArgs a;
   a.rp = rp;
   a.g = g;
+  a.gf = geo_float(g);
   a.el = el;
+  a.jac = workspace;
   a.tsince = tsince;
   a.T = T;
   a.per_sat = per_sat;
@@ -596,6 +870,7 @@ cudaError_t launch_adjoint(const RecordPtrs& rp, const Geo& g, const double* el,
   AdjArgs a;
   a.rp = rp;
   a.g = g;
+  a.gf = geo_float(g);
   a.tsince = tsince;
   a.T = T;
   a.per_sat = per_sat;

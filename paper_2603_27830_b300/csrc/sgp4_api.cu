@@ -299,10 +299,13 @@ sgp4_result sgp4_adjoint(const double* elements, const sgp4_records* records,
   return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
 }
 
+size_t sgp4_fit_workspace_bytes(int64_t n) { return sgp4::fit_workspace_bytes(n); }
+
 sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
                           const double* tsince, int64_t t_count, int grid_per_sat,
                           sgp4_precision precision, const double* r_obs, const double* lambda,
-                          double* elements_out, double* sse, void* stream) {
+                          double* elements_out, double* sse, void* workspace,
+                          size_t workspace_bytes, void* stream) {
   if (!records_ok(records) || t_count < 0) return SGP4_ERR_ARG;
   if (precision != SGP4_FP64 && precision != SGP4_FP32) return SGP4_ERR_ARG;
   const int64_t n = records->n;
@@ -315,10 +318,12 @@ sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
   if (elements_out == elements) return SGP4_ERR_ARG;
   if (t_count > 0 && (!tsince || !r_obs || !aligned(tsince, 8) || !aligned(r_obs, 8)))
     return SGP4_ERR_ARG;
+  if (!workspace || !aligned(workspace, 8)) return SGP4_ERR_ARG;
+  if (workspace_bytes < sgp4::fit_workspace_bytes(n)) return SGP4_ERR_OOM;
   cudaError_t e = sgp4::launch_fit_step(
       sgp4::record_ptrs(records->arena, n), make_geo(records->consts), elements, tsince, t_count,
       grid_per_sat ? 1 : 0, precision == SGP4_FP32, r_obs, lambda, elements_out, sse,
-      static_cast<cudaStream_t>(stream));
+      static_cast<double*>(workspace), static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
 }
 

@@ -61,11 +61,13 @@ cudaError_t launch_adjoint(const RecordPtrs& rp, const Geo& g, const double* el,
                            const void* grad_r, const void* grad_v, double* grad_el,
                            double* workspace, cudaStream_t stream);
 
-// One batch-least-squares (Levenberg-Marquardt) step per satellite.
+// One batch-least-squares (Levenberg-Marquardt) step per satellite: the init-Jacobian
+// workspace bytes and the two-kernel launch.
+size_t fit_workspace_bytes(int64_t n);
 cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el,
                             const double* tsince, int64_t T, int per_sat, bool fp32,
                             const double* r_obs, const double* lambda, double* el_out,
-                            double* sse, cudaStream_t stream);
+                            double* sse, double* workspace, cudaStream_t stream);
 
 // Float copy of the Earth model for the FP32 path (host side, once per call).
 inline GeoF geo_float(const Geo& g) {

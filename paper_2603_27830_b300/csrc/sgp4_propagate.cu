@@ -34,11 +34,6 @@ constexpr int kThreads = 128;
 #define SGP4_MIN_BLOCKS_FP64 4
 #endif
 
-template <typename OutT>
-__device__ __forceinline__ void nan_fill(OutT x[3]) {
-  x[0] = x[1] = x[2] = OutT(__longlong_as_double(0x7ff8000000000000LL));
-}
-
 template <bool kFP32>
 struct Stage {
   using OutT = typename std::conditional<kFP32, float, double>::type;
@@ -76,7 +71,6 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
 
   for (int64_t base = beg; base < end; base += kThreads) {
     const int64_t idx = base + tid;
-    OutT rr[3], vv[3];
     int code = 0;
     if (idx < end) {
       const int64_t rec = rg.sat0 + j;
@@ -85,6 +79,7 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
         cur = j;
       }
       const double t = rg.per_sat ? __ldg(rg.tsince + j * T + i) : __ldg(rg.tsince + i);
+      OutT rr[3], vv[3];
       if (kFP32) {
         // The 160-byte FP32 row is re-read every state (ten 16-byte loads that L1
         // serves as broadcasts) instead of being held in registers across states.
@@ -93,20 +88,27 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
         split_double(t, th, tl);
         float r32[3], v32[3];
         code = state32(rc32, gf, th, tl, r32, v32);
-        if (code == kRecomputeFP64) {
-          code = state64_fallback(rp, g, rec, t, r32, v32);
-          ++nfix;
-        }
         for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r32[c]; vv[c] = (OutT)v32[c]; }
       } else {
         double r64[3], v64[3];
         code = state64(rc64, g, t, r64, v64);
         for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r64[c]; vv[c] = (OutT)v64[c]; }
       }
-      if (code != 0 && code != 6) { nan_fill(rr); nan_fill(vv); }
+      sm.r[3 * tid + 0] = rr[0]; sm.r[3 * tid + 1] = rr[1]; sm.r[3 * tid + 2] = rr[2];
+      sm.v[3 * tid + 0] = vv[0]; sm.v[3 * tid + 1] = vv[1]; sm.v[3 * tid + 2] = vv[2];
+      if (kFP32 && code == kRecomputeFP64) {
+        // The out-of-line recomputation writes its float results straight into this
+        // thread's staging slots, so no local array has its address taken.
+        code = state64_fallback(rp, g, rec, t, reinterpret_cast<float*>(&sm.r[3 * tid]),
+                                reinterpret_cast<float*>(&sm.v[3 * tid]));
+        ++nfix;
+      }
+      if (code != 0 && code != 6) {
+        const OutT q = OutT(__longlong_as_double(0x7ff8000000000000LL));
+        sm.r[3 * tid + 0] = q; sm.r[3 * tid + 1] = q; sm.r[3 * tid + 2] = q;
+        sm.v[3 * tid + 0] = q; sm.v[3 * tid + 1] = q; sm.v[3 * tid + 2] = q;
+      }
     }
-    sm.r[3 * tid + 0] = rr[0]; sm.r[3 * tid + 1] = rr[1]; sm.r[3 * tid + 2] = rr[2];
-    sm.v[3 * tid + 0] = vv[0]; sm.v[3 * tid + 1] = vv[1]; sm.v[3 * tid + 2] = vv[2];
     sm.st[tid] = code;
     __syncthreads();
 

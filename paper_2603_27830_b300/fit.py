@@ -29,11 +29,13 @@ def fit_step(elements: torch.Tensor, tsince: torch.Tensor, r_obs: torch.Tensor,
     out = torch.empty_like(elements)
     sse = torch.empty(n, dtype=torch.float64, device=elements.device)
     lib = _lib.load()
+    ws_bytes = int(lib.sgp4_fit_workspace_bytes(n))
+    ws = torch.empty(max(ws_bytes // 8, 1), dtype=torch.float64, device=elements.device)
     _lib.check("sgp4_fit_step",
                lib.sgp4_fit_step(_ptr(elements), ctypes.byref(recs.c), _ptr(tsince),
                                  tsince.shape[-1], 1 if tsince.dim() == 2 else 0,
                                  PRECISIONS[precision], _ptr(r_obs), _ptr(lam), _ptr(out),
-                                 _ptr(sse), _stream_handle(stream)))
+                                 _ptr(sse), _ptr(ws), ws_bytes, _stream_handle(stream)))
     return out, sse
 
 
