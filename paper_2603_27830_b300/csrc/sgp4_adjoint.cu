@@ -27,6 +27,7 @@
 // cycles, so a handful of FP64 operations per state would bound the whole kernel.
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "sgp4.h"
 #include "sgp4_device.cuh"
@@ -46,19 +47,28 @@ enum AdjField {
 
 constexpr int kAdjThreads = 128;
 constexpr int kAdjWarps = kAdjThreads / 32;
+// Resident blocks per SM asked of the register allocator for the FP32 sweeps.  Their
+// forward values take 260 B of shared memory per thread (33 KB per block), so six
+// blocks is the most an SM holds; on B300 six (80 registers, some spilled to L1) ran
+// 20% faster than two (255 registers, no spills) and 7% faster than four.
+constexpr int kAdjMinBlocksFP32 = 6;
 
 // Values of the forward pass of one state that the reverse sweep reads (names as in
-// the propagation: a, e, a_xN, a_yN, E, p_L, r, u and the short-period terms).
+// the propagation: a, e, a_xN, a_yN, E, p_L, r, u and the short-period terms).  The
+// FP32 kernels keep one per thread in shared memory (an odd number of 4-byte words, so
+// that the 32 threads of a warp hit 32 different banks).
 template <class T>
 struct Fwd {
   T tt, t2, t3, t4;
   T sMdf, cMdf, c, sMM, cMM;   // sin/cos M_DF, 1 + eta cos M_DF, sin/cos(M_DF + dd)
   T tempa, templ, a, sqa, n, e, om, q, sw, cw, axn, ayn;
-  bool clamped;                // e was raised to 1e-6
+  T keep_e;                    // 0 where e was raised to 1e-6, else 1
   T sp, cp, ecosE, esinE, eL2, pL, rl, rdotl, sqp, rfdotl, betal, opb, w, aor, As, Ac;
   T sinu, cosu, sin2u, cos2u, k, kp, fac, rk, nk, rdotk, rfdotk;
   T su, cu, sO, cO, si, ci, mx, my, mz, Ux, Uy, Uz, Vx, Vy, Vz;
+  T pad;
 };
+static_assert(sizeof(Fwd<float>) % 8 == 4, "odd word count for conflict-free rows");
 
 // Per-satellite constants of the reverse sweep.
 template <class T>
@@ -137,8 +147,8 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
   f.n = g.xke * ia15;
   const double e1 = rc.e0 - tempe;
   if (e1 >= 1.0 || e1 < -0.001) return 1;
-  f.clamped = e1 < 1.0e-6;
-  f.e = f.clamped ? 1.0e-6 : e1;
+  f.keep_e = e1 < 1.0e-6 ? 0.0 : 1.0;
+  f.e = fmax(e1, 1.0e-6);
   raan = wrap_2pi(raan);
   argp = wrap_2pi(argp);
   const double mpa = mdf + argpdf + rc.n0pp * templ;   // M + argp (drag terms cancel)
@@ -232,7 +242,7 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
   if (!(fabsf(e1 - 1.0f) >= kGuardE && fabsf(e1 + 0.001f) >= kGuardE && f.a > 1.0e-3f))
     return kRecomputeFP64;
   if (e1 >= 1.0f || e1 < -0.001f) return 1;
-  f.clamped = e1 < 1.0e-6f;
+  f.keep_e = e1 < 1.0e-6f ? 0.0f : 1.0f;
   f.e = fmaxf(e1, 1.0e-6f);
   const float ra = rsqrtf(f.a);
   f.sqa = f.a * ra;
@@ -442,7 +452,7 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
   const T argp1b = Ub + argpb;
   sink(aN0pp, mm2b * f.templ);
   const T templb = mm2b * rc.n0pp;
-  const T e1b = f.clamped ? T(0) : eb;
+  const T e1b = f.keep_e * eb;
   sink(aE0, e1b);
   const T tempeb = -e1b;
   ab += nb * T(-1.5) * f.n / f.a;
@@ -492,26 +502,25 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
 __device__ __forceinline__ bool usable(int code) { return code == 0 || code == 6; }
 
 // FP64 forward and reverse sweeps of one state for the FP32 kernels (guard-band
-// states).  nseed seeds (g_r, g_v) of 6 values each in `seeds`; writes nseed x 33
-// field adjoints to bar and the position (km) to r.  Out of line: rarely taken.
+// states), for the seed (g_r, g_v): writes the 33 field adjoints to bar and, if r is
+// not null, the position (km) to r.  Out of line: rarely taken.
 static __device__ __noinline__ int adjoint_fallback(RecordPtrs rp, Geo g, int64_t j, double t,
-                                                    const float* seeds, int nseed, float* bar,
-                                                    float* r) {
+                                                    float gr0, float gr1, float gr2, float gv0,
+                                                    float gv1, float gv2, float* bar, float* r) {
   const Rec64 rc = load_rec64(rp, j);
   Fwd<double> f;
   const int code = forward64(rc, g, t, f);
   if (!usable(code)) return code;
   const RevC<double> k = rev_consts(rc, g);
-  for (int s = 0; s < nseed; ++s) {
-    const double gr[3] = {seeds[6 * s + 0], seeds[6 * s + 1], seeds[6 * s + 2]};
-    const double gv[3] = {seeds[6 * s + 3], seeds[6 * s + 4], seeds[6 * s + 5]};
-    float* out = bar + s * kNumAdj;
-    for (int q = 0; q < kNumAdj; ++q) out[q] = 0.0f;
-    reverse(f, k, gr, gv, [&](int q, double v) { out[q] = (float)v; });
+  const double gr[3] = {gr0, gr1, gr2};
+  const double gv[3] = {gv0, gv1, gv2};
+  for (int q = 0; q < kNumAdj; ++q) bar[q] = 0.0f;
+  reverse(f, k, gr, gv, [&](int q, double v) { bar[q] = (float)v; });
+  if (r) {
+    r[0] = (float)(f.rk * g.re * f.Ux);
+    r[1] = (float)(f.rk * g.re * f.Uy);
+    r[2] = (float)(f.rk * g.re * f.Uz);
   }
-  r[0] = (float)(f.rk * g.re * f.Ux);
-  r[1] = (float)(f.rk * g.re * f.Uy);
-  r[2] = (float)(f.rk * g.re * f.Uz);
   return code;
 }
 
@@ -534,28 +543,46 @@ struct AdjArgs {
   double* field_bar;   // [n][kNumAdj], workspace
 };
 
+// The record and the reverse-sweep constants of the block's satellite, in shared
+// memory (every thread reads the same words: broadcasts).
 template <class T>
-__global__ void __launch_bounds__(kAdjThreads) adjoint_prop_kernel(AdjArgs a) {
-  __shared__ T part[kNumAdj][kAdjWarps];
-  constexpr bool kFP32 = sizeof(T) == 4;
-  const int tid = threadIdx.x;
-  const int64_t j = blockIdx.x;
+struct SatShared {
+  typename std::conditional<sizeof(T) == 4, Rec32, Rec64>::type rc;
+  RevC<T> k;
+};
+
+template <class T>
+__device__ __forceinline__ void load_sat(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
+                                         int64_t j, SatShared<T>& s) {
+  if constexpr (sizeof(T) == 4) {
+    s.rc = load_rec32(rp, j);
+    s.k = rev_consts(s.rc, gf);
+  } else {
+    s.rc = load_rec64(rp, j);
+    s.k = rev_consts(s.rc, g);
+  }
+}
+
+// Forward values of one state: shared memory for FP32 (the reverse sweep then reads
+// them from there instead of holding ~65 values in registers, which would leave two
+// blocks per SM), registers for FP64 (whose kernels are bound by the FP64 unit).
+template <class T>
+struct FwdSlot {
+  static constexpr int kRows = sizeof(T) == 4 ? kAdjThreads : 1;
+};
+
+// Compiler barrier between the forward and the reverse sweep: the reverse reloads the
+// forward values from shared memory instead of keeping them live in registers.
+__device__ __forceinline__ void reload_barrier() { asm volatile("" ::: "memory"); }
+
+// The states of satellite j handled by this thread: forward, reverse sweep, and the
+// field adjoints summed into acc.  f is the thread's forward-value slot.
+template <class T>
+__device__ __forceinline__ void prop_loop(const AdjArgs& a, const SatShared<T>& sat,
+                                          Fwd<T>& f, T (&acc)[kNumAdj], int64_t j) {
   const T* gr = static_cast<const T*>(a.grad_r);
   const T* gv = static_cast<const T*>(a.grad_v);
-  T acc[kNumAdj];
-#pragma unroll
-  for (int q = 0; q < kNumAdj; ++q) acc[q] = T(0);
-  Rec64 rc64;
-  Rec32 rc32;
-  RevC<T> k;
-  if constexpr (kFP32) {
-    rc32 = load_rec32(a.rp, j);
-    k = rev_consts(rc32, a.gf);
-  } else {
-    rc64 = load_rec64(a.rp, j);
-    k = rev_consts(rc64, a.g);
-  }
-  for (int64_t i = tid; i < a.T; i += kAdjThreads) {
+  for (int64_t i = threadIdx.x; i < a.T; i += kAdjThreads) {
     const int64_t s = j * a.T + i;
     const double t = a.per_sat ? __ldg(a.tsince + s) : __ldg(a.tsince + i);
     T g_r[3], g_v[3];
@@ -564,24 +591,46 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_prop_kernel(AdjArgs a) {
       g_v[c] = gv ? gv[s * 3 + c] : T(0);
     }
     auto add = [&](int q, T v) { acc[q] += v; };
-    Fwd<T> f;
-    if constexpr (kFP32) {
+    if constexpr (sizeof(T) == 4) {
       float th, tl;
       split_double(t, th, tl);
-      const int code = forward32(rc32, a.gf, th, tl, f);
+      const int code = forward32(sat.rc, a.gf, th, tl, f);
+      reload_barrier();
       if (code == kRecomputeFP64) {
-        const float seed[6] = {g_r[0], g_r[1], g_r[2], g_v[0], g_v[1], g_v[2]};
-        float bar[kNumAdj], r[3];
-        if (usable(adjoint_fallback(a.rp, a.g, j, t, seed, 1, bar, r))) {
+        float* bar = reinterpret_cast<float*>(&f);   // the slot holds the 33 adjoints
+        if (usable(adjoint_fallback(a.rp, a.g, j, t, g_r[0], g_r[1], g_r[2], g_v[0], g_v[1],
+                                    g_v[2], bar, nullptr))) {
 #pragma unroll
           for (int q = 0; q < kNumAdj; ++q) acc[q] += bar[q];
         }
+        reload_barrier();
       } else if (usable(code)) {
-        reverse(f, k, g_r, g_v, add);
+        reverse(f, sat.k, g_r, g_v, add);
       }
     } else {
-      if (usable(forward64(rc64, a.g, t, f))) reverse(f, k, g_r, g_v, add);
+      if (usable(forward64(sat.rc, a.g, t, f))) reverse(f, sat.k, g_r, g_v, add);
     }
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP32 : 1)
+    adjoint_prop_kernel(AdjArgs a) {
+  __shared__ T part[kNumAdj][kAdjWarps];
+  __shared__ SatShared<T> sat;
+  __shared__ Fwd<T> sfwd[FwdSlot<T>::kRows];
+  const int tid = threadIdx.x;
+  const int64_t j = blockIdx.x;
+  if (tid == 0) load_sat(a.rp, a.g, a.gf, j, sat);
+  __syncthreads();
+  T acc[kNumAdj];
+#pragma unroll
+  for (int q = 0; q < kNumAdj; ++q) acc[q] = T(0);
+  if constexpr (sizeof(T) == 4) {
+    prop_loop(a, sat, sfwd[tid], acc, j);
+  } else {
+    Fwd<T> f;
+    prop_loop(a, sat, f, acc, j);
   }
 #pragma unroll
   for (int q = 0; q < kNumAdj; ++q) warp_partial(acc[q], q, part);
@@ -673,82 +722,45 @@ struct FitArgs {
   double* sse;           // [n] sum of squared position residuals at el (km^2)
 };
 
-// One Gauss-Newton / Levenberg-Marquardt step of batch least squares per satellite:
-// residuals res_t = r_t(el) - r_obs_t over the states with finite output, the
-// position Jacobian J_t = dr_t/del (one forward and three reverse sweeps per state,
-// contracted with the init Jacobian), A = sum J_t^T J_t, b = sum J_t^T res_t, and the
-// step delta = -(A + lambda diag A)^-1 b solved by Cholesky on the Jacobi-scaled
-// matrix.  Per-thread sums in T, warp sums by shuffles, the warps' sums in FP64.
+// The states of satellite j handled by this thread: residuals, the rows of dr/del
+// (the field adjoints of the seeds e_x, e_y, e_z contracted with the init Jacobian Ji)
+// and their sums A += J_c^T J_c, b += J_c^T res_c, sse += |res|^2.
 template <class T>
-__global__ void __launch_bounds__(kAdjThreads) fit_step_kernel(FitArgs a) {
-  constexpr bool kFP32 = sizeof(T) == 4;
-  __shared__ T Ji[kNumAdj][7];
-  __shared__ T part[36][kAdjWarps];
-  __shared__ double S[36];
-  __shared__ int s_ok;
-  const int tid = threadIdx.x;
-  const int64_t j = blockIdx.x;
-  if (tid == 0) {
-    double e7[7];
-    for (int k = 0; k < 7; ++k) e7[k] = a.el[j * 7 + k];
-    s_ok = elements_usable(e7) ? 1 : 0;
-  }
-  for (int q = tid; q < kNumAdj * 7; q += kAdjThreads)
-    (&Ji[0][0])[q] = T(a.jac[j * kNumAdj * 7 + q]);
-  __syncthreads();
-  if (!s_ok) {
-    if (tid < 7) a.el_out[j * 7 + tid] = a.el[j * 7 + tid];
-    if (tid == 0) a.sse[j] = 0.0;
-    return;
-  }
-  Rec64 rc64;
-  Rec32 rc32;
-  RevC<T> k;
-  if constexpr (kFP32) {
-    rc32 = load_rec32(a.rp, j);
-    k = rev_consts(rc32, a.gf);
-  } else {
-    rc64 = load_rec64(a.rp, j);
-    k = rev_consts(rc64, a.g);
-  }
-  T A[28], b[7], sse = T(0);
-#pragma unroll
-  for (int q = 0; q < 28; ++q) A[q] = T(0);
-#pragma unroll
-  for (int q = 0; q < 7; ++q) b[q] = T(0);
-  for (int64_t i = tid; i < a.T; i += kAdjThreads) {
+__device__ __forceinline__ void fit_loop(const FitArgs& a, const SatShared<T>& sat, Fwd<T>& f,
+                                         const T (*Ji)[7], T (&A)[28], T (&b)[7], T& sse,
+                                         int64_t j) {
+  for (int64_t i = threadIdx.x; i < a.T; i += kAdjThreads) {
     const int64_t s = j * a.T + i;
     const double t = a.per_sat ? __ldg(a.tsince + s) : __ldg(a.tsince + i);
-    Fwd<T> f;
     int code;
     bool fell_back = false;
-    float fb_bar[3 * kNumAdj], fb_r[3] = {0.0f, 0.0f, 0.0f};
-    if constexpr (kFP32) {
+    T r[3];
+    float* slot = reinterpret_cast<float*>(&f);   // fallback: 33 adjoints + position
+    if constexpr (sizeof(T) == 4) {
       float th, tl;
       split_double(t, th, tl);
-      code = forward32(rc32, a.gf, th, tl, f);
+      code = forward32(sat.rc, a.gf, th, tl, f);
+      reload_barrier();
       if (code == kRecomputeFP64) {
-        const float seeds[18] = {1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0};
-        code = adjoint_fallback(a.rp, a.g, j, t, seeds, 3, fb_bar, fb_r);
+        code = adjoint_fallback(a.rp, a.g, j, t, 1.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, slot,
+                                slot + kNumAdj);
+        reload_barrier();
         fell_back = true;
       }
     } else {
-      code = forward64(rc64, a.g, t, f);
+      code = forward64(sat.rc, a.g, t, f);
     }
     if (!usable(code)) continue;
-    T r[3];
     if (fell_back) {
-      r[0] = T(fb_r[0]); r[1] = T(fb_r[1]); r[2] = T(fb_r[2]);
+      r[0] = T(slot[kNumAdj]); r[1] = T(slot[kNumAdj + 1]); r[2] = T(slot[kNumAdj + 2]);
     } else {
-      const T rs = f.rk * k.re;
+      const T rs = f.rk * sat.k.re;
       r[0] = rs * f.Ux; r[1] = rs * f.Uy; r[2] = rs * f.Uz;
     }
     T res[3];
     for (int c = 0; c < 3; ++c) res[c] = r[c] - T(a.r_obs[s * 3 + c]);
     if (!(isfinite(res[0]) && isfinite(res[1]) && isfinite(res[2]))) continue;
     sse += res[0] * res[0] + res[1] * res[1] + res[2] * res[2];
-    // Row c of dr/del: J_c = (field adjoints of seed e_c) . Ji; then A += J_c^T J_c and
-    // b += J_c^T res_c.
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       T Jc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -757,11 +769,16 @@ __global__ void __launch_bounds__(kAdjThreads) fit_step_kernel(FitArgs a) {
         for (int m = 0; m < 7; ++m) Jc[m] += v * Ji[q][m];
       };
       if (fell_back) {
-        for (int q = 0; q < kNumAdj; ++q) contract(q, T(fb_bar[c * kNumAdj + q]));
+        if (c > 0) {
+          adjoint_fallback(a.rp, a.g, j, t, c == 1 ? 1.0f : 0.0f, c == 2 ? 1.0f : 0.0f, 0.0f,
+                           0.0f, 0.0f, 0.0f, slot, nullptr);
+          reload_barrier();
+        }
+        for (int q = 0; q < kNumAdj; ++q) contract(q, T(slot[q]));
       } else {
         const T zero3[3] = {T(0), T(0), T(0)};
         const T seed[3] = {T(c == 0), T(c == 1), T(c == 2)};
-        reverse(f, k, seed, zero3, contract);
+        reverse(f, sat.k, seed, zero3, contract);
       }
       int idx = 0;
 #pragma unroll
@@ -771,6 +788,50 @@ __global__ void __launch_bounds__(kAdjThreads) fit_step_kernel(FitArgs a) {
         for (int l = 0; l <= m; ++l, ++idx) A[idx] += Jc[m] * Jc[l];
       }
     }
+  }
+}
+
+// One Gauss-Newton / Levenberg-Marquardt step of batch least squares per satellite:
+// residuals res_t = r_t(el) - r_obs_t over the states with finite output, the
+// position Jacobian J_t = dr_t/del (one forward and three reverse sweeps per state,
+// contracted with the init Jacobian), A = sum J_t^T J_t, b = sum J_t^T res_t, and the
+// step delta = -(A + lambda diag A)^-1 b solved by Cholesky on the Jacobi-scaled
+// matrix.  Per-thread sums in T, warp sums by shuffles, the warps' sums in FP64.
+template <class T>
+__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP32 : 1)
+    fit_step_kernel(FitArgs a) {
+  __shared__ T Ji[kNumAdj][7];
+  __shared__ T part[36][kAdjWarps];
+  __shared__ double S[36];
+  __shared__ int s_ok;
+  __shared__ SatShared<T> sat;
+  __shared__ Fwd<T> sfwd[FwdSlot<T>::kRows];
+  const int tid = threadIdx.x;
+  const int64_t j = blockIdx.x;
+  if (tid == 0) {
+    double e7[7];
+    for (int k = 0; k < 7; ++k) e7[k] = a.el[j * 7 + k];
+    s_ok = elements_usable(e7) ? 1 : 0;
+    load_sat(a.rp, a.g, a.gf, j, sat);
+  }
+  for (int q = tid; q < kNumAdj * 7; q += kAdjThreads)
+    (&Ji[0][0])[q] = T(a.jac[j * kNumAdj * 7 + q]);
+  __syncthreads();
+  if (!s_ok) {
+    if (tid < 7) a.el_out[j * 7 + tid] = a.el[j * 7 + tid];
+    if (tid == 0) a.sse[j] = 0.0;
+    return;
+  }
+  T A[28], b[7], sse = T(0);
+#pragma unroll
+  for (int q = 0; q < 28; ++q) A[q] = T(0);
+#pragma unroll
+  for (int q = 0; q < 7; ++q) b[q] = T(0);
+  if constexpr (sizeof(T) == 4) {
+    fit_loop(a, sat, sfwd[tid], Ji, A, b, sse, j);
+  } else {
+    Fwd<T> f;
+    fit_loop(a, sat, f, Ji, A, b, sse, j);
   }
 #pragma unroll
   for (int q = 0; q < 28; ++q) warp_partial(A[q], q, part);

@@ -5,7 +5,9 @@
 Workloads: near-earth (64 x 100), starlink (9,341 x 1,000), catalogue (1,000,000 x
 100; ``--n`` shrinks it), batch (64 uneven requests, N_i log-U[100,5e3], T_i
 log-U[10,500]: the batched persistent launch), adjoint (the fitting workload,
-10,000 x 500: one sgp4_adjoint call).  Prints the wall time of each repetition.
+10,000 x 500: one sgp4_adjoint call), fit (the same workload: one sgp4_fit_step call
+against observations of the perturbed elements).  Prints the wall time of each
+repetition.
 """
 from __future__ import annotations
 
@@ -56,10 +58,25 @@ def run_adjoint(args):
                lambda: sgp4_adjoint(el, recs, ts, g, g, prec), args.reps)
 
 
+def run_fit(args):
+    from .fit import fit_step
+    w = W.config5(n=args.n or 10_000)
+    el = torch.as_tensor(w.elements, device="cuda")
+    ts = torch.as_tensor(w.tsince, device="cuda")
+    truth, _ = sgp4_init(torch.as_tensor(w.meta["truth"], device="cuda"))
+    r_true = sgp4_propagate(truth, ts, "fp64")[0]
+    r_obs = r_true + torch.as_tensor(w.meta["noise"](tuple(r_true.shape)), device="cuda")
+    lam = torch.full((w.n,), 1e-3, dtype=torch.float64, device="cuda")
+    precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
+    for prec in precs:
+        _timed(f"fit step {w.states} states {prec}",
+               lambda: fit_step(el, ts, r_obs, lam, prec), args.reps)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=["near-earth", "starlink", "catalogue", "batch",
-                                           "adjoint"],
+                                           "adjoint", "fit"],
                     default="starlink")
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="fp32")
     ap.add_argument("--reps", type=int, default=2)
@@ -69,6 +86,8 @@ def main():
         return run_batch(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "fit":
+        return run_fit(args)
     if args.workload == "near-earth":
         w = W.config1()
     elif args.workload == "starlink":
