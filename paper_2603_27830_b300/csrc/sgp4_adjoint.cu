@@ -14,8 +14,8 @@
 //    function theorem); the clamps and threshold decisions are constants of the sweep.
 //  * adjoint_init_kernel: one thread per satellite pushes the 7 element directions
 //    through sgp4init with dual numbers (the record build is per satellite, so
-//    forward mode costs nothing next to the per-state sweep) and contracts the
-//    record-field Jacobian with the accumulated field adjoints.
+//    forward mode costs little next to the per-state sweep; FP32 duals for the FP32
+//    path) and contracts the record-field Jacobian with the accumulated adjoints.
 //  * fit_jacobian_kernel + fit_step_kernel: one Levenberg-Marquardt step of batch
 //    least squares per satellite (three reverse sweeps per state after one forward).
 // States whose status is 1, 2 or 4 (NaN output) contribute nothing.
@@ -649,23 +649,29 @@ __device__ __forceinline__ bool elements_usable(const double e7[7]) {
 }
 
 // Record-field Jacobian of sgp4init, d(field)/d(element), [kNumAdj][7] row-major, by
-// dual numbers (false for unusable elements).
-__device__ bool init_jacobian(const double e7[7], const Geo& g, double* J) {
+// dual numbers over R (false for unusable elements).  R = float serves the FP32
+// sweeps: their field adjoints carry FP32 rounding already, and B300 runs FP32 dual
+// arithmetic 64 times faster than FP64.  The branch decisions of the record build
+// (simplified drag, s*, e0 > 1e-4) are then taken on FP32 values.
+template <class R>
+__device__ bool init_jacobian(const double e7[7], const Geo& g, R* J) {
   if (!elements_usable(e7)) return false;
-  D7 x[7];
-  for (int k = 0; k < 7; ++k) x[k] = d7var(e7[k], k);
-  InitFields<D7> o;
+  Dual7<R> x[7];
+  for (int k = 0; k < 7; ++k) x[k] = d7var(R(e7[k]), k);
+  InitFields<Dual7<R>> o;
   init_fields(x, g, o);
-  const D7* f[kNumAdj] = {&o.n0pp, &o.a0pp, &o.e0, &o.i0, &o.raan0, &o.argp0, &o.m0,
-                          &o.mdot, &o.argpdot, &o.raandot, &o.raan_cf, &o.argp_cf, &o.m_cf,
-                          &o.c1, &o.bc4, &o.bc5, &o.d2, &o.d3, &o.d4, &o.l2, &o.l3, &o.l4,
-                          &o.l5, &o.eta, &o.delm0, &o.sinm0, &o.xlcof, &o.aycof, &o.cosi,
-                          &o.sini, &o.x3thm1, &o.x1mth2, &o.x7thm1};
+  const Dual7<R>* f[kNumAdj] = {&o.n0pp, &o.a0pp, &o.e0, &o.i0, &o.raan0, &o.argp0, &o.m0,
+                                &o.mdot, &o.argpdot, &o.raandot, &o.raan_cf, &o.argp_cf,
+                                &o.m_cf, &o.c1, &o.bc4, &o.bc5, &o.d2, &o.d3, &o.d4, &o.l2,
+                                &o.l3, &o.l4, &o.l5, &o.eta, &o.delm0, &o.sinm0, &o.xlcof,
+                                &o.aycof, &o.cosi, &o.sini, &o.x3thm1, &o.x1mth2, &o.x7thm1};
   for (int q = 0; q < kNumAdj; ++q)
     for (int k = 0; k < 7; ++k) J[q * 7 + k] = f[q]->d[k];
   return true;
 }
 
+// One thread per satellite: grad[j] = field_bar[j] . J (the init Jacobian over R).
+template <class R>
 __global__ void __launch_bounds__(64) adjoint_init_kernel(const double* __restrict__ el,
                                                           const double* __restrict__ field_bar,
                                                           int64_t n, Geo g,
@@ -674,37 +680,29 @@ __global__ void __launch_bounds__(64) adjoint_init_kernel(const double* __restri
   if (j >= n) return;
   double e7[7];
   for (int k = 0; k < 7; ++k) e7[k] = el[j * 7 + k];
-  if (!elements_usable(e7)) {
+  R J[kNumAdj * 7];
+  if (!init_jacobian(e7, g, J)) {
     for (int k = 0; k < 7; ++k) grad[j * 7 + k] = 0.0;
     return;
   }
-  D7 x[7];
-  for (int k = 0; k < 7; ++k) x[k] = d7var(e7[k], k);
-  InitFields<D7> o;
-  init_fields(x, g, o);
-  const D7* f[kNumAdj] = {&o.n0pp, &o.a0pp, &o.e0, &o.i0, &o.raan0, &o.argp0, &o.m0,
-                          &o.mdot, &o.argpdot, &o.raandot, &o.raan_cf, &o.argp_cf, &o.m_cf,
-                          &o.c1, &o.bc4, &o.bc5, &o.d2, &o.d3, &o.d4, &o.l2, &o.l3, &o.l4,
-                          &o.l5, &o.eta, &o.delm0, &o.sinm0, &o.xlcof, &o.aycof, &o.cosi,
-                          &o.sini, &o.x3thm1, &o.x1mth2, &o.x7thm1};
-  double out[7] = {0, 0, 0, 0, 0, 0, 0};
+  R out[7] = {R(0), R(0), R(0), R(0), R(0), R(0), R(0)};
   for (int q = 0; q < kNumAdj; ++q) {
-    const double b = field_bar[j * kNumAdj + q];
-    for (int k = 0; k < 7; ++k) out[k] += b * f[q]->d[k];
+    const R b = R(field_bar[j * kNumAdj + q]);
+    for (int k = 0; k < 7; ++k) out[k] += b * J[q * 7 + k];
   }
   for (int k = 0; k < 7; ++k) grad[j * 7 + k] = out[k];
 }
 
 // One thread per satellite: the init Jacobian of the fit step into the workspace.
+template <class R>
 __global__ void __launch_bounds__(64) fit_jacobian_kernel(const double* __restrict__ el,
-                                                          int64_t n, Geo g,
-                                                          double* __restrict__ jac) {
+                                                          int64_t n, Geo g, R* __restrict__ jac) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   double e7[7];
   for (int k = 0; k < 7; ++k) e7[k] = el[j * 7 + k];
   if (!init_jacobian(e7, g, jac + j * kNumAdj * 7))
-    for (int q = 0; q < kNumAdj * 7; ++q) jac[j * kNumAdj * 7 + q] = 0.0;
+    for (int q = 0; q < kNumAdj * 7; ++q) jac[j * kNumAdj * 7 + q] = R(0);
 }
 
 struct FitArgs {
@@ -712,7 +710,7 @@ struct FitArgs {
   Geo g;
   GeoF gf;
   const double* el;      // [n][7]
-  const double* jac;     // [n][kNumAdj][7], fit_jacobian_kernel
+  const void* jac;       // [n][kNumAdj][7] of the kernel's T, fit_jacobian_kernel
   const double* tsince;
   int64_t T;
   int per_sat;
@@ -815,7 +813,7 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
     load_sat(a.rp, a.g, a.gf, j, sat);
   }
   for (int q = tid; q < kNumAdj * 7; q += kAdjThreads)
-    (&Ji[0][0])[q] = T(a.jac[j * kNumAdj * 7 + q]);
+    (&Ji[0][0])[q] = static_cast<const T*>(a.jac)[j * kNumAdj * 7 + q];
   __syncthreads();
   if (!s_ok) {
     if (tid < 7) a.el_out[j * 7 + tid] = a.el[j * 7 + tid];
@@ -897,8 +895,12 @@ cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el
                             double* sse, double* workspace, cudaStream_t stream) {
   if (rp.n == 0) return cudaSuccess;
   const int threads = 64;
-  fit_jacobian_kernel<<<(unsigned)((rp.n + threads - 1) / threads), threads, 0, stream>>>(
-      el, rp.n, g, workspace);
+  const unsigned blocks = (unsigned)((rp.n + threads - 1) / threads);
+  if (fp32)
+    fit_jacobian_kernel<float><<<blocks, threads, 0, stream>>>(
+        el, rp.n, g, reinterpret_cast<float*>(workspace));
+  else
+    fit_jacobian_kernel<double><<<blocks, threads, 0, stream>>>(el, rp.n, g, workspace);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   FitArgs a;
@@ -943,8 +945,11 @@ cudaError_t launch_adjoint(const RecordPtrs& rp, const Geo& g, const double* el,
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int threads = 64;
-  adjoint_init_kernel<<<(unsigned)((rp.n + threads - 1) / threads), threads, 0, stream>>>(
-      el, workspace, rp.n, g, grad_el);
+  const unsigned blocks = (unsigned)((rp.n + threads - 1) / threads);
+  if (fp32)
+    adjoint_init_kernel<float><<<blocks, threads, 0, stream>>>(el, workspace, rp.n, g, grad_el);
+  else
+    adjoint_init_kernel<double><<<blocks, threads, 0, stream>>>(el, workspace, rp.n, g, grad_el);
   return cudaGetLastError();
 }
 

@@ -1,8 +1,9 @@
 // Initialisation constants of near-Earth SGP4 as a function of the mean elements,
 // (x^(2/3) as cbrt(x^2), x^3.5 as x^3 sqrt(x), one sincos per angle: the record
 // build runs on B300's small FP64 unit, so its operation count is its cost),
-// templated on the scalar: double for the record builder, D7 (value + derivatives
-// with respect to the 7 elements) for the Jacobian the adjoint needs.  Equations of
+// templated on the scalar: double for the record builder, Dual7<double> or
+// Dual7<float> (value + derivatives with respect to the 7 elements) for the Jacobian
+// the adjoint needs.  Equations of
 // Spacetrack Report #3 as revised in 2006 (paper Sec. 2.1); readings: a0'' from
 // n0'' by Kepler's third law, D4 with a0''^2.
 #pragma once
@@ -13,97 +14,152 @@
 
 namespace sgp4 {
 
-// Forward-mode dual number with 7 tangent directions (n0, e0, i0, RAAN0, argp0, M0, B*).
-struct D7 {
-  double v;
-  double d[7];
+// Forward-mode dual number with 7 tangent directions (n0, e0, i0, RAAN0, argp0, M0, B*)
+// over the scalar R: double for the FP64 paths, float for the Jacobians of the FP32
+// adjoint (B300's FP32 lanes are 64 times its FP64 rate).
+template <class R>
+struct Dual7 {
+  R v;
+  R d[7];
 };
+using D7 = Dual7<double>;
 
-__device__ __forceinline__ D7 d7c(double x) {
-  D7 r;
+// Scalar functions of R (the float versions are the accurate library ones, not the
+// SFU intrinsics).
+__device__ __forceinline__ double sc_sin(double x) { return ::sin(x); }
+__device__ __forceinline__ float sc_sin(float x) { return ::sinf(x); }
+__device__ __forceinline__ double sc_cos(double x) { return ::cos(x); }
+__device__ __forceinline__ float sc_cos(float x) { return ::cosf(x); }
+__device__ __forceinline__ double sc_sqrt(double x) { return ::sqrt(x); }
+__device__ __forceinline__ float sc_sqrt(float x) { return ::sqrtf(x); }
+__device__ __forceinline__ double sc_pow(double x, double p) { return ::pow(x, p); }
+__device__ __forceinline__ float sc_pow(float x, float p) { return ::powf(x, p); }
+__device__ __forceinline__ double sc_cbrt(double x) { return ::cbrt(x); }
+__device__ __forceinline__ float sc_cbrt(float x) { return ::cbrtf(x); }
+__device__ __forceinline__ void sc_sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
+__device__ __forceinline__ void sc_sincos(float x, float* s, float* c) { ::sincosf(x, s, c); }
+
+template <class R>
+__device__ __forceinline__ Dual7<R> d7c(R x) {
+  Dual7<R> r;
   r.v = x;
 #pragma unroll
-  for (int k = 0; k < 7; ++k) r.d[k] = 0.0;
+  for (int k = 0; k < 7; ++k) r.d[k] = R(0);
   return r;
 }
-__device__ __forceinline__ D7 d7var(double x, int k) {
-  D7 r = d7c(x);
-  r.d[k] = 1.0;
+template <class R>
+__device__ __forceinline__ Dual7<R> d7var(R x, int k) {
+  Dual7<R> r = d7c(x);
+  r.d[k] = R(1);
   return r;
 }
-__device__ __forceinline__ D7 d7chain(const D7& a, double val, double dfda) {
-  D7 r;
+template <class R>
+__device__ __forceinline__ Dual7<R> d7chain(const Dual7<R>& a, R val, R dfda) {
+  Dual7<R> r;
   r.v = val;
 #pragma unroll
   for (int k = 0; k < 7; ++k) r.d[k] = dfda * a.d[k];
   return r;
 }
-__device__ __forceinline__ D7 operator+(const D7& a, const D7& b) {
-  D7 r; r.v = a.v + b.v;
+template <class R>
+__device__ __forceinline__ Dual7<R> operator+(const Dual7<R>& a, const Dual7<R>& b) {
+  Dual7<R> r; r.v = a.v + b.v;
 #pragma unroll
   for (int k = 0; k < 7; ++k) r.d[k] = a.d[k] + b.d[k];
   return r;
 }
-__device__ __forceinline__ D7 operator-(const D7& a, const D7& b) {
-  D7 r; r.v = a.v - b.v;
+template <class R>
+__device__ __forceinline__ Dual7<R> operator-(const Dual7<R>& a, const Dual7<R>& b) {
+  Dual7<R> r; r.v = a.v - b.v;
 #pragma unroll
   for (int k = 0; k < 7; ++k) r.d[k] = a.d[k] - b.d[k];
   return r;
 }
-__device__ __forceinline__ D7 operator-(const D7& a) {
-  D7 r; r.v = -a.v;
+template <class R>
+__device__ __forceinline__ Dual7<R> operator-(const Dual7<R>& a) {
+  Dual7<R> r; r.v = -a.v;
 #pragma unroll
   for (int k = 0; k < 7; ++k) r.d[k] = -a.d[k];
   return r;
 }
-__device__ __forceinline__ D7 operator*(const D7& a, const D7& b) {
-  D7 r; r.v = a.v * b.v;
+template <class R>
+__device__ __forceinline__ Dual7<R> operator*(const Dual7<R>& a, const Dual7<R>& b) {
+  Dual7<R> r; r.v = a.v * b.v;
 #pragma unroll
   for (int k = 0; k < 7; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
   return r;
 }
-__device__ __forceinline__ D7 operator/(const D7& a, const D7& b) {
-  D7 r; r.v = a.v / b.v;
-  const double ib = 1.0 / b.v;
+template <class R>
+__device__ __forceinline__ Dual7<R> operator/(const Dual7<R>& a, const Dual7<R>& b) {
+  Dual7<R> r; r.v = a.v / b.v;
+  const R ib = R(1) / b.v;
 #pragma unroll
   for (int k = 0; k < 7; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
   return r;
 }
-__device__ __forceinline__ D7 operator+(const D7& a, double b) { D7 r = a; r.v += b; return r; }
-__device__ __forceinline__ D7 operator+(double a, const D7& b) { return b + a; }
-__device__ __forceinline__ D7 operator-(const D7& a, double b) { D7 r = a; r.v -= b; return r; }
-__device__ __forceinline__ D7 operator-(double a, const D7& b) { return -b + a; }
-__device__ __forceinline__ D7 operator*(const D7& a, double b) { return d7chain(a, a.v * b, b); }
-__device__ __forceinline__ D7 operator*(double a, const D7& b) { return b * a; }
-__device__ __forceinline__ D7 operator/(const D7& a, double b) { return a * (1.0 / b); }
-__device__ __forceinline__ D7 operator/(double a, const D7& b) {
-  const double q = a / b.v;
+template <class R>
+__device__ __forceinline__ Dual7<R> operator+(const Dual7<R>& a, double b) {
+  Dual7<R> r = a; r.v += R(b); return r;
+}
+template <class R>
+__device__ __forceinline__ Dual7<R> operator+(double a, const Dual7<R>& b) { return b + a; }
+template <class R>
+__device__ __forceinline__ Dual7<R> operator-(const Dual7<R>& a, double b) {
+  Dual7<R> r = a; r.v -= R(b); return r;
+}
+template <class R>
+__device__ __forceinline__ Dual7<R> operator-(double a, const Dual7<R>& b) { return -b + a; }
+template <class R>
+__device__ __forceinline__ Dual7<R> operator*(const Dual7<R>& a, double b) {
+  return d7chain(a, a.v * R(b), R(b));
+}
+template <class R>
+__device__ __forceinline__ Dual7<R> operator*(double a, const Dual7<R>& b) { return b * a; }
+template <class R>
+__device__ __forceinline__ Dual7<R> operator/(const Dual7<R>& a, double b) {
+  return a * (1.0 / b);
+}
+template <class R>
+__device__ __forceinline__ Dual7<R> operator/(double a, const Dual7<R>& b) {
+  const R q = R(a) / b.v;
   return d7chain(b, q, -q / b.v);
 }
-__device__ __forceinline__ D7 sin(const D7& a) { return d7chain(a, ::sin(a.v), ::cos(a.v)); }
-__device__ __forceinline__ D7 cos(const D7& a) { return d7chain(a, ::cos(a.v), -::sin(a.v)); }
-__device__ __forceinline__ D7 sqrt(const D7& a) {
-  const double s = ::sqrt(a.v);
-  return d7chain(a, s, 0.5 / s);
+template <class R>
+__device__ __forceinline__ Dual7<R> sin(const Dual7<R>& a) {
+  return d7chain(a, sc_sin(a.v), sc_cos(a.v));
 }
-__device__ __forceinline__ D7 pow(const D7& a, double p) {
-  const double y = ::pow(a.v, p);
-  return d7chain(a, y, p * y / a.v);
+template <class R>
+__device__ __forceinline__ Dual7<R> cos(const Dual7<R>& a) {
+  return d7chain(a, sc_cos(a.v), -sc_sin(a.v));
 }
-__device__ __forceinline__ D7 fabs(const D7& a) { return a.v < 0.0 ? -a : a; }
-__device__ __forceinline__ D7 cbrt(const D7& a) {
-  const double y = ::cbrt(a.v);
-  return d7chain(a, y, y / (3.0 * a.v));
+template <class R>
+__device__ __forceinline__ Dual7<R> sqrt(const Dual7<R>& a) {
+  const R s = sc_sqrt(a.v);
+  return d7chain(a, s, R(0.5) / s);
 }
-__device__ __forceinline__ void sincos(const D7& a, D7* s, D7* c) {
-  double sv, cv;
-  ::sincos(a.v, &sv, &cv);
+template <class R>
+__device__ __forceinline__ Dual7<R> pow(const Dual7<R>& a, double p) {
+  const R y = sc_pow(a.v, R(p));
+  return d7chain(a, y, R(p) * y / a.v);
+}
+template <class R>
+__device__ __forceinline__ Dual7<R> fabs(const Dual7<R>& a) { return a.v < R(0) ? -a : a; }
+template <class R>
+__device__ __forceinline__ Dual7<R> cbrt(const Dual7<R>& a) {
+  const R y = sc_cbrt(a.v);
+  return d7chain(a, y, y / (R(3) * a.v));
+}
+template <class R>
+__device__ __forceinline__ void sincos(const Dual7<R>& a, Dual7<R>* s, Dual7<R>* c) {
+  R sv, cv;
+  sc_sincos(a.v, &sv, &cv);
   *s = d7chain(a, sv, cv);
   *c = d7chain(a, cv, -sv);
 }
-__device__ __forceinline__ double val(const D7& a) { return a.v; }
+template <class R>
+__device__ __forceinline__ R val(const Dual7<R>& a) { return a.v; }
 __device__ __forceinline__ double val(double a) { return a; }
-// Keep the double versions visible next to the D7 overloads in this namespace.
+// Keep the double versions visible next to the dual overloads in this namespace.
 using ::cbrt;
 using ::cos;
 using ::fabs;
@@ -205,7 +261,7 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
   o.l2 = 1.5 * C1;
 
   S opc = 1.0 + cosi;
-  if (::fabs(val(opc)) <= 1.5e-12) opc = 0.0 * opc + 1.5e-12;
+  if (::fabs((double)val(opc)) <= 1.5e-12) opc = 0.0 * opc + 1.5e-12;
   o.xlcof = -0.25 * g.j3oj2 * sini * (3.0 + 5.0 * cosi) / opc;
   o.aycof = -0.5 * g.j3oj2 * sini;
   S sinm, cosm;
