@@ -7,6 +7,11 @@ terms, Kepler, short-period terms, TEME output) of the Starlink-shaped workload,
 the plain FP64 GPU path is timed beside it.  Inputs are resident in HBM when the
 timed region starts; L2 is flushed (256 MB write) between timed steps.
 
+Beside the headline the line carries the FP64 path, the batched uneven-request launch
+(256 requests, CUDA-graph replay) and the adjoint / fitting workload (10,000 x 500:
+sgp4_adjoint and one Levenberg-Marquardt step, FP32 and FP64), each with its rate and
+roofline fraction.
+
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (the
 only reference this project has: the paper ships no runnable code here).
 Under torchrun each rank propagates its own copy of the workload (independent
@@ -36,6 +41,21 @@ BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
 # Starlink-shaped workload (FADD 45 + FFMA 68 + FMUL 104 + SFU 16.5 thread instructions,
 # counted with ncu; the command is in the design doc and profiles/).
 ALG_OPS_FP32 = 234
+# DRAM bytes (read + write) of one launch of the FP32 propagate kernel on this workload,
+# from an ncu capture of the current kernel (dram__bytes_read.sum 1,600,768 +
+# dram__bytes_write.sum 203,119,360): below the 28 B/state written because L2 still
+# holds the tail of the output when the kernel ends.
+TRAFFIC_FP32_BYTES = 204_720_128
+# FP64 arithmetic (DADD + DMUL + DFMA thread instructions) per state of the FP64
+# propagation on the Starlink-shaped workload, counted with ncu.
+ALG_OPS_FP64 = 395
+# Per state of the adjoint sweep on the fitting workload (10,000 x 500), counted with
+# ncu: FP32 path FADD + FMUL + FFMA + SFU; FP64 path DADD + DMUL + DFMA.
+ALG_OPS_ADJ_FP32 = 670
+ALG_OPS_ADJ_FP64 = 862
+# B300's FP64 unit: 2 lanes per SM per clock (one warp instruction per 64 cycles per
+# SM sub-partition; ncu's fp64-pipe utilisation and instruction count give the rate).
+FP64_LANES_PER_SM_CLK = 2
 
 
 def _peaks():
@@ -196,6 +216,59 @@ def run_batched(torch, dev, stream, flush, steps):
            "note": "N_i log-U[100,5e4], T_i log-U[10,5e3], grids U[-720,2880] min; "
                    "one CUDA-graph replay (counter reset + persistent kernel)"}
     del out, recs, el, ts
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_adjoint(torch, dev, stream, flush, steps, alu_peak, fp64_peak):
+    """Adjoint and fitting workload (10,000 satellites x 500 times over one day): one
+    sgp4_adjoint call (sweep kernel + init-Jacobian kernel) per step in FP32 and FP64,
+    and one Levenberg-Marquardt step (sgp4_init + Jacobian + fit kernel)."""
+    from paper_2603_27830_b300 import sgp4_adjoint, sgp4_init, sgp4_propagate
+    from paper_2603_27830_b300 import workloads as W
+    from paper_2603_27830_b300.fit import fit_step
+    w = W.config5()
+    states = w.n * w.t_count
+    el = torch.as_tensor(w.elements, device=dev)
+    ts = torch.as_tensor(w.tsince, device=dev)
+    recs, _ = sgp4_init(el)
+    truth, _ = sgp4_init(torch.as_tensor(w.meta["truth"], device=dev))
+    r_true = sgp4_propagate(truth, ts, "fp64")[0]
+    r_obs = r_true + torch.as_tensor(w.meta["noise"](tuple(r_true.shape)), device=dev)
+    lam = torch.full((w.n,), 1e-3, dtype=torch.float64, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    g64 = torch.randn((w.n, w.t_count, 3), dtype=torch.float64, device=dev, generator=gen)
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            e = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            e.record(stream)
+            e.synchronize()
+            ms.append(a.elapsed_time(e))
+        return statistics.median(ms)
+
+    res = {"workload": w.name, "n_sats": w.n, "t_count": w.t_count}
+    for prec, ops, peak, unit_kind in (("fp32", ALG_OPS_ADJ_FP32, alu_peak, "alu"),
+                                       ("fp64", ALG_OPS_ADJ_FP64, fp64_peak, "fp64")):
+        g = g64.float() if prec == "fp32" else g64
+        ms = timed(lambda: sgp4_adjoint(el, recs, ts, g, g, prec))
+        fit_ms = timed(lambda: fit_step(el, ts, r_obs, lam, prec))
+        achieved = ops * states / (ms * 1e-3) / 1e9
+        res[prec] = {"value": states / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms,
+                     "roofline": {"bound": unit_kind, "achieved": achieved, "peak": peak,
+                                  "unit": "Gop/s", "frac": achieved / peak,
+                                  "ops_per_state": ops,
+                                  "timed": "whole sgp4_adjoint call (sweep + init Jacobian)"},
+                     "fit_step_ms": fit_ms, "fit_step_states_per_s": states / (fit_ms * 1e-3)}
+    del g64, r_obs, r_true, recs, truth
     torch.cuda.empty_cache()
     return res
 
@@ -369,7 +442,7 @@ def run_ours(args):
     bytes_per_launch = BYTES_PER_STATE["fp32"] * states
     achieved_gbs = bytes_per_launch / (kern_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved_gops, "peak": alu_peak, "unit": "Gop/s",
-                "frac": achieved_gops / alu_peak, "traffic": None,
+                "frac": achieved_gops / alu_peak, "traffic": TRAFFIC_FP32_BYTES,
                 "kernel": "propagate_kernel<fp32>", "kernel_ms": kern_ms,
                 "ops_per_state": ALG_OPS_FP32,
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
@@ -377,11 +450,27 @@ def run_ours(args):
                         "frac": achieved_gbs / peaks["hbm_gbs"], "peak_kind": peak_kind,
                         "bytes_per_state": BYTES_PER_STATE["fp32"]}}
 
+    # The FP64 path is bound by B300's FP64 unit: ALG_OPS_FP64 operations per state
+    # against 2 FP64 lanes per SM per clock.
+    fp64_peak = n_sm * FP64_LANES_PER_SM_CLK * sm_mhz * 1e6 / 1e9   # Gop/s
+    kern64_ms = statistics.mean(per64_k)
+    fp64_achieved = ALG_OPS_FP64 * states / (kern64_ms * 1e-3) / 1e9
+    fp64_roofline = {"bound": "fp64", "achieved": fp64_achieved, "peak": fp64_peak,
+                     "unit": "Gop/s", "frac": fp64_achieved / fp64_peak,
+                     "kernel": "propagate_kernel<fp64>", "kernel_ms": kern64_ms,
+                     "ops_per_state": ALG_OPS_FP64,
+                     "peak_basis": f"{n_sm} SMs x {FP64_LANES_PER_SM_CLK} FP64 lanes x "
+                                   f"{sm_mhz:.0f} MHz"}
+
     # Batched uneven requests: 256 requests, each with its own grid, in one persistent
     # launch replayed from a CUDA graph with the autotuned tile (FP32).
     batched = None
     if not args.no_batched:
         batched = run_batched(torch, dev, stream, flush, max(3, min(args.steps, 5)))
+    adjoint = None
+    if not args.no_adjoint:
+        adjoint = run_adjoint(torch, dev, stream, flush, max(3, min(args.steps, 5)), alu_peak,
+                              fp64_peak)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -403,9 +492,10 @@ def run_ours(args):
                        "(256 MB write)", "parallelism": f"replicas x{world}"},
             "fp32_max_dr_km_sample": max_dr_km,
             "fp64": {"value": fp64_value, "unit": UNIT, "ms_per_step": ms64 / max(1, min(args.steps, 5)),
-                     "kernel_ms": statistics.mean(per64_k)},
+                     "kernel_ms": kern64_ms, "roofline": fp64_roofline},
             "roofline": roofline,
             "batched": batched,
+            "adjoint": adjoint,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -428,6 +518,7 @@ def main():
     ap.add_argument("--ref-sats", type=int, default=1000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
