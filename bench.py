@@ -67,6 +67,24 @@ def _peaks():
         return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
+def max_over_ranks(x: float, device) -> float:
+    """Largest x over the ranks of the default process group (x when there is none):
+    the job's time is that of its slowest rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(states_per_rank: int, steps: int, world: int, ms_total: float) -> float:
+    """Whole-job states/s: every rank propagates its own replica of the workload (the
+    states are independent; there is no data-path collective)."""
+    return world * states_per_rank * steps / (ms_total * 1e-3)
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -370,10 +388,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-            t = torch.tensor([tot], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        return tot, per
+        return max_over_ranks(tot, dev), per
 
     # correctness spot check against the oracle (rank 0, before timing)
     max_dr_km = None
@@ -398,8 +413,8 @@ def run_ours(args):
     ms64, _ = timed("fp64", out64, max(1, min(args.steps, 5)), 1)
     ms64_k, per64_k = timed("fp64", out64, max(1, min(args.steps, 5)), 1, kernel_only=True)
 
-    value = world * states * args.steps / (ms32 * 1e-3)
-    fp64_value = world * states * max(1, min(args.steps, 5)) / (ms64 * 1e-3)
+    value = job_rate(states, args.steps, world, ms32)
+    fp64_value = job_rate(states, max(1, min(args.steps, 5)), world, ms64)
 
     # end to end through the public API with pinned host buffers
     r_h = torch.empty((n, T, 3), dtype=torch.float32).pin_memory()
@@ -426,7 +441,7 @@ def run_ours(args):
     b.record(stream)
     b.synchronize()
     e2e_ms = a.elapsed_time(b)
-    e2e_value = world * states * e2e_steps / (e2e_ms * 1e-3)
+    e2e_value = job_rate(states, e2e_steps, world, max_over_ranks(e2e_ms, dev))
     h2d = el_h.numel() * 8 + ts_h.numel() * 8
     d2h = (r_h.numel() + v_h.numel()) * 4 + s_h.numel() * 4
 
