@@ -56,10 +56,13 @@ struct Range {
 
 // States [beg, end) of one problem (local flattened index j * T + i).  Every thread
 // of the block calls it with the same arguments (it contains block barriers).
+// split, if not null, holds the problem's shared grid already split into float
+// hi + lo (FP32 path), one entry per time index.
 template <bool kFP32>
 __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
                                           const Range& rg, int64_t beg, int64_t end,
-                                          Stage<kFP32>& sm, unsigned long long& nfix) {
+                                          Stage<kFP32>& sm, unsigned long long& nfix,
+                                          const float2* split = nullptr) {
   using OutT = typename Stage<kFP32>::OutT;
   const int tid = threadIdx.x;
   const int64_t T = rg.T;            // <= INT32_MAX (checked by the API)
@@ -78,20 +81,26 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
         rc64 = load_rec64(rp, rec);
         cur = j;
       }
-      const double t = rg.per_sat ? __ldg(rg.tsince + j * T + i) : __ldg(rg.tsince + i);
+      const double* tp = rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i;
       OutT rr[3], vv[3];
       if (kFP32) {
         // The 160-byte FP32 row is re-read every state (ten 16-byte loads that L1
         // serves as broadcasts) instead of being held in registers across states.
         const Rec32 rc32 = load_rec32(rp, rec);
         float th, tl;
-        split_double(t, th, tl);
+        if (split) {
+          const float2 p = split[i];
+          th = p.x;
+          tl = p.y;
+        } else {
+          split_double(__ldg(tp), th, tl);
+        }
         float r32[3], v32[3];
         code = state32(rc32, gf, th, tl, r32, v32);
         for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r32[c]; vv[c] = (OutT)v32[c]; }
       } else {
         double r64[3], v64[3];
-        code = state64(rc64, g, t, r64, v64);
+        code = state64(rc64, g, __ldg(tp), r64, v64);
         for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r64[c]; vv[c] = (OutT)v64[c]; }
       }
       sm.r[3 * tid + 0] = rr[0]; sm.r[3 * tid + 1] = rr[1]; sm.r[3 * tid + 2] = rr[2];
@@ -99,7 +108,7 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
       if (kFP32 && code == kRecomputeFP64) {
         // The out-of-line recomputation writes its float results straight into this
         // thread's staging slots, so no local array has its address taken.
-        code = state64_fallback(rp, g, rec, t, reinterpret_cast<float*>(&sm.r[3 * tid]),
+        code = state64_fallback(rp, g, rec, __ldg(tp), reinterpret_cast<float*>(&sm.r[3 * tid]),
                                 reinterpret_cast<float*>(&sm.v[3 * tid]));
         ++nfix;
       }
@@ -145,14 +154,29 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
   }
 }
 
+// FP32 launches on a shared grid of at most this many times split the grid into float
+// hi + lo once per block, into dynamic shared memory (16 KB at most), instead of once
+// per state.
+constexpr int kSplitMaxT = 2048;
+
 template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
   __shared__ Stage<kFP32> sm;
+  extern __shared__ float2 s_split[];   // [t_count] when use_split
   const int64_t total = a.rp.n * a.t_count;
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
+  const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
+  if (use_split) {
+    for (int k = threadIdx.x; k < (int)a.t_count; k += kThreads) {
+      float h, l;
+      split_double(__ldg(a.tsince + k), h, l);
+      s_split[k] = make_float2(h, l);
+    }
+    __syncthreads();
+  }
   const GeoF gf = a.gf;
   Range rg;
   rg.tsince = a.tsince;
@@ -163,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.v = a.v;
   rg.status = a.status;
   unsigned long long nfix = 0;
-  run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, sm, nfix);
+  run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, sm, nfix, use_split ? s_split : nullptr);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
 
@@ -215,9 +239,10 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
 }
 
 template <typename K>
-int blocks_per_sm_of(K kernel) {
+int blocks_per_sm_of(K kernel, size_t dyn_smem = 0) {
   int bps = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kThreads, 0) != cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, kThreads, dyn_smem) !=
+      cudaSuccess)
     return 1;
   return bps > 0 ? bps : 1;
 }
@@ -226,13 +251,18 @@ template <bool kFP32>
 cudaError_t launch(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * a.t_count;
   if (total == 0) return cudaSuccess;
-  static int bps = 0;   // resident blocks per SM of this kernel (same on every B300)
-  if (bps == 0) bps = blocks_per_sm_of(propagate_kernel<kFP32>);
+  const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
+  const size_t dyn = use_split ? (size_t)a.t_count * sizeof(float2) : 0;
+  // Resident blocks per SM of this kernel (same on every B300), taken with the largest
+  // split table so that the wave below is resident whatever the grid length.
+  static int bps = 0;
+  if (bps == 0)
+    bps = blocks_per_sm_of(propagate_kernel<kFP32>, kFP32 ? kSplitMaxT * sizeof(float2) : 0);
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
   const int64_t blocks = (total + chunk - 1) / chunk;
-  propagate_kernel<kFP32><<<(unsigned)blocks, kThreads, 0, stream>>>(a, chunk);
+  propagate_kernel<kFP32><<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
   return cudaGetLastError();
 }
 
