@@ -268,7 +268,8 @@ sgp4_result sgp4_adjoint(const double* elements, const sgp4_records* records,
  *   elements_out  [n][7] double (may not alias elements)
  *   sse           [n] double out: sum of squared residuals at `elements`, km^2
  *   workspace     device, sgp4_fit_workspace_bytes(n) bytes, 8-byte aligned (holds
- *                 the Jacobian of sgp4init per satellite during the call)
+ *                 the Jacobian of sgp4init and the normal equations per satellite
+ *                 during the call)
  * SGP4_FP32 runs the sweeps in FP32 as sgp4_adjoint does and forms A and b per thread
  * in FP32 (sums over warps in FP64); the Cholesky solve is FP64 in both precisions.
  * Unusable records keep their elements and get sse 0.  Errors as sgp4_adjoint.

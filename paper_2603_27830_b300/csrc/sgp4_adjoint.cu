@@ -715,9 +715,7 @@ struct FitArgs {
   int64_t T;
   int per_sat;
   const double* r_obs;   // [n][T][3]
-  const double* lambda;  // [n] Levenberg-Marquardt damping
-  double* el_out;        // [n][7]
-  double* sse;           // [n] sum of squared position residuals at el (km^2)
+  double* normal;        // [n][36] out: A lower triangle (28), b (7), sse, in FP64
 };
 
 // The states of satellite j handled by this thread: residuals, the rows of dr/del
@@ -759,7 +757,9 @@ __device__ __forceinline__ void fit_loop(const FitArgs& a, const SatShared<T>& s
     for (int c = 0; c < 3; ++c) res[c] = r[c] - T(a.r_obs[s * 3 + c]);
     if (!(isfinite(res[0]) && isfinite(res[1]) && isfinite(res[2]))) continue;
     sse += res[0] * res[0] + res[1] * res[1] + res[2] * res[2];
-#pragma unroll
+    // Not unrolled: one copy of the sweep keeps the kernel within the instruction
+    // cache (the unrolled form ran 8% slower, stalled on instruction fetch).
+#pragma unroll 1
     for (int c = 0; c < 3; ++c) {
       T Jc[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
       auto contract = [&](int q, T v) {
@@ -789,18 +789,17 @@ __device__ __forceinline__ void fit_loop(const FitArgs& a, const SatShared<T>& s
   }
 }
 
-// One Gauss-Newton / Levenberg-Marquardt step of batch least squares per satellite:
-// residuals res_t = r_t(el) - r_obs_t over the states with finite output, the
-// position Jacobian J_t = dr_t/del (one forward and three reverse sweeps per state,
-// contracted with the init Jacobian), A = sum J_t^T J_t, b = sum J_t^T res_t, and the
-// step delta = -(A + lambda diag A)^-1 b solved by Cholesky on the Jacobi-scaled
-// matrix.  Per-thread sums in T, warp sums by shuffles, the warps' sums in FP64.
+// Normal equations of one Gauss-Newton / Levenberg-Marquardt step of batch least
+// squares per satellite (one block each): residuals res_t = r_t(el) - r_obs_t over the
+// states with finite output, the position Jacobian J_t = dr_t/del (one forward and
+// three reverse sweeps per state, contracted with the init Jacobian), A = sum J_t^T
+// J_t and b = sum J_t^T res_t.  Per-thread sums in T, warp sums by shuffles, the
+// warps' sums in FP64.  fit_solve_kernel then takes the step.
 template <class T>
 __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP32 : 1)
     fit_step_kernel(FitArgs a) {
   __shared__ T Ji[kNumAdj][7];
   __shared__ T part[36][kAdjWarps];
-  __shared__ double S[36];
   __shared__ int s_ok;
   __shared__ SatShared<T> sat;
   __shared__ Fwd<T> sfwd[FwdSlot<T>::kRows];
@@ -815,11 +814,7 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
   for (int q = tid; q < kNumAdj * 7; q += kAdjThreads)
     (&Ji[0][0])[q] = static_cast<const T*>(a.jac)[j * kNumAdj * 7 + q];
   __syncthreads();
-  if (!s_ok) {
-    if (tid < 7) a.el_out[j * 7 + tid] = a.el[j * 7 + tid];
-    if (tid == 0) a.sse[j] = 0.0;
-    return;
-  }
+  if (!s_ok) return;   // fit_solve_kernel keeps the elements of unusable records
   T A[28], b[7], sse = T(0);
 #pragma unroll
   for (int q = 0; q < 28; ++q) A[q] = T(0);
@@ -840,17 +835,35 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
   if (tid < 36) {
     double v = 0.0;
     for (int w = 0; w < kAdjWarps; ++w) v += (double)part[tid][w];
-    S[tid] = v;
+    a.normal[j * 36 + tid] = v;
   }
-  __syncthreads();
-  if (tid != 0) return;
-  // Unpack A (lower triangle), Jacobi scaling, damping, Cholesky.
+}
+
+// One thread per satellite: the Levenberg-Marquardt step from the normal equations
+// (A lower triangle, b, sse) of fit_step_kernel: Jacobi scaling, damping, Cholesky.
+// A thread per satellite shares each FP64 warp instruction among 32 satellites (the
+// FP64 unit charges per warp instruction).
+__global__ void __launch_bounds__(64) fit_solve_kernel(const double* __restrict__ el,
+                                                       const double* __restrict__ normal,
+                                                       const double* __restrict__ lambda,
+                                                       int64_t n, double* __restrict__ el_out,
+                                                       double* __restrict__ sse) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double e7[7];
+  for (int k = 0; k < 7; ++k) e7[k] = el[j * 7 + k];
+  if (!elements_usable(e7)) {
+    for (int k = 0; k < 7; ++k) el_out[j * 7 + k] = e7[k];
+    sse[j] = 0.0;
+    return;
+  }
+  const double* S = normal + j * 36;
   double M[7][7], rhs[7], d[7];
   int q = 0;
   for (int m = 0; m < 7; ++m)
     for (int l = 0; l <= m; ++l, ++q) M[m][l] = M[l][m] = S[q];
   for (int m = 0; m < 7; ++m) d[m] = M[m][m] > 0.0 ? 1.0 / sqrt(M[m][m]) : 0.0;
-  const double lam = a.lambda[j];
+  const double lam = lambda[j];
   for (int m = 0; m < 7; ++m) {
     for (int l = 0; l < 7; ++l) M[m][l] *= d[m] * d[l];
     M[m][m] = (d[m] > 0.0 ? M[m][m] : 1.0) * (1.0 + lam);
@@ -879,14 +892,16 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
       x[m] = v / M[m][m];
     }
   }
-  for (int m = 0; m < 7; ++m) a.el_out[j * 7 + m] = a.el[j * 7 + m] + x[m] * d[m];
-  a.sse[j] = S[35];
+  for (int m = 0; m < 7; ++m) el_out[j * 7 + m] = e7[m] + x[m] * d[m];
+  sse[j] = S[35];
 }
 
 }  // namespace
 
+// Workspace: the init Jacobians [n][kNumAdj][7] (of the sweep's precision, in a
+// double-sized slot) and the normal equations [n][36] (FP64).
 size_t fit_workspace_bytes(int64_t n) {
-  return n <= 0 ? 0 : (size_t)n * kNumAdj * 7 * sizeof(double);
+  return n <= 0 ? 0 : (size_t)n * (kNumAdj * 7 + 36) * sizeof(double);
 }
 
 cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el,
@@ -896,6 +911,7 @@ cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el
   if (rp.n == 0) return cudaSuccess;
   const int threads = 64;
   const unsigned blocks = (unsigned)((rp.n + threads - 1) / threads);
+  double* normal = workspace + rp.n * kNumAdj * 7;
   if (fp32)
     fit_jacobian_kernel<float><<<blocks, threads, 0, stream>>>(
         el, rp.n, g, reinterpret_cast<float*>(workspace));
@@ -913,11 +929,12 @@ cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el
   a.T = T;
   a.per_sat = per_sat;
   a.r_obs = r_obs;
-  a.lambda = lambda;
-  a.el_out = el_out;
-  a.sse = sse;
+  a.normal = normal;
   if (fp32) fit_step_kernel<float><<<(unsigned)rp.n, kAdjThreads, 0, stream>>>(a);
   else fit_step_kernel<double><<<(unsigned)rp.n, kAdjThreads, 0, stream>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  fit_solve_kernel<<<blocks, threads, 0, stream>>>(el, normal, lambda, rp.n, el_out, sse);
   return cudaGetLastError();
 }
 
