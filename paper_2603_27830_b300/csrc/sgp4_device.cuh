@@ -422,6 +422,26 @@ __device__ __forceinline__ void split_double(double t, float& hi, float& lo) {
   lo = sign ? -l : l;
 }
 
+// double -> float rounded to nearest (ties to even) with integer operations only, for
+// code that runs on B300's small FP64 unit, where a conversion instruction costs as
+// much as a DFMA.  |x| below the smallest normal float (2^-126) gives a signed zero;
+// beyond the float range +-inf; NaN stays NaN.
+__device__ __forceinline__ float f32_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned w1 = (unsigned)(b >> 32), w0 = (unsigned)b;
+  const int e = (int)((w1 >> 20) & 0x7ffu);
+  const unsigned sign = w1 & 0x80000000u;
+  if (e == 0x7ff)
+    return __uint_as_float(sign | 0x7f800000u | (((w1 & 0xfffffu) | w0) ? 0x400000u : 0u));
+  if (e < 897) return __uint_as_float(sign);
+  if (e > 1150) return __uint_as_float(sign | 0x7f800000u);
+  const unsigned m = ((w1 & 0xfffffu) << 3) | (w0 >> 29);   // top 23 fraction bits
+  const unsigned rem = w0 & 0x1fffffffu;                     // the 29 bits dropped
+  unsigned f = ((unsigned)(e - 896) << 23) + m;              // float exponent bias 127
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) f += 1u;   // carry is exact
+  return __uint_as_float(sign | f);
+}
+
 // sin and cos of x, |x| <= 2^12, to ~1e-7 absolute: Cody-Waite reduction by pi/2
 // with a two-part constant applied by FMA, then the Taylor series of sin (degree 9)
 // and cos (degree 10) on [-pi/4, pi/4] (truncation below 2e-9), and the quadrant

@@ -12,11 +12,6 @@ namespace sgp4 {
 
 namespace {
 
-__device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
-  hi = __double2float_rn(x);
-  lo = __double2float_rn(x - (double)hi);
-}
-
 // Satellites per 32-lane warp.  The record build is bound by B300's small FP64 unit,
 // which works through the active lanes of a warp instruction; a Starlink-sized set
 // (9,341) fills only half of the SM sub-partitions at 32 per warp, so fewer
@@ -28,7 +23,7 @@ __device__ __forceinline__ void split_df(double x, float& hi, float& lo) {
 __global__ void __launch_bounds__(32) init_kernel(const double* __restrict__ el,
                                                    const int32_t* __restrict__ epoch_day,
                                                    const double* __restrict__ epoch_frac,
-                                                   RecordPtrs rp, Geo g,
+                                                   RecordPtrs rp, Geo g, GeoF gf,
                                                    int32_t* __restrict__ init_status) {
   if (threadIdx.x >= SGP4_INIT_LANES) return;
   const int64_t j = (int64_t)blockIdx.x * SGP4_INIT_LANES + threadIdx.x;
@@ -88,38 +83,40 @@ __global__ void __launch_bounds__(32) init_kernel(const double* __restrict__ el,
   f[kX7thm1 * s + j] = x7thm1;
 
   // FP32 row: angles in revolutions, the argument-of-latitude phase as double-float.
+  // Conversions to float by integer operations (f32_rn, split_double): this kernel is
+  // bound by the FP64 unit, where each conversion instruction would cost a DFMA.
   const double inv2pi = 1.0 / kTwoPi;
   double phi0 = (m0 + argp0) * inv2pi;
   phi0 -= floor(phi0);
   float hi, lo;
-  split_df(phi0, hi, lo);
+  split_double(phi0, hi, lo);
   h[fPhi0H] = hi; h[fPhi0L] = lo;
-  split_df((mdot + argpdot) * inv2pi, hi, lo);
+  split_double((mdot + argpdot) * inv2pi, hi, lo);
   h[fPhiDH] = hi; h[fPhiDL] = lo;
   double m0r = m0 * inv2pi;       m0r -= floor(m0r);
   double argp0r = argp0 * inv2pi; argp0r -= floor(argp0r);
   double raan0r = raan0 * inv2pi; raan0r -= floor(raan0r);
-  h[fM0r] = (float)m0r;
-  h[fMdr] = (float)(mdot * inv2pi);
-  h[fArgp0r] = (float)argp0r;
-  h[fArgpdr] = (float)(argpdot * inv2pi);
-  h[fRaan0r] = (float)raan0r;
-  h[fRaandr] = (float)(raandot * inv2pi);
-  h[fRaanCfr] = (float)(raan_cf * inv2pi);
-  h[fN0ppr] = (float)(n0pp * inv2pi);
-  h[fA0pp] = (float)a0pp;   h[fE0] = (float)e0;     h[fC1] = (float)C1;
-  h[fBC4] = (float)bc4;     h[fBC5] = (float)bc5;   h[fD2] = (float)D2;
-  h[fD3] = (float)D3;       h[fD4] = (float)D4;     h[fL2] = (float)L2;
-  h[fL3] = (float)L3;       h[fL4] = (float)L4;     h[fL5] = (float)L5;
-  h[fEta] = (float)eta;     h[fDelM0] = (float)delm0; h[fSinM0] = (float)sinm0;
-  h[fArgpCf] = (float)argp_cf; h[fMCf] = (float)m_cf;
-  h[fXlcof] = (float)xlcof; h[fAycof] = (float)aycof;
-  h[fCosi] = (float)cosi;   h[fSini] = (float)sini;
-  h[fX3thm1] = (float)(1.5 * x3thm1); h[fX1mth2] = (float)x1mth2;
-  h[fX7thm1] = (float)(-0.25 * x7thm1);
-  h[fHalfX1mth2] = (float)(0.5 * x1mth2);
-  h[fC15Cosi] = (float)(1.5 * cosi);
-  h[fC15CosiSini] = (float)(1.5 * cosi * sini);
+  h[fM0r] = f32_rn(m0r);
+  h[fMdr] = f32_rn(mdot * inv2pi);
+  h[fArgp0r] = f32_rn(argp0r);
+  h[fArgpdr] = f32_rn(argpdot * inv2pi);
+  h[fRaan0r] = f32_rn(raan0r);
+  h[fRaandr] = f32_rn(raandot * inv2pi);
+  h[fRaanCfr] = f32_rn(raan_cf * inv2pi);
+  h[fN0ppr] = f32_rn(n0pp * inv2pi);
+  h[fA0pp] = f32_rn(a0pp);   h[fE0] = f32_rn(e0);     h[fC1] = f32_rn(C1);
+  h[fBC4] = f32_rn(bc4);     h[fBC5] = f32_rn(bc5);   h[fD2] = f32_rn(D2);
+  h[fD3] = f32_rn(D3);       h[fD4] = f32_rn(D4);     h[fL2] = f32_rn(L2);
+  h[fL3] = f32_rn(L3);       h[fL4] = f32_rn(L4);     h[fL5] = f32_rn(L5);
+  h[fEta] = f32_rn(eta);     h[fDelM0] = f32_rn(delm0); h[fSinM0] = f32_rn(sinm0);
+  h[fArgpCf] = f32_rn(argp_cf); h[fMCf] = f32_rn(m_cf);
+  h[fXlcof] = f32_rn(xlcof); h[fAycof] = f32_rn(aycof);
+  h[fCosi] = f32_rn(cosi);   h[fSini] = f32_rn(sini);
+  h[fX3thm1] = f32_rn(1.5 * x3thm1); h[fX1mth2] = f32_rn(x1mth2);
+  h[fX7thm1] = f32_rn(-0.25 * x7thm1);
+  h[fHalfX1mth2] = f32_rn(0.5 * x1mth2);
+  h[fC15Cosi] = f32_rn(1.5 * cosi);
+  h[fC15CosiSini] = f32_rn(1.5 * cosi * sini);
 
   int flags = 0;
   if (isimp) flags |= kFlagIsimp;
@@ -132,13 +129,6 @@ __global__ void __launch_bounds__(32) init_kernel(const double* __restrict__ el,
   // its FP64 recomputation inside the guard bands (so it equals the FP64 decision).
   {
     const Rec32 r32 = read_own_rec32(h);
-    GeoF gf;
-    gf.xke = (float)g.xke;
-    gf.inv_xke = (float)(1.0 / g.xke);
-    gf.j2 = (float)g.j2;
-    gf.re = (float)g.re;
-    gf.vkmps = (float)g.vkmps;
-    gf.half_j2 = (float)(0.5 * g.j2);
     float r[3], v[3];
     const int code = state32(r32, gf, 0.0f, 0.0f, r, v);
     if (code != kRecomputeFP64) {
@@ -166,7 +156,7 @@ cudaError_t launch_init(const double* el, const int32_t* epoch_day, const double
   const int threads = 32;
   const int64_t blocks = (rp.n + SGP4_INIT_LANES - 1) / SGP4_INIT_LANES;
   init_kernel<<<(unsigned)blocks, threads, 0, stream>>>(el, epoch_day, epoch_frac, rp, g,
-                                                        init_status);
+                                                        geo_float(g), init_status);
   return cudaGetLastError();
 }
 

@@ -159,6 +159,38 @@ __device__ __forceinline__ void sincos(const Dual7<R>& a, Dual7<R>* s, Dual7<R>*
 template <class R>
 __device__ __forceinline__ R val(const Dual7<R>& a) { return a.v; }
 __device__ __forceinline__ double val(double a) { return a; }
+// Exact float -> double with integer operations (normal floats and zero; the values
+// passed are FP32 approximations of positive normal doubles).
+__device__ __forceinline__ double f64_exact(float v) {
+  const unsigned u = __float_as_uint(v);
+  const unsigned e = (u >> 23) & 0xffu;
+  if (e == 0u) return 0.0;
+  const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+// Cube root of the positive doubles of the record build, (ke/n)^(2/3) = cbrt((ke/n)^2):
+// an FP32 seed refined by two Newton steps y <- y - (y^3 - x) / (3 y^2) in FP64 with the
+// reciprocal of 3 y^2 taken in FP32.  Each step multiplies the relative error by about
+// that reciprocal's error (1e-7) and adds its square, so two steps take a 1e-7 seed to
+// the last bits of a double.  Outside [1e-30, 1e30] the library's cbrt.  On B300 this
+// is a dozen FP64-unit instructions; the record build is bound by that unit.
+__device__ __forceinline__ double cbrt_pos(double x) {
+  if (!(x > 1.0e-30 && x < 1.0e30)) return ::cbrt(x);
+  double y = f64_exact(::cbrtf(f32_rn(x)));
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double y2 = y * y;
+    const double r = f64_exact(1.0f / (3.0f * f32_rn(y2)));
+    y = fma(-fma(y2, y, -x), r, y);
+  }
+  return y;
+}
+template <class R>
+__device__ __forceinline__ Dual7<R> cbrt_pos(const Dual7<R>& a) { return cbrt(a); }
+
 // Keep the double versions visible next to the dual overloads in this namespace.
 using ::cbrt;
 using ::cos;
@@ -197,13 +229,13 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
 
   // Kozai -> Brouwer mean motion and semi-major axis.
   const S x1 = g.xke / n0;
-  const S a1 = cbrt(x1 * x1);                 // (ke / n0)^(2/3)
+  const S a1 = cbrt_pos(x1 * x1);             // (ke / n0)^(2/3)
   const S d1 = 1.5 * k2 * x3thm1 / (a1 * a1 * b3);
   const S a0 = a1 * (1.0 - d1 / 3.0 - d1 * d1 - (134.0 / 81.0) * d1 * d1 * d1);
   const S d0 = 1.5 * k2 * x3thm1 / (a0 * a0 * b3);
   const S n0pp = n0 / (1.0 + d0);
   const S xpp = g.xke / n0pp;
-  const S a0pp = cbrt(xpp * xpp);             // (ke / n0'')^(2/3)
+  const S a0pp = cbrt_pos(xpp * xpp);         // (ke / n0'')^(2/3)
 
   // Atmosphere: s and (q0 - s)^4 by perigee height.
   const S rp_er = a0pp * (1.0 - e0);

@@ -146,7 +146,7 @@ def test_edge_elements(prec):
 
 
 @pytest.mark.parametrize("n,T", [(1, 1), (1, 127), (3, 1), (7, 13), (129, 1), (33, 129),
-                                 (5, 1000), (1000, 3)])
+                                 (5, 1000), (1000, 3), (3, 2048), (2, 2049)])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_ragged_shapes(n, T, prec):
     rng = np.random.default_rng(n * 1000 + T)
@@ -214,3 +214,38 @@ def test_fp32_time_split_keeps_minute_fractions():
     assert_status_and_nan(st, sr, r, v, ist, isr)
     dr, dv = state_errors(r, v, rr, vr, sr)
     assert dr.max() < 0.02, error_summary(dr, dv)
+
+
+# The record layout of the C ABI (sgp4.h): FP64 planes, then one row of 40 floats per
+# satellite.  Plane and row indices of the fields the FP32 row carries unscaled.
+_N_PLANES, _ROW = 35, 40
+_PLANE_ROW = {"a0pp": (1, 12), "e0": (2, 13), "c1": (14, 14), "bc4": (15, 15), "bc5": (16, 16),
+              "d2": (17, 17), "d3": (18, 18), "d4": (19, 19), "l2": (20, 20), "l3": (21, 21),
+              "l4": (22, 22), "l5": (23, 23), "eta": (24, 24), "delm0": (25, 25),
+              "sinm0": (26, 26), "argp_cf": (12, 27), "m_cf": (13, 28), "xlcof": (27, 29),
+              "aycof": (28, 30), "cosi": (29, 31), "sini": (30, 32), "x1mth2": (32, 34)}
+
+
+def test_fp32_rows_are_nearest_floats_of_the_fp64_planes():
+    """The record builder converts to float with integer operations; each unscaled
+    field of the FP32 row must be numpy's round-to-nearest float of the FP64 plane
+    (values below the smallest normal float become zero)."""
+    import torch
+
+    from paper_2603_27830_b300 import sgp4_init
+    rng = np.random.default_rng(11)
+    el = np.concatenate([W.config2().elements[:3000],
+                         W.catalogue_elements(rng, 3000, invalid_frac=0.0)])
+    n = el.shape[0]
+    recs, _ = sgp4_init(torch.as_tensor(el, device="cuda"))
+    torch.cuda.synchronize()
+    stride = int(recs.c.stride)
+    raw = recs.arena.cpu().numpy()
+    planes = raw[:_N_PLANES * stride * 8].view(np.float64).reshape(_N_PLANES, stride)[:, :n]
+    rows = raw[_N_PLANES * stride * 8:(_N_PLANES * stride * 8 + stride * _ROW * 4)]
+    rows = rows.view(np.float32).reshape(stride, _ROW)[:n]
+    for name, (p, r) in _PLANE_ROW.items():
+        want = planes[p].astype(np.float32)
+        want[np.abs(planes[p]) < 2.0 ** -126] = 0.0
+        got = rows[:, r]
+        assert np.array_equal(got, want), name          # -0.0 == 0.0 for flushed values
