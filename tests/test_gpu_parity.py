@@ -249,3 +249,12 @@ def test_fp32_rows_are_nearest_floats_of_the_fp64_planes():
         want[np.abs(planes[p]) < 2.0 ** -126] = 0.0
         got = rows[:, r]
         assert np.array_equal(got, want), name          # -0.0 == 0.0 for flushed values
+
+
+def test_scaling_sweep_runs_and_reports_rates():
+    from paper_2603_27830_b300 import scaling
+    rows = scaling.run([("NxT", 3, 5), ("1xT", 1, 2049)], precisions=("fp32", "fp64"))
+    assert len(rows) == 4
+    for r in rows:
+        assert r["ms_per_call"] > 0 and r["states_per_s"] == pytest.approx(
+            r["states"] / (r["ms_per_call"] * 1e-3))
