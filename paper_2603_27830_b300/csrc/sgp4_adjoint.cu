@@ -264,7 +264,9 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
   f.om = 1.0f - f.e * f.e;
   f.q = rcp_pos(f.a * f.om);
   f.ayn = fmaf(f.e, f.sw, f.q * rc.aycof);
-  const float U = wrap_rev(y + f.q * rc.xlcof * f.axn * kInvTwoPiF) * kTwoPiF;
+  const float lpt = f.q * rc.xlcof * f.axn;
+  if (!(fabsf(lpt) < kGuardLongPeriod)) return kRecomputeFP64;
+  const float U = wrap_rev(y + lpt * kInvTwoPiF) * kTwoPiF;
   f.eL2 = f.axn * f.axn + f.ayn * f.ayn;
   float psi = U;
   const int K = newton_steps(f.eL2);

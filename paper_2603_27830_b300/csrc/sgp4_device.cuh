@@ -499,6 +499,11 @@ __device__ __forceinline__ int newton_steps(float eL2) {
 constexpr float kGuardE = 2.0e-5f;
 constexpr float kGuardP = 2.0e-5f;
 constexpr float kGuardR = 5.0e-5f;
+// The long-period correction of U, q xlcof a_xN (rad), has the factor 1 / (1 + cos i)
+// and grows without bound as the inclination nears 180 degrees; in FP32 its rounding
+// error (~6e-8 of it) reaches the position once it exceeds a radian, so such states are
+// recomputed in FP64 too (inclinations within a few hundredths of a degree of 180).
+constexpr float kGuardLongPeriod = 1.0f;
 constexpr int kRecomputeFP64 = -1;
 
 // One state in FP32 with the n*t phase in double-float.  (th, tl) is tsince split as
@@ -509,8 +514,7 @@ constexpr int kRecomputeFP64 = -1;
 __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th, float tl,
                                        float r[3], float v[3]) {
   const int fatal = (rc.flags >> kFatalShift) & 0xff;
-  int code = fatal ? fatal : ((rc.flags & kFlagN0ppNonPos) ? 2 : 0);
-  bool need64 = false;
+  const int code0 = fatal ? fatal : ((rc.flags & kFlagN0ppNonPos) ? 2 : 0);
   const bool isimp = rc.flags & kFlagIsimp;
   const float t = th;
   const float t2 = t * t;
@@ -533,9 +537,11 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   }
   const float a = rc.a0pp * tempa * tempa;
   float e = rc.e0 - tempe;
-  const bool near_e = !(fabsf(e - 1.0f) >= kGuardE && fabsf(e + 0.001f) >= kGuardE && a > 1.0e-3f);
-  need64 = need64 || (code == 0 && near_e);
-  if (code == 0 && !need64 && (e >= 1.0f || e < -0.001f)) code = 1;
+  // Status checks in the theory's order (2, 1, 4, 6) and the guard bands around them,
+  // as predicates combined at the end.
+  const bool g_e = !(fabsf(e - 1.0f) >= kGuardE) | !(fabsf(e + 0.001f) >= kGuardE) |
+                   !(a > 1.0e-3f);
+  const bool f_e = (e >= 1.0f) | (e < -0.001f);
   e = fmaxf(e, 1.0e-6f);
   const float ra = rsqrtf(a);
   const float sa = a * ra;
@@ -561,7 +567,9 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   const float axn = e * cw;
   const float q = rcp_pos(a * (1.0f - e * e));
   const float ayn = fmaf(e, sw, q * rc.aycof);
-  const float U = wrap_rev(y + q * rc.xlcof * axn * kInvTwoPiF) * kTwoPiF;
+  const float lpt = q * rc.xlcof * axn;
+  const bool g_lp = !(fabsf(lpt) < kGuardLongPeriod);
+  const float U = wrap_rev(y + lpt * kInvTwoPiF) * kTwoPiF;
   const float eL2 = axn * axn + ayn * ayn;
 
   // Kepler: Newton from psi = U, clamped to +-0.95, step count from the e_L bound.
@@ -581,8 +589,8 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   const float ecosE = axn * cp + ayn * sp;
   const float esinE = axn * sp - ayn * cp;
   const float pL = a * (1.0f - eL2);
-  need64 = need64 || (code == 0 && !(fabsf(pL) >= kGuardP));
-  if (code == 0 && !need64 && pL < 0.0f) code = 4;
+  const bool g_p = !(fabsf(pL) >= kGuardP);
+  const bool f_p = pL < 0.0f;
   const float rl = a * (1.0f - ecosE);
   const float invr = rcp_pos(rl);
   const float rdotl = sa * esinE * invr;
@@ -602,7 +610,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   const float k = g.half_j2 * invp;
   const float kp = k * invp;
   const float rk = rl * fmaf(-kp * betal, rc.x3thm1_15, 1.0f) + k * rc.half_x1mth2 * cos2u;
-  need64 = need64 || (code == 0 && !(fabsf(rk - 1.0f) >= kGuardR));
+  const bool g_r = !(fabsf(rk - 1.0f) >= kGuardR);
   const float nk = ra3 * k;                 // n k / ke
   const float rdotk = rdotl - nk * rc.x1mth2 * sin2u;
   const float rfdotk = fmaf(nk, fmaf(rc.x1mth2, cos2u, rc.x3thm1_15), rfdotl);
@@ -611,7 +619,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   const float du = kp * rc.x7thm1_m025 * sin2u;
   const float dO = kp * rc.c15cosi * sin2u;
   const float di = kp * rc.c15cosisini * cos2u;
-  need64 = need64 || (code == 0 && !(fmaxf(fabsf(du), fmaxf(fabsf(dO), fabsf(di))) < 4.0e-3f));
+  const bool g_d = !(fmaxf(fabsf(du), fmaxf(fabsf(dO), fabsf(di))) < 4.0e-3f);
   const float nrm = rsqrtf(sinu * sinu + cosu * cosu);
   float su = sinu * nrm, cu = cosu * nrm;
   rotate_small(su, cu, du);
@@ -629,8 +637,11 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   v[0] = (rdotk * ux + rfdotk * vx) * g.vkmps;
   v[1] = (rdotk * uy + rfdotk * vy) * g.vkmps;
   v[2] = (rdotk * uz + rfdotk * vz) * g.vkmps;
-  if (need64) return kRecomputeFP64;
-  return code != 0 ? code : (rk < 1.0f ? 6 : 0);
+  // A guard matters only while no earlier check has failed for certain.
+  const bool need64 = g_e | (!f_e & (g_lp | g_p | (!f_p & (g_r | g_d))));
+  int code = f_e ? 1 : (f_p ? 4 : (rk < 1.0f ? 6 : 0));
+  code = need64 ? kRecomputeFP64 : code;
+  return code0 ? code0 : code;
 }
 
 }  // namespace sgp4

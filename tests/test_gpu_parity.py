@@ -258,3 +258,29 @@ def test_scaling_sweep_runs_and_reports_rates():
     for r in rows:
         assert r["ms_per_call"] > 0 and r["states_per_s"] == pytest.approx(
             r["states"] / (r["ms_per_call"] * 1e-3))
+
+
+def test_precision_study_bins_and_bounds():
+    from paper_2603_27830_b300 import precision_study
+    rows = precision_study.study("starlink-200", W.config2(seed=1, n=200).elements, 2.0, 48)
+    assert [r["day"] for r in rows] == [0, 1]
+    for r in rows:
+        assert r["status_mismatches"] == 0
+        assert r["dr_median_km"] <= r["dr_p99_km"] <= r["dr_max_km"] <= 0.1
+
+
+def test_fp32_near_retrograde_equatorial():
+    """Inclinations within a hair of 180 degrees: the long-period term carries
+    1 / (1 + cos i) and reaches hundreds of radians; the FP32 path hands those states
+    to the FP64 recomputation, so it stays within the one-day target."""
+    rng = np.random.default_rng(17)
+    n = 64
+    di = 10.0 ** rng.uniform(-7, -2, n)                   # pi - i, rad
+    el = np.column_stack([rng.uniform(6.8, 15.5, n) * REV, rng.uniform(0.01, 0.2, n),
+                          math.pi - di, rng.uniform(0, 2 * math.pi, (n, 3)),
+                          10.0 ** rng.uniform(-5, -3, n)])
+    perigee_ok = (0.0743669161 / el[:, 0]) ** (2 / 3) * (1 - el[:, 1]) * 6378.135 > 6578.0
+    el = el[perigee_ok]
+    t = np.linspace(0.0, 1440.0, 97)
+    summ = _check_fp32(el, t, 0.1, 1e-4)
+    assert summ["fp64_fixups"] > 0
