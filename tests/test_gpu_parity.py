@@ -33,17 +33,25 @@ def _check_fp64(el, t):
     return error_summary(dr, dv)
 
 
-def _check_fp32(el, t, max_dr_km, max_dv_kms):
+def _check_fp32(el, t, max_dr_km, max_dv_kms, max_dr_code0_km=None):
+    """FP32 path vs the oracle: exact statuses, NaN where they say so, and |dr|, |dv|
+    bounds over the states with output (optionally a tighter |dr| bound over the states
+    with status 0, i.e. not yet decayed)."""
     r, v, st, ist, nfix = gpu_propagate(el, t, "fp32", fixups=True)
     rr, vr, sr, isr = oracle.propagate(el, t)
     assert_status_and_nan(st, sr, r, v, ist, isr)
     dr, dv = state_errors(r, v, rr, vr, sr)
     summ = error_summary(dr, dv)
     summ["fp64_fixups"] = nfix
+    ok0 = sr == 0
+    summ["max_dr_code0_km"] = (float(np.linalg.norm(r[ok0] - rr[ok0], axis=-1).max())
+                               if ok0.any() else 0.0)
     print(json.dumps(summ))
     if dr.size:
         assert dr.max() <= max_dr_km, summ
         assert dv.max() <= max_dv_kms, summ
+    if max_dr_code0_km is not None:
+        assert summ["max_dr_code0_km"] <= max_dr_code0_km, summ
     return summ
 
 
@@ -78,8 +86,10 @@ def test_catalogue_small_fp64():
 
 def test_catalogue_small_fp32():
     w = W.config3(seed=7, n=20_000)
-    # seven days and B* up to 1e-2: bounded but looser than the one-day target
-    _check_fp32(w.elements, w.tsince, 2.0, 2e-3)
+    # seven days and B* up to 1e-2; the largest errors (0.17 km) are in records that
+    # have decayed days earlier (deliberately invalid ones with a perigee below the
+    # surface among them), whose states alternate between status 6 and 0
+    _check_fp32(w.elements, w.tsince, 0.25, 2e-3)
 
 
 def test_catalogue_full_size_sampled():
