@@ -107,10 +107,11 @@ sgp4_result sgp4_records_bind(void* arena, size_t bytes, int64_t n, const sgp4_c
  * C++ baseline).  One thread per satellite, FP64.
  *   elements     [n][7] double, row-major: n0 (rad/min, Kozai), e0, i0, RAAN0,
  *                argp0, M0 (rad), B* (1/Earth radii)
- *   epoch_day    [n] int32 and epoch_frac [n] double: epoch as integer day plus
- *                fraction (paper Sec. 6: a split epoch avoids the FP32 epoch
- *                rounding).  Both may be NULL; they are stored, not used by
- *                tsince-based propagation.
+ *   epoch_day    [n] int32 and epoch_frac [n] double: epoch as Julian date split
+ *                into an integer day and a fraction in [0, 1) (paper Sec. 6: a split
+ *                epoch avoids the FP32 epoch rounding).  Both may be NULL (epoch 0).
+ *                Stored in the records; sgp4_propagate_jd measures time from them,
+ *                tsince-based propagation does not use them.
  *   init_status  [n] int32 out: 1/2 for unusable input (fatal for the record),
  *                otherwise the status of the state at tsince = 0.
  * Errors: SGP4_ERR_ARG for NULL elements/records/init_status with n > 0, a record
@@ -137,6 +138,23 @@ sgp4_result sgp4_init(const double* elements, const int32_t* epoch_day, const do
 sgp4_result sgp4_propagate(const sgp4_records* records, const double* tsince, int64_t t_count,
                            int grid_per_sat, sgp4_precision precision, void* r, void* v,
                            int32_t* status, unsigned long long* fixups, void* stream);
+
+/*
+ * sgp4_propagate_jd: as sgp4_propagate, for absolute times shared by all satellites,
+ * given as Julian dates split into day and fraction (paper Sec. 6 on epochs; the
+ * theory propagates from each record's own epoch).  For record j and time i,
+ *   tsince = 1440 ((jd_day[i] - epoch_day[j]) + (jd_frac[i] - epoch_frac[j])) minutes,
+ * with the day difference taken in integers, evaluated on the device in FP64 (then
+ * split into float hi + lo for the FP32 path).
+ *   jd_day       [t_count] int32, 4-byte aligned; jd_frac [t_count] double, 8-byte aligned
+ *   other arguments as in sgp4_propagate (outputs [n][t_count][3], [n][t_count])
+ * |jd_day[i] - epoch_day[j]| must stay below 1,491,308 days (the int32 product by 1440).
+ * Errors as sgp4_propagate.
+ */
+sgp4_result sgp4_propagate_jd(const sgp4_records* records, const int32_t* jd_day,
+                              const double* jd_frac, int64_t t_count, sgp4_precision precision,
+                              void* r, void* v, int32_t* status, unsigned long long* fixups,
+                              void* stream);
 
 /*
  * Batched propagation of many uneven problems in one persistent launch.  The paper
@@ -310,6 +328,49 @@ sgp4_result sgp4_propagate_batched_static(const sgp4_request* requests, int32_t 
                                           const double* tsince, int64_t tsince_len,
                                           sgp4_precision precision, void* r, void* v,
                                           int32_t* status, int64_t out_len, void* stream);
+
+/*
+ * Two-line element sets (host functions; no device work).  The NORAD fixed-column
+ * format: line 1 carries the catalogue number (five digits or "Alpha-5"), the epoch
+ * (two-digit year, 57-99 -> 19xx, 00-56 -> 20xx, and day of year with fraction) and
+ * B*; line 2 inclination, RAAN, eccentricity (implied leading point), argument of
+ * perigee, mean anomaly (degrees) and mean motion (rev/day); each line ends with a
+ * modulo-10 checksum of its first 68 columns ('-' counts 1).
+ *
+ * sgp4_tle_parse: one set into the units of sgp4_init.
+ *   line1, line2   NUL-terminated lines of at least 69 columns (trailing CR/LF/blanks ok)
+ *   elements       [7] out: n0 rad/min, e0, i0, RAAN0, argp0, M0 (rad), B* (1/Earth radii)
+ *   epoch_day, epoch_frac  out: epoch as Julian date, integer day + fraction in [0, 1)
+ *   satnum         out (may be NULL): catalogue number
+ * Errors: SGP4_ERR_ARG for NULL pointers, short lines, wrong line numbers, a checksum
+ * mismatch, different catalogue numbers on the two lines, or a malformed field.
+ */
+sgp4_result sgp4_tle_parse(const char* line1, const char* line2, double* elements,
+                           int32_t* epoch_day, double* epoch_frac, int32_t* satnum);
+
+/*
+ * sgp4_tle_parse_text: every set in a text of two- or three-line sets (name lines and
+ * blank lines are skipped), in order.  Stores at most `capacity` sets into elements
+ * [capacity][7], epoch_day, epoch_frac and satnum (may be NULL); returns the number of
+ * valid sets found (which may exceed capacity: call again with more room), or -1 for
+ * bad arguments.  n_rejected (may be NULL) receives the number of sets or orphan
+ * line-1s rejected.
+ */
+int64_t sgp4_tle_parse_text(const char* text, size_t len, int64_t capacity, double* elements,
+                            int32_t* epoch_day, double* epoch_frac, int32_t* satnum,
+                            int64_t* n_rejected);
+
+/*
+ * sgp4_tle_format: the set for elements (units of sgp4_init) and a split Julian epoch,
+ * with first and second derivatives of the mean motion zero, at the format's
+ * resolution (1e-4 deg, 1e-7 in e, 1e-8 rev/day, 1e-8 day in the epoch, 5 digits of B*).
+ *   line1, line2   out: 70-byte buffers (69 columns + NUL)
+ * Errors: SGP4_ERR_ARG for NULL pointers, satnum outside 0..99999, epoch_frac outside
+ * [0, 1), an epoch outside 1957-2056, mean motion outside (0, 100) rev/day, e outside
+ * [0, 1), inclination outside [0, 180] deg, or |B*| beyond the exponent digit.
+ */
+sgp4_result sgp4_tle_format(const double* elements, int32_t epoch_day, double epoch_frac,
+                            int32_t satnum, char* line1, char* line2);
 
 /* Library version (major*10000 + minor*100 + patch). */
 int sgp4_version(void);

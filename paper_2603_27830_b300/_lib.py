@@ -26,10 +26,11 @@ RESULT_NAMES = {0: "SGP4_OK", -1: "SGP4_ERR_ARG", -2: "SGP4_ERR_CUDA", -3: "SGP4
 # Every symbol include/sgp4.h declares (checked by the CPU tests).
 EXPORTS = (
     "sgp4_version", "sgp4_wgs72", "sgp4_records_bytes", "sgp4_records_bind", "sgp4_init",
-    "sgp4_propagate", "sgp4_batch_workspace_bytes", "sgp4_batch_plan_init",
+    "sgp4_propagate", "sgp4_propagate_jd", "sgp4_batch_workspace_bytes", "sgp4_batch_plan_init",
     "sgp4_propagate_batched", "sgp4_batch_graph_create", "sgp4_batch_graph_launch",
     "sgp4_batch_graph_destroy", "sgp4_propagate_batched_static", "sgp4_adjoint_workspace_bytes",
-    "sgp4_adjoint", "sgp4_fit_workspace_bytes", "sgp4_fit_step",
+    "sgp4_adjoint", "sgp4_fit_workspace_bytes", "sgp4_fit_step", "sgp4_tle_parse",
+    "sgp4_tle_parse_text", "sgp4_tle_format",
 )
 STATIC_MAX_REQUESTS = 1024
 
@@ -81,6 +82,8 @@ def _declare(lib):
     lib.sgp4_init.restype = I32
     lib.sgp4_propagate.argtypes = [R, P, I64, I32, I32, P, P, P, P, P]
     lib.sgp4_propagate.restype = I32
+    lib.sgp4_propagate_jd.argtypes = [R, P, P, I64, I32, P, P, P, P, P]
+    lib.sgp4_propagate_jd.restype = I32
     BP = ctypes.POINTER(Sgp4BatchPlan)
     lib.sgp4_batch_workspace_bytes.argtypes = [ctypes.c_int32]
     lib.sgp4_batch_workspace_bytes.restype = ctypes.c_size_t
@@ -107,6 +110,13 @@ def _declare(lib):
     lib.sgp4_fit_workspace_bytes.restype = ctypes.c_size_t
     lib.sgp4_fit_step.argtypes = [P, R, P, I64, I32, I32, P, P, P, P, P, ctypes.c_size_t, P]
     lib.sgp4_fit_step.restype = I32
+    CP = ctypes.c_char_p
+    lib.sgp4_tle_parse.argtypes = [CP, CP, P, P, P, P]
+    lib.sgp4_tle_parse.restype = I32
+    lib.sgp4_tle_parse_text.argtypes = [CP, ctypes.c_size_t, I64, P, P, P, P, P]
+    lib.sgp4_tle_parse_text.restype = I64
+    lib.sgp4_tle_format.argtypes = [P, I32, ctypes.c_double, I32, P, P]
+    lib.sgp4_tle_format.restype = I32
     return lib
 
 

@@ -121,6 +121,38 @@ def sgp4_propagate(records: Records, tsince: torch.Tensor, precision: str = "fp3
     return r, v, st
 
 
+def sgp4_propagate_jd(records: Records, jd_day: torch.Tensor, jd_frac: torch.Tensor,
+                      precision: str = "fp32", out: tuple | None = None,
+                      fixups: torch.Tensor | None = None, stream=None):
+    """r, v [n, T, 3] and status [n, T] at absolute times given as Julian dates split
+    into int32 days jd_day [T] and fractions jd_frac [T]; each record propagates from
+    the split epoch it was built with (sgp4_init's epoch_day, epoch_frac)."""
+    _require_cuda("jd_day", jd_day, torch.int32)
+    _require_cuda("jd_frac", jd_frac, torch.float64)
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    if jd_day.dim() != 1 or jd_frac.shape != jd_day.shape:
+        raise ValueError("jd_day and jd_frac must both be [T]")
+    n = records.n
+    T = jd_day.shape[0]
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    dev = jd_day.device
+    if out is None:
+        r = torch.empty((n, T, 3), dtype=dt, device=dev)
+        v = torch.empty((n, T, 3), dtype=dt, device=dev)
+        st = torch.empty((n, T), dtype=torch.int32, device=dev)
+    else:
+        r, v, st = out
+    if fixups is not None:
+        _require_cuda("fixups", fixups, torch.int64)
+    lib = _lib.load()
+    _lib.check("sgp4_propagate_jd",
+               lib.sgp4_propagate_jd(ctypes.byref(records.c), _ptr(jd_day), _ptr(jd_frac), T,
+                                     PRECISIONS[precision], _ptr(r), _ptr(v), _ptr(st),
+                                     _ptr(fixups), _stream_handle(stream)))
+    return r, v, st
+
+
 def propagate_host(elements, tsince, precision: str = "fp32", device="cuda"):
     """End-to-end call on host arrays: copy in, init, propagate, copy out (numpy out)."""
     import numpy as np

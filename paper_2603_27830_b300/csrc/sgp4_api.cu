@@ -162,6 +162,39 @@ sgp4_result sgp4_propagate(const sgp4_records* records, const double* tsince, in
   return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
 }
 
+sgp4_result sgp4_propagate_jd(const sgp4_records* records, const int32_t* jd_day,
+                              const double* jd_frac, int64_t t_count, sgp4_precision precision,
+                              void* r, void* v, int32_t* status, unsigned long long* fixups,
+                              void* stream) {
+  if (!records_ok(records) || t_count < 0 || t_count > INT32_MAX) return SGP4_ERR_ARG;
+  if (precision != SGP4_FP64 && precision != SGP4_FP32) return SGP4_ERR_ARG;
+  const int64_t n = records->n;
+  if (n == 0 || t_count == 0) return SGP4_OK;
+  if (n > INT64_MAX / 3 / t_count) return SGP4_ERR_ARG;
+  if (!jd_day || !jd_frac || !r || !v || !status) return SGP4_ERR_ARG;
+  if (!aligned(jd_day, 4) || !aligned(jd_frac, 8) || !aligned(r, 16) || !aligned(v, 16) ||
+      !aligned(status, 16))
+    return SGP4_ERR_ARG;
+  if (fixups && !aligned(fixups, 8)) return SGP4_ERR_ARG;
+  sgp4::PropArgs a;
+  a.rp = sgp4::record_ptrs(records->arena, n);
+  a.g = make_geo(records->consts);
+  a.gf = sgp4::geo_float(a.g);
+  a.tsince = nullptr;
+  a.jd_day = jd_day;
+  a.jd_frac = jd_frac;
+  a.t_count = t_count;
+  a.grid_per_sat = 0;
+  a.r = r;
+  a.v = v;
+  a.status = status;
+  a.fixups = fixups;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = precision == SGP4_FP64 ? sgp4::launch_propagate64(a, s)
+                                         : sgp4::launch_propagate32(a, s);
+  return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
+}
+
 size_t sgp4_batch_workspace_bytes(int32_t n_requests) {
   if (n_requests < 0) return 0;
   return ws_reqs_off(n_requests) + round256(sizeof(sgp4_request) * (size_t)n_requests);

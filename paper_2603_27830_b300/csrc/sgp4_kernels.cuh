@@ -18,6 +18,8 @@ struct PropArgs {
   Geo g;
   GeoF gf;        // float copy of g, made on the host
   const double* tsince;
+  const int32_t* jd_day = nullptr;   // absolute-time grid (Julian day + fraction), or null
+  const double* jd_frac = nullptr;
   int64_t t_count;
   int grid_per_sat;
   void* r;

@@ -45,6 +45,8 @@ struct Stage {
 // One problem's view: its time grid, its first record and its output base.
 struct Range {
   const double* tsince;   // [T], or [n][T] when per_sat
+  const int32_t* jd_day;  // absolute times [T] as Julian day + fraction, or null
+  const double* jd_frac;
   int64_t T;
   int per_sat;
   int64_t sat0;           // record index of the problem's satellite 0
@@ -81,7 +83,16 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
         rc64 = load_rec64(rp, rec);
         cur = j;
       }
-      const double* tp = rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i;
+      // Minutes since the record's epoch: from the grid, or from absolute times and the
+      // record's split epoch, 1440 (dday + dfrac) with the day difference exact.
+      auto tsince_at = [&]() -> double {
+        if (rg.jd_day) {
+          const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
+          const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
+          return fma(1440.0, dfrac, (double)(dday * 1440));
+        }
+        return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
+      };
       OutT rr[3], vv[3];
       if (kFP32) {
         // The 160-byte FP32 row is re-read every state (ten 16-byte loads that L1
@@ -93,14 +104,14 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
           th = p.x;
           tl = p.y;
         } else {
-          split_double(__ldg(tp), th, tl);
+          split_double(tsince_at(), th, tl);
         }
         float r32[3], v32[3];
         code = state32(rc32, gf, th, tl, r32, v32);
         for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r32[c]; vv[c] = (OutT)v32[c]; }
       } else {
         double r64[3], v64[3];
-        code = state64(rc64, g, __ldg(tp), r64, v64);
+        code = state64(rc64, g, tsince_at(), r64, v64);
         for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r64[c]; vv[c] = (OutT)v64[c]; }
       }
       sm.r[3 * tid + 0] = rr[0]; sm.r[3 * tid + 1] = rr[1]; sm.r[3 * tid + 2] = rr[2];
@@ -108,7 +119,7 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
       if (kFP32 && code == kRecomputeFP64) {
         // The out-of-line recomputation writes its float results straight into this
         // thread's staging slots, so no local array has its address taken.
-        code = state64_fallback(rp, g, rec, __ldg(tp), reinterpret_cast<float*>(&sm.r[3 * tid]),
+        code = state64_fallback(rp, g, rec, tsince_at(), reinterpret_cast<float*>(&sm.r[3 * tid]),
                                 reinterpret_cast<float*>(&sm.v[3 * tid]));
         ++nfix;
       }
@@ -168,7 +179,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
-  const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
+  const bool use_split = kFP32 && !a.grid_per_sat && !a.jd_day && a.t_count <= kSplitMaxT;
   if (use_split) {
     for (int k = threadIdx.x; k < (int)a.t_count; k += kThreads) {
       float h, l;
@@ -180,6 +191,8 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   const GeoF gf = a.gf;
   Range rg;
   rg.tsince = a.tsince;
+  rg.jd_day = a.jd_day;
+  rg.jd_frac = a.jd_frac;
   rg.T = a.t_count;
   rg.per_sat = a.grid_per_sat;
   rg.sat0 = 0;
@@ -222,6 +235,8 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
     const int64_t end = min(states, beg + a.tile_states);
     Range rg;
     rg.tsince = a.tsince + q.t_offset;
+    rg.jd_day = nullptr;
+    rg.jd_frac = nullptr;
     rg.T = q.t_count;
     rg.per_sat = 0;
     rg.sat0 = q.sat_offset;
@@ -251,7 +266,7 @@ template <bool kFP32>
 cudaError_t launch(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * a.t_count;
   if (total == 0) return cudaSuccess;
-  const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
+  const bool use_split = kFP32 && !a.grid_per_sat && !a.jd_day && a.t_count <= kSplitMaxT;
   const size_t dyn = use_split ? (size_t)a.t_count * sizeof(float2) : 0;
   // Resident blocks per SM of this kernel (same on every B300), taken with the largest
   // split table so that the wave below is resident whatever the grid length.

@@ -294,3 +294,35 @@ def test_fp32_near_retrograde_equatorial():
     t = np.linspace(0.0, 1440.0, 97)
     summ = _check_fp32(el, t, 0.1, 1e-4)
     assert summ["fp64_fixups"] > 0
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_julian_date_grid_from_each_records_split_epoch(prec):
+    """Absolute times (Julian day + fraction) against records with their own split
+    epochs: equal to the oracle at tsince = 1440 ((day - epoch_day) + (frac -
+    epoch_frac)), computed here in numpy."""
+    import torch
+
+    from paper_2603_27830_b300 import sgp4_init, sgp4_propagate_jd
+    rng = np.random.default_rng(23)
+    el = np.concatenate([W.config2(seed=3, n=250).elements, _edge_elements()])
+    n = len(el)
+    eday = (2461040 + rng.integers(-5, 6, n)).astype(np.int32)
+    efrac = rng.uniform(0.0, 1.0, n)
+    jd_day = (2461040 + rng.integers(-5, 6, 60)).astype(np.int32)
+    jd_frac = rng.uniform(0.0, 1.0, 60)
+    tsince = ((jd_day[None, :] - eday[:, None]).astype(np.float64)
+              + (jd_frac[None, :] - efrac[:, None])) * 1440.0
+    dev = "cuda"
+    recs, ist = sgp4_init(torch.as_tensor(el, device=dev),
+                          epoch_day=torch.as_tensor(eday, device=dev),
+                          epoch_frac=torch.as_tensor(efrac, device=dev))
+    r, v, st = sgp4_propagate_jd(recs, torch.as_tensor(jd_day, device=dev),
+                                 torch.as_tensor(jd_frac, device=dev), prec)
+    torch.cuda.synchronize()
+    r, v, st = r.double().cpu().numpy(), v.double().cpu().numpy(), st.cpu().numpy()
+    rr, vr, sr, isr = oracle.propagate(el, tsince)
+    assert_status_and_nan(st, sr, r, v, ist.cpu().numpy(), isr)
+    dr, dv = state_errors(r, v, rr, vr, sr)
+    tol_r, tol_v = (FP64_TOL_R_KM, FP64_TOL_V_KMS) if prec == "fp64" else (0.1, 1e-4)
+    assert dr.max() <= tol_r and dv.max() <= tol_v, error_summary(dr, dv)
