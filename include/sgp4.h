@@ -300,6 +300,33 @@ sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
                           size_t workspace_bytes, void* stream);
 
 /*
+ * Per-state Jacobians of the TEME state with respect to the mean elements, through
+ * sgp4init and the propagation (paper Sec. 5: derivatives of the propagator), and the
+ * propagation of an element covariance to the state (P = J C J^T), the form used to
+ * screen conjunctions.  For each state J = d(r_x, r_y, r_z, v_x, v_y, v_z) /
+ * d(n0, e0, i0, RAAN0, argp0, M0, B*) (km and km/s per element unit), from one
+ * forward pass and six reverse sweeps.
+ *   elements, records, tsince, t_count, grid_per_sat, precision  as in sgp4_adjoint
+ *   r, v        [n][t_count][3] out (may be NULL), float for SGP4_FP32, else double
+ *   status      [n][t_count] int32 out (required), as sgp4_propagate
+ *   jac         [n][t_count][6][7] out (may be NULL), precision's type
+ *   cov         [n][7][7] double element covariance (read only if cov_out is given)
+ *   cov_out     [n][t_count][21] out (may be NULL): upper triangle of P, row by row
+ *               ((0,0), (0,1) .. (0,5), (1,1) .. (5,5)), precision's type
+ *   workspace   device, sgp4_jacobian_workspace_bytes(n) bytes, 8-byte aligned
+ * States with status 1, 2 or 4 get NaN in r, v, jac and cov_out.  Errors:
+ * SGP4_ERR_ARG for NULL elements / tsince / status, cov_out without cov, misaligned
+ * arrays, a bad precision or sizes; SGP4_ERR_OOM for a small workspace; SGP4_ERR_CUDA
+ * for a failed launch.
+ */
+size_t sgp4_jacobian_workspace_bytes(int64_t n);
+sgp4_result sgp4_jacobian(const double* elements, const sgp4_records* records,
+                          const double* tsince, int64_t t_count, int grid_per_sat,
+                          sgp4_precision precision, void* r, void* v, int32_t* status, void* jac,
+                          const double* cov, void* cov_out, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/*
  * Batched propagation without any device allocation by the caller.  The paper has
  * no counterpart; this serves callers that cannot allocate device memory (a host
  * application that owns the allocator and hands out only fixed buffers, real-time

@@ -7,8 +7,9 @@ marshals torch tensors to that ABI; there is no CPU fallback.
 from .api import (Batch, BatchGraph, BatchPlan, Records, alloc_records,  # noqa: F401
                   SGP4Function, make_batch, plan_batch, propagate_host, sgp4_adjoint,
                   sgp4_differentiable, sgp4_init, sgp4_propagate, sgp4_propagate_batched,
-                  sgp4_propagate_jd)
+                  sgp4_propagate_jd, sgp4_jacobian)
 
 __all__ = ["Batch", "BatchGraph", "BatchPlan", "Records", "alloc_records", "make_batch",
            "plan_batch", "propagate_host", "sgp4_init", "sgp4_propagate", "sgp4_propagate_jd",
-           "sgp4_propagate_batched", "SGP4Function", "sgp4_adjoint", "sgp4_differentiable"]
+           "sgp4_propagate_batched", "SGP4Function", "sgp4_adjoint", "sgp4_differentiable",
+           "sgp4_jacobian"]

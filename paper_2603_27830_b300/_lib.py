@@ -30,7 +30,7 @@ EXPORTS = (
     "sgp4_propagate_batched", "sgp4_batch_graph_create", "sgp4_batch_graph_launch",
     "sgp4_batch_graph_destroy", "sgp4_propagate_batched_static", "sgp4_adjoint_workspace_bytes",
     "sgp4_adjoint", "sgp4_fit_workspace_bytes", "sgp4_fit_step", "sgp4_tle_parse",
-    "sgp4_tle_parse_text", "sgp4_tle_format",
+    "sgp4_tle_parse_text", "sgp4_tle_format", "sgp4_jacobian_workspace_bytes", "sgp4_jacobian",
 )
 STATIC_MAX_REQUESTS = 1024
 
@@ -110,6 +110,10 @@ def _declare(lib):
     lib.sgp4_fit_workspace_bytes.restype = ctypes.c_size_t
     lib.sgp4_fit_step.argtypes = [P, R, P, I64, I32, I32, P, P, P, P, P, ctypes.c_size_t, P]
     lib.sgp4_fit_step.restype = I32
+    lib.sgp4_jacobian_workspace_bytes.argtypes = [I64]
+    lib.sgp4_jacobian_workspace_bytes.restype = ctypes.c_size_t
+    lib.sgp4_jacobian.argtypes = [P, R, P, I64, I32, I32, P, P, P, P, P, P, P, ctypes.c_size_t, P]
+    lib.sgp4_jacobian.restype = I32
     CP = ctypes.c_char_p
     lib.sgp4_tle_parse.argtypes = [CP, CP, P, P, P, P]
     lib.sgp4_tle_parse.restype = I32

@@ -153,6 +153,45 @@ def sgp4_propagate_jd(records: Records, jd_day: torch.Tensor, jd_frac: torch.Ten
     return r, v, st
 
 
+def sgp4_jacobian(elements: torch.Tensor, records: Records, tsince: torch.Tensor,
+                  precision: str = "fp64", cov: torch.Tensor | None = None,
+                  want_state: bool = True, want_jac: bool = True, stream=None) -> dict:
+    """Per-state Jacobians J = d(r, v)/d(elements) [n, T, 6, 7] and, given an element
+    covariance cov [n, 7, 7], the state covariance J cov J^T as its upper triangle
+    [n, T, 21] (row by row).  Returns a dict with 'status' and those of 'r', 'v', 'jac',
+    'cov' that were asked for."""
+    _require_cuda("elements", elements, torch.float64)
+    _require_cuda("tsince", tsince, torch.float64)
+    if precision not in PRECISIONS:
+        raise ValueError(f"precision must be one of {sorted(PRECISIONS)}")
+    n = records.n
+    per_sat = tsince.dim() == 2
+    T = tsince.shape[-1]
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    dev = tsince.device
+    out = {"status": torch.empty((n, T), dtype=torch.int32, device=dev)}
+    if want_state:
+        out["r"] = torch.empty((n, T, 3), dtype=dt, device=dev)
+        out["v"] = torch.empty((n, T, 3), dtype=dt, device=dev)
+    if want_jac:
+        out["jac"] = torch.empty((n, T, 6, 7), dtype=dt, device=dev)
+    if cov is not None:
+        _require_cuda("cov", cov, torch.float64)
+        if tuple(cov.shape) != (n, 7, 7):
+            raise ValueError("cov must be [n, 7, 7]")
+        out["cov"] = torch.empty((n, T, 21), dtype=dt, device=dev)
+    lib = _lib.load()
+    ws_bytes = int(lib.sgp4_jacobian_workspace_bytes(n))
+    ws = torch.empty(max(ws_bytes // 8, 1), dtype=torch.float64, device=dev)
+    _lib.check("sgp4_jacobian",
+               lib.sgp4_jacobian(_ptr(elements), ctypes.byref(records.c), _ptr(tsince), T,
+                                 1 if per_sat else 0, PRECISIONS[precision], _ptr(out.get("r")),
+                                 _ptr(out.get("v")), _ptr(out["status"]), _ptr(out.get("jac")),
+                                 _ptr(cov), _ptr(out.get("cov")), _ptr(ws), ws_bytes,
+                                 _stream_handle(stream)))
+    return out
+
+
 def propagate_host(elements, tsince, precision: str = "fp32", device="cuda"):
     """End-to-end call on host arrays: copy in, init, propagate, copy out (numpy out)."""
     import numpy as np

@@ -360,6 +360,42 @@ sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
   return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
 }
 
+size_t sgp4_jacobian_workspace_bytes(int64_t n) { return sgp4::jacobian_workspace_bytes(n); }
+
+sgp4_result sgp4_jacobian(const double* elements, const sgp4_records* records,
+                          const double* tsince, int64_t t_count, int grid_per_sat,
+                          sgp4_precision precision, void* r, void* v, int32_t* status, void* jac,
+                          const double* cov, void* cov_out, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+  if (!records_ok(records) || t_count < 0 || t_count > INT32_MAX) return SGP4_ERR_ARG;
+  if (precision != SGP4_FP64 && precision != SGP4_FP32) return SGP4_ERR_ARG;
+  const int64_t n = records->n;
+  if (n == 0 || t_count == 0) return SGP4_OK;
+  if (n > 0x7fffffffLL) return SGP4_ERR_ARG;   // one block per satellite
+  if (n > INT64_MAX / 42 / t_count) return SGP4_ERR_ARG;
+  if (!elements || !aligned(elements, 8) || !tsince || !aligned(tsince, 8)) return SGP4_ERR_ARG;
+  if (!status || !aligned(status, 4)) return SGP4_ERR_ARG;
+  const size_t esz = precision == SGP4_FP32 ? 4 : 8;
+  const void* outs[] = {r, v, jac, cov_out};
+  for (const void* p : outs)
+    if (p && !aligned(p, esz)) return SGP4_ERR_ARG;
+  if (cov_out && (!cov || !aligned(cov, 8))) return SGP4_ERR_ARG;
+  if (!workspace || !aligned(workspace, 8)) return SGP4_ERR_ARG;
+  if (workspace_bytes < sgp4::jacobian_workspace_bytes(n)) return SGP4_ERR_OOM;
+  sgp4::JacOut out;
+  out.r = r;
+  out.v = v;
+  out.status = status;
+  out.jac = jac;
+  out.cov = cov_out ? cov : nullptr;
+  out.cov_out = cov_out;
+  cudaError_t e = sgp4::launch_jacobian(
+      sgp4::record_ptrs(records->arena, n), make_geo(records->consts), elements, tsince, t_count,
+      grid_per_sat ? 1 : 0, precision == SGP4_FP32, out, workspace,
+      static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
+}
+
 sgp4_result sgp4_batch_graph_launch(void* graph, void* stream) {
   if (!graph) return SGP4_ERR_ARG;
   BatchGraph* bg = static_cast<BatchGraph*>(graph);

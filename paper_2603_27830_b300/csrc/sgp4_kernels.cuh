@@ -71,6 +71,24 @@ cudaError_t launch_fit_step(const RecordPtrs& rp, const Geo& g, const double* el
                             const double* r_obs, const double* lambda, double* el_out,
                             double* sse, double* workspace, cudaStream_t stream);
 
+// Record-field Jacobian of sgp4init per satellite, [n][33][7] of float (fp32) or double.
+cudaError_t launch_init_jacobian(const double* el, int64_t n, const Geo& g, bool fp32,
+                                 void* out, cudaStream_t stream);
+
+// Per-state Jacobians d(r, v)/d(elements) and covariance propagation.
+struct JacOut {
+  void* r;            // [n][T][3] or null
+  void* v;            // [n][T][3] or null
+  int32_t* status;    // [n][T]
+  void* jac;          // [n][T][6][7] or null
+  const double* cov;  // [n][7][7] element covariance, or null
+  void* cov_out;      // [n][T][21] upper triangle of J C J^T, or null
+};
+size_t jacobian_workspace_bytes(int64_t n);
+cudaError_t launch_jacobian(const RecordPtrs& rp, const Geo& g, const double* el,
+                            const double* tsince, int64_t T, int per_sat, bool fp32,
+                            const JacOut& out, void* workspace, cudaStream_t stream);
+
 // Float copy of the Earth model for the FP32 path (host side, once per call).
 inline GeoF geo_float(const Geo& g) {
   GeoF gf;
