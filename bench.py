@@ -9,8 +9,8 @@ timed region starts; L2 is flushed (256 MB write) between timed steps.
 
 Beside the headline the line carries the FP64 path, the batched uneven-request launch
 (256 requests, CUDA-graph replay) and the adjoint / fitting workload (10,000 x 500:
-sgp4_adjoint and one Levenberg-Marquardt step, FP32 and FP64), each with its rate and
-roofline fraction.
+sgp4_adjoint, one Levenberg-Marquardt step and the per-state Jacobians with covariance,
+FP32 and FP64), each with its rate and roofline fraction.
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle instead (the
 only reference this project has: the paper ships no runnable code here).
@@ -242,7 +242,7 @@ def run_adjoint(torch, dev, stream, flush, steps, alu_peak, fp64_peak):
     """Adjoint and fitting workload (10,000 satellites x 500 times over one day): one
     sgp4_adjoint call (sweep kernel + init-Jacobian kernel) per step in FP32 and FP64,
     and one Levenberg-Marquardt step (sgp4_init + Jacobian + fit kernel)."""
-    from paper_2603_27830_b300 import sgp4_adjoint, sgp4_init, sgp4_propagate
+    from paper_2603_27830_b300 import sgp4_adjoint, sgp4_init, sgp4_jacobian, sgp4_propagate
     from paper_2603_27830_b300 import workloads as W
     from paper_2603_27830_b300.fit import fit_step
     w = W.config5()
@@ -256,6 +256,9 @@ def run_adjoint(torch, dev, stream, flush, steps, alu_peak, fp64_peak):
     lam = torch.full((w.n,), 1e-3, dtype=torch.float64, device=dev)
     gen = torch.Generator(device=dev).manual_seed(0)
     g64 = torch.randn((w.n, w.t_count, 3), dtype=torch.float64, device=dev, generator=gen)
+    sig = torch.tensor([1e-8, 1e-5, 1e-5, 1e-5, 1e-4, 1e-4, 1e-6], dtype=torch.float64,
+                       device=dev)
+    cov = torch.diag(sig * sig).expand(w.n, 7, 7).contiguous()
 
     def timed(fn):
         for _ in range(2):
@@ -279,14 +282,18 @@ def run_adjoint(torch, dev, stream, flush, steps, alu_peak, fp64_peak):
         g = g64.float() if prec == "fp32" else g64
         ms = timed(lambda: sgp4_adjoint(el, recs, ts, g, g, prec))
         fit_ms = timed(lambda: fit_step(el, ts, r_obs, lam, prec))
+        jac_ms = timed(lambda: sgp4_jacobian(el, recs, ts, prec, cov=cov))
         achieved = ops * states / (ms * 1e-3) / 1e9
         res[prec] = {"value": states / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms,
                      "roofline": {"bound": unit_kind, "achieved": achieved, "peak": peak,
                                   "unit": "Gop/s", "frac": achieved / peak,
                                   "ops_per_state": ops,
                                   "timed": "whole sgp4_adjoint call (sweep + init Jacobian)"},
-                     "fit_step_ms": fit_ms, "fit_step_states_per_s": states / (fit_ms * 1e-3)}
-    del g64, r_obs, r_true, recs, truth
+                     "fit_step_ms": fit_ms, "fit_step_states_per_s": states / (fit_ms * 1e-3),
+                     "jacobian_ms": jac_ms, "jacobian_states_per_s": states / (jac_ms * 1e-3),
+                     "jacobian_note": "sgp4_jacobian: r, v, status, 6x7 J and 6x6 J C J^T "
+                                      "per state"}
+    del g64, r_obs, r_true, recs, truth, cov
     torch.cuda.empty_cache()
     return res
 
