@@ -515,26 +515,21 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
                                        float r[3], float v[3]) {
   const int fatal = (rc.flags >> kFatalShift) & 0xff;
   const int code0 = fatal ? fatal : ((rc.flags & kFlagN0ppNonPos) ? 2 : 0);
-  const bool isimp = rc.flags & kFlagIsimp;
   const float t = th;
   const float t2 = t * t;
 
-  // Secular drag polynomials.
-  float tempa = 1.0f - rc.c1 * t;
-  float tempe = rc.bc4 * t;
-  float templ = rc.l2 * t2;
-  float dd = 0.0f;   // dargp + dM: moves M forward and argp back by the same angle
-  if (!isimp) {
-    const float dargp = rc.argpcf * t;
-    const float mdf = wrap_rev(fmaf(rc.mdr, t, rc.m0r)) * kTwoPiF;
-    const float c = 1.0f + rc.eta * __cosf(mdf);
-    const float dm = rc.mcf * (c * c * c - rc.delm0);
-    dd = dargp + dm;
-    const float t3 = t2 * t, t4 = t3 * t;
-    tempa = tempa - rc.d2 * t2 - rc.d3 * t3 - rc.d4 * t4;
-    tempe = tempe + rc.bc5 * (__sinf(mdf + dd) - rc.sinm0);
-    templ = templ + rc.l3 * t3 + t4 * (rc.l4 + t * rc.l5);
-  }
+  // Secular drag polynomials.  Simplified-drag records carry zero d2..l5, bc5, argpcf
+  // and mcf in the FP32 row, so the full form gives their truncated one without a
+  // branch.
+  const float dargp = rc.argpcf * t;
+  const float mdf = wrap_rev(fmaf(rc.mdr, t, rc.m0r)) * kTwoPiF;
+  const float c = 1.0f + rc.eta * __cosf(mdf);
+  const float dm = rc.mcf * (c * c * c - rc.delm0);
+  const float dd = dargp + dm;   // moves M forward and argp back by the same angle
+  const float t3 = t2 * t, t4 = t3 * t;
+  const float tempa = 1.0f - rc.c1 * t - rc.d2 * t2 - rc.d3 * t3 - rc.d4 * t4;
+  const float tempe = rc.bc4 * t + rc.bc5 * (__sinf(mdf + dd) - rc.sinm0);
+  const float templ = rc.l2 * t2 + rc.l3 * t3 + t4 * (rc.l4 + t * rc.l5);
   const float a = rc.a0pp * tempa * tempa;
   float e = rc.e0 - tempe;
   // Status checks in the theory's order (2, 1, 4, 6) and the guard bands around them,
@@ -574,7 +569,10 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
 
   // Kepler: Newton from psi = U, clamped to +-0.95, step count from the e_L bound.
   float psi = U;
-  const int K = newton_steps(eL2);
+  // The warp's largest step count, so that the loop is uniform across the warp (the
+  // lanes of a warp are mostly one satellite at neighbouring times; extra steps only
+  // refine a converged root).
+  const int K = __reduce_max_sync(__activemask(), newton_steps(eL2));
   for (int k = 0; k < K; ++k) {
     float sp, cp;
     __sincosf(psi, &sp, &cp);

@@ -105,11 +105,15 @@ __global__ void __launch_bounds__(32) init_kernel(const double* __restrict__ el,
   h[fRaanCfr] = f32_rn(raan_cf * inv2pi);
   h[fN0ppr] = f32_rn(n0pp * inv2pi);
   h[fA0pp] = f32_rn(a0pp);   h[fE0] = f32_rn(e0);     h[fC1] = f32_rn(C1);
-  h[fBC4] = f32_rn(bc4);     h[fBC5] = f32_rn(bc5);   h[fD2] = f32_rn(D2);
+  h[fBC4] = f32_rn(bc4);     h[fBC5] = isimp ? 0.0f : f32_rn(bc5);   h[fD2] = f32_rn(D2);
   h[fD3] = f32_rn(D3);       h[fD4] = f32_rn(D4);     h[fL2] = f32_rn(L2);
   h[fL3] = f32_rn(L3);       h[fL4] = f32_rn(L4);     h[fL5] = f32_rn(L5);
   h[fEta] = f32_rn(eta);     h[fDelM0] = f32_rn(delm0); h[fSinM0] = f32_rn(sinm0);
-  h[fArgpCf] = f32_rn(argp_cf); h[fMCf] = f32_rn(m_cf);
+  // Simplified-drag records (perigee below 220 km) drop the drag terms these three
+  // carry: zero in the FP32 row, so that the FP32 state evaluates the drag block
+  // unconditionally (no branch) and gets the theory's zero contributions.
+  h[fArgpCf] = isimp ? 0.0f : f32_rn(argp_cf);
+  h[fMCf] = isimp ? 0.0f : f32_rn(m_cf);
   h[fXlcof] = f32_rn(xlcof); h[fAycof] = f32_rn(aycof);
   h[fCosi] = f32_rn(cosi);   h[fSini] = f32_rn(sini);
   h[fX3thm1] = f32_rn(1.5 * x3thm1); h[fX1mth2] = f32_rn(x1mth2);

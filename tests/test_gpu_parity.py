@@ -254,9 +254,13 @@ def test_fp32_rows_are_nearest_floats_of_the_fp64_planes():
     planes = raw[:_N_PLANES * stride * 8].view(np.float64).reshape(_N_PLANES, stride)[:, :n]
     rows = raw[_N_PLANES * stride * 8:(_N_PLANES * stride * 8 + stride * _ROW * 4)]
     rows = rows.view(np.float32).reshape(stride, _ROW)[:n]
+    isimp = (rows[:, 36].view(np.int32) & 1) != 0     # flags word, simplified drag
+    assert isimp.any() and (~isimp).any()
     for name, (p, r) in _PLANE_ROW.items():
         want = planes[p].astype(np.float32)
         want[np.abs(planes[p]) < 2.0 ** -126] = 0.0
+        if name in ("bc5", "argp_cf", "m_cf"):
+            want[isimp] = 0.0                            # drag terms the truncated form drops
         got = rows[:, r]
         assert np.array_equal(got, want), name          # -0.0 == 0.0 for flushed values
 
