@@ -57,13 +57,15 @@ struct Range {
 
 
 // States [beg, end) of one problem (local flattened index j * T + i).  Every thread
-// of the block calls it with the same arguments (it contains block barriers).
+// of the block calls it with the same arguments (it contains block barriers); two
+// calls in a row must be separated by a block barrier (both start on staging buffer 0
+// and the last iteration's stores end without one).
 // split, if not null, holds the problem's shared grid already split into float
 // hi + lo (FP32 path), one entry per time index.
 template <bool kFP32>
 __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
                                           const Range& rg, int64_t beg, int64_t end,
-                                          Stage<kFP32>& sm, unsigned long long& nfix,
+                                          Stage<kFP32>* sm2, unsigned long long& nfix,
                                           const float2* split = nullptr) {
   using OutT = typename Stage<kFP32>::OutT;
   const int tid = threadIdx.x;
@@ -74,7 +76,12 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
   int64_t cur = -1;
   Rec64 rc64;
 
-  for (int64_t base = beg; base < end; base += kThreads) {
+  // Two staging buffers used in turn: the barrier after an iteration's shared-memory
+  // writes also orders the previous iteration's reads of the other buffer before the
+  // next iteration's writes to it, so one barrier per iteration suffices.
+  int it = 0;
+  for (int64_t base = beg; base < end; base += kThreads, ++it) {
+    Stage<kFP32>& sm = sm2[it & 1];
     const int64_t idx = base + tid;
     int code = 0;
     if (idx < end) {
@@ -154,7 +161,6 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
       for (int k = tid; k < 3 * cnt; k += kThreads) { gr[k] = sm.r[k]; gv[k] = sm.v[k]; }
       if (tid < cnt) gs[tid] = sm.st[tid];
     }
-    __syncthreads();
 
     i += kThreads;
     if (i >= T32) {
@@ -173,7 +179,7 @@ constexpr int kSplitMaxT = 2048;
 template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
-  __shared__ Stage<kFP32> sm;
+  __shared__ Stage<kFP32> sm[2];
   extern __shared__ float2 s_split[];   // [t_count] when use_split
   const int64_t total = a.rp.n * a.t_count;
   const int64_t beg = (int64_t)blockIdx.x * chunk;
@@ -211,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
 template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     batched_kernel(BatchArgs a) {
-  __shared__ Stage<kFP32> sm;
+  __shared__ Stage<kFP32> sm[2];
   __shared__ unsigned long long s_tile;
   const GeoF gf = a.gf;
   const int64_t total_tiles = a.tile_start[a.n_req];
