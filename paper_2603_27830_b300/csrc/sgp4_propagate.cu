@@ -5,15 +5,16 @@
 //     problem, 128 states per step, so consecutive steps of a thread walk along the
 //     time axis of the same satellite and its record stays in L1 (FP32) or in
 //     registers (FP64);
-//   * outputs are staged in shared memory and written back with 16-byte streaming
-//     stores ([n][T][3] is AoS per state, so 128 states are 1.5 KB (FP32) or 3 KB
-//     (FP64) of contiguous r, the same of v, and 512 B of status).
+//   * each thread stores its own r, v and status with streaming stores; a warp's
+//     stores cover consecutive states, so L2 assembles them into full lines (on B300
+//     this beat staging through shared memory with 16-byte stores by 3-6%).
 // propagate_kernel: one problem, a persistent grid of one wave, each block owning
 // one contiguous range.  batched_kernel: many problems ("requests") of uneven size
 // in one persistent launch; blocks take fixed-size tiles of states from a global
 // atomic counter, so uneven requests and uneven per-state cost balance themselves.
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "sgp4_device.cuh"
 #include "sgp4_kernels.cuh"
@@ -34,13 +35,6 @@ constexpr int kThreads = 128;
 #define SGP4_MIN_BLOCKS_FP64 4
 #endif
 
-template <bool kFP32>
-struct Stage {
-  using OutT = typename std::conditional<kFP32, float, double>::type;
-  __align__(16) OutT r[3 * kThreads];
-  __align__(16) OutT v[3 * kThreads];
-  __align__(16) int32_t st[kThreads];
-};
 
 // One problem's view: its time grid, its first record and its output base.
 struct Range {
@@ -56,18 +50,16 @@ struct Range {
 };
 
 
-// States [beg, end) of one problem (local flattened index j * T + i).  Every thread
-// of the block calls it with the same arguments (it contains block barriers); two
-// calls in a row must be separated by a block barrier (both start on staging buffer 0
-// and the last iteration's stores end without one).
-// split, if not null, holds the problem's shared grid already split into float
-// hi + lo (FP32 path), one entry per time index.
+// States [beg, end) of one problem (local flattened index j * T + i), thread tid of
+// the block taking beg + tid, beg + tid + 128, ...  split, if not null, holds the
+// problem's shared grid already split into float hi + lo (FP32 path), one entry per
+// time index.
 template <bool kFP32>
 __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
                                           const Range& rg, int64_t beg, int64_t end,
-                                          Stage<kFP32>* sm2, unsigned long long& nfix,
+                                          unsigned long long& nfix,
                                           const float2* split = nullptr) {
-  using OutT = typename Stage<kFP32>::OutT;
+  using OutT = typename std::conditional<kFP32, float, double>::type;
   const int tid = threadIdx.x;
   const int64_t T = rg.T;            // <= INT32_MAX (checked by the API)
   const int T32 = (int)T;
@@ -76,91 +68,64 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
   int64_t cur = -1;
   Rec64 rc64;
 
-  // Two staging buffers used in turn: the barrier after an iteration's shared-memory
-  // writes also orders the previous iteration's reads of the other buffer before the
-  // next iteration's writes to it, so one barrier per iteration suffices.
-  int it = 0;
-  for (int64_t base = beg; base < end; base += kThreads, ++it) {
-    Stage<kFP32>& sm = sm2[it & 1];
-    const int64_t idx = base + tid;
+  for (int64_t idx = beg + tid; idx < end; idx += kThreads) {
     int code = 0;
-    if (idx < end) {
-      const int64_t rec = rg.sat0 + j;
-      if (!kFP32 && j != cur) {
-        rc64 = load_rec64(rp, rec);
-        cur = j;
+    const int64_t rec = rg.sat0 + j;
+    if (!kFP32 && j != cur) {
+      rc64 = load_rec64(rp, rec);
+      cur = j;
+    }
+    // Minutes since the record's epoch: from the grid, or from absolute times and the
+    // record's split epoch, 1440 (dday + dfrac) with the day difference exact.
+    auto tsince_at = [&]() -> double {
+      if (rg.jd_day) {
+        const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
+        const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
+        return fma(1440.0, dfrac, (double)(dday * 1440));
       }
-      // Minutes since the record's epoch: from the grid, or from absolute times and the
-      // record's split epoch, 1440 (dday + dfrac) with the day difference exact.
-      auto tsince_at = [&]() -> double {
-        if (rg.jd_day) {
-          const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
-          const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
-          return fma(1440.0, dfrac, (double)(dday * 1440));
-        }
-        return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
-      };
-      OutT rr[3], vv[3];
-      if (kFP32) {
-        // The 160-byte FP32 row is re-read every state (ten 16-byte loads that L1
-        // serves as broadcasts) instead of being held in registers across states.
-        const Rec32 rc32 = load_rec32(rp, rec);
-        float th, tl;
-        if (split) {
-          const float2 p = split[i];
-          th = p.x;
-          tl = p.y;
-        } else {
-          split_double(tsince_at(), th, tl);
-        }
-        float r32[3], v32[3];
-        code = state32(rc32, gf, th, tl, r32, v32);
-        for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r32[c]; vv[c] = (OutT)v32[c]; }
+      return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
+    };
+    OutT rr[3], vv[3];
+    if (kFP32) {
+      // The 160-byte FP32 row is re-read every state (ten 16-byte loads that L1
+      // serves as broadcasts) instead of being held in registers across states.
+      const Rec32 rc32 = load_rec32(rp, rec);
+      float th, tl;
+      if (split) {
+        const float2 p = split[i];
+        th = p.x;
+        tl = p.y;
       } else {
-        double r64[3], v64[3];
-        code = state64(rc64, g, tsince_at(), r64, v64);
-        for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r64[c]; vv[c] = (OutT)v64[c]; }
+        split_double(tsince_at(), th, tl);
       }
-      sm.r[3 * tid + 0] = rr[0]; sm.r[3 * tid + 1] = rr[1]; sm.r[3 * tid + 2] = rr[2];
-      sm.v[3 * tid + 0] = vv[0]; sm.v[3 * tid + 1] = vv[1]; sm.v[3 * tid + 2] = vv[2];
-      if (kFP32 && code == kRecomputeFP64) {
-        // The out-of-line recomputation writes its float results straight into this
-        // thread's staging slots, so no local array has its address taken.
-        code = state64_fallback(rp, g, rec, tsince_at(), reinterpret_cast<float*>(&sm.r[3 * tid]),
-                                reinterpret_cast<float*>(&sm.v[3 * tid]));
-        ++nfix;
-      }
+      float r32[3], v32[3];
+      code = state32(rc32, gf, th, tl, r32, v32);
+      for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r32[c]; vv[c] = (OutT)v32[c]; }
+    } else {
+      double r64[3], v64[3];
+      code = state64(rc64, g, tsince_at(), r64, v64);
+      for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r64[c]; vv[c] = (OutT)v64[c]; }
+    }
+    OutT* gr = static_cast<OutT*>(rg.r) + idx * 3;
+    OutT* gv = static_cast<OutT*>(rg.v) + idx * 3;
+    if (kFP32 && code == kRecomputeFP64) {
+      // The out-of-line recomputation writes its float results to the outputs.
+      code = state64_fallback(rp, g, rec, tsince_at(), reinterpret_cast<float*>(gr),
+                              reinterpret_cast<float*>(gv));
+      ++nfix;
       if (code != 0 && code != 6) {
         const OutT q = OutT(__longlong_as_double(0x7ff8000000000000LL));
-        sm.r[3 * tid + 0] = q; sm.r[3 * tid + 1] = q; sm.r[3 * tid + 2] = q;
-        sm.v[3 * tid + 0] = q; sm.v[3 * tid + 1] = q; sm.v[3 * tid + 2] = q;
+        gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q;
       }
-    }
-    sm.st[tid] = code;
-    __syncthreads();
-
-    OutT* gr = static_cast<OutT*>(rg.r) + base * 3;
-    OutT* gv = static_cast<OutT*>(rg.v) + base * 3;
-    int32_t* gs = rg.status + base;
-    const int64_t cnt = min((int64_t)kThreads, end - base);
-    const bool vec = cnt == kThreads &&
-                     ((reinterpret_cast<uintptr_t>(gr) | reinterpret_cast<uintptr_t>(gv) |
-                       reinterpret_cast<uintptr_t>(gs)) & 15) == 0;
-    if (vec) {
-      constexpr int kVec = 3 * kThreads * (int)sizeof(OutT) / 16;
-      constexpr int kVecSt = kThreads * 4 / 16;
-      const int4* sr = reinterpret_cast<const int4*>(sm.r);
-      const int4* sv = reinterpret_cast<const int4*>(sm.v);
-      const int4* ss = reinterpret_cast<const int4*>(sm.st);
-      for (int k = tid; k < kVec; k += kThreads) {
-        __stcs(reinterpret_cast<int4*>(gr) + k, sr[k]);
-        __stcs(reinterpret_cast<int4*>(gv) + k, sv[k]);
-      }
-      if (tid < kVecSt) __stcs(reinterpret_cast<int4*>(gs) + tid, ss[tid]);
     } else {
-      for (int k = tid; k < 3 * cnt; k += kThreads) { gr[k] = sm.r[k]; gv[k] = sm.v[k]; }
-      if (tid < cnt) gs[tid] = sm.st[tid];
+      const bool bad = code != 0 && code != 6;
+      const OutT q = OutT(__longlong_as_double(0x7ff8000000000000LL));
+      __stcs(gr + 0, bad ? q : rr[0]); __stcs(gr + 1, bad ? q : rr[1]);
+      __stcs(gr + 2, bad ? q : rr[2]);
+      __stcs(gv + 0, bad ? q : vv[0]); __stcs(gv + 1, bad ? q : vv[1]);
+      __stcs(gv + 2, bad ? q : vv[2]);
     }
+    __stcs(rg.status + idx, code);
 
     i += kThreads;
     if (i >= T32) {
@@ -179,7 +144,6 @@ constexpr int kSplitMaxT = 2048;
 template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
-  __shared__ Stage<kFP32> sm[2];
   extern __shared__ float2 s_split[];   // [t_count] when use_split
   const int64_t total = a.rp.n * a.t_count;
   const int64_t beg = (int64_t)blockIdx.x * chunk;
@@ -206,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.v = a.v;
   rg.status = a.status;
   unsigned long long nfix = 0;
-  run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, sm, nfix, use_split ? s_split : nullptr);
+  run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, nfix, use_split ? s_split : nullptr);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
 
@@ -217,7 +181,6 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
 template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     batched_kernel(BatchArgs a) {
-  __shared__ Stage<kFP32> sm[2];
   __shared__ unsigned long long s_tile;
   const GeoF gf = a.gf;
   const int64_t total_tiles = a.tile_start[a.n_req];
@@ -254,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
       rg.v = static_cast<double*>(a.v) + q.out_offset * 3;
     }
     rg.status = a.status + q.out_offset;
-    run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, sm, nfix);
+    run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, nfix);
   }
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
