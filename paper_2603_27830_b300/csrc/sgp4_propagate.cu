@@ -18,6 +18,7 @@
 
 #include "sgp4_device.cuh"
 #include "sgp4_kernels.cuh"
+#include "sgp4_state32x2.cuh"
 
 namespace sgp4 {
 
@@ -136,6 +137,74 @@ __device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, co
   }
 }
 
+// FP32, two states per thread (packed arithmetic, state32x2): unit u of [ubeg, uend)
+// is satellite j = u / Th, times i0 = u % Th and i1 = i0 + Th (Th = ceil(T / 2); i1 does
+// not exist for the last unit of an odd T), so both states share the record.
+__device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
+                                             const Range& rg, int64_t ubeg, int64_t uend,
+                                             unsigned long long& nfix, const float2* split) {
+  const int tid = threadIdx.x;
+  const int T = (int)rg.T;            // <= INT32_MAX (checked by the API)
+  const int Th = (T + 1) / 2;
+  int64_t j = (ubeg + tid) / Th;
+  int i0 = (int)((ubeg + tid) - j * Th);
+  for (int64_t u = ubeg + tid; u < uend; u += kThreads) {
+    const int64_t rec = rg.sat0 + j;
+    const int i1 = i0 + Th;
+    const bool has1 = i1 < T;
+    const int it[2] = {i0, has1 ? i1 : i0};
+    auto tsince_at = [&](int i) -> double {
+      if (rg.jd_day) {
+        const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
+        const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
+        return fma(1440.0, dfrac, (double)(dday * 1440));
+      }
+      return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
+    };
+    float2 th, tl;
+    if (split) {
+      const float2 a0 = split[it[0]], a1 = split[it[1]];
+      th = make_float2(a0.x, a1.x);
+      tl = make_float2(a0.y, a1.y);
+    } else {
+      split_double(tsince_at(it[0]), th.x, tl.x);
+      split_double(tsince_at(it[1]), th.y, tl.y);
+    }
+    const Rec32 rc32 = load_rec32(rp, rec);
+    float2 r2[3], v2[3];
+    int code[2];
+    state32x2(rc32, gf, th, tl, r2, v2, code);
+    const float q = __int_as_float(0x7fc00000);
+    for (int l = 0; l < 2; ++l) {
+      if (l == 1 && !has1) break;
+      const int64_t idx = j * T + it[l];
+      float* gr = static_cast<float*>(rg.r) + idx * 3;
+      float* gv = static_cast<float*>(rg.v) + idx * 3;
+      int cd = code[l];
+      if (cd == kRecomputeFP64) {
+        cd = state64_fallback(rp, g, rec, tsince_at(it[l]), gr, gv);
+        ++nfix;
+        if (cd != 0 && cd != 6) { gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q; }
+      } else {
+        const bool bad = cd != 0 && cd != 6;
+        const float rv[3] = {l ? r2[0].y : r2[0].x, l ? r2[1].y : r2[1].x, l ? r2[2].y : r2[2].x};
+        const float vv[3] = {l ? v2[0].y : v2[0].x, l ? v2[1].y : v2[1].x, l ? v2[2].y : v2[2].x};
+        __stcs(gr + 0, bad ? q : rv[0]); __stcs(gr + 1, bad ? q : rv[1]);
+        __stcs(gr + 2, bad ? q : rv[2]);
+        __stcs(gv + 0, bad ? q : vv[0]); __stcs(gv + 1, bad ? q : vv[1]);
+        __stcs(gv + 2, bad ? q : vv[2]);
+      }
+      __stcs(rg.status + idx, cd);
+    }
+    i0 += kThreads;
+    if (i0 >= Th) {
+      const int qd = i0 / Th;
+      j += qd;
+      i0 -= qd * Th;
+    }
+  }
+}
+
 // FP32 launches on a shared grid of at most this many times split the grid into float
 // hi + lo once per block, into dynamic shared memory (16 KB at most), instead of once
 // per state.
@@ -145,7 +214,8 @@ template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
   extern __shared__ float2 s_split[];   // [t_count] when use_split
-  const int64_t total = a.rp.n * a.t_count;
+  // FP32: units of two states (run_range_x2); FP64: states
+  const int64_t total = a.rp.n * (kFP32 ? (a.t_count + 1) / 2 : a.t_count);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
@@ -170,7 +240,8 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.v = a.v;
   rg.status = a.status;
   unsigned long long nfix = 0;
-  run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, nfix, use_split ? s_split : nullptr);
+  if (kFP32) run_range_x2(a.rp, a.g, gf, rg, beg, end, nfix, use_split ? s_split : nullptr);
+  else run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, nfix);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
 
@@ -233,7 +304,7 @@ int blocks_per_sm_of(K kernel, size_t dyn_smem = 0) {
 
 template <bool kFP32>
 cudaError_t launch(const PropArgs& a, cudaStream_t stream) {
-  const int64_t total = a.rp.n * a.t_count;
+  const int64_t total = a.rp.n * (kFP32 ? (a.t_count + 1) / 2 : a.t_count);
   if (total == 0) return cudaSuccess;
   const bool use_split = kFP32 && !a.grid_per_sat && !a.jd_day && a.t_count <= kSplitMaxT;
   const size_t dyn = use_split ? (size_t)a.t_count * sizeof(float2) : 0;

@@ -1,0 +1,245 @@
+// Two states of one satellite in one thread, in packed FP32 arithmetic (internal to
+// the library).
+//
+// B300's FP32 instructions come in a packed form that applies one add, multiply or
+// FMA to a pair of floats (__fadd2_rn, __fmul2_rn, __ffma2_rn: two lanes of work per
+// issue slot, each lane rounded as its scalar instruction).  The FP32 propagation is
+// bound by instruction issue, so the kernel runs two states of the same satellite
+// (two times) per thread: the time-dependent values are pairs, the record's fields are
+// shared scalars, and every add, multiply and FMA of the state is one packed
+// instruction for both.  Transcendentals (SFU), compares, selects and the integer work
+// stay per state.  The arithmetic is that of state32 (same formulation, guard bands and
+// status logic); only the fusing of some products into FMAs differs.
+#pragma once
+
+#include "sgp4_device.cuh"
+
+namespace sgp4 {
+namespace x2 {
+
+using F2 = float2;
+
+__device__ __forceinline__ F2 S(float a) { return make_float2(a, a); }
+__device__ __forceinline__ F2 add(F2 a, F2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ F2 mul(F2 a, F2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
+// a - b with one rounding (b * -1 is exact)
+__device__ __forceinline__ F2 sub(F2 a, F2 b) { return __ffma2_rn(b, S(-1.0f), a); }
+
+// x - rint(x) by the 1.5 * 2^23 rounding trick, lane by lane exact for |x| < 2^22.
+__device__ __forceinline__ F2 wrap_rev(F2 x) {
+  const F2 r = add(add(x, S(kRoundMagic)), S(-kRoundMagic));
+  return sub(x, r);
+}
+
+__device__ __forceinline__ F2 rsqrt(F2 x) { return make_float2(rsqrtf(x.x), rsqrtf(x.y)); }
+// 1 / y for y > 0 as rsqrt(y)^2
+__device__ __forceinline__ F2 rcp_pos(F2 y) {
+  const F2 r = rsqrt(y);
+  return mul(r, r);
+}
+__device__ __forceinline__ void sincos_sfu(F2 x, F2& s, F2& c) {
+  __sincosf(x.x, &s.x, &c.x);
+  __sincosf(x.y, &s.y, &c.y);
+}
+
+// sincos_acc of both lanes: Cody-Waite reduction by pi/2 and the Taylor polynomials
+// packed; the quadrant swap per lane.
+__device__ __forceinline__ void sincos_acc(F2 x, F2& s, F2& c) {
+  const F2 y = fma(x, S(0.636619772367581343f), S(kRoundMagic));
+  const int q0 = __float_as_int(y.x) - __float_as_int(kRoundMagic);
+  const int q1 = __float_as_int(y.y) - __float_as_int(kRoundMagic);
+  const F2 k = add(y, S(-kRoundMagic));
+  F2 r = fma(k, S(-1.57079637050628662f), x);
+  r = fma(k, S(4.37113900018624284e-8f), r);
+  const F2 r2 = mul(r, r);
+  F2 ps = fma(r2, S(2.75573192239858907e-6f), S(-1.98412698412698413e-4f));
+  ps = fma(r2, ps, S(8.33333333333333333e-3f));
+  ps = fma(r2, ps, S(-1.66666666666666667e-1f));
+  const F2 sn = fma(mul(r, r2), ps, r);
+  F2 pc = fma(r2, S(-2.75573192239858907e-7f), S(2.48015873015873016e-5f));
+  pc = fma(r2, pc, S(-1.38888888888888889e-3f));
+  pc = fma(r2, pc, S(4.16666666666666667e-2f));
+  pc = fma(r2, pc, S(-0.5f));
+  const F2 cs = fma(r2, pc, S(1.0f));
+  auto lane = [](int q, float sn1, float cs1, float& so, float& co) {
+    const float s0 = (q & 1) ? cs1 : sn1;
+    const float c0 = (q & 1) ? sn1 : cs1;
+    so = (q & 2) ? -s0 : s0;
+    co = ((q + 1) & 2) ? -c0 : c0;
+  };
+  lane(q0, sn.x, cs.x, s.x, c.x);
+  lane(q1, sn.y, cs.y, s.y, c.y);
+}
+
+// (s, c) = (sin a, cos a) -> (sin(a + d), cos(a + d)) for the small short-period
+// corrections (callers check |d| < 4e-3, as in rotate_small).
+__device__ __forceinline__ void rotate_small(F2& s, F2& c, F2 d) {
+  const F2 d2 = mul(d, d);
+  const F2 sd = fma(mul(d2, S(-1.0f / 6.0f)), d, d);
+  const F2 cd = fma(S(-0.5f), d2, S(1.0f));
+  const F2 s2 = fma(s, cd, mul(c, sd));
+  const F2 c2 = fma(c, cd, mul(mul(s, sd), S(-1.0f)));
+  s = s2;
+  c = c2;
+}
+
+__device__ __forceinline__ bool lt_abs(float x, float lim) { return fabsf(x) < lim; }
+
+}  // namespace x2
+
+// Two states of one record at times (th.x + tl.x) and (th.y + tl.y).  Returns the two
+// status codes (or kRecomputeFP64) in code[0], code[1]; r and v as pairs.
+__device__ __forceinline__ void state32x2(const Rec32& rc, const GeoF& g, float2 th, float2 tl,
+                                          float2 r[3], float2 v[3], int code[2]) {
+  using namespace x2;
+  const int fatal = (rc.flags >> kFatalShift) & 0xff;
+  const int code0 = fatal ? fatal : ((rc.flags & kFlagN0ppNonPos) ? 2 : 0);
+  const F2 t = th;
+  const F2 t2 = mul(t, t);
+
+  // Secular drag polynomials (simplified-drag records carry zero drag terms).
+  const F2 dargp = mul(S(rc.argpcf), t);
+  const F2 mdf = mul(wrap_rev(fma(S(rc.mdr), t, S(rc.m0r))), S(kTwoPiF));
+  const F2 cm = make_float2(__cosf(mdf.x), __cosf(mdf.y));
+  const F2 c = fma(S(rc.eta), cm, S(1.0f));
+  const F2 dm = mul(S(rc.mcf), fma(mul(c, c), c, S(-rc.delm0)));
+  const F2 dd = add(dargp, dm);
+  const F2 t3 = mul(t2, t), t4 = mul(t3, t);
+  F2 tempa = fma(S(-rc.c1), t, S(1.0f));
+  tempa = fma(S(-rc.d2), t2, tempa);
+  tempa = fma(S(-rc.d3), t3, tempa);
+  tempa = fma(S(-rc.d4), t4, tempa);
+  const F2 md = add(mdf, dd);
+  const F2 sm = make_float2(__sinf(md.x), __sinf(md.y));
+  const F2 tempe = fma(S(rc.bc5), add(sm, S(-rc.sinm0)), mul(S(rc.bc4), t));
+  const F2 templ = fma(t4, fma(t, S(rc.l5), S(rc.l4)), fma(S(rc.l3), t3, mul(S(rc.l2), t2)));
+  const F2 a = mul(S(rc.a0pp), mul(tempa, tempa));
+  F2 e = add(S(rc.e0), mul(tempe, S(-1.0f)));
+  // Status checks in the theory's order and the guard bands, per lane.
+  bool g_e[2], f_e[2];
+  {
+    const float ev[2] = {e.x, e.y}, av[2] = {a.x, a.y};
+    for (int l = 0; l < 2; ++l) {
+      g_e[l] = !(fabsf(ev[l] - 1.0f) >= kGuardE) | !(fabsf(ev[l] + 0.001f) >= kGuardE) |
+               !(av[l] > 1.0e-3f);
+      f_e[l] = (ev[l] >= 1.0f) | (ev[l] < -0.001f);
+    }
+  }
+  e = make_float2(fmaxf(e.x, 1.0e-6f), fmaxf(e.y, 1.0e-6f));
+  const F2 ra = rsqrt(a);
+  const F2 sa = mul(a, ra);
+  const F2 ra3 = mul(mul(ra, ra), ra);
+
+  // Phase of M + argp in revolutions; the n*t product as a double-float.
+  F2 p = mul(S(rc.phidh), th);
+  const F2 pe = fma(S(rc.phidh), th, mul(p, S(-1.0f)));     // exact rounding error of p
+  const F2 s = fma(S(rc.phidh), tl, fma(S(rc.phidl), th, pe));
+  p = wrap_rev(p);                                             // exact
+  F2 y = wrap_rev(add(p, S(rc.phi0h)));
+  y = add(y, add(s, S(rc.phi0l)));
+  y = add(y, wrap_rev(mul(S(rc.n0ppr), templ)));
+
+  const F2 argp =
+      mul(wrap_rev(fma(dd, S(-kInvTwoPiF), fma(S(rc.argpdr), t, S(rc.argp0r)))), S(kTwoPiF));
+  const F2 raan =
+      mul(wrap_rev(fma(S(rc.raancfr), t2, fma(S(rc.raandr), t, S(rc.raan0r)))), S(kTwoPiF));
+
+  // Long-period periodics (J3).
+  F2 sw, cw;
+  sincos_sfu(argp, sw, cw);
+  const F2 axn = mul(e, cw);
+  const F2 q = rcp_pos(mul(a, fma(mul(e, S(-1.0f)), e, S(1.0f))));
+  const F2 ayn = fma(e, sw, mul(q, S(rc.aycof)));
+  const F2 lpt = mul(mul(q, S(rc.xlcof)), axn);
+  const bool g_lp[2] = {!x2::lt_abs(lpt.x, kGuardLongPeriod), !x2::lt_abs(lpt.y, kGuardLongPeriod)};
+  const F2 U = mul(wrap_rev(fma(lpt, S(kInvTwoPiF), y)), S(kTwoPiF));
+  const F2 eL2 = fma(axn, axn, mul(ayn, ayn));
+
+  // Kepler: Newton from psi = U, warp-uniform step count from the e_L bound.
+  F2 psi = U;
+  const int K = __reduce_max_sync(__activemask(),
+                                  max(newton_steps(eL2.x), newton_steps(eL2.y)));
+  const F2 nayn = mul(ayn, S(-1.0f)), naxn = mul(axn, S(-1.0f));
+  for (int k = 0; k < K; ++k) {
+    F2 sp, cp;
+    sincos_sfu(psi, sp, cp);
+    const F2 f = sub(fma(axn, sp, fma(nayn, cp, U)), psi);
+    const F2 fp = fma(naxn, cp, fma(nayn, sp, S(1.0f)));
+    const F2 st = mul(f, rcp_pos(fp));
+    psi = add(psi, make_float2(fminf(fmaxf(st.x, -0.95f), 0.95f),
+                               fminf(fmaxf(st.y, -0.95f), 0.95f)));
+  }
+  F2 sp, cp;
+  x2::sincos_acc(psi, sp, cp);
+
+  // Short-period preliminaries.
+  const F2 ecosE = fma(axn, cp, mul(ayn, sp));
+  const F2 esinE = fma(axn, sp, mul(nayn, cp));
+  const F2 omel = fma(eL2, S(-1.0f), S(1.0f));
+  const F2 pL = mul(a, omel);
+  const bool g_p[2] = {!(fabsf(pL.x) >= kGuardP), !(fabsf(pL.y) >= kGuardP)};
+  const bool f_p[2] = {pL.x < 0.0f, pL.y < 0.0f};
+  const F2 rl = mul(a, fma(ecosE, S(-1.0f), S(1.0f)));
+  const F2 invr = rcp_pos(rl);
+  const F2 rdotl = mul(mul(sa, esinE), invr);
+  const F2 rpl = rsqrt(pL);
+  const F2 rfdotl = mul(mul(pL, rpl), invr);
+  const F2 betal = mul(omel, rsqrt(omel));
+  const F2 w = mul(esinE, rcp_pos(add(betal, S(1.0f))));
+  const F2 aor = mul(a, invr);
+  const F2 sinu = mul(aor, fma(naxn, w, sub(sp, ayn)));
+  const F2 cosu = mul(aor, fma(ayn, w, sub(cp, axn)));
+  const F2 sin2u = mul(mul(cosu, sinu), S(2.0f));
+  const F2 cos2u = fma(mul(sinu, sinu), S(-2.0f), S(1.0f));
+
+  // Short-period periodics (J2).
+  const F2 invp = mul(rpl, rpl);
+  const F2 k = mul(S(g.half_j2), invp);
+  const F2 kp = mul(k, invp);
+  const F2 rk = fma(rl, fma(mul(kp, betal), S(-rc.x3thm1_15), S(1.0f)),
+                    mul(mul(k, S(rc.half_x1mth2)), cos2u));
+  const bool g_r[2] = {!(fabsf(rk.x - 1.0f) >= kGuardR), !(fabsf(rk.y - 1.0f) >= kGuardR)};
+  const F2 nk = mul(ra3, k);
+  const F2 rdotk = fma(mul(nk, S(-rc.x1mth2)), sin2u, rdotl);
+  const F2 rfdotk = fma(nk, fma(S(rc.x1mth2), cos2u, S(rc.x3thm1_15)), rfdotl);
+
+  // u_k, RAAN_k and i_k as small rotations of (sin, cos) pairs.
+  const F2 du = mul(mul(kp, S(rc.x7thm1_m025)), sin2u);
+  const F2 dO = mul(mul(kp, S(rc.c15cosi)), sin2u);
+  const F2 di = mul(mul(kp, S(rc.c15cosisini)), cos2u);
+  const bool g_d[2] = {
+      !(fmaxf(fabsf(du.x), fmaxf(fabsf(dO.x), fabsf(di.x))) < 4.0e-3f),
+      !(fmaxf(fabsf(du.y), fmaxf(fabsf(dO.y), fabsf(di.y))) < 4.0e-3f)};
+  const F2 nrm = rsqrt(fma(sinu, sinu, mul(cosu, cosu)));
+  F2 su = mul(sinu, nrm), cu = mul(cosu, nrm);
+  x2::rotate_small(su, cu, du);
+  F2 sO, cO;
+  sincos_sfu(raan, sO, cO);
+  x2::rotate_small(sO, cO, dO);
+  F2 si = S(rc.sini), ci = S(rc.cosi);
+  x2::rotate_small(si, ci, di);
+
+  const F2 nsO = mul(sO, S(-1.0f));
+  const F2 mx = mul(nsO, ci), my = mul(cO, ci), mz = si;
+  const F2 ux = fma(mx, su, mul(cO, cu)), uy = fma(my, su, mul(sO, cu)), uz = mul(mz, su);
+  const F2 vx = fma(mx, cu, mul(mul(cO, su), S(-1.0f)));
+  const F2 vy = fma(my, cu, mul(nsO, su));
+  const F2 vz = mul(mz, cu);
+  const F2 rs = mul(rk, S(g.re));
+  r[0] = mul(rs, ux); r[1] = mul(rs, uy); r[2] = mul(rs, uz);
+  const F2 vk = S(g.vkmps);
+  v[0] = mul(fma(rdotk, ux, mul(rfdotk, vx)), vk);
+  v[1] = mul(fma(rdotk, uy, mul(rfdotk, vy)), vk);
+  v[2] = mul(fma(rdotk, uz, mul(rfdotk, vz)), vk);
+
+  const float rkv[2] = {rk.x, rk.y};
+  for (int l = 0; l < 2; ++l) {
+    const bool need64 = g_e[l] | (!f_e[l] & (g_lp[l] | g_p[l] | (!f_p[l] & (g_r[l] | g_d[l]))));
+    int cd = f_e[l] ? 1 : (f_p[l] ? 4 : (rkv[l] < 1.0f ? 6 : 0));
+    cd = need64 ? kRecomputeFP64 : cd;
+    code[l] = code0 ? code0 : cd;
+  }
+}
+
+}  // namespace sgp4

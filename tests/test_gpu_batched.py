@@ -58,8 +58,11 @@ def test_batched_equals_per_request_launches(precision):
         r1, v1, s1 = sgp4_propagate(recs, ts, precision)
         sl = slice(out0, out0 + n * T)
         assert torch.equal(st[sl], s1.reshape(-1))
-        # same per-state code, but two kernels: the compiler may contract differently
-        tol_r, tol_v = (1e-9, 1e-12) if precision == "fp64" else (2e-3, 2e-6)
+        # FP64: the same per-state code in two kernels (the compiler may contract
+        # differently); FP32: the single-problem kernel runs two states per thread in
+        # packed arithmetic, the batched kernel one, so they differ by the FP32 path's
+        # rounding (metres; each is within the FP32 bounds of the oracle tests)
+        tol_r, tol_v = (1e-9, 1e-12) if precision == "fp64" else (0.02, 2e-5)
         dr = (r[sl] - r1.reshape(-1, 3)).nan_to_num(0.0).abs().max()
         dv = (v[sl] - v1.reshape(-1, 3)).nan_to_num(0.0).abs().max()
         assert float(dr) <= tol_r and float(dv) <= tol_v, (float(dr), float(dv))
