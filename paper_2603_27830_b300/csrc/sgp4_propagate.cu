@@ -1,16 +1,17 @@
-// Propagation kernels: one (satellite, time) state per thread (paper Sec. 2.2,
+// Propagation kernels: independent (satellite, time) states (paper Sec. 2.2,
 // "Vectorisation": f(s, t) under a vmap over times composed with a vmap over
-// satellites).  Both kernels run the same range loop, run_range():
-//   * a block walks a contiguous range of the flattened [n][T] state space of one
-//     problem, 128 states per step, so consecutive steps of a thread walk along the
-//     time axis of the same satellite and its record stays in L1 (FP32) or in
-//     registers (FP64);
+// satellites).  Both kernels work in units of two states of one satellite, times i
+// and i + ceil(T/2): run_range_x2 (FP32) computes the pair in packed FP32 arithmetic
+// (state32x2), run_units64 (FP64) runs the two in turn on one load of the record.
+//   * a block walks a contiguous range of units, 128 per step, so consecutive steps of
+//     a thread stay on one satellite and its record stays in L1 (FP32) or registers
+//     (FP64);
 //   * each thread stores its own r, v and status with streaming stores; a warp's
 //     stores cover consecutive states, so L2 assembles them into full lines (on B300
 //     this beat staging through shared memory with 16-byte stores by 3-6%).
 // propagate_kernel: one problem, a persistent grid of one wave, each block owning
 // one contiguous range.  batched_kernel: many problems ("requests") of uneven size
-// in one persistent launch; blocks take fixed-size tiles of states from a global
+// in one persistent launch; blocks take fixed-size tiles of units from a global
 // atomic counter, so uneven requests and uneven per-state cost balance themselves.
 #include <algorithm>
 #include <cstdint>
@@ -26,9 +27,9 @@ namespace {
 
 constexpr int kThreads = 128;
 // Minimum resident 128-thread blocks per SM requested from the register allocator.
-// The FP32 kernel is latency bound at low occupancy: on B300, 8 blocks (64
-// registers) ran 5% (Starlink) to 15% (catalogue) faster than 4 blocks (128
-// registers).  The FP64 kernel is bound by the FP64 pipe and keeps 4.
+// FP32: 8 blocks (64 registers, some spilled to L1) ran as fast as 4 (128 registers)
+// on the Starlink workload and 6% faster on the catalogue with two states per thread.
+// The FP64 kernel is bound by the FP64 pipe and keeps 4.
 #ifndef SGP4_MIN_BLOCKS_FP32
 #define SGP4_MIN_BLOCKS_FP32 8
 #endif
@@ -50,92 +51,6 @@ struct Range {
   int32_t* status;
 };
 
-
-// States [beg, end) of one problem (local flattened index j * T + i), thread tid of
-// the block taking beg + tid, beg + tid + 128, ...  split, if not null, holds the
-// problem's shared grid already split into float hi + lo (FP32 path), one entry per
-// time index.
-template <bool kFP32>
-__device__ __forceinline__ void run_range(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
-                                          const Range& rg, int64_t beg, int64_t end,
-                                          unsigned long long& nfix,
-                                          const float2* split = nullptr) {
-  using OutT = typename std::conditional<kFP32, float, double>::type;
-  const int tid = threadIdx.x;
-  const int64_t T = rg.T;            // <= INT32_MAX (checked by the API)
-  const int T32 = (int)T;
-  int64_t j = (beg + tid) / T;
-  int i = (int)((beg + tid) - j * T);
-  int64_t cur = -1;
-  Rec64 rc64;
-
-  for (int64_t idx = beg + tid; idx < end; idx += kThreads) {
-    int code = 0;
-    const int64_t rec = rg.sat0 + j;
-    if (!kFP32 && j != cur) {
-      rc64 = load_rec64(rp, rec);
-      cur = j;
-    }
-    // Minutes since the record's epoch: from the grid, or from absolute times and the
-    // record's split epoch, 1440 (dday + dfrac) with the day difference exact.
-    auto tsince_at = [&]() -> double {
-      if (rg.jd_day) {
-        const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
-        const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
-        return fma(1440.0, dfrac, (double)(dday * 1440));
-      }
-      return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
-    };
-    OutT rr[3], vv[3];
-    if (kFP32) {
-      // The 160-byte FP32 row is re-read every state (ten 16-byte loads that L1
-      // serves as broadcasts) instead of being held in registers across states.
-      const Rec32 rc32 = load_rec32(rp, rec);
-      float th, tl;
-      if (split) {
-        const float2 p = split[i];
-        th = p.x;
-        tl = p.y;
-      } else {
-        split_double(tsince_at(), th, tl);
-      }
-      float r32[3], v32[3];
-      code = state32(rc32, gf, th, tl, r32, v32);
-      for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r32[c]; vv[c] = (OutT)v32[c]; }
-    } else {
-      double r64[3], v64[3];
-      code = state64(rc64, g, tsince_at(), r64, v64);
-      for (int c = 0; c < 3; ++c) { rr[c] = (OutT)r64[c]; vv[c] = (OutT)v64[c]; }
-    }
-    OutT* gr = static_cast<OutT*>(rg.r) + idx * 3;
-    OutT* gv = static_cast<OutT*>(rg.v) + idx * 3;
-    if (kFP32 && code == kRecomputeFP64) {
-      // The out-of-line recomputation writes its float results to the outputs.
-      code = state64_fallback(rp, g, rec, tsince_at(), reinterpret_cast<float*>(gr),
-                              reinterpret_cast<float*>(gv));
-      ++nfix;
-      if (code != 0 && code != 6) {
-        const OutT q = OutT(__longlong_as_double(0x7ff8000000000000LL));
-        gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q;
-      }
-    } else {
-      const bool bad = code != 0 && code != 6;
-      const OutT q = OutT(__longlong_as_double(0x7ff8000000000000LL));
-      __stcs(gr + 0, bad ? q : rr[0]); __stcs(gr + 1, bad ? q : rr[1]);
-      __stcs(gr + 2, bad ? q : rr[2]);
-      __stcs(gv + 0, bad ? q : vv[0]); __stcs(gv + 1, bad ? q : vv[1]);
-      __stcs(gv + 2, bad ? q : vv[2]);
-    }
-    __stcs(rg.status + idx, code);
-
-    i += kThreads;
-    if (i >= T32) {
-      const int q = i / T32;
-      j += q;
-      i -= q * T32;
-    }
-  }
-}
 
 // FP32, two states per thread (packed arithmetic, state32x2): unit u of [ubeg, uend)
 // is satellite j = u / Th, times i0 = u % Th and i1 = i0 + Th (Th = ceil(T / 2); i1 does
@@ -205,6 +120,57 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
   }
 }
 
+// FP64 over the same units as run_range_x2 (both kernels work in units of two states
+// of one satellite in both precisions): the thread runs the two states in turn, on one
+// load of the record.
+__device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, const Range& rg,
+                                            int64_t ubeg, int64_t uend) {
+  const int tid = threadIdx.x;
+  const int T = (int)rg.T;
+  const int Th = (T + 1) / 2;
+  int64_t j = (ubeg + tid) / Th;
+  int i0 = (int)((ubeg + tid) - j * Th);
+  int64_t cur = -1;
+  Rec64 rc;
+  const double q = __longlong_as_double(0x7ff8000000000000LL);
+  for (int64_t u = ubeg + tid; u < uend; u += kThreads) {
+    const int64_t rec = rg.sat0 + j;
+    if (j != cur) {
+      rc = load_rec64(rp, rec);
+      cur = j;
+    }
+    for (int l = 0; l < 2; ++l) {
+      const int i = i0 + l * Th;
+      if (i >= T) break;
+      double t;
+      if (rg.jd_day) {
+        const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
+        const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
+        t = fma(1440.0, dfrac, (double)(dday * 1440));
+      } else {
+        t = __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
+      }
+      double r[3], v[3];
+      const int code = state64(rc, g, t, r, v);
+      const bool bad = code != 0 && code != 6;
+      const int64_t idx = j * T + i;
+      double* gr = static_cast<double*>(rg.r) + idx * 3;
+      double* gv = static_cast<double*>(rg.v) + idx * 3;
+      for (int c = 0; c < 3; ++c) {
+        __stcs(gr + c, bad ? q : r[c]);
+        __stcs(gv + c, bad ? q : v[c]);
+      }
+      __stcs(rg.status + idx, code);
+    }
+    i0 += kThreads;
+    if (i0 >= Th) {
+      const int qd = i0 / Th;
+      j += qd;
+      i0 -= qd * Th;
+    }
+  }
+}
+
 // FP32 launches on a shared grid of at most this many times split the grid into float
 // hi + lo once per block, into dynamic shared memory (16 KB at most), instead of once
 // per state.
@@ -214,8 +180,7 @@ template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
   extern __shared__ float2 s_split[];   // [t_count] when use_split
-  // FP32: units of two states (run_range_x2); FP64: states
-  const int64_t total = a.rp.n * (kFP32 ? (a.t_count + 1) / 2 : a.t_count);
+  const int64_t total = a.rp.n * ((a.t_count + 1) / 2);   // units of two states
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
@@ -241,7 +206,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.status = a.status;
   unsigned long long nfix = 0;
   if (kFP32) run_range_x2(a.rp, a.g, gf, rg, beg, end, nfix, use_split ? s_split : nullptr);
-  else run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, nfix);
+  else run_units64(a.rp, a.g, rg, beg, end);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
 
@@ -269,10 +234,12 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
       const int mid = (lo + hi + 1) >> 1;
       if (__ldg(a.tile_start + mid) <= tile) lo = mid; else hi = mid - 1;
     }
+    // Tiles count units of two states of one satellite (tile_states / 2 per tile).
     const sgp4_request q = a.reqs[lo];
-    const int64_t states = q.n * q.t_count;
-    const int64_t beg = (tile - __ldg(a.tile_start + lo)) * a.tile_states;
-    const int64_t end = min(states, beg + a.tile_states);
+    const int64_t units = q.n * ((q.t_count + 1) / 2);
+    const int64_t per_tile = a.tile_states / 2;
+    const int64_t beg = (tile - __ldg(a.tile_start + lo)) * per_tile;
+    const int64_t end = min(units, beg + per_tile);
     Range rg;
     rg.tsince = a.tsince + q.t_offset;
     rg.jd_day = nullptr;
@@ -288,7 +255,8 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
       rg.v = static_cast<double*>(a.v) + q.out_offset * 3;
     }
     rg.status = a.status + q.out_offset;
-    run_range<kFP32>(a.rp, a.g, gf, rg, beg, end, nfix);
+    if (kFP32) run_range_x2(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
+    else run_units64(a.rp, a.g, rg, beg, end);
   }
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
@@ -304,7 +272,7 @@ int blocks_per_sm_of(K kernel, size_t dyn_smem = 0) {
 
 template <bool kFP32>
 cudaError_t launch(const PropArgs& a, cudaStream_t stream) {
-  const int64_t total = a.rp.n * (kFP32 ? (a.t_count + 1) / 2 : a.t_count);
+  const int64_t total = a.rp.n * ((a.t_count + 1) / 2);   // units of two states
   if (total == 0) return cudaSuccess;
   const bool use_split = kFP32 && !a.grid_per_sat && !a.jd_day && a.t_count <= kSplitMaxT;
   const size_t dyn = use_split ? (size_t)a.t_count * sizeof(float2) : 0;

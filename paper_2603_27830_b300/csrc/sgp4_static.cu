@@ -43,8 +43,8 @@ __global__ void __launch_bounds__(1024) prepare_static_kernel(int32_t n, int64_t
   const int k = threadIdx.x;
   int64_t tiles = 0;
   if (k < n) {
-    const int64_t st = reqs[k].n * reqs[k].t_count;
-    tiles = (st + tile_states - 1) / tile_states;
+    const int64_t units = reqs[k].n * ((reqs[k].t_count + 1) / 2);   // two states each
+    tiles = (units + tile_states / 2 - 1) / (tile_states / 2);
   }
   part[k] = tiles;
   __syncthreads();
@@ -100,7 +100,7 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
     if (q.sat_offset > records->n - q.n || q.t_offset > tsince_len - q.t_count ||
         q.out_offset > out_len - st)
       return SGP4_ERR_ARG;
-    total_tiles += (st + tile_states - 1) / tile_states;
+    total_tiles += (q.n * ((q.t_count + 1) / 2) + tile_states / 2 - 1) / (tile_states / 2);
     if (st == 0) continue;
     for (int32_t m = 0; m < k; ++m) {
       const sgp4_request& p = requests[m];
