@@ -237,10 +237,13 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   const double eL2 = axn * axn + ayn * ayn;
 
   // Kepler's equation: Newton with clamped steps, count from the e_L bound.
-  double psi = U, sp = 0.0, cp = 1.0, step = 0.0;
+  // sin, cos of the first iterate from sincos, of later ones by rotating the previous
+  // pair by the step taken (Taylor for small steps): one FP64 sincos per state.
+  double psi = U, sp, cp, step = 0.0;
+  sincos(U, &sp, &cp);
   const int K = newton_steps64(eL2);
   for (int k = 0; k < K; ++k) {
-    sincos(psi, &sp, &cp);
+    if (k > 0) rotate64(sp, cp, step);
     step = (U - ayn * cp + axn * sp - psi) / (1.0 - ayn * sp - axn * cp);
     step = fmin(fmax(step, -0.95), 0.95);
     psi += step;

@@ -141,10 +141,13 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
   f.ayn = f.e * f.sw + f.q * rc.aycof;
   const double U = wrap_2pi(mpa + f.q * rc.xlcof * f.axn);
   f.eL2 = f.axn * f.axn + f.ayn * f.ayn;
-  double psi = U, sp = 0.0, cp = 1.0, step = 0.0;
+  // sin, cos of the first iterate from sincos, of later ones by rotating the previous
+  // pair by the step taken (Taylor for small steps): one FP64 sincos per state.
+  double psi = U, sp, cp, step = 0.0;
+  sincos(U, &sp, &cp);
   const int K = newton_steps64(f.eL2);
   for (int k = 0; k < K; ++k) {
-    sincos(psi, &sp, &cp);
+    if (k > 0) rotate64(sp, cp, step);
     step = (U - f.ayn * cp + f.axn * sp - psi) / (1.0 - f.ayn * sp - f.axn * cp);
     step = fmin(fmax(step, -0.95), 0.95);
     psi += step;
