@@ -154,10 +154,9 @@ __device__ __forceinline__ double wrap_2pi(double x) {
   return fma(-kTwoPi, trunc(x * (1.0 / kTwoPi)), x);
 }
 
-// Rotate (s, c) = (sin a, cos a) to (sin(a+d), cos(a+d)) in FP64: 7th/6th-order Taylor
-// pair for |d| < 1e-2 (truncation below 3e-18), the full sincos beyond.
-__device__ __forceinline__ void rotate64(double& s, double& c, double d) {
-  double sd, cd;
+// sin d and cos d in FP64: 7th/6th-order Taylor pair for |d| < 1e-2 (truncation below
+// 3e-18), the full sincos beyond.
+__device__ __forceinline__ void sincos_small64(double d, double& sd, double& cd) {
   if (fabs(d) < 1.0e-2) {
     const double d2 = d * d;
     sd = d * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0))));
@@ -165,6 +164,11 @@ __device__ __forceinline__ void rotate64(double& s, double& c, double d) {
   } else {
     sincos(d, &sd, &cd);
   }
+}
+// Rotate (s, c) = (sin a, cos a) to (sin(a+d), cos(a+d)) in FP64.
+__device__ __forceinline__ void rotate64(double& s, double& c, double d) {
+  double sd, cd;
+  sincos_small64(d, sd, cd);
   const double s2 = s * cd + c * sd;
   const double c2 = c * cd - s * sd;
   s = s2;
@@ -211,7 +215,7 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
     const double t3 = t2 * t, t4 = t3 * t;
     tempa = tempa - rc.d2 * t2 - rc.d3 * t3 - rc.d4 * t4;
     double sdd, cdd;
-    sincos(dd, &sdd, &cdd);
+    sincos_small64(dd, sdd, cdd);   // the drag shift dd is usually small
     tempe = tempe + rc.bc5 * (sm * cdd + cm * sdd - rc.sinm0);   // sin(M_DF + dd)
     templ = templ + rc.l3 * t3 + t4 * (rc.l4 + t * rc.l5);
   }

@@ -115,7 +115,7 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
     argp = argpdf - dd;
     tempa = tempa - rc.d2 * f.t2 - rc.d3 * f.t3 - rc.d4 * f.t4;
     double sdd, cdd;
-    sincos(dd, &sdd, &cdd);
+    sincos_small64(dd, sdd, cdd);
     f.sMM = f.sMdf * cdd + f.cMdf * sdd;
     f.cMM = f.cMdf * cdd - f.sMdf * sdd;
     tempe = tempe + rc.bc5 * (f.sMM - rc.sinm0);
