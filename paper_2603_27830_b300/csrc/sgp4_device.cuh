@@ -221,8 +221,11 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   }
   if (rc.flags & kFlagN0ppNonPos) return 2;
   const double a = rc.a0pp * tempa * tempa;
-  const double sa = sqrt(a);
-  const double ia15 = 1.0 / (a * sa);                  // n / ke
+  // square roots and reciprocals through rsqrt (one FP64-unit sequence instead of a
+  // square root and a division)
+  const double ra = rsqrt(a);
+  const double sa = a * ra;
+  const double ia15 = ra * ra * ra;                    // n / ke
   double e = rc.e0 - tempe;
   if (e >= 1.0 || e < -0.001) return 1;
   if (e < 1.0e-6) e = 1.0e-6;
@@ -263,7 +266,8 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   const double rl = a * (1.0 - ecosE);
   const double invr = 1.0 / rl;
   const double rdotl = sa * esinE * invr;
-  const double spl = sqrt(pL);
+  const double rpl = rsqrt(pL);
+  const double spl = pL * rpl;
   const double rfdotl = spl * invr;
   const double betal = sqrt(1.0 - eL2);
   const double w = esinE / (1.0 + betal);
@@ -274,7 +278,7 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   const double cos2u = 1.0 - 2.0 * sinu * sinu;
 
   // Short-period periodics (J2).
-  const double invp = 1.0 / pL;
+  const double invp = rpl * rpl;
   const double k = 0.5 * g.j2 * invp;
   const double kp = k * invp;
   const double rk = rl * (1.0 - 1.5 * kp * betal * rc.x3thm1) + 0.5 * k * rc.x1mth2 * cos2u;
@@ -283,7 +287,7 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   const double rfdotk = rfdotl + nk * (rc.x1mth2 * cos2u + 1.5 * rc.x3thm1);
 
   // u_k, RAAN_k and i_k as rotations of (sin, cos) pairs.
-  const double nrm = 1.0 / sqrt(sinu * sinu + cosu * cosu);
+  const double nrm = rsqrt(sinu * sinu + cosu * cosu);
   double su = sinu * nrm, cu = cosu * nrm;
   rotate64(su, cu, -0.25 * kp * rc.x7thm1 * sin2u);
   double sO, cO;

@@ -124,8 +124,9 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
   f.tempa = tempa;
   f.templ = templ;
   f.a = rc.a0pp * tempa * tempa;
-  f.sqa = sqrt(f.a);
-  const double ia15 = 1.0 / (f.a * f.sqa);
+  const double ra = rsqrt(f.a);
+  f.sqa = f.a * ra;
+  const double ia15 = ra * ra * ra;
   f.n = g.xke * ia15;
   const double e1 = rc.e0 - tempe;
   if (e1 >= 1.0 || e1 < -0.001) return 1;
@@ -162,7 +163,8 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
   f.rl = f.a * (1.0 - f.ecosE);
   const double invr = 1.0 / f.rl;
   f.rdotl = f.sqa * f.esinE * invr;
-  f.sqp = sqrt(f.pL);
+  const double rpl = rsqrt(f.pL);
+  f.sqp = f.pL * rpl;
   f.rfdotl = f.sqp * invr;
   f.betal = sqrt(1.0 - f.eL2);
   f.opb = 1.0 + f.betal;
@@ -174,7 +176,7 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
   f.cosu = f.aor * f.Ac;
   f.sin2u = 2.0 * f.cosu * f.sinu;
   f.cos2u = 1.0 - 2.0 * f.sinu * f.sinu;
-  const double invp = 1.0 / f.pL;
+  const double invp = rpl * rpl;
   f.k = 0.5 * g.j2 * invp;
   f.kp = f.k * invp;
   f.fac = 1.0 - 1.5 * f.kp * f.betal * rc.x3thm1;
@@ -182,7 +184,7 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
   f.nk = ia15 * f.k;
   f.rdotk = f.rdotl - f.nk * rc.x1mth2 * f.sin2u;
   f.rfdotk = f.rfdotl + f.nk * (rc.x1mth2 * f.cos2u + 1.5 * rc.x3thm1);
-  const double nrm = 1.0 / sqrt(f.sinu * f.sinu + f.cosu * f.cosu);
+  const double nrm = rsqrt(f.sinu * f.sinu + f.cosu * f.cosu);
   f.su = f.sinu * nrm; f.cu = f.cosu * nrm;
   rotate64(f.su, f.cu, -0.25 * f.kp * rc.x7thm1 * f.sin2u);
   sincos(raan, &f.sO, &f.cO);
