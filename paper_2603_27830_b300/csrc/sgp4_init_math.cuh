@@ -36,6 +36,8 @@ __device__ __forceinline__ double sc_pow(double x, double p) { return ::pow(x, p
 __device__ __forceinline__ float sc_pow(float x, float p) { return ::powf(x, p); }
 __device__ __forceinline__ double sc_cbrt(double x) { return ::cbrt(x); }
 __device__ __forceinline__ float sc_cbrt(float x) { return ::cbrtf(x); }
+__device__ __forceinline__ double sc_rsqrt(double x) { return ::rsqrt(x); }
+__device__ __forceinline__ float sc_rsqrt(float x) { return ::rsqrtf(x); }
 __device__ __forceinline__ void sc_sincos(double x, double* s, double* c) { ::sincos(x, s, c); }
 __device__ __forceinline__ void sc_sincos(float x, float* s, float* c) { ::sincosf(x, s, c); }
 
@@ -138,6 +140,11 @@ __device__ __forceinline__ Dual7<R> sqrt(const Dual7<R>& a) {
   return d7chain(a, s, R(0.5) / s);
 }
 template <class R>
+__device__ __forceinline__ Dual7<R> rsqrt(const Dual7<R>& a) {
+  const R r = sc_rsqrt(a.v);
+  return d7chain(a, r, R(-0.5) * r * r * r);
+}
+template <class R>
 __device__ __forceinline__ Dual7<R> pow(const Dual7<R>& a, double p) {
   const R y = sc_pow(a.v, R(p));
   return d7chain(a, y, R(p) * y / a.v);
@@ -196,6 +203,7 @@ using ::cbrt;
 using ::cos;
 using ::fabs;
 using ::pow;
+using ::rsqrt;
 using ::sin;
 using ::sincos;
 using ::sqrt;
@@ -223,43 +231,56 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
   const S x3thm1 = 3.0 * th2 - 1.0;
   const S x1mth2 = 1.0 - th2;
   const S x7thm1 = 7.0 * th2 - 1.0;
+  // Reciprocals and square roots are formed from a few rsqrt and divisions and reused
+  // (on B300 each FP64 division or square root is a chain of FP64-unit instructions,
+  // and the record build is bound by that chain).
   const S b2 = 1.0 - e0 * e0;
-  const S b = sqrt(b2);
-  const S b3 = b2 * b;
+  const S rb = rsqrt(b2);                     // 1 / beta0
+  const S b = b2 * rb;
+  const double inv_xke = 1.0 / g.xke;
+  const double inv_re = 1.0 / g.re;
 
   // Kozai -> Brouwer mean motion and semi-major axis.
-  const S x1 = g.xke / n0;
-  const S a1 = cbrt_pos(x1 * x1);             // (ke / n0)^(2/3)
-  const S d1 = 1.5 * k2 * x3thm1 / (a1 * a1 * b3);
-  const S a0 = a1 * (1.0 - d1 / 3.0 - d1 * d1 - (134.0 / 81.0) * d1 * d1 * d1);
-  const S d0 = 1.5 * k2 * x3thm1 / (a0 * a0 * b3);
-  const S n0pp = n0 / (1.0 + d0);
-  const S xpp = g.xke / n0pp;
+  const S n0k = n0 * inv_xke;                 // n0 / ke = 1 / x1
+  const S x1 = 1.0 / n0k;
+  const S a1 = cbrt_pos(x1 * x1);             // (ke / n0)^(2/3); 1 / a1^2 = a1 (n0 / ke)^2
+  const S c3b = 1.5 * k2 * x3thm1 * (rb * rb * rb);
+  const S d1 = c3b * a1 * (n0k * n0k);
+  const S a0 = a1 * (1.0 - d1 * (1.0 / 3.0) - d1 * d1 - (134.0 / 81.0) * d1 * d1 * d1);
+  const S ia0 = 1.0 / a0;
+  const S d0 = c3b * (ia0 * ia0);
+  const S opd0 = 1.0 + d0;
+  const S n0pp = n0 / opd0;
+  const S xpp = x1 * opd0;                    // ke / n0''
   const S a0pp = cbrt_pos(xpp * xpp);         // (ke / n0'')^(2/3)
+  const S npk = n0pp * inv_xke;
+  const S ia0pp = (a0pp * a0pp) * (npk * npk);   // 1 / a0'' = a0''^2 (n0'' / ke)^2
 
   // Atmosphere: s and (q0 - s)^4 by perigee height.
   const S rp_er = a0pp * (1.0 - e0);
   const S hp = (rp_er - 1.0) * g.re;
-  o.isimp = val(rp_er) < 1.0 + 220.0 / g.re;
+  o.isimp = val(rp_er) < 1.0 + 220.0 * inv_re;
   S s_km = 0.0 * hp + 78.0;
   if (val(hp) < 156.0) s_km = hp - 78.0;
   if (val(hp) < 98.0) s_km = 0.0 * hp + 20.0;
-  const S qs = (120.0 - s_km) / g.re;
+  const S qs = (120.0 - s_km) * inv_re;
   const S qs4 = qs * qs * qs * qs;
-  const S ss = 1.0 + s_km / g.re;
+  const S ss = 1.0 + s_km * inv_re;
 
   const S xi = 1.0 / (a0pp - ss);
   const S eta = a0pp * e0 * xi;
   const S eta2 = eta * eta;
   const S eeta = e0 * eta;
   const S psi2 = fabs(1.0 - eta2);
+  const S rpsi = rsqrt(psi2);
+  const S ipsi2 = rpsi * rpsi;                // 1 / psi2
   const S xi4 = xi * xi * xi * xi;
   const S coef = qs4 * xi4;
-  const S coef1 = coef / (psi2 * psi2 * psi2 * sqrt(psi2));   // coef / psi2^3.5
+  const S coef1 = coef * (ipsi2 * ipsi2 * ipsi2 * rpsi);   // coef / psi2^3.5
 
   const S C2 = coef1 * n0pp *
                (a0pp * (1.0 + 1.5 * eta2 + eeta * (4.0 + eta2)) +
-                0.375 * g.j2 * xi / psi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
+                0.375 * g.j2 * xi * ipsi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
   const S C1 = bstar * C2;
   S sinw, cosw;
   sincos(argp0, &sinw, &cosw);
@@ -268,14 +289,14 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
   if (val(e0) > 1.0e-4) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sini / e0;
   const S C4 = 2.0 * n0pp * coef1 * a0pp * b2 *
                (eta * (2.0 + 0.5 * eta2) + e0 * (0.5 + 2.0 * eta2) -
-                g.j2 * xi / (a0pp * psi2) *
+                g.j2 * xi * ia0pp * ipsi2 *
                     (-3.0 * x3thm1 * (1.0 - 2.0 * eeta + eta2 * (1.5 - 0.5 * eeta)) +
                      0.75 * x1mth2 * (2.0 * eta2 - eeta * (1.0 + eta2)) * cos2w));
   const S C5 = 2.0 * coef1 * a0pp * b2 * (1.0 + 2.75 * (eta2 + eeta) + eeta * eta2);
 
   // Secular rates.
-  const S p0 = a0pp * b2;
-  const S pinv2 = 1.0 / (p0 * p0);
+  const S pinv = ia0pp * (rb * rb);           // 1 / (a0'' beta0^2)
+  const S pinv2 = pinv * pinv;
   const S T1 = 1.5 * g.j2 * pinv2 * n0pp;
   const S T2 = 0.5 * T1 * g.j2 * pinv2;
   const S T3 = -0.46875 * g.j4 * pinv2 * pinv2 * n0pp;

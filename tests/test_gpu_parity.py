@@ -335,12 +335,15 @@ def test_julian_date_grid_from_each_records_split_epoch(prec):
     dr, dv = state_errors(r[rows], v[rows], rr[rows], vr[rows], sr[rows])
     if prec == "fp64":
         # the enormous-drag edge record reaches |r| ~ 6.5e8 km at negative t, where the
-        # theory is ill-conditioned: there the bound is relative (1e-11 |r|)
+        # theory is ill-conditioned (an ulp in a record constant moves r by ~1e-11 of
+        # itself): there the bound is relative, 1e-10 |r|
         keep = (sr[rows] == 0) | (sr[rows] == 6)
         rn = np.linalg.norm(rr[rows][keep], axis=-1)
-        assert np.all(dr <= np.maximum(FP64_TOL_R_KM, 1e-11 * rn)), error_summary(dr, dv)
-        assert np.all(dv <= np.maximum(FP64_TOL_V_KMS, 1e-11 * np.linalg.norm(
+        assert np.all(dr <= np.maximum(FP64_TOL_R_KM, 1e-10 * rn)), error_summary(dr, dv)
+        assert np.all(dv <= np.maximum(FP64_TOL_V_KMS, 1e-10 * np.linalg.norm(
             vr[rows][keep], axis=-1) * np.maximum(1.0, rn / 1e5))), error_summary(dr, dv)
+        well = rn < 1e5
+        assert dr[well].max() <= FP64_TOL_R_KM, error_summary(dr[well], dv[well])
     else:
         assert dr.max() <= 0.1 and dv.max() <= 1e-4, error_summary(dr, dv)
 
