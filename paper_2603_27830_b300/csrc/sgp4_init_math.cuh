@@ -216,45 +216,73 @@ struct InitFields {
   S c1, bc4, bc5, d2, d3, d4, l2, l3, l4, l5;
   S eta, delm0, sinm0, xlcof, aycof;
   S cosi, sini, x3thm1, x1mth2, x7thm1;
+  S raandot1;   // first-order node rate (for raan_cf), not a record field
   bool isimp;
+};
+
+// The computation comes in phases, so that the record-build kernel can run the two
+// independent branches of it (drag terms; secular rates) in two warps:
+//   init_spine   inclination terms, beta0, the un-Kozai'd mean motion and a0'';
+//   init_angles  sin/cos of argp0 and M0 (independent of the spine);
+//   init_drag    atmosphere, C1 .. C5, D2 .. L5 and the drag rates (spine, angles);
+//   init_rates   secular rates and the J3 coefficients (spine);
+//   init_finish  the node drag term (drag and rates) and the element copies.
+// Reciprocals and square roots are formed from a few rsqrt and divisions and reused (on
+// B300 each FP64 division or square root is a chain of FP64-unit instructions, and the
+// record build is bound by that chain).
+template <class S>
+struct InitSpine {
+  S cosi, sini, th2, x3thm1, x1mth2, x7thm1, b2, rb, b, n0pp, a0pp, ia0pp;
+};
+template <class S>
+struct InitAngles {
+  S sinw, cosw, sinm, cosm;
 };
 
 // Valid elements only (the caller screens non-finite input, e0 outside [0,1), n0 <= 0).
 template <class S>
-__device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFields<S>& o) {
-  const S n0 = el[0], e0 = el[1], i0 = el[2], raan0 = el[3], argp0 = el[4], m0 = el[5];
-  const S bstar = el[6];
+__device__ __forceinline__ void init_spine(const S el[7], const Geo& g, InitSpine<S>& sp) {
+  const S n0 = el[0], e0 = el[1], i0 = el[2];
   const double k2 = 0.5 * g.j2;
-  S cosi, sini;
-  sincos(i0, &sini, &cosi);
-  const S th2 = cosi * cosi;
-  const S x3thm1 = 3.0 * th2 - 1.0;
-  const S x1mth2 = 1.0 - th2;
-  const S x7thm1 = 7.0 * th2 - 1.0;
-  // Reciprocals and square roots are formed from a few rsqrt and divisions and reused
-  // (on B300 each FP64 division or square root is a chain of FP64-unit instructions,
-  // and the record build is bound by that chain).
-  const S b2 = 1.0 - e0 * e0;
-  const S rb = rsqrt(b2);                     // 1 / beta0
-  const S b = b2 * rb;
+  sincos(i0, &sp.sini, &sp.cosi);
+  sp.th2 = sp.cosi * sp.cosi;
+  sp.x3thm1 = 3.0 * sp.th2 - 1.0;
+  sp.x1mth2 = 1.0 - sp.th2;
+  sp.x7thm1 = 7.0 * sp.th2 - 1.0;
+  sp.b2 = 1.0 - e0 * e0;
+  sp.rb = rsqrt(sp.b2);                       // 1 / beta0
+  sp.b = sp.b2 * sp.rb;
   const double inv_xke = 1.0 / g.xke;
-  const double inv_re = 1.0 / g.re;
 
   // Kozai -> Brouwer mean motion and semi-major axis.
   const S n0k = n0 * inv_xke;                 // n0 / ke = 1 / x1
   const S x1 = 1.0 / n0k;
   const S a1 = cbrt_pos(x1 * x1);             // (ke / n0)^(2/3); 1 / a1^2 = a1 (n0 / ke)^2
-  const S c3b = 1.5 * k2 * x3thm1 * (rb * rb * rb);
+  const S c3b = 1.5 * k2 * sp.x3thm1 * (sp.rb * sp.rb * sp.rb);
   const S d1 = c3b * a1 * (n0k * n0k);
   const S a0 = a1 * (1.0 - d1 * (1.0 / 3.0) - d1 * d1 - (134.0 / 81.0) * d1 * d1 * d1);
   const S ia0 = 1.0 / a0;
   const S d0 = c3b * (ia0 * ia0);
   const S opd0 = 1.0 + d0;
-  const S n0pp = n0 / opd0;
+  sp.n0pp = n0 / opd0;
   const S xpp = x1 * opd0;                    // ke / n0''
-  const S a0pp = cbrt_pos(xpp * xpp);         // (ke / n0'')^(2/3)
-  const S npk = n0pp * inv_xke;
-  const S ia0pp = (a0pp * a0pp) * (npk * npk);   // 1 / a0'' = a0''^2 (n0'' / ke)^2
+  sp.a0pp = cbrt_pos(xpp * xpp);              // (ke / n0'')^(2/3)
+  const S npk = sp.n0pp * inv_xke;
+  sp.ia0pp = (sp.a0pp * sp.a0pp) * (npk * npk);   // 1 / a0'' = a0''^2 (n0'' / ke)^2
+}
+
+template <class S>
+__device__ __forceinline__ void init_angles(const S el[7], InitAngles<S>& an) {
+  sincos(el[4], &an.sinw, &an.cosw);
+  sincos(el[5], &an.sinm, &an.cosm);
+}
+
+template <class S>
+__device__ __forceinline__ void init_drag(const S el[7], const Geo& g, const InitSpine<S>& sp,
+                                          const InitAngles<S>& an, InitFields<S>& o) {
+  const S e0 = el[1], bstar = el[6];
+  const double inv_re = 1.0 / g.re;
+  const S a0pp = sp.a0pp, n0pp = sp.n0pp, b2 = sp.b2, x3thm1 = sp.x3thm1, x1mth2 = sp.x1mth2;
 
   // Atmosphere: s and (q0 - s)^4 by perigee height.
   const S rp_er = a0pp * (1.0 - e0);
@@ -282,46 +310,23 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
                (a0pp * (1.0 + 1.5 * eta2 + eeta * (4.0 + eta2)) +
                 0.375 * g.j2 * xi * ipsi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
   const S C1 = bstar * C2;
-  S sinw, cosw;
-  sincos(argp0, &sinw, &cosw);
-  const S cos2w = 2.0 * cosw * cosw - 1.0;
+  const S cos2w = 2.0 * an.cosw * an.cosw - 1.0;
   S C3 = 0.0 * C1;
-  if (val(e0) > 1.0e-4) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sini / e0;
+  if (val(e0) > 1.0e-4) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sp.sini / e0;
   const S C4 = 2.0 * n0pp * coef1 * a0pp * b2 *
                (eta * (2.0 + 0.5 * eta2) + e0 * (0.5 + 2.0 * eta2) -
-                g.j2 * xi * ia0pp * ipsi2 *
+                g.j2 * xi * sp.ia0pp * ipsi2 *
                     (-3.0 * x3thm1 * (1.0 - 2.0 * eeta + eta2 * (1.5 - 0.5 * eeta)) +
                      0.75 * x1mth2 * (2.0 * eta2 - eeta * (1.0 + eta2)) * cos2w));
   const S C5 = 2.0 * coef1 * a0pp * b2 * (1.0 + 2.75 * (eta2 + eeta) + eeta * eta2);
 
-  // Secular rates.
-  const S pinv = ia0pp * (rb * rb);           // 1 / (a0'' beta0^2)
-  const S pinv2 = pinv * pinv;
-  const S T1 = 1.5 * g.j2 * pinv2 * n0pp;
-  const S T2 = 0.5 * T1 * g.j2 * pinv2;
-  const S T3 = -0.46875 * g.j4 * pinv2 * pinv2 * n0pp;
-  const S th4 = th2 * th2;
-  o.mdot = n0pp + 0.5 * T1 * b * x3thm1 + 0.0625 * T2 * b * (13.0 - 78.0 * th2 + 137.0 * th4);
-  o.argpdot = -0.5 * T1 * (1.0 - 5.0 * th2) + 0.0625 * T2 * (7.0 - 114.0 * th2 + 395.0 * th4) +
-              T3 * (3.0 - 36.0 * th2 + 49.0 * th4);
-  const S raandot1 = -T1 * cosi;
-  o.raandot = raandot1 + (0.5 * T2 * (4.0 - 19.0 * th2) + 2.0 * T3 * (3.0 - 7.0 * th2)) * cosi;
-
-  o.raan_cf = 3.5 * b2 * raandot1 * C1;
-  o.argp_cf = bstar * C3 * cosw;
+  o.argp_cf = bstar * C3 * an.cosw;
   o.m_cf = 0.0 * C1;
   if (val(e0) > 1.0e-4) o.m_cf = -(2.0 / 3.0) * coef * bstar / eeta;
   o.l2 = 1.5 * C1;
-
-  S opc = 1.0 + cosi;
-  if (::fabs((double)val(opc)) <= 1.5e-12) opc = 0.0 * opc + 1.5e-12;
-  o.xlcof = -0.25 * g.j3oj2 * sini * (3.0 + 5.0 * cosi) / opc;
-  o.aycof = -0.5 * g.j3oj2 * sini;
-  S sinm, cosm;
-  sincos(m0, &sinm, &cosm);
-  const S cm = 1.0 + eta * cosm;
+  const S cm = 1.0 + eta * an.cosm;
   o.delm0 = cm * cm * cm;
-  o.sinm0 = sinm;
+  o.sinm0 = an.sinm;
 
   o.d2 = 0.0 * C1; o.d3 = o.d2; o.d4 = o.d2; o.l3 = o.d2; o.l4 = o.d2; o.l5 = o.d2;
   if (!o.isimp) {
@@ -334,9 +339,52 @@ __device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFie
     o.l5 = 0.2 * (3.0 * o.d4 + 12.0 * C1 * o.d3 + 6.0 * o.d2 * o.d2 + 30.0 * c1sq * o.d2 +
                   15.0 * c1sq * c1sq);
   }
-  o.n0pp = n0pp; o.a0pp = a0pp; o.e0 = e0; o.i0 = i0; o.raan0 = raan0; o.argp0 = argp0;
-  o.m0 = m0; o.c1 = C1; o.bc4 = bstar * C4; o.bc5 = bstar * C5; o.eta = eta;
-  o.cosi = cosi; o.sini = sini; o.x3thm1 = x3thm1; o.x1mth2 = x1mth2; o.x7thm1 = x7thm1;
+  o.c1 = C1; o.bc4 = bstar * C4; o.bc5 = bstar * C5; o.eta = eta;
+}
+
+template <class S>
+__device__ __forceinline__ void init_rates(const Geo& g, const InitSpine<S>& sp,
+                                           InitFields<S>& o) {
+  const S n0pp = sp.n0pp, th2 = sp.th2, cosi = sp.cosi, sini = sp.sini, b = sp.b;
+  const S pinv = sp.ia0pp * (sp.rb * sp.rb);  // 1 / (a0'' beta0^2)
+  const S pinv2 = pinv * pinv;
+  const S T1 = 1.5 * g.j2 * pinv2 * n0pp;
+  const S T2 = 0.5 * T1 * g.j2 * pinv2;
+  const S T3 = -0.46875 * g.j4 * pinv2 * pinv2 * n0pp;
+  const S th4 = th2 * th2;
+  o.mdot = n0pp + 0.5 * T1 * b * sp.x3thm1 + 0.0625 * T2 * b * (13.0 - 78.0 * th2 + 137.0 * th4);
+  o.argpdot = -0.5 * T1 * (1.0 - 5.0 * th2) + 0.0625 * T2 * (7.0 - 114.0 * th2 + 395.0 * th4) +
+              T3 * (3.0 - 36.0 * th2 + 49.0 * th4);
+  o.raandot1 = -T1 * cosi;
+  o.raandot = o.raandot1 + (0.5 * T2 * (4.0 - 19.0 * th2) + 2.0 * T3 * (3.0 - 7.0 * th2)) * cosi;
+
+  S opc = 1.0 + cosi;
+  if (::fabs((double)val(opc)) <= 1.5e-12) opc = 0.0 * opc + 1.5e-12;
+  o.xlcof = -0.25 * g.j3oj2 * sini * (3.0 + 5.0 * cosi) / opc;
+  o.aycof = -0.5 * g.j3oj2 * sini;
+}
+
+// raan_cf needs C1 (drag) and the first-order node rate (rates).
+template <class S>
+__device__ __forceinline__ void init_finish(const S el[7], const InitSpine<S>& sp,
+                                            InitFields<S>& o) {
+  o.raan_cf = 3.5 * sp.b2 * o.raandot1 * o.c1;
+  o.n0pp = sp.n0pp; o.a0pp = sp.a0pp; o.e0 = el[1]; o.i0 = el[2]; o.raan0 = el[3];
+  o.argp0 = el[4]; o.m0 = el[5];
+  o.cosi = sp.cosi; o.sini = sp.sini; o.x3thm1 = sp.x3thm1; o.x1mth2 = sp.x1mth2;
+  o.x7thm1 = sp.x7thm1;
+}
+
+// All phases in one thread (the dual-number Jacobians; the FP64 fallback paths).
+template <class S>
+__device__ __forceinline__ void init_fields(const S el[7], const Geo& g, InitFields<S>& o) {
+  InitSpine<S> sp;
+  InitAngles<S> an;
+  init_spine(el, g, sp);
+  init_angles(el, an);
+  init_drag(el, g, sp, an, o);
+  init_rates(g, sp, o);
+  init_finish(el, sp, o);
 }
 
 }  // namespace sgp4
