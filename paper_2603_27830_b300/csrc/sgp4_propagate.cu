@@ -63,6 +63,7 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
   const int Th = (T + 1) / 2;
   int64_t j = (ubeg + tid) / Th;
   int i0 = (int)((ubeg + tid) - j * Th);
+  const int jstep = kThreads / Th, istep = kThreads - jstep * Th;
   for (int64_t u = ubeg + tid; u < uend; u += kThreads) {
     const int64_t rec = rg.sat0 + j;
     const int i1 = i0 + Th;
@@ -90,7 +91,22 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
     int code[2];
     state32x2(rc32, gf, th, tl, r2, v2, code);
     const float q = __int_as_float(0x7fc00000);
-    for (int l = 0; l < 2; ++l) {
+    // Common case, both states present and valid (status 0 or 6): twelve floats and two
+    // statuses stored without per-lane branches or NaN selects.
+    const bool fast = has1 & ((code[0] == 0) | (code[0] == 6)) & ((code[1] == 0) | (code[1] == 6));
+    if (fast) {
+      const int64_t idx = j * T + i0;
+      float* gr = static_cast<float*>(rg.r) + idx * 3;
+      float* gv = static_cast<float*>(rg.v) + idx * 3;
+      const int o1 = Th * 3;   // state i1 = i0 + Th of the same satellite
+      __stcs(gr + 0, r2[0].x); __stcs(gr + 1, r2[1].x); __stcs(gr + 2, r2[2].x);
+      __stcs(gv + 0, v2[0].x); __stcs(gv + 1, v2[1].x); __stcs(gv + 2, v2[2].x);
+      __stcs(gr + o1 + 0, r2[0].y); __stcs(gr + o1 + 1, r2[1].y); __stcs(gr + o1 + 2, r2[2].y);
+      __stcs(gv + o1 + 0, v2[0].y); __stcs(gv + o1 + 1, v2[1].y); __stcs(gv + o1 + 2, v2[2].y);
+      __stcs(rg.status + idx, code[0]);
+      __stcs(rg.status + idx + Th, code[1]);
+    } else
+    for (int l = 0; l < 2; ++l) {   // per lane: the last unit of an odd T, NaN outputs, FP64 recomputation
       if (l == 1 && !has1) break;
       const int64_t idx = j * T + it[l];
       float* gr = static_cast<float*>(rg.r) + idx * 3;
@@ -111,11 +127,12 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
       }
       __stcs(rg.status + idx, cd);
     }
-    i0 += kThreads;
+    // next unit of this thread: kThreads = jstep * Th + istep, so at most one wrap
+    j += jstep;
+    i0 += istep;
     if (i0 >= Th) {
-      const int qd = i0 / Th;
-      j += qd;
-      i0 -= qd * Th;
+      ++j;
+      i0 -= Th;
     }
   }
 }
@@ -130,6 +147,7 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
   const int Th = (T + 1) / 2;
   int64_t j = (ubeg + tid) / Th;
   int i0 = (int)((ubeg + tid) - j * Th);
+  const int jstep = kThreads / Th, istep = kThreads - jstep * Th;
   int64_t cur = -1;
   Rec64 rc;
   const double q = __longlong_as_double(0x7ff8000000000000LL);
@@ -162,11 +180,12 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
       }
       __stcs(rg.status + idx, code);
     }
-    i0 += kThreads;
+    // next unit of this thread: kThreads = jstep * Th + istep, so at most one wrap
+    j += jstep;
+    i0 += istep;
     if (i0 >= Th) {
-      const int qd = i0 / Th;
-      j += qd;
-      i0 -= qd * Th;
+      ++j;
+      i0 -= Th;
     }
   }
 }

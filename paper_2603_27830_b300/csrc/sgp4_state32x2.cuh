@@ -9,7 +9,10 @@
 // shared scalars, and every add, multiply and FMA of the state is one packed
 // instruction for both.  Transcendentals (SFU), compares, selects and the integer work
 // stay per state.  The arithmetic is that of state32 (same formulation, guard bands and
-// status logic); only the fusing of some products into FMAs differs.
+// status logic); the fusing of products into FMAs and the evaluation order of the drag
+// polynomials (Horner form) differ.  A record field enters a packed operation as a
+// pair of equal halves, so the formulas are arranged to need no negated fields and no
+// multiplications by -1 (each would be one more instruction per use).
 #pragma once
 
 #include "sgp4_device.cuh"
@@ -23,16 +26,27 @@ __device__ __forceinline__ F2 S(float a) { return make_float2(a, a); }
 __device__ __forceinline__ F2 add(F2 a, F2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ F2 mul(F2 a, F2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
-// a - b with one rounding (b * -1 is exact)
-__device__ __forceinline__ F2 sub(F2 a, F2 b) { return __ffma2_rn(b, S(-1.0f), a); }
+// a - b, one rounding per lane (the packed subtract)
+__device__ __forceinline__ F2 sub(F2 a, F2 b) {
+  F2 d;
+  asm("{\n\t.reg .b64 pa, pb, pd;\n\t"
+      "mov.b64 pa, {%2, %3};\n\t"
+      "mov.b64 pb, {%4, %5};\n\t"
+      "sub.rn.f32x2 pd, pa, pb;\n\t"
+      "mov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
 
 // x - rint(x) by the 1.5 * 2^23 rounding trick, lane by lane exact for |x| < 2^22.
 __device__ __forceinline__ F2 wrap_rev(F2 x) {
-  const F2 r = add(add(x, S(kRoundMagic)), S(-kRoundMagic));
+  const F2 r = sub(add(x, S(kRoundMagic)), S(kRoundMagic));
   return sub(x, r);
 }
 
-__device__ __forceinline__ F2 rsqrt(F2 x) { return make_float2(rsqrtf(x.x), rsqrtf(x.y)); }
+// rsqrt_ftz per lane (its arguments are normal numbers outside the guard bands)
+__device__ __forceinline__ F2 rsqrt(F2 x) { return make_float2(rsqrt_ftz(x.x), rsqrt_ftz(x.y)); }
 // 1 / y for y > 0 as rsqrt(y)^2
 __device__ __forceinline__ F2 rcp_pos(F2 y) {
   const F2 r = rsqrt(y);
@@ -79,7 +93,7 @@ __device__ __forceinline__ void rotate_small(F2& s, F2& c, F2 d) {
   const F2 sd = fma(mul(d2, S(-1.0f / 6.0f)), d, d);
   const F2 cd = fma(S(-0.5f), d2, S(1.0f));
   const F2 s2 = fma(s, cd, mul(c, sd));
-  const F2 c2 = fma(c, cd, mul(mul(s, sd), S(-1.0f)));
+  const F2 c2 = sub(mul(c, cd), mul(s, sd));
   s = s2;
   c = c2;
 }
@@ -103,19 +117,23 @@ __device__ __forceinline__ void state32x2(const Rec32& rc, const GeoF& g, float2
   const F2 mdf = mul(wrap_rev(fma(S(rc.mdr), t, S(rc.m0r))), S(kTwoPiF));
   const F2 cm = make_float2(__cosf(mdf.x), __cosf(mdf.y));
   const F2 c = fma(S(rc.eta), cm, S(1.0f));
-  const F2 dm = mul(S(rc.mcf), fma(mul(c, c), c, S(-rc.delm0)));
+  const F2 dm = mul(S(rc.mcf), sub(mul(mul(c, c), c), S(rc.delm0)));
   const F2 dd = add(dargp, dm);
-  const F2 t3 = mul(t2, t), t4 = mul(t3, t);
-  F2 tempa = fma(S(-rc.c1), t, S(1.0f));
-  tempa = fma(S(-rc.d2), t2, tempa);
-  tempa = fma(S(-rc.d3), t3, tempa);
-  tempa = fma(S(-rc.d4), t4, tempa);
+  // tempa = 1 - C1 t - D2 t^2 - D3 t^3 - D4 t^4 and the t^2 .. t^5 mean-longitude
+  // polynomial, both in Horner form
+  F2 h = fma(S(rc.d4), t, S(rc.d3));
+  h = fma(h, t, S(rc.d2));
+  h = fma(h, t, S(rc.c1));
+  const F2 tempa = sub(S(1.0f), mul(h, t));
   const F2 md = add(mdf, dd);
   const F2 sm = make_float2(__sinf(md.x), __sinf(md.y));
-  const F2 tempe = fma(S(rc.bc5), add(sm, S(-rc.sinm0)), mul(S(rc.bc4), t));
-  const F2 templ = fma(t4, fma(t, S(rc.l5), S(rc.l4)), fma(S(rc.l3), t3, mul(S(rc.l2), t2)));
+  const F2 tempe = fma(S(rc.bc5), sub(sm, S(rc.sinm0)), mul(S(rc.bc4), t));
+  F2 hl = fma(S(rc.l5), t, S(rc.l4));
+  hl = fma(hl, t, S(rc.l3));
+  hl = fma(hl, t, S(rc.l2));
+  const F2 templ = mul(hl, t2);
   const F2 a = mul(S(rc.a0pp), mul(tempa, tempa));
-  F2 e = add(S(rc.e0), mul(tempe, S(-1.0f)));
+  F2 e = sub(S(rc.e0), tempe);
   // Status checks in the theory's order and the guard bands, per lane.
   bool g_e[2], f_e[2];
   {
@@ -149,7 +167,7 @@ __device__ __forceinline__ void state32x2(const Rec32& rc, const GeoF& g, float2
   F2 sw, cw;
   sincos_sfu(argp, sw, cw);
   const F2 axn = mul(e, cw);
-  const F2 q = rcp_pos(mul(a, fma(mul(e, S(-1.0f)), e, S(1.0f))));
+  const F2 q = rcp_pos(mul(a, sub(S(1.0f), mul(e, e))));
   const F2 ayn = fma(e, sw, mul(q, S(rc.aycof)));
   const F2 lpt = mul(mul(q, S(rc.xlcof)), axn);
   const bool g_lp[2] = {!x2::lt_abs(lpt.x, kGuardLongPeriod), !x2::lt_abs(lpt.y, kGuardLongPeriod)};
@@ -176,11 +194,11 @@ __device__ __forceinline__ void state32x2(const Rec32& rc, const GeoF& g, float2
   // Short-period preliminaries.
   const F2 ecosE = fma(axn, cp, mul(ayn, sp));
   const F2 esinE = fma(axn, sp, mul(nayn, cp));
-  const F2 omel = fma(eL2, S(-1.0f), S(1.0f));
+  const F2 omel = sub(S(1.0f), eL2);
   const F2 pL = mul(a, omel);
   const bool g_p[2] = {!(fabsf(pL.x) >= kGuardP), !(fabsf(pL.y) >= kGuardP)};
   const bool f_p[2] = {pL.x < 0.0f, pL.y < 0.0f};
-  const F2 rl = mul(a, fma(ecosE, S(-1.0f), S(1.0f)));
+  const F2 rl = mul(a, sub(S(1.0f), ecosE));
   const F2 invr = rcp_pos(rl);
   const F2 rdotl = mul(mul(sa, esinE), invr);
   const F2 rpl = rsqrt(pL);
@@ -223,7 +241,7 @@ __device__ __forceinline__ void state32x2(const Rec32& rc, const GeoF& g, float2
   const F2 nsO = mul(sO, S(-1.0f));
   const F2 mx = mul(nsO, ci), my = mul(cO, ci), mz = si;
   const F2 ux = fma(mx, su, mul(cO, cu)), uy = fma(my, su, mul(sO, cu)), uz = mul(mz, su);
-  const F2 vx = fma(mx, cu, mul(mul(cO, su), S(-1.0f)));
+  const F2 vx = sub(mul(mx, cu), mul(cO, su));
   const F2 vy = fma(my, cu, mul(nsO, su));
   const F2 vz = mul(mz, cu);
   const F2 rs = mul(rk, S(g.re));

@@ -231,7 +231,7 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
   if (e1 >= 1.0f || e1 < -0.001f) return 1;
   f.keep_e = e1 < 1.0e-6f ? 0.0f : 1.0f;
   f.e = fmaxf(e1, 1.0e-6f);
-  const float ra = rsqrtf(f.a);
+  const float ra = rsqrt_ftz(f.a);
   f.sqa = f.a * ra;
   const float ra3 = ra * ra * ra;
   f.n = g.xke * ra3;
@@ -273,11 +273,11 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
   f.rl = f.a * (1.0f - f.ecosE);
   const float invr = rcp_pos(f.rl);
   f.rdotl = f.sqa * f.esinE * invr;
-  const float rpl = rsqrtf(f.pL);
+  const float rpl = rsqrt_ftz(f.pL);
   f.sqp = f.pL * rpl;
   f.rfdotl = f.sqp * invr;
   const float omel = 1.0f - f.eL2;
-  f.betal = omel * rsqrtf(omel);
+  f.betal = omel * rsqrt_ftz(omel);
   f.opb = 1.0f + f.betal;
   f.w = f.esinE * rcp_pos(f.opb);
   f.aor = f.a * invr;
@@ -300,7 +300,7 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
   const float dO = f.kp * rc.c15cosi * f.sin2u;
   const float di = f.kp * rc.c15cosisini * f.cos2u;
   if (!(fmaxf(fabsf(du), fmaxf(fabsf(dO), fabsf(di))) < 4.0e-3f)) return kRecomputeFP64;
-  const float nrm = rsqrtf(f.sinu * f.sinu + f.cosu * f.cosu);
+  const float nrm = rsqrt_ftz(f.sinu * f.sinu + f.cosu * f.cosu);
   f.su = f.sinu * nrm; f.cu = f.cosu * nrm;
   rotate_small(f.su, f.cu, du);
   __sincosf(raan, &f.sO, &f.cO);
