@@ -14,17 +14,6 @@ namespace {
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
-sgp4::Geo make_geo(const sgp4_consts& c) {
-  sgp4::Geo g;
-  g.xke = 60.0 / std::sqrt(c.radius_km * c.radius_km * c.radius_km / c.mu_km3s2);
-  g.j2 = c.j2;
-  g.j3oj2 = (c.j2 != 0.0) ? c.j3 / c.j2 : 0.0;
-  g.j4 = c.j4;
-  g.re = c.radius_km;
-  g.vkmps = c.radius_km * g.xke / 60.0;
-  return g;
-}
-
 bool consts_ok(const sgp4_consts& c) {
   return std::isfinite(c.mu_km3s2) && c.mu_km3s2 > 0 && std::isfinite(c.radius_km) &&
          c.radius_km > 0 && std::isfinite(c.j2) && std::isfinite(c.j3) && std::isfinite(c.j4);
@@ -64,7 +53,7 @@ sgp4_result batch_args(const sgp4_batch_plan* plan, const sgp4_records* records,
   if (fixups && !aligned(fixups, 8)) return SGP4_ERR_ARG;
   char* ws = static_cast<char*>(plan->workspace);
   a->rp = sgp4::record_ptrs(records->arena, records->n);
-  a->g = make_geo(records->consts);
+  a->g = sgp4::make_geo(records->consts);
   a->gf = sgp4::geo_float(a->g);
   a->tsince = tsince;
   a->reqs = reinterpret_cast<const sgp4_request*>(ws + ws_reqs_off(plan->n_requests));
@@ -128,7 +117,7 @@ sgp4_result sgp4_init(const double* elements, const int32_t* epoch_day, const do
   if (!elements || !init_status || !aligned(elements, 8)) return SGP4_ERR_ARG;
   const sgp4::RecordPtrs rp = sgp4::record_ptrs(records->arena, n);
   cudaError_t e = sgp4::launch_init(elements, epoch_day, epoch_frac, rp,
-                                    make_geo(records->consts), init_status,
+                                    sgp4::make_geo(records->consts), init_status,
                                     static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
 }
@@ -147,7 +136,7 @@ sgp4_result sgp4_propagate(const sgp4_records* records, const double* tsince, in
   if (fixups && !aligned(fixups, 8)) return SGP4_ERR_ARG;
   sgp4::PropArgs a;
   a.rp = sgp4::record_ptrs(records->arena, n);
-  a.g = make_geo(records->consts);
+  a.g = sgp4::make_geo(records->consts);
   a.gf = sgp4::geo_float(a.g);
   a.tsince = tsince;
   a.t_count = t_count;
@@ -178,7 +167,7 @@ sgp4_result sgp4_propagate_jd(const sgp4_records* records, const int32_t* jd_day
   if (fixups && !aligned(fixups, 8)) return SGP4_ERR_ARG;
   sgp4::PropArgs a;
   a.rp = sgp4::record_ptrs(records->arena, n);
-  a.g = make_geo(records->consts);
+  a.g = sgp4::make_geo(records->consts);
   a.gf = sgp4::geo_float(a.g);
   a.tsince = nullptr;
   a.jd_day = jd_day;
@@ -327,7 +316,7 @@ sgp4_result sgp4_adjoint(const double* elements, const sgp4_records* records,
   if (workspace_bytes < sgp4::adjoint_workspace_bytes(n)) return SGP4_ERR_OOM;
   if (n > 0x7fffffffLL) return SGP4_ERR_ARG;   // one block per satellite
   cudaError_t e = sgp4::launch_adjoint(
-      sgp4::record_ptrs(records->arena, n), make_geo(records->consts), elements, tsince, t_count,
+      sgp4::record_ptrs(records->arena, n), sgp4::make_geo(records->consts), elements, tsince, t_count,
       grid_per_sat ? 1 : 0, precision == SGP4_FP32, t_count > 0 ? grad_r : nullptr,
       t_count > 0 ? grad_v : nullptr, grad_elements, static_cast<double*>(workspace),
       static_cast<cudaStream_t>(stream));
@@ -356,7 +345,7 @@ sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
   if (!workspace || !aligned(workspace, 8)) return SGP4_ERR_ARG;
   if (workspace_bytes < sgp4::fit_workspace_bytes(n)) return SGP4_ERR_OOM;
   cudaError_t e = sgp4::launch_fit_step(
-      sgp4::record_ptrs(records->arena, n), make_geo(records->consts), elements, tsince, t_count,
+      sgp4::record_ptrs(records->arena, n), sgp4::make_geo(records->consts), elements, tsince, t_count,
       grid_per_sat ? 1 : 0, precision == SGP4_FP32, r_obs, lambda, elements_out, sse,
       static_cast<double*>(workspace), static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
@@ -392,7 +381,7 @@ sgp4_result sgp4_jacobian(const double* elements, const sgp4_records* records,
   out.cov = cov_out ? cov : nullptr;
   out.cov_out = cov_out;
   cudaError_t e = sgp4::launch_jacobian(
-      sgp4::record_ptrs(records->arena, n), make_geo(records->consts), elements, tsince, t_count,
+      sgp4::record_ptrs(records->arena, n), sgp4::make_geo(records->consts), elements, tsince, t_count,
       grid_per_sat ? 1 : 0, precision == SGP4_FP32, out, workspace,
       static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;

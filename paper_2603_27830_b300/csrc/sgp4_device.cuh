@@ -91,6 +91,8 @@ struct Geo {
   double j4;
   double re;      // km
   double vkmps;   // re * xke / 60: Earth radii per (1/xke min) -> km/s
+  double inv_xke; // 1 / xke and 1 / re, taken once on the host (an FP64 division is a
+  double inv_re;  // chain of FP64-unit instructions on B300)
 };
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;

@@ -252,7 +252,7 @@ __device__ __forceinline__ void init_spine(const S el[7], const Geo& g, InitSpin
   sp.b2 = 1.0 - e0 * e0;
   sp.rb = rsqrt(sp.b2);                       // 1 / beta0
   sp.b = sp.b2 * sp.rb;
-  const double inv_xke = 1.0 / g.xke;
+  const double inv_xke = g.inv_xke;
 
   // Kozai -> Brouwer mean motion and semi-major axis.
   const S n0k = n0 * inv_xke;                 // n0 / ke = 1 / x1
@@ -281,7 +281,7 @@ template <class S>
 __device__ __forceinline__ void init_drag(const S el[7], const Geo& g, const InitSpine<S>& sp,
                                           const InitAngles<S>& an, InitFields<S>& o) {
   const S e0 = el[1], bstar = el[6];
-  const double inv_re = 1.0 / g.re;
+  const double inv_re = g.inv_re;
   const S a0pp = sp.a0pp, n0pp = sp.n0pp, b2 = sp.b2, x3thm1 = sp.x3thm1, x1mth2 = sp.x1mth2;
 
   // Atmosphere: s and (q0 - s)^4 by perigee height.
@@ -311,8 +311,12 @@ __device__ __forceinline__ void init_drag(const S el[7], const Geo& g, const Ini
                 0.375 * g.j2 * xi * ipsi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
   const S C1 = bstar * C2;
   const S cos2w = 2.0 * an.cosw * an.cosw - 1.0;
+  // C3 and the mean-anomaly drag term divide by e0 and by e0 eta; one reciprocal of e0
+  // serves both (1 / eta = (a0'' - s) / (a0'' e0)).
+  const bool e_big = val(e0) > 1.0e-4;
+  const S ie0 = e_big ? 1.0 / e0 : 0.0 * e0;
   S C3 = 0.0 * C1;
-  if (val(e0) > 1.0e-4) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sp.sini / e0;
+  if (e_big) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sp.sini * ie0;
   const S C4 = 2.0 * n0pp * coef1 * a0pp * b2 *
                (eta * (2.0 + 0.5 * eta2) + e0 * (0.5 + 2.0 * eta2) -
                 g.j2 * xi * sp.ia0pp * ipsi2 *
@@ -322,7 +326,7 @@ __device__ __forceinline__ void init_drag(const S el[7], const Geo& g, const Ini
 
   o.argp_cf = bstar * C3 * an.cosw;
   o.m_cf = 0.0 * C1;
-  if (val(e0) > 1.0e-4) o.m_cf = -(2.0 / 3.0) * coef * bstar / eeta;
+  if (e_big) o.m_cf = -(2.0 / 3.0) * coef * bstar * (ie0 * ie0) * ((a0pp - ss) * sp.ia0pp);
   o.l2 = 1.5 * C1;
   const S cm = 1.0 + eta * an.cosm;
   o.delm0 = cm * cm * cm;

@@ -1,6 +1,7 @@
 // Host-side launch wrappers of the SGP4 kernels (internal to the library).
 #pragma once
 
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -88,6 +89,20 @@ size_t jacobian_workspace_bytes(int64_t n);
 cudaError_t launch_jacobian(const RecordPtrs& rp, const Geo& g, const double* el,
                             const double* tsince, int64_t T, int per_sat, bool fp32,
                             const JacOut& out, void* workspace, cudaStream_t stream);
+
+// Earth model of the call's constants (host side, once per call).
+inline Geo make_geo(const sgp4_consts& c) {
+  Geo g;
+  g.xke = 60.0 / std::sqrt(c.radius_km * c.radius_km * c.radius_km / c.mu_km3s2);
+  g.j2 = c.j2;
+  g.j3oj2 = (c.j2 != 0.0) ? c.j3 / c.j2 : 0.0;
+  g.j4 = c.j4;
+  g.re = c.radius_km;
+  g.vkmps = c.radius_km * g.xke / 60.0;
+  g.inv_xke = 1.0 / g.xke;
+  g.inv_re = 1.0 / c.radius_km;
+  return g;
+}
 
 // Float copy of the Earth model for the FP32 path (host side, once per call).
 inline GeoF geo_float(const Geo& g) {

@@ -58,17 +58,6 @@ __global__ void __launch_bounds__(1024) prepare_static_kernel(int32_t n, int64_t
   if (k == 0) tile_start[0] = 0;
 }
 
-sgp4::Geo make_geo(const sgp4_consts& c) {
-  sgp4::Geo g;
-  g.xke = 60.0 / std::sqrt(c.radius_km * c.radius_km * c.radius_km / c.mu_km3s2);
-  g.j2 = c.j2;
-  g.j3oj2 = (c.j2 != 0.0) ? c.j3 / c.j2 : 0.0;
-  g.j4 = c.j4;
-  g.re = c.radius_km;
-  g.vkmps = c.radius_km * g.xke / 60.0;
-  return g;
-}
-
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
 }  // namespace
@@ -145,7 +134,7 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
 
   sgp4::BatchArgs a;
   a.rp = sgp4::record_ptrs(records->arena, records->n);
-  a.g = make_geo(records->consts);
+  a.g = sgp4::make_geo(records->consts);
   a.gf = sgp4::geo_float(a.g);
   a.tsince = tsince;
   a.reqs = reinterpret_cast<const sgp4_request*>(scratch + kCounterBytes + kTileStartBytes);
