@@ -1,8 +1,10 @@
 // Propagation kernels: independent (satellite, time) states (paper Sec. 2.2,
 // "Vectorisation": f(s, t) under a vmap over times composed with a vmap over
-// satellites).  Both kernels work in units of two states of one satellite, times i
-// and i + ceil(T/2): run_range_x2 (FP32) computes the pair in packed FP32 arithmetic
-// (state32x2), run_units64 (FP64) runs the two in turn on one load of the record.
+// satellites).  A thread takes a unit of states of one satellite that share the
+// record: four (times i + k ceil(T/4)) in the single-problem FP32 kernel, as two pairs
+// in packed FP32 arithmetic (run_range_x4, state32x2); two (times i and i + ceil(T/2))
+// in the batched FP32 kernel (run_range_x2) and in both FP64 kernels (run_units64, the
+// two in turn on one load of the record).
 //   * a block walks a contiguous range of units, 128 per step, so consecutive steps of
 //     a thread stay on one satellite and its record stays in L1 (FP32) or registers
 //     (FP64);
@@ -27,11 +29,15 @@ namespace {
 
 constexpr int kThreads = 128;
 // Minimum resident 128-thread blocks per SM requested from the register allocator.
-// FP32: 8 blocks (64 registers, some spilled to L1) ran as fast as 4 (128 registers)
-// on the Starlink workload and 6% faster on the catalogue with two states per thread.
-// The FP64 kernel is bound by the FP64 pipe and keeps 4.
+// Batched FP32 (two states per thread): 8 blocks (64 registers, some spilled to L1)
+// ran as fast as 4 (128 registers) on the Starlink workload and 6% faster on the
+// catalogue.  Single-problem FP32 (four states per thread): 4 blocks (128 registers);
+// at 8 it spills heavily.  The FP64 kernels are bound by the FP64 pipe and keep 4.
 #ifndef SGP4_MIN_BLOCKS_FP32
 #define SGP4_MIN_BLOCKS_FP32 8
+#endif
+#ifndef SGP4_MIN_BLOCKS_FP32X4
+#define SGP4_MIN_BLOCKS_FP32X4 4
 #endif
 #ifndef SGP4_MIN_BLOCKS_FP64
 #define SGP4_MIN_BLOCKS_FP64 4
@@ -137,6 +143,103 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
   }
 }
 
+// FP32, four states per thread: unit u is satellite j = u / Tq and times i0 + k Tq
+// (k = 0..3, Tq = ceil(T / 4), the last ones absent past T), computed as two packed
+// pairs (k = 0, 2) and (k = 1, 3) on one load of the record.
+__device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
+                                             const Range& rg, int64_t ubeg, int64_t uend,
+                                             unsigned long long& nfix, const float2* split) {
+  const int tid = threadIdx.x;
+  const int T = (int)rg.T;
+  const int Tq = (T + 3) / 4;
+  int64_t j = (ubeg + tid) / Tq;
+  int i0 = (int)((ubeg + tid) - j * Tq);
+  const int jstep = kThreads / Tq, istep = kThreads - jstep * Tq;
+  for (int64_t u = ubeg + tid; u < uend; u += kThreads) {
+    const int64_t rec = rg.sat0 + j;
+    int it[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k * Tq;
+      it[k] = i < T ? i : i0;
+    }
+    const bool has3 = i0 + 3 * Tq < T;   // then all four exist
+    auto tsince_at = [&](int i) -> double {
+      if (rg.jd_day) {
+        const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
+        const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
+        return fma(1440.0, dfrac, (double)(dday * 1440));
+      }
+      return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
+    };
+    float th[4], tl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (split) {
+        const float2 a = split[it[k]];
+        th[k] = a.x;
+        tl[k] = a.y;
+      } else {
+        split_double(tsince_at(it[k]), th[k], tl[k]);
+      }
+    }
+    const Rec32 rc32 = load_rec32(rp, rec);
+    float2 rA[3], vA[3], rB[3], vB[3];
+    int cA[2], cB[2];
+    state32x2(rc32, gf, make_float2(th[0], th[2]), make_float2(tl[0], tl[2]), rA, vA, cA);
+    state32x2(rc32, gf, make_float2(th[1], th[3]), make_float2(tl[1], tl[3]), rB, vB, cB);
+    auto ok = [](int c) { return (c == 0) | (c == 6); };
+    const int64_t idx0 = j * T + i0;
+    if (has3 & ok(cA[0]) & ok(cA[1]) & ok(cB[0]) & ok(cB[1])) {
+      float* gr = static_cast<float*>(rg.r) + idx0 * 3;
+      float* gv = static_cast<float*>(rg.v) + idx0 * 3;
+      const int o = Tq * 3;
+      __stcs(gr + 0, rA[0].x); __stcs(gr + 1, rA[1].x); __stcs(gr + 2, rA[2].x);
+      __stcs(gv + 0, vA[0].x); __stcs(gv + 1, vA[1].x); __stcs(gv + 2, vA[2].x);
+      __stcs(gr + o + 0, rB[0].x); __stcs(gr + o + 1, rB[1].x); __stcs(gr + o + 2, rB[2].x);
+      __stcs(gv + o + 0, vB[0].x); __stcs(gv + o + 1, vB[1].x); __stcs(gv + o + 2, vB[2].x);
+      __stcs(gr + 2 * o + 0, rA[0].y); __stcs(gr + 2 * o + 1, rA[1].y); __stcs(gr + 2 * o + 2, rA[2].y);
+      __stcs(gv + 2 * o + 0, vA[0].y); __stcs(gv + 2 * o + 1, vA[1].y); __stcs(gv + 2 * o + 2, vA[2].y);
+      __stcs(gr + 3 * o + 0, rB[0].y); __stcs(gr + 3 * o + 1, rB[1].y); __stcs(gr + 3 * o + 2, rB[2].y);
+      __stcs(gv + 3 * o + 0, vB[0].y); __stcs(gv + 3 * o + 1, vB[1].y); __stcs(gv + 3 * o + 2, vB[2].y);
+      __stcs(rg.status + idx0, cA[0]);
+      __stcs(rg.status + idx0 + Tq, cB[0]);
+      __stcs(rg.status + idx0 + 2 * Tq, cA[1]);
+      __stcs(rg.status + idx0 + 3 * Tq, cB[1]);
+    } else {
+      const float q = __int_as_float(0x7fc00000);
+      for (int k = 0; k < 4; ++k) {
+        if (i0 + k * Tq >= T) break;
+        const float2* rr = (k & 1) ? rB : rA;
+        const float2* vv = (k & 1) ? vB : vA;
+        const bool hi = k >= 2;
+        int cd = (k & 1) ? cB[hi] : cA[hi];
+        const int64_t idx = idx0 + k * Tq;
+        float* gr = static_cast<float*>(rg.r) + idx * 3;
+        float* gv = static_cast<float*>(rg.v) + idx * 3;
+        if (cd == kRecomputeFP64) {
+          cd = state64_fallback(rp, g, rec, tsince_at(it[k]), gr, gv);
+          ++nfix;
+          if (cd != 0 && cd != 6) { gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q; }
+        } else {
+          const bool bad = cd != 0 && cd != 6;
+          for (int c = 0; c < 3; ++c) {
+            __stcs(gr + c, bad ? q : (hi ? rr[c].y : rr[c].x));
+            __stcs(gv + c, bad ? q : (hi ? vv[c].y : vv[c].x));
+          }
+        }
+        __stcs(rg.status + idx, cd);
+      }
+    }
+    j += jstep;
+    i0 += istep;
+    if (i0 >= Tq) {
+      ++j;
+      i0 -= Tq;
+    }
+  }
+}
+
 // FP64 over the same units as run_range_x2 (both kernels work in units of two states
 // of one satellite in both precisions): the thread runs the two states in turn, on one
 // load of the record.
@@ -196,10 +299,10 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
 constexpr int kSplitMaxT = 2048;
 
 template <bool kFP32>
-__global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
+__global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32X4 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
   extern __shared__ float2 s_split[];   // [t_count] when use_split
-  const int64_t total = a.rp.n * ((a.t_count + 1) / 2);   // units of two states
+  const int64_t total = a.rp.n * (kFP32 ? (a.t_count + 3) / 4 : (a.t_count + 1) / 2);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
@@ -224,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.v = a.v;
   rg.status = a.status;
   unsigned long long nfix = 0;
-  if (kFP32) run_range_x2(a.rp, a.g, gf, rg, beg, end, nfix, use_split ? s_split : nullptr);
+  if (kFP32) run_range_x4(a.rp, a.g, gf, rg, beg, end, nfix, use_split ? s_split : nullptr);
   else run_units64(a.rp, a.g, rg, beg, end);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
@@ -291,7 +394,7 @@ int blocks_per_sm_of(K kernel, size_t dyn_smem = 0) {
 
 template <bool kFP32>
 cudaError_t launch(const PropArgs& a, cudaStream_t stream) {
-  const int64_t total = a.rp.n * ((a.t_count + 1) / 2);   // units of two states
+  const int64_t total = a.rp.n * (kFP32 ? (a.t_count + 3) / 4 : (a.t_count + 1) / 2);
   if (total == 0) return cudaSuccess;
   const bool use_split = kFP32 && !a.grid_per_sat && !a.jd_day && a.t_count <= kSplitMaxT;
   const size_t dyn = use_split ? (size_t)a.t_count * sizeof(float2) : 0;
