@@ -42,10 +42,10 @@ BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
 # counted with ncu; the command is in the design doc and profiles/).
 ALG_OPS_FP32 = 234
 # DRAM bytes (read + write) of one launch of the FP32 propagate kernel on this workload,
-# from an ncu capture of the current kernel (dram__bytes_read.sum 1,852,416 +
-# dram__bytes_write.sum 214,920,704): below the 28 B/state written because L2 still
+# from an ncu capture of the current kernel (dram__bytes_read.sum 2,210,816 +
+# dram__bytes_write.sum 203,375,872): below the 28 B/state written because L2 still
 # holds the tail of the output when the kernel ends.
-TRAFFIC_FP32_BYTES = 216_773_120
+TRAFFIC_FP32_BYTES = 205_586_688
 # FP64 arithmetic (DADD + DMUL + DFMA thread instructions) per state of the FP64
 # propagation on the Starlink-shaped workload, counted with ncu (DADD 15.0, DMUL 140.0,
 # DFMA 210.0).
