@@ -55,7 +55,7 @@ static_assert(sizeof(Fwd<float>) % 8 == 4, "odd word count for conflict-free row
 // Per-satellite constants of the reverse sweep.
 template <class T>
 struct RevC {
-  T bc5, sinm0, mcf, delm0, eta, a0pp, xke, n0pp, xlcof, aycof;
+  T bc5, sinm0, mcf, delm0, eta, a0pp, xke, ixke, n0pp, xlcof, aycof;
   T x3thm1, x1mth2, x7thm1, cosi, sini, re, vk;
   bool isimp;
 };
@@ -63,7 +63,8 @@ struct RevC {
 __device__ __forceinline__ RevC<double> rev_consts(const Rec64& rc, const Geo& g) {
   RevC<double> k;
   k.bc5 = rc.bc5; k.sinm0 = rc.sinm0; k.mcf = rc.m_cf; k.delm0 = rc.delm0; k.eta = rc.eta;
-  k.a0pp = rc.a0pp; k.xke = g.xke; k.n0pp = rc.n0pp; k.xlcof = rc.xlcof; k.aycof = rc.aycof;
+  k.a0pp = rc.a0pp; k.xke = g.xke; k.ixke = g.inv_xke; k.n0pp = rc.n0pp; k.xlcof = rc.xlcof;
+  k.aycof = rc.aycof;
   k.x3thm1 = rc.x3thm1; k.x1mth2 = rc.x1mth2; k.x7thm1 = rc.x7thm1;
   k.cosi = rc.cosi; k.sini = rc.sini; k.re = g.re; k.vk = g.vkmps;
   k.isimp = rc.flags & kFlagIsimp;
@@ -73,13 +74,20 @@ __device__ __forceinline__ RevC<double> rev_consts(const Rec64& rc, const Geo& g
 __device__ __forceinline__ RevC<float> rev_consts(const Rec32& rc, const GeoF& g) {
   RevC<float> k;
   k.bc5 = rc.bc5; k.sinm0 = rc.sinm0; k.mcf = rc.mcf; k.delm0 = rc.delm0; k.eta = rc.eta;
-  k.a0pp = rc.a0pp; k.xke = g.xke; k.n0pp = rc.n0ppr * kTwoPiF; k.xlcof = rc.xlcof;
+  k.a0pp = rc.a0pp; k.xke = g.xke; k.ixke = g.inv_xke; k.n0pp = rc.n0ppr * kTwoPiF;
+  k.xlcof = rc.xlcof;
   k.aycof = rc.aycof; k.x3thm1 = rc.x3thm1_15 * (1.0f / 1.5f); k.x1mth2 = rc.x1mth2;
   k.x7thm1 = rc.x7thm1_m025 * -4.0f; k.cosi = rc.cosi; k.sini = rc.sini; k.re = g.re;
   k.vk = g.vkmps;
   k.isimp = rc.flags & kFlagIsimp;
   return k;
 }
+
+// Reciprocal of a positive quantity of the sweep (every divisor of the reverse sweep is
+// positive on a usable state): FP32 through the flush-to-zero rsqrt (rcp_pos), FP64 a
+// division.  Each reciprocal is taken once and reused.
+__device__ __forceinline__ float inv_pos(float x) { return rcp_pos(x); }
+__device__ __forceinline__ double inv_pos(double x) { return 1.0 / x; }
 
 // The position and velocity unit vectors U, V and the rest of the output frame.
 template <class T>
@@ -349,8 +357,8 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
   T sin2ub = -rdotkb * f.nk * rc.x1mth2;
   T cos2ub = rfdotkb * f.nk * rc.x1mth2;
   T x3thm1b = rfdotkb * f.nk * c15;
-  const T nb = nkb * f.k / rc.xke;
-  T kb = nkb * f.n / rc.xke;
+  const T nb = nkb * f.k * rc.ixke;
+  T kb = nkb * f.n * rc.ixke;
   // i_k = i0 + 1.5 kp cosi sini cos2u, RAAN_k = RAAN + 1.5 kp cosi sin2u,
   // u_k = u - 0.25 kp x7thm1 sin2u
   T kpb = ikb * c15 * rc.cosi * rc.sini * f.cos2u;
@@ -372,15 +380,16 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
   x1mth2b += rkb * half * f.k * f.cos2u;
   cos2ub += rkb * half * f.k * rc.x1mth2;
   // kp = k / pL, k = j2 / (2 pL)
-  kb += kpb / f.pL;
-  T pLb = -kpb * f.kp / f.pL;
-  pLb += -kb * f.k / f.pL;
+  const T ipL = inv_pos(f.pL);
+  kb += kpb * ipL;
+  T pLb = -kpb * f.kp * ipL;
+  pLb += -kb * f.k * ipL;
   // sin 2u, cos 2u, u = atan2(sin u, cos u)
   T sinub = two * f.cosu * sin2ub - T(4) * f.sinu * cos2ub;
   T cosub = two * f.sinu * sin2ub;
-  const T den = f.sinu * f.sinu + f.cosu * f.cosu;
-  sinub += ukb * f.cosu / den;
-  cosub += -ukb * f.sinu / den;
+  const T iden = inv_pos(f.sinu * f.sinu + f.cosu * f.cosu);
+  sinub += ukb * f.cosu * iden;
+  cosub += -ukb * f.sinu * iden;
   // sin u = aor As, cos u = aor Ac
   const T aorb = sinub * f.As + cosub * f.Ac;
   const T Asb = sinub * f.aor, Acb = cosub * f.aor;
@@ -388,17 +397,18 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
   T aynb = -Asb + Acb * f.w;
   T axnb = -Asb * f.w - Acb;
   const T wb = -Asb * f.axn + Acb * f.ayn;
-  T ab = aorb / f.rl;
-  rlb += -aorb * f.aor / f.rl;
-  T esinEb = wb / f.opb;
-  betalb += -wb * f.w / f.opb;
-  T eL2b = -betalb * half / f.betal;
-  const T sqpb = rfdotkb / f.rl;
-  rlb += -rfdotkb * f.rfdotl / f.rl;
-  pLb += sqpb * half / f.sqp;
-  const T sqab = rdotkb * f.esinE / f.rl;
-  esinEb += rdotkb * f.sqa / f.rl;
-  rlb += -rdotkb * f.rdotl / f.rl;
+  const T irl = inv_pos(f.rl), iopb = inv_pos(f.opb);
+  T ab = aorb * irl;
+  rlb += -aorb * f.aor * irl;
+  T esinEb = wb * iopb;
+  betalb += -wb * f.w * iopb;
+  T eL2b = -betalb * half * inv_pos(f.betal);
+  const T sqpb = rfdotkb * irl;
+  rlb += -rfdotkb * f.rfdotl * irl;
+  pLb += sqpb * half * inv_pos(f.sqp);
+  const T sqab = rdotkb * f.esinE * irl;
+  esinEb += rdotkb * f.sqa * irl;
+  rlb += -rdotkb * f.rdotl * irl;
   ab += rlb * (one - f.ecosE);
   const T ecosEb = -rlb * f.a;
   ab += pLb * (one - f.eL2);
@@ -415,10 +425,10 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
   spb += ecosEb * f.ayn;
   // Kepler at its root: psi - axn sin psi + ayn cos psi = U
   const T psib = spb * f.cp - cpb * f.sp;
-  const T D = one - f.axn * f.cp - f.ayn * f.sp;
-  const T Ub = psib / D;
-  axnb += psib * f.sp / D;
-  aynb += -psib * f.cp / D;
+  const T iD = inv_pos(one - f.axn * f.cp - f.ayn * f.sp);
+  const T Ub = psib * iD;
+  axnb += psib * f.sp * iD;
+  aynb += -psib * f.cp * iD;
   // U = (M + argp) + q xlcof axn
   T qb = Ub * rc.xlcof * f.axn;
   sink(aXlcof, Ub * f.q * f.axn);
@@ -444,8 +454,8 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
   const T e1b = f.keep_e * eb;
   sink(aE0, e1b);
   const T tempeb = -e1b;
-  ab += nb * T(-1.5) * f.n / f.a;
-  ab += sqab * half / f.sqa;
+  ab += nb * T(-1.5) * f.n * inv_pos(f.a);
+  ab += sqab * half * inv_pos(f.sqa);
   sink(aA0pp, ab * f.tempa * f.tempa);
   const T tempab = ab * rc.a0pp * two * f.tempa;
   T mdfb = mm2b, argpdfb = argp1b;
