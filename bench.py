@@ -52,8 +52,8 @@ TRAFFIC_FP32_BYTES = 205_586_688
 ALG_OPS_FP64 = 365
 # Per state of the adjoint sweep on the fitting workload (10,000 x 500), counted with
 # ncu: FP32 path FADD + FMUL + FFMA + SFU; FP64 path DADD + DMUL + DFMA.
-ALG_OPS_ADJ_FP32 = 670
-ALG_OPS_ADJ_FP64 = 835
+ALG_OPS_ADJ_FP32 = 531
+ALG_OPS_ADJ_FP64 = 707
 # B300's FP64 unit: 2 lanes per SM per clock (one warp instruction per 64 cycles per
 # SM sub-partition; ncu's fp64-pipe utilisation and instruction count give the rate).
 FP64_LANES_PER_SM_CLK = 2
