@@ -38,9 +38,11 @@ UNIT = "states/s"
 # Per-state algorithmic output bytes (r, v as float32 x3 + int32 status; FP64: doubles).
 BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
 # FP32 arithmetic + SFU operations per state of the FP32 formulation on the
-# Starlink-shaped workload (FADD 45 + FFMA 68 + FMUL 104 + SFU 16.5 thread instructions,
-# counted with ncu; the command is in the design doc and profiles/).
-ALG_OPS_FP32 = 234
+# Starlink-shaped workload, counted with ncu on the current kernel: each packed
+# instruction (FADD2, FMUL2, FFMA2) is two lane operations, one for each state of its
+# pair: FADD 37.1 + FMUL 97.1 + FFMA 67.1 + SFU 16.1 per state (the commands are in
+# profiles/propagate_fp32_starlink_9341x1000.md).
+ALG_OPS_FP32 = 217
 # DRAM bytes (read + write) of one launch of the FP32 propagate kernel on this workload,
 # from an ncu capture of the current kernel (dram__bytes_read.sum 2,210,816 +
 # dram__bytes_write.sum 203,375,872): below the 28 B/state written because L2 still
