@@ -183,8 +183,10 @@ typedef struct sgp4_request {
 typedef struct sgp4_batch_plan {
   void* workspace;        /* device, caller-owned, sgp4_batch_workspace_bytes(n) */
   int32_t n_requests;
-  int32_t tile_states;    /* states per work tile, a multiple of 128 (a tile is
-                             tile_states / 2 units of two states of one satellite) */
+  int32_t tile_states;    /* states per work tile, a multiple of 128 (the FP32
+                             kernel walks a tile in units of four states of one
+                             satellite, the FP64 kernel in units of two; each request
+                             gets the larger of the two tile counts) */
   int32_t grid_blocks;    /* persistent grid size; 0 = one full wave on the device */
   int32_t reserved;
   int64_t total_tiles;

@@ -216,10 +216,7 @@ sgp4_result sgp4_batch_plan_init(const sgp4_request* requests, int32_t n_request
     outs = std::max(outs, q.out_offset + st);
     total_states += st;
     if (total_states > kLimit) return SGP4_ERR_ARG;
-    // tiles of tile_states / 2 units, a unit being two states of one satellite
-    const int64_t units = q.n * ((q.t_count + 1) / 2);
-    const int64_t tiles = (units + tile_states / 2 - 1) / (tile_states / 2);
-    tile_start[(size_t)k + 1] = tile_start[(size_t)k] + tiles;
+    tile_start[(size_t)k + 1] = tile_start[(size_t)k] + sgp4::request_tiles(q.n, q.t_count, tile_states);
     if (st > 0) spans.emplace_back(q.out_offset, q.out_offset + st);
   }
   std::sort(spans.begin(), spans.end());

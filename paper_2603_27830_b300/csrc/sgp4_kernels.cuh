@@ -90,6 +90,21 @@ cudaError_t launch_jacobian(const RecordPtrs& rp, const Geo& g, const double* el
                             const double* tsince, int64_t T, int per_sat, bool fp32,
                             const JacOut& out, void* workspace, cudaStream_t stream);
 
+// Work tiles of one batched request (n satellites x t_count times): a tile is
+// tile_states consecutive states' worth of units, walked in units of four states of
+// one satellite by the FP32 kernel and of two by the FP64 kernel; the plan, built
+// before the precision is known, gives each request the larger of the two counts (a
+// kernel skips tiles past its own units).  tile_states is a multiple of 128.
+__host__ __device__ inline int64_t units_per_sat(int64_t t_count, int states_per_unit) {
+  return (t_count + states_per_unit - 1) / states_per_unit;
+}
+__host__ __device__ inline int64_t request_tiles(int64_t n, int64_t t_count, int64_t tile_states) {
+  const int64_t u2 = n * units_per_sat(t_count, 2), p2 = tile_states / 2;
+  const int64_t u4 = n * units_per_sat(t_count, 4), p4 = tile_states / 4;
+  const int64_t t2 = (u2 + p2 - 1) / p2, t4 = (u4 + p4 - 1) / p4;
+  return t2 > t4 ? t2 : t4;
+}
+
 // Earth model of the call's constants (host side, once per call).
 inline Geo make_geo(const sgp4_consts& c) {
   Geo g;

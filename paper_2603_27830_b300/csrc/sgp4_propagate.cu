@@ -1,10 +1,9 @@
 // Propagation kernels: independent (satellite, time) states (paper Sec. 2.2,
 // "Vectorisation": f(s, t) under a vmap over times composed with a vmap over
 // satellites).  A thread takes a unit of states of one satellite that share the
-// record: four (times i + k ceil(T/4)) in the single-problem FP32 kernel, as two pairs
-// in packed FP32 arithmetic (run_range_x4, state32x2); two (times i and i + ceil(T/2))
-// in the batched FP32 kernel (run_range_x2) and in both FP64 kernels (run_units64, the
-// two in turn on one load of the record).
+// record: four (times i + k ceil(T/4)) in the FP32 kernels, as two pairs in packed FP32
+// arithmetic (run_range_x4, state32x2); two (times i and i + ceil(T/2)) in the FP64
+// kernels (run_units64, the two in turn on one load of the record).
 //   * a block walks a contiguous range of units, 128 per step, so consecutive steps of
 //     a thread stay on one satellite and its record stays in L1 (FP32) or registers
 //     (FP64);
@@ -29,15 +28,11 @@ namespace {
 
 constexpr int kThreads = 128;
 // Minimum resident 128-thread blocks per SM requested from the register allocator.
-// Batched FP32 (two states per thread): 8 blocks (64 registers, some spilled to L1)
-// ran as fast as 4 (128 registers) on the Starlink workload and 6% faster on the
-// catalogue.  Single-problem FP32 (four states per thread): 4 blocks (128 registers);
-// at 8 it spills heavily.  The FP64 kernels are bound by the FP64 pipe and keep 4.
+// FP32 (four states per thread): 4 blocks (128 registers); at 8 (64 registers) it
+// spills heavily, 3 and 5 were slower.  The FP64 kernels are bound by the FP64 pipe
+// and keep 4.
 #ifndef SGP4_MIN_BLOCKS_FP32
-#define SGP4_MIN_BLOCKS_FP32 8
-#endif
-#ifndef SGP4_MIN_BLOCKS_FP32X4
-#define SGP4_MIN_BLOCKS_FP32X4 4
+#define SGP4_MIN_BLOCKS_FP32 4
 #endif
 #ifndef SGP4_MIN_BLOCKS_FP64
 #define SGP4_MIN_BLOCKS_FP64 4
@@ -57,91 +52,6 @@ struct Range {
   int32_t* status;
 };
 
-
-// FP32, two states per thread (packed arithmetic, state32x2): unit u of [ubeg, uend)
-// is satellite j = u / Th, times i0 = u % Th and i1 = i0 + Th (Th = ceil(T / 2); i1 does
-// not exist for the last unit of an odd T), so both states share the record.
-__device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
-                                             const Range& rg, int64_t ubeg, int64_t uend,
-                                             unsigned long long& nfix, const float2* split) {
-  const int tid = threadIdx.x;
-  const int T = (int)rg.T;            // <= INT32_MAX (checked by the API)
-  const int Th = (T + 1) / 2;
-  int64_t j = (ubeg + tid) / Th;
-  int i0 = (int)((ubeg + tid) - j * Th);
-  const int jstep = kThreads / Th, istep = kThreads - jstep * Th;
-  for (int64_t u = ubeg + tid; u < uend; u += kThreads) {
-    const int64_t rec = rg.sat0 + j;
-    const int i1 = i0 + Th;
-    const bool has1 = i1 < T;
-    const int it[2] = {i0, has1 ? i1 : i0};
-    auto tsince_at = [&](int i) -> double {
-      if (rg.jd_day) {
-        const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
-        const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
-        return fma(1440.0, dfrac, (double)(dday * 1440));
-      }
-      return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
-    };
-    float2 th, tl;
-    if (split) {
-      const float2 a0 = split[it[0]], a1 = split[it[1]];
-      th = make_float2(a0.x, a1.x);
-      tl = make_float2(a0.y, a1.y);
-    } else {
-      split_double(tsince_at(it[0]), th.x, tl.x);
-      split_double(tsince_at(it[1]), th.y, tl.y);
-    }
-    const Rec32 rc32 = load_rec32(rp, rec);
-    float2 r2[3], v2[3];
-    int code[2];
-    state32x2(rc32, gf, th, tl, r2, v2, code);
-    const float q = __int_as_float(0x7fc00000);
-    // Common case, both states present and valid (status 0 or 6): twelve floats and two
-    // statuses stored without per-lane branches or NaN selects.
-    const bool fast = has1 & ((code[0] == 0) | (code[0] == 6)) & ((code[1] == 0) | (code[1] == 6));
-    if (fast) {
-      const int64_t idx = j * T + i0;
-      float* gr = static_cast<float*>(rg.r) + idx * 3;
-      float* gv = static_cast<float*>(rg.v) + idx * 3;
-      const int o1 = Th * 3;   // state i1 = i0 + Th of the same satellite
-      __stcs(gr + 0, r2[0].x); __stcs(gr + 1, r2[1].x); __stcs(gr + 2, r2[2].x);
-      __stcs(gv + 0, v2[0].x); __stcs(gv + 1, v2[1].x); __stcs(gv + 2, v2[2].x);
-      __stcs(gr + o1 + 0, r2[0].y); __stcs(gr + o1 + 1, r2[1].y); __stcs(gr + o1 + 2, r2[2].y);
-      __stcs(gv + o1 + 0, v2[0].y); __stcs(gv + o1 + 1, v2[1].y); __stcs(gv + o1 + 2, v2[2].y);
-      __stcs(rg.status + idx, code[0]);
-      __stcs(rg.status + idx + Th, code[1]);
-    } else
-    for (int l = 0; l < 2; ++l) {   // per lane: the last unit of an odd T, NaN outputs, FP64 recomputation
-      if (l == 1 && !has1) break;
-      const int64_t idx = j * T + it[l];
-      float* gr = static_cast<float*>(rg.r) + idx * 3;
-      float* gv = static_cast<float*>(rg.v) + idx * 3;
-      int cd = code[l];
-      if (cd == kRecomputeFP64) {
-        cd = state64_fallback(rp, g, rec, tsince_at(it[l]), gr, gv);
-        ++nfix;
-        if (cd != 0 && cd != 6) { gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q; }
-      } else {
-        const bool bad = cd != 0 && cd != 6;
-        const float rv[3] = {l ? r2[0].y : r2[0].x, l ? r2[1].y : r2[1].x, l ? r2[2].y : r2[2].x};
-        const float vv[3] = {l ? v2[0].y : v2[0].x, l ? v2[1].y : v2[1].x, l ? v2[2].y : v2[2].x};
-        __stcs(gr + 0, bad ? q : rv[0]); __stcs(gr + 1, bad ? q : rv[1]);
-        __stcs(gr + 2, bad ? q : rv[2]);
-        __stcs(gv + 0, bad ? q : vv[0]); __stcs(gv + 1, bad ? q : vv[1]);
-        __stcs(gv + 2, bad ? q : vv[2]);
-      }
-      __stcs(rg.status + idx, cd);
-    }
-    // next unit of this thread: kThreads = jstep * Th + istep, so at most one wrap
-    j += jstep;
-    i0 += istep;
-    if (i0 >= Th) {
-      ++j;
-      i0 -= Th;
-    }
-  }
-}
 
 // FP32, four states per thread: unit u is satellite j = u / Tq and times i0 + k Tq
 // (k = 0..3, Tq = ceil(T / 4), the last ones absent past T), computed as two packed
@@ -240,9 +150,8 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
   }
 }
 
-// FP64 over the same units as run_range_x2 (both kernels work in units of two states
-// of one satellite in both precisions): the thread runs the two states in turn, on one
-// load of the record.
+// FP64, two states per thread: unit u is satellite j = u / Th and times i0 and
+// i0 + Th (Th = ceil(T / 2)), run in turn on one load of the record.
 __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, const Range& rg,
                                             int64_t ubeg, int64_t uend) {
   const int tid = threadIdx.x;
@@ -299,7 +208,7 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
 constexpr int kSplitMaxT = 2048;
 
 template <bool kFP32>
-__global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32X4 : SGP4_MIN_BLOCKS_FP64)
+__global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
   extern __shared__ float2 s_split[];   // [t_count] when use_split
   const int64_t total = a.rp.n * (kFP32 ? (a.t_count + 3) / 4 : (a.t_count + 1) / 2);
@@ -356,12 +265,15 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
       const int mid = (lo + hi + 1) >> 1;
       if (__ldg(a.tile_start + mid) <= tile) lo = mid; else hi = mid - 1;
     }
-    // Tiles count units of two states of one satellite (tile_states / 2 per tile).
+    // A tile is tile_states / 4 units of four states (FP32) or tile_states / 2 units of
+    // two (FP64); the request's tiles past this kernel's units are empty.
     const sgp4_request q = a.reqs[lo];
-    const int64_t units = q.n * ((q.t_count + 1) / 2);
-    const int64_t per_tile = a.tile_states / 2;
+    const int spu = kFP32 ? 4 : 2;
+    const int64_t units = q.n * units_per_sat(q.t_count, spu);
+    const int64_t per_tile = a.tile_states / spu;
     const int64_t beg = (tile - __ldg(a.tile_start + lo)) * per_tile;
     const int64_t end = min(units, beg + per_tile);
+    if (beg >= end) continue;
     Range rg;
     rg.tsince = a.tsince + q.t_offset;
     rg.jd_day = nullptr;
@@ -377,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
       rg.v = static_cast<double*>(a.v) + q.out_offset * 3;
     }
     rg.status = a.status + q.out_offset;
-    if (kFP32) run_range_x2(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
+    if (kFP32) run_range_x4(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
     else run_units64(a.rp, a.g, rg, beg, end);
   }
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);

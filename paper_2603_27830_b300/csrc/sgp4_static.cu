@@ -42,10 +42,7 @@ __global__ void __launch_bounds__(1024) prepare_static_kernel(int32_t n, int64_t
   int64_t* tile_start = reinterpret_cast<int64_t*>(g_scratch + kCounterBytes);
   const int k = threadIdx.x;
   int64_t tiles = 0;
-  if (k < n) {
-    const int64_t units = reqs[k].n * ((reqs[k].t_count + 1) / 2);   // two states each
-    tiles = (units + tile_states / 2 - 1) / (tile_states / 2);
-  }
+  if (k < n) tiles = sgp4::request_tiles(reqs[k].n, reqs[k].t_count, tile_states);
   part[k] = tiles;
   __syncthreads();
   for (int off = 1; off < 1024; off <<= 1) {   // inclusive scan (Hillis-Steele)
@@ -89,7 +86,7 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
     if (q.sat_offset > records->n - q.n || q.t_offset > tsince_len - q.t_count ||
         q.out_offset > out_len - st)
       return SGP4_ERR_ARG;
-    total_tiles += (q.n * ((q.t_count + 1) / 2) + tile_states / 2 - 1) / (tile_states / 2);
+    total_tiles += sgp4::request_tiles(q.n, q.t_count, tile_states);
     if (st == 0) continue;
     for (int32_t m = 0; m < k; ++m) {
       const sgp4_request& p = requests[m];
