@@ -169,6 +169,20 @@ def test_ragged_shapes(n, T, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("T", [1, 2, 3, 5, 6, 7])
+def test_partial_units(T, prec):
+    """Time counts that leave the units of two (FP64) or four (FP32) states of one
+    satellite partly empty, across several satellites per warp."""
+    rng = np.random.default_rng(100 + T)
+    el = W.catalogue_elements(rng, 45, invalid_frac=0.05)
+    t = np.sort(rng.uniform(-300, 3000, T))
+    if prec == "fp64":
+        _check_fp64(el, t)
+    else:
+        _check_fp32(el, t, 1.0, 1e-3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_per_satellite_grid(prec):
     rng = np.random.default_rng(3)
     el = W.catalogue_elements(rng, 300, invalid_frac=0.02)
