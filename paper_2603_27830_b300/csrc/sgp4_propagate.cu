@@ -53,6 +53,94 @@ struct Range {
 };
 
 
+// FP32, two states per thread (packed arithmetic, state32x2): unit u of [ubeg, uend)
+// is satellite j = u / Th, times i0 = u % Th and i1 = i0 + Th (Th = ceil(T / 2); i1 does
+// not exist for the last unit of an odd T), so both states share the record.
+__device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
+                                             const Range& rg, int64_t ubeg, int64_t uend,
+                                             unsigned long long& nfix, const float2* split) {
+  const int tid = threadIdx.x;
+  const int T = (int)rg.T;            // <= INT32_MAX (checked by the API)
+  const int Th = (T + 1) / 2;
+  int64_t j = (ubeg + tid) / Th;
+  int i0 = (int)((ubeg + tid) - j * Th);
+  const int jstep = kThreads / Th, istep = kThreads - jstep * Th;
+  for (int64_t u = ubeg + tid; u < uend; u += kThreads) {
+    const int64_t rec = rg.sat0 + j;
+    const int i1 = i0 + Th;
+    const bool has1 = i1 < T;
+    const int it[2] = {i0, has1 ? i1 : i0};
+    auto tsince_at = [&](int i) -> double {
+      if (rg.jd_day) {
+        const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
+        const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
+        return fma(1440.0, dfrac, (double)(dday * 1440));
+      }
+      return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
+    };
+    float2 th, tl;
+    if (split) {
+      const float2 a0 = split[it[0]], a1 = split[it[1]];
+      th = make_float2(a0.x, a1.x);
+      tl = make_float2(a0.y, a1.y);
+    } else {
+      split_double(tsince_at(it[0]), th.x, tl.x);
+      split_double(tsince_at(it[1]), th.y, tl.y);
+    }
+    const Rec32 rc32 = load_rec32(rp, rec);
+    float2 r2[3], v2[3];
+    int code[2];
+    state32x2(rc32, gf, th, tl, r2, v2, code);
+    const float q = __int_as_float(0x7fc00000);
+    // Common case, every present state valid (status 0 or 6): stores without per-lane
+    // branches or NaN selects
+    // (an absent second state repeats time i0, so its code equals the first state's)
+    const bool fast = ((code[0] == 0) | (code[0] == 6)) & ((code[1] == 0) | (code[1] == 6));
+    if (fast) {
+      const int64_t idx = j * T + i0;
+      float* gr = static_cast<float*>(rg.r) + idx * 3;
+      float* gv = static_cast<float*>(rg.v) + idx * 3;
+      const int o1 = Th * 3;   // state i1 = i0 + Th of the same satellite
+      __stcs(gr + 0, r2[0].x); __stcs(gr + 1, r2[1].x); __stcs(gr + 2, r2[2].x);
+      __stcs(gv + 0, v2[0].x); __stcs(gv + 1, v2[1].x); __stcs(gv + 2, v2[2].x);
+      __stcs(rg.status + idx, code[0]);
+      if (has1) {
+        __stcs(gr + o1 + 0, r2[0].y); __stcs(gr + o1 + 1, r2[1].y); __stcs(gr + o1 + 2, r2[2].y);
+        __stcs(gv + o1 + 0, v2[0].y); __stcs(gv + o1 + 1, v2[1].y); __stcs(gv + o1 + 2, v2[2].y);
+        __stcs(rg.status + idx + Th, code[1]);
+      }
+    } else
+    for (int l = 0; l < 2; ++l) {   // per lane: the last unit of an odd T, NaN outputs, FP64 recomputation
+      if (l == 1 && !has1) break;
+      const int64_t idx = j * T + it[l];
+      float* gr = static_cast<float*>(rg.r) + idx * 3;
+      float* gv = static_cast<float*>(rg.v) + idx * 3;
+      int cd = code[l];
+      if (cd == kRecomputeFP64) {
+        cd = state64_fallback(rp, g, rec, tsince_at(it[l]), gr, gv);
+        ++nfix;
+        if (cd != 0 && cd != 6) { gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q; }
+      } else {
+        const bool bad = cd != 0 && cd != 6;
+        const float rv[3] = {l ? r2[0].y : r2[0].x, l ? r2[1].y : r2[1].x, l ? r2[2].y : r2[2].x};
+        const float vv[3] = {l ? v2[0].y : v2[0].x, l ? v2[1].y : v2[1].x, l ? v2[2].y : v2[2].x};
+        __stcs(gr + 0, bad ? q : rv[0]); __stcs(gr + 1, bad ? q : rv[1]);
+        __stcs(gr + 2, bad ? q : rv[2]);
+        __stcs(gv + 0, bad ? q : vv[0]); __stcs(gv + 1, bad ? q : vv[1]);
+        __stcs(gv + 2, bad ? q : vv[2]);
+      }
+      __stcs(rg.status + idx, cd);
+    }
+    // next unit of this thread: kThreads = jstep * Th + istep, so at most one wrap
+    j += jstep;
+    i0 += istep;
+    if (i0 >= Th) {
+      ++j;
+      i0 -= Th;
+    }
+  }
+}
+
 // FP32, four states per thread: unit u is satellite j = u / Tq and times i0 + k Tq
 // (k = 0..3, Tq = ceil(T / 4), the last ones absent past T), computed as two packed
 // pairs (k = 0, 2) and (k = 1, 3) on one load of the record.
@@ -101,6 +189,7 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
     auto ok = [](int c) { return (c == 0) | (c == 6); };
     const int64_t idx0 = j * T + i0;
     if (has3 & ok(cA[0]) & ok(cA[1]) & ok(cB[0]) & ok(cB[1])) {
+      // all four present and valid (status 0 or 6): stores without branches or selects
       float* gr = static_cast<float*>(rg.r) + idx0 * 3;
       float* gv = static_cast<float*>(rg.v) + idx0 * 3;
       const int o = Tq * 3;
@@ -150,13 +239,16 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
   }
 }
 
-// FP64, two states per thread: unit u is satellite j = u / Th and times i0 and
-// i0 + Th (Th = ceil(T / 2)), run in turn on one load of the record.
+// FP64, kSpu (1 or 2) states per thread: unit u is satellite j = u / Th and times
+// i0 + l Th (Th = ceil(T / kSpu)), run in turn on one load of the record.  One state
+// per thread for problems that fit one wave: the FP64 state is a long dependent chain
+// on B300's FP64 unit (~15 us), so two in turn would double a small call's latency.
+template <int kSpu>
 __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, const Range& rg,
                                             int64_t ubeg, int64_t uend) {
   const int tid = threadIdx.x;
   const int T = (int)rg.T;
-  const int Th = (T + 1) / 2;
+  const int Th = (T + kSpu - 1) / kSpu;
   int64_t j = (ubeg + tid) / Th;
   int i0 = (int)((ubeg + tid) - j * Th);
   const int jstep = kThreads / Th, istep = kThreads - jstep * Th;
@@ -169,7 +261,7 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
       rc = load_rec64(rp, rec);
       cur = j;
     }
-    for (int l = 0; l < 2; ++l) {
+    for (int l = 0; l < kSpu; ++l) {
       const int i = i0 + l * Th;
       if (i >= T) break;
       double t;
@@ -207,11 +299,12 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
 // per state.
 constexpr int kSplitMaxT = 2048;
 
-template <bool kFP32>
+// kSpu: states per unit (FP32 2 or 4, FP64 1 or 2), chosen at launch.
+template <bool kFP32, int kSpu>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
   extern __shared__ float2 s_split[];   // [t_count] when use_split
-  const int64_t total = a.rp.n * (kFP32 ? (a.t_count + 3) / 4 : (a.t_count + 1) / 2);
+  const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
@@ -236,8 +329,10 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.v = a.v;
   rg.status = a.status;
   unsigned long long nfix = 0;
-  if (kFP32) run_range_x4(a.rp, a.g, gf, rg, beg, end, nfix, use_split ? s_split : nullptr);
-  else run_units64(a.rp, a.g, rg, beg, end);
+  const float2* split = use_split ? s_split : nullptr;
+  if constexpr (kFP32 && kSpu == 4) run_range_x4(a.rp, a.g, gf, rg, beg, end, nfix, split);
+  else if constexpr (kFP32) run_range_x2(a.rp, a.g, gf, rg, beg, end, nfix, split);
+  else run_units64<kSpu>(a.rp, a.g, rg, beg, end);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
 
@@ -289,8 +384,8 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
       rg.v = static_cast<double*>(a.v) + q.out_offset * 3;
     }
     rg.status = a.status + q.out_offset;
-    if (kFP32) run_range_x4(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
-    else run_units64(a.rp, a.g, rg, beg, end);
+    if constexpr (kFP32) run_range_x4(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
+    else run_units64<2>(a.rp, a.g, rg, beg, end);
   }
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
@@ -304,9 +399,9 @@ int blocks_per_sm_of(K kernel, size_t dyn_smem = 0) {
   return bps > 0 ? bps : 1;
 }
 
-template <bool kFP32>
-cudaError_t launch(const PropArgs& a, cudaStream_t stream) {
-  const int64_t total = a.rp.n * (kFP32 ? (a.t_count + 3) / 4 : (a.t_count + 1) / 2);
+template <bool kFP32, int kSpu>
+cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
+  const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   if (total == 0) return cudaSuccess;
   const bool use_split = kFP32 && !a.grid_per_sat && !a.jd_day && a.t_count <= kSplitMaxT;
   const size_t dyn = use_split ? (size_t)a.t_count * sizeof(float2) : 0;
@@ -314,13 +409,35 @@ cudaError_t launch(const PropArgs& a, cudaStream_t stream) {
   // split table so that the wave below is resident whatever the grid length.
   static int bps = 0;
   if (bps == 0)
-    bps = blocks_per_sm_of(propagate_kernel<kFP32>, kFP32 ? kSplitMaxT * sizeof(float2) : 0);
+    bps = blocks_per_sm_of(propagate_kernel<kFP32, kSpu>, kFP32 ? kSplitMaxT * sizeof(float2) : 0);
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
   const int64_t blocks = (total + chunk - 1) / chunk;
-  propagate_kernel<kFP32><<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
+  propagate_kernel<kFP32, kSpu><<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
   return cudaGetLastError();
+}
+
+// FP32: four states per unit (on full units 0.94 of the time of two units of two) where
+// partly empty units are rare: T a multiple of 4, or T >= 48 (at most 3 in 12 units;
+// an absent state is computed anyway and a partly empty unit stores state by state).
+// Other T take units of two, whose one possibly absent state is a predicated store
+// (1e6 satellites x 10 times: 282 -> 130 us; x 1 time: 53 -> 41 us).
+bool fp32_units_of_four(int64_t T) { return T % 4 == 0 || T >= 48; }
+
+cudaError_t launch_fp32(const PropArgs& a, cudaStream_t stream) {
+  return fp32_units_of_four(a.t_count) ? launch_spu<true, 4>(a, stream)
+                                       : launch_spu<true, 2>(a, stream);
+}
+
+// FP64: one state per thread while the two-state units would not fill one wave of the
+// kernel (148 SMs x 4 blocks x 128 threads), two otherwise.
+cudaError_t launch_fp64(const PropArgs& a, cudaStream_t stream) {
+  static int bps = 0;
+  if (bps == 0) bps = blocks_per_sm_of(propagate_kernel<false, 2>);
+  const int64_t wave = (int64_t)device_sm_count() * bps * kThreads;
+  return a.rp.n * units_per_sat(a.t_count, 2) < wave ? launch_spu<false, 1>(a, stream)
+                                                     : launch_spu<false, 2>(a, stream);
 }
 
 template <bool kFP32>
@@ -341,11 +458,11 @@ int device_sm_count() {
 }
 
 cudaError_t launch_propagate64(const PropArgs& a, cudaStream_t stream) {
-  return launch<false>(a, stream);
+  return launch_fp64(a, stream);
 }
 
 cudaError_t launch_propagate32(const PropArgs& a, cudaStream_t stream) {
-  return launch<true>(a, stream);
+  return launch_fp32(a, stream);
 }
 
 int64_t batched_grid(bool fp32, int64_t total_tiles, int grid_blocks) {
