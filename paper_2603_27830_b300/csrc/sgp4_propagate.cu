@@ -143,7 +143,11 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
 
 // FP32, four states per thread: unit u is satellite j = u / Tq and times i0 + k Tq
 // (k = 0..3, Tq = ceil(T / 4), the last ones absent past T), computed as two packed
-// pairs (k = 0, 2) and (k = 1, 3) on one load of the record.
+// pairs (k = 0, 2) and (k = 1, 3) on one load of the record.  kPre (grids in minutes
+// read per state, no split table): the next unit's four times are loaded while this
+// unit computes (1 satellite x 1e7 times: 163 -> 126 us); a separate instantiation, as
+// the prefetch's registers slow the split-table path.
+template <bool kPre>
 __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
                                              const Range& rg, int64_t ubeg, int64_t uend,
                                              unsigned long long& nfix, const float2* split) {
@@ -153,6 +157,17 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
   int64_t j = (ubeg + tid) / Tq;
   int i0 = (int)((ubeg + tid) - j * Tq);
   const int jstep = kThreads / Tq, istep = kThreads - jstep * Tq;
+  auto fetch = [&](int64_t jj, int ii0, double out[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = ii0 + k * Tq < T ? ii0 + k * Tq : ii0;
+      out[k] = __ldg(rg.per_sat ? rg.tsince + jj * T + i : rg.tsince + i);
+    }
+  };
+  double tn[4] = {0.0, 0.0, 0.0, 0.0};
+  if constexpr (kPre) {
+    if (ubeg + tid < uend) fetch(j, i0, tn);
+  }
   for (int64_t u = ubeg + tid; u < uend; u += kThreads) {
     const int64_t rec = rg.sat0 + j;
     int it[4];
@@ -162,6 +177,18 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
       it[k] = i < T ? i : i0;
     }
     const bool has3 = i0 + 3 * Tq < T;   // then all four exist
+    double tc[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tc[k] = tn[k];
+    if constexpr (kPre) {
+      int64_t jn = j + jstep;
+      int i0n = i0 + istep;
+      if (i0n >= Tq) {
+        ++jn;
+        i0n -= Tq;
+      }
+      if (u + kThreads < uend) fetch(jn, i0n, tn);
+    }
     auto tsince_at = [&](int i) -> double {
       if (rg.jd_day) {
         const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
@@ -178,7 +205,7 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
         th[k] = a.x;
         tl[k] = a.y;
       } else {
-        split_double(tsince_at(it[k]), th[k], tl[k]);
+        split_double(kPre ? tc[k] : tsince_at(it[k]), th[k], tl[k]);
       }
     }
     const Rec32 rc32 = load_rec32(rp, rec);
@@ -295,12 +322,13 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
 }
 
 // FP32 launches on a shared grid of at most this many times split the grid into float
-// hi + lo once per block, into dynamic shared memory (16 KB at most), instead of once
-// per state.
-constexpr int kSplitMaxT = 2048;
+// hi + lo once per block, into dynamic shared memory (48 KB at most: four resident
+// blocks share an SM's 228 KB), instead of once per state (1,000 x 4,096: 55 -> 49 us).
+constexpr int kSplitMaxT = 6144;
 
-// kSpu: states per unit (FP32 2 or 4, FP64 1 or 2), chosen at launch.
-template <bool kFP32, int kSpu>
+// kSpu: states per unit (FP32 2 or 4, FP64 1 or 2), chosen at launch; kPre: FP32
+// four-state units with times read per state, prefetched (run_range_x4).
+template <bool kFP32, int kSpu, bool kPre = false>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
   extern __shared__ float2 s_split[];   // [t_count] when use_split
@@ -330,7 +358,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.status = a.status;
   unsigned long long nfix = 0;
   const float2* split = use_split ? s_split : nullptr;
-  if constexpr (kFP32 && kSpu == 4) run_range_x4(a.rp, a.g, gf, rg, beg, end, nfix, split);
+  if constexpr (kFP32 && kSpu == 4) run_range_x4<kPre>(a.rp, a.g, gf, rg, beg, end, nfix, split);
   else if constexpr (kFP32) run_range_x2(a.rp, a.g, gf, rg, beg, end, nfix, split);
   else run_units64<kSpu>(a.rp, a.g, rg, beg, end);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
@@ -384,7 +412,8 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
       rg.v = static_cast<double*>(a.v) + q.out_offset * 3;
     }
     rg.status = a.status + q.out_offset;
-    if constexpr (kFP32) run_range_x4(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
+    // (no prefetch: tiles are short, and it measured 1% slower on the 256-request batch)
+    if constexpr (kFP32) run_range_x4<false>(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
     else run_units64<2>(a.rp, a.g, rg, beg, end);
   }
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
@@ -399,7 +428,7 @@ int blocks_per_sm_of(K kernel, size_t dyn_smem = 0) {
   return bps > 0 ? bps : 1;
 }
 
-template <bool kFP32, int kSpu>
+template <bool kFP32, int kSpu, bool kPre = false>
 cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   if (total == 0) return cudaSuccess;
@@ -409,12 +438,13 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   // split table so that the wave below is resident whatever the grid length.
   static int bps = 0;
   if (bps == 0)
-    bps = blocks_per_sm_of(propagate_kernel<kFP32, kSpu>, kFP32 ? kSplitMaxT * sizeof(float2) : 0);
+    bps = blocks_per_sm_of(propagate_kernel<kFP32, kSpu, kPre>,
+                           kFP32 ? kSplitMaxT * sizeof(float2) : 0);
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
   const int64_t blocks = (total + chunk - 1) / chunk;
-  propagate_kernel<kFP32, kSpu><<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
+  propagate_kernel<kFP32, kSpu, kPre><<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
   return cudaGetLastError();
 }
 
@@ -426,8 +456,10 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
 bool fp32_units_of_four(int64_t T) { return T % 4 == 0 || T >= 48; }
 
 cudaError_t launch_fp32(const PropArgs& a, cudaStream_t stream) {
-  return fp32_units_of_four(a.t_count) ? launch_spu<true, 4>(a, stream)
-                                       : launch_spu<true, 2>(a, stream);
+  if (!fp32_units_of_four(a.t_count)) return launch_spu<true, 2>(a, stream);
+  const bool per_state = a.grid_per_sat || a.t_count > kSplitMaxT;   // minutes, no table
+  if (per_state && !a.jd_day) return launch_spu<true, 4, true>(a, stream);
+  return launch_spu<true, 4>(a, stream);
 }
 
 // FP64: one state per thread while the two-state units would not fill one wave of the
