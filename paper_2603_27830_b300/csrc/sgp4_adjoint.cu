@@ -105,17 +105,40 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
   for (int q = 0; q < kNumAdj; ++q) acc[q] = T(0);
   if constexpr (sizeof(T) == 4) {
     prop_loop(a, sat, sfwd[tid], acc, j);
+    // Block sum through the forward-value slots, free now: each thread writes its 33
+    // sums to its row, then 3 x 33 threads sum the columns in three interleaved parts
+    // (rows of 65 words: conflict-free).  A warp-shuffle tree cost 165 shuffles and adds
+    // per thread, spread over only T / 128 states.
+    constexpr int kParts = 3;
+    static_assert(kNumAdj * kParts <= kAdjThreads && kParts <= kAdjWarps, "reduction layout");
+    __syncthreads();
+    float* row = reinterpret_cast<float*>(&sfwd[tid]);
+#pragma unroll
+    for (int q = 0; q < kNumAdj; ++q) row[q] = acc[q];
+    __syncthreads();
+    if (tid < kNumAdj * kParts) {
+      const int c = tid % kNumAdj, p0 = tid / kNumAdj;
+      float sum = 0.0f;
+      for (int r = p0; r < kAdjThreads; r += kParts) sum += reinterpret_cast<const float*>(&sfwd[r])[c];
+      part[c][p0] = sum;
+    }
+    __syncthreads();
+    if (tid < kNumAdj) {
+      double sum = 0.0;
+      for (int w = 0; w < kParts; ++w) sum += (double)part[tid][w];
+      a.field_bar[j * kNumAdj + tid] = sum;
+    }
   } else {
     Fwd<T> f;
     prop_loop(a, sat, f, acc, j);
-  }
 #pragma unroll
-  for (int q = 0; q < kNumAdj; ++q) warp_partial(acc[q], q, part);
-  __syncthreads();
-  if (tid < kNumAdj) {
-    double sum = 0.0;
-    for (int w = 0; w < kAdjWarps; ++w) sum += (double)part[tid][w];
-    a.field_bar[j * kNumAdj + tid] = sum;
+    for (int q = 0; q < kNumAdj; ++q) warp_partial(acc[q], q, part);
+    __syncthreads();
+    if (tid < kNumAdj) {
+      double sum = 0.0;
+      for (int w = 0; w < kAdjWarps; ++w) sum += (double)part[tid][w];
+      a.field_bar[j * kNumAdj + tid] = sum;
+    }
   }
 }
 
