@@ -44,6 +44,7 @@ struct Range {
   const double* tsince;   // [T], or [n][T] when per_sat
   const int32_t* jd_day;  // absolute times [T] as Julian day + fraction, or null
   const double* jd_frac;
+  int32_t jd0;            // with a split table of absolute times: the table's day origin
   int64_t T;
   int per_sat;
   int64_t sat0;           // record index of the problem's satellite 0
@@ -52,6 +53,27 @@ struct Range {
   int32_t* status;
 };
 
+
+// a - b for double-floats (hi + lo, |lo| <= ulp(hi) / 2): Knuth's two-sum of the high
+// parts, the low parts added, the sum renormalised.  On the FP32 pipes; the absolute-time
+// path uses it instead of per-state FP64 arithmetic.
+__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float& h,
+                                       float& l) {
+  const float s = ah - bh;
+  const float v = s - ah;
+  const float e = (ah - (s - v)) + (-bh - v);
+  const float lo = e + (al - bl);
+  h = s + lo;
+  l = lo - (h - s);
+}
+
+// Minutes from day jd0 to the epoch of record rec, as float hi + lo (three FP64
+// instructions, once per unit).
+__device__ __forceinline__ void epoch_minutes(const RecordPtrs& rp, int64_t rec, int32_t jd0,
+                                              float& h, float& l) {
+  const double d = (double)(__ldg(rp.epoch_day + rec) - jd0);
+  split_double(fma(1440.0, __ldg(rp.f64 + kEpochFrac * rp.stride + rec), 1440.0 * d), h, l);
+}
 
 // FP32, two states per thread (packed arithmetic, state32x2): unit u of [ubeg, uend)
 // is satellite j = u / Th, times i0 = u % Th and i1 = i0 + Th (Th = ceil(T / 2); i1 does
@@ -83,6 +105,12 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
       const float2 a0 = split[it[0]], a1 = split[it[1]];
       th = make_float2(a0.x, a1.x);
       tl = make_float2(a0.y, a1.y);
+      if (rg.jd_day) {   // table of minutes from day jd0: subtract the record's epoch
+        float eh, el;
+        epoch_minutes(rp, rec, rg.jd0, eh, el);
+        df_sub(a0.x, a0.y, eh, el, th.x, tl.x);
+        df_sub(a1.x, a1.y, eh, el, th.y, tl.y);
+      }
     } else {
       split_double(tsince_at(it[0]), th.x, tl.x);
       split_double(tsince_at(it[1]), th.y, tl.y);
@@ -198,12 +226,15 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
       return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
     };
     float th[4], tl[4];
+    float eh = 0.0f, el = 0.0f;   // absolute times: the record's epoch from day jd0
+    if (split && rg.jd_day) epoch_minutes(rp, rec, rg.jd0, eh, el);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (split) {
         const float2 a = split[it[k]];
         th[k] = a.x;
         tl[k] = a.y;
+        if (rg.jd_day) df_sub(a.x, a.y, eh, el, th[k], tl[k]);
       } else {
         split_double(kPre ? tc[k] : tsince_at(it[k]), th[k], tl[k]);
       }
@@ -336,11 +367,17 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
-  const bool use_split = kFP32 && !a.grid_per_sat && !a.jd_day && a.t_count <= kSplitMaxT;
+  const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
+  const int32_t jd0 = a.jd_day ? __ldg(a.jd_day) : 0;
   if (use_split) {
+    // minutes since epoch, or for absolute times minutes from the grid's first day (each
+    // unit then subtracts its record's epoch in double-float arithmetic)
     for (int k = threadIdx.x; k < (int)a.t_count; k += kThreads) {
+      const double t = a.jd_day ? fma(1440.0, __ldg(a.jd_frac + k),
+                                      1440.0 * (double)(__ldg(a.jd_day + k) - jd0))
+                                : __ldg(a.tsince + k);
       float h, l;
-      split_double(__ldg(a.tsince + k), h, l);
+      split_double(t, h, l);
       s_split[k] = make_float2(h, l);
     }
     __syncthreads();
@@ -350,6 +387,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.tsince = a.tsince;
   rg.jd_day = a.jd_day;
   rg.jd_frac = a.jd_frac;
+  rg.jd0 = jd0;
   rg.T = a.t_count;
   rg.per_sat = a.grid_per_sat;
   rg.sat0 = 0;
@@ -401,6 +439,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
     rg.tsince = a.tsince + q.t_offset;
     rg.jd_day = nullptr;
     rg.jd_frac = nullptr;
+    rg.jd0 = 0;
     rg.T = q.t_count;
     rg.per_sat = 0;
     rg.sat0 = q.sat_offset;
@@ -432,7 +471,7 @@ template <bool kFP32, int kSpu, bool kPre = false>
 cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   if (total == 0) return cudaSuccess;
-  const bool use_split = kFP32 && !a.grid_per_sat && !a.jd_day && a.t_count <= kSplitMaxT;
+  const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
   const size_t dyn = use_split ? (size_t)a.t_count * sizeof(float2) : 0;
   // Resident blocks per SM of this kernel (same on every B300), taken with the largest
   // split table so that the wave below is resident whatever the grid length.
