@@ -362,6 +362,41 @@ def test_julian_date_grid_from_each_records_split_epoch(prec):
         assert dr.max() <= 0.1 and dv.max() <= 1e-4, error_summary(dr, dv)
 
 
+def test_julian_dates_far_from_the_epochs_fp32():
+    """FP32 absolute times with epochs up to 120 days from the grid and arbitrary
+    fractions (tsince up to 1.7e5 minutes): the grid is tabulated as minutes from its
+    first day and each record's epoch subtracted in double-float arithmetic, which must
+    agree with the oracle at the FP64 tsince.  Drag-free Starlink-shaped orbits, so the
+    states stay valid over the span."""
+    import torch
+
+    from paper_2603_27830_b300 import sgp4_init, sgp4_propagate_jd
+    rng = np.random.default_rng(29)
+    el = W.config2(seed=5, n=200).elements.copy()
+    el[:, 6] = 0.0
+    n = len(el)
+    eday = (2461040 + rng.integers(-120, 121, n)).astype(np.int32)
+    efrac = rng.uniform(0.0, 1.0, n)
+    jd_day = np.full(97, 2461040, dtype=np.int32)
+    jd_frac = np.sort(rng.uniform(0.0, 1.0, 97))
+    jd_day[60:] += 1                                        # the grid crosses a day
+    tsince = ((jd_day[None, :] - eday[:, None]).astype(np.float64)
+              + (jd_frac[None, :] - efrac[:, None])) * 1440.0
+    dev = "cuda"
+    recs, ist = sgp4_init(torch.as_tensor(el, device=dev),
+                          epoch_day=torch.as_tensor(eday, device=dev),
+                          epoch_frac=torch.as_tensor(efrac, device=dev))
+    r, v, st = sgp4_propagate_jd(recs, torch.as_tensor(jd_day, device=dev),
+                                 torch.as_tensor(jd_frac, device=dev), "fp32")
+    torch.cuda.synchronize()
+    r, v, st = r.double().cpu().numpy(), v.double().cpu().numpy(), st.cpu().numpy()
+    rr, vr, sr, isr = oracle.propagate(el, tsince)
+    assert (sr == 0).all()
+    assert_status_and_nan(st, sr, r, v, ist.cpu().numpy(), isr)
+    dr, dv = state_errors(r, v, rr, vr, sr)
+    assert dr.max() <= 0.1 and dv.max() <= 1e-4, error_summary(dr, dv)
+
+
 def test_tle_catalogue_to_julian_date_propagation():
     """A synthetic TLE catalogue written and read back by the library, built with its
     epochs and propagated to absolute times, against the oracle on the parsed elements."""
