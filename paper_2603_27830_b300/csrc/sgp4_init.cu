@@ -16,6 +16,16 @@ namespace sgp4 {
 
 namespace {
 
+// Named barrier `id` over `n` threads (a multiple of 32): arrive without waiting, or
+// wait for all n.  Every thread of both warps of a block reaches them, whatever its
+// satellite's state.
+__device__ __forceinline__ void named_barrier_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_barrier_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
 // 32 satellites per block.  With kSplit, two warps share them: a lone warp on a
 // sub-partition issues one FP64 instruction per ~64 cycles, so for small catalogues
 // (fewer warps than sub-partitions) the record build takes as long as its longest chain
@@ -35,6 +45,7 @@ __global__ void __launch_bounds__(kSplit ? 64 : 32) init_kernel(const double* __
   __shared__ double sh_sp[12][kInitSats];     // InitSpine
   __shared__ double sh_an[4][kInitSats];      // InitAngles
   __shared__ double sh_x[2][kInitSats];       // C1 (drag), first-order node rate (rates)
+  __shared__ double sh_dc[7][kInitSats];      // DragCore (warp 0 -> warp 1)
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const bool w0 = !kSplit || w == 0;   // this thread runs the spine / drag branch
@@ -102,72 +113,109 @@ __global__ void __launch_bounds__(kSplit ? 64 : 32) init_kernel(const double* __
     }
   }
 
-  // Phase 2: drag terms (warp 0) and secular rates (warp 1), each writing its own
-  // fields to the FP64 planes and the FP32 row.  FP32 conversions by integer operations
-  // (f32_rn, split_double): an FP64-unit conversion would cost as much as a DFMA.
+  // Phase 2: drag terms and secular rates, each branch writing its own fields to the
+  // FP64 planes and the FP32 row.  Warp 0: the drag core (atmosphere, xi, eta, the C
+  // factors), published through shared memory with a non-blocking arrival on named
+  // barrier 1, then C1 and the D / L coefficients.  Warp 1: the secular rates, then
+  // (after barrier 1) C3, C4, C5 and their terms, which nothing of warp 0's needs.
+  // FP32 conversions by integer operations (f32_rn, split_double): an FP64-unit
+  // conversion would cost as much as a DFMA.
   const double inv2pi = 1.0 / kTwoPi;
-  InitFields<double> o;
-  if (run && w0) {
-    init_drag(e7, g, sp, an, o);
-    if (kSplit) sh_x[0][lane] = o.c1;
-    const bool isimp = o.isimp;
-    f[kN0pp * s + j] = sp.n0pp;  f[kA0pp * s + j] = sp.a0pp;  f[kE0 * s + j] = e0;
-    f[kI0 * s + j] = i0;         f[kRaan0 * s + j] = raan0;   f[kArgp0 * s + j] = argp0;
-    f[kM0 * s + j] = m0;         f[kBstar * s + j] = bstar;
-    f[kArgpCf * s + j] = o.argp_cf; f[kMCf * s + j] = o.m_cf;  f[kC1 * s + j] = o.c1;
-    f[kBC4 * s + j] = o.bc4;     f[kBC5 * s + j] = o.bc5;     f[kD2 * s + j] = o.d2;
-    f[kD3 * s + j] = o.d3;       f[kD4 * s + j] = o.d4;       f[kL2 * s + j] = o.l2;
-    f[kL3 * s + j] = o.l3;       f[kL4 * s + j] = o.l4;       f[kL5 * s + j] = o.l5;
-    f[kEta * s + j] = o.eta;     f[kDelM0 * s + j] = o.delm0; f[kSinM0 * s + j] = o.sinm0;
-    f[kCosi * s + j] = sp.cosi;  f[kSini * s + j] = sp.sini;  f[kX3thm1 * s + j] = sp.x3thm1;
-    f[kX1mth2 * s + j] = sp.x1mth2; f[kX7thm1 * s + j] = sp.x7thm1;
-    h[fA0pp] = f32_rn(sp.a0pp); h[fE0] = f32_rn(e0);     h[fC1] = f32_rn(o.c1);
-    h[fBC4] = f32_rn(o.bc4);   h[fBC5] = isimp ? 0.0f : f32_rn(o.bc5);   h[fD2] = f32_rn(o.d2);
-    h[fD3] = f32_rn(o.d3);     h[fD4] = f32_rn(o.d4);     h[fL2] = f32_rn(o.l2);
-    h[fL3] = f32_rn(o.l3);     h[fL4] = f32_rn(o.l4);     h[fL5] = f32_rn(o.l5);
-    h[fEta] = f32_rn(o.eta);   h[fDelM0] = f32_rn(o.delm0); h[fSinM0] = f32_rn(o.sinm0);
-    // Simplified-drag records (perigee below 220 km) drop the drag terms these three
-    // carry: zero in the FP32 row, so that the FP32 state evaluates the drag block
-    // unconditionally (no branch) and gets the theory's zero contributions.
+  InitFields<double> o = {};
+  DragCore<double> dc = {};
+  auto store_c = [&]() {   // C3 .. C5 terms (simplified drag: zero in the FP32 row)
+    const bool isimp = dc.isimp;
+    f[kArgpCf * s + j] = o.argp_cf; f[kMCf * s + j] = o.m_cf;
+    f[kBC4 * s + j] = o.bc4;       f[kBC5 * s + j] = o.bc5;
+    h[fBC4] = f32_rn(o.bc4);
+    h[fBC5] = isimp ? 0.0f : f32_rn(o.bc5);
     h[fArgpCf] = isimp ? 0.0f : f32_rn(o.argp_cf);
     h[fMCf] = isimp ? 0.0f : f32_rn(o.m_cf);
-    h[fCosi] = f32_rn(sp.cosi); h[fSini] = f32_rn(sp.sini);
-    h[fX3thm1] = f32_rn(1.5 * sp.x3thm1); h[fX1mth2] = f32_rn(sp.x1mth2);
-    h[fX7thm1] = f32_rn(-0.25 * sp.x7thm1);
-    h[fHalfX1mth2] = f32_rn(0.5 * sp.x1mth2);
-    h[fC15Cosi] = f32_rn(1.5 * sp.cosi);
-    h[fC15CosiSini] = f32_rn(1.5 * sp.cosi * sp.sini);
-    int flags = 0;
-    if (isimp) flags |= kFlagIsimp;
-    if (sp.n0pp <= 0.0) flags |= kFlagN0ppNonPos;
-    rp.flags[j] = flags;
-    h[fFlags] = __int_as_float(flags);
-    for (int k = kNumF32Used; k < kF32Row; ++k) h[k] = 0.0f;
+  };
+  if (w0) {
+    if (run) init_drag_core(e7, g, sp, dc);
+    if constexpr (kSplit) {
+      if (run) {
+        sh_dc[0][lane] = dc.ss;    sh_dc[1][lane] = dc.xi;    sh_dc[2][lane] = dc.eta;
+        sh_dc[3][lane] = dc.ipsi2; sh_dc[4][lane] = dc.coef;  sh_dc[5][lane] = dc.coef1;
+        sh_dc[6][lane] = dc.isimp ? 1.0 : 0.0;
+      }
+      __threadfence_block();
+      named_barrier_arrive(1, 2 * kInitSats);
+    }
+    if (run) {
+      if (!kSplit) {   // one warp: the C terms first (measured 6% faster than after)
+        init_drag_c(e7, g, sp, an, dc, o);
+        store_c();
+      }
+      init_drag_d(e7, g, sp, an, dc, o);
+      if (kSplit) sh_x[0][lane] = o.c1;
+      const bool isimp = dc.isimp;
+      f[kN0pp * s + j] = sp.n0pp;  f[kA0pp * s + j] = sp.a0pp;  f[kE0 * s + j] = e0;
+      f[kI0 * s + j] = i0;         f[kRaan0 * s + j] = raan0;   f[kArgp0 * s + j] = argp0;
+      f[kM0 * s + j] = m0;         f[kBstar * s + j] = bstar;   f[kC1 * s + j] = o.c1;
+      f[kD2 * s + j] = o.d2;       f[kD3 * s + j] = o.d3;       f[kD4 * s + j] = o.d4;
+      f[kL2 * s + j] = o.l2;       f[kL3 * s + j] = o.l3;       f[kL4 * s + j] = o.l4;
+      f[kL5 * s + j] = o.l5;       f[kEta * s + j] = o.eta;     f[kDelM0 * s + j] = o.delm0;
+      f[kSinM0 * s + j] = o.sinm0; f[kCosi * s + j] = sp.cosi;  f[kSini * s + j] = sp.sini;
+      f[kX3thm1 * s + j] = sp.x3thm1; f[kX1mth2 * s + j] = sp.x1mth2;
+      f[kX7thm1 * s + j] = sp.x7thm1;
+      h[fA0pp] = f32_rn(sp.a0pp); h[fE0] = f32_rn(e0);     h[fC1] = f32_rn(o.c1);
+      h[fD2] = f32_rn(o.d2);     h[fD3] = f32_rn(o.d3);     h[fD4] = f32_rn(o.d4);
+      h[fL2] = f32_rn(o.l2);     h[fL3] = f32_rn(o.l3);     h[fL4] = f32_rn(o.l4);
+      h[fL5] = f32_rn(o.l5);     h[fEta] = f32_rn(o.eta);   h[fDelM0] = f32_rn(o.delm0);
+      h[fSinM0] = f32_rn(o.sinm0);
+      h[fCosi] = f32_rn(sp.cosi); h[fSini] = f32_rn(sp.sini);
+      h[fX3thm1] = f32_rn(1.5 * sp.x3thm1); h[fX1mth2] = f32_rn(sp.x1mth2);
+      h[fX7thm1] = f32_rn(-0.25 * sp.x7thm1);
+      h[fHalfX1mth2] = f32_rn(0.5 * sp.x1mth2);
+      h[fC15Cosi] = f32_rn(1.5 * sp.cosi);
+      h[fC15CosiSini] = f32_rn(1.5 * sp.cosi * sp.sini);
+      int flags = 0;
+      if (isimp) flags |= kFlagIsimp;
+      if (sp.n0pp <= 0.0) flags |= kFlagN0ppNonPos;
+      rp.flags[j] = flags;
+      h[fFlags] = __int_as_float(flags);
+      for (int k = kNumF32Used; k < kF32Row; ++k) h[k] = 0.0f;
+    }
   }
-  if (run && w1) {
-    init_rates(g, sp, o);
-    if (kSplit) sh_x[1][lane] = o.raandot1;
-    f[kMdot * s + j] = o.mdot;   f[kArgpdot * s + j] = o.argpdot; f[kRaandot * s + j] = o.raandot;
-    f[kXlcof * s + j] = o.xlcof; f[kAycof * s + j] = o.aycof;
-    // FP32 row: angles in revolutions, the argument-of-latitude phase as double-float.
-    double phi0 = (m0 + argp0) * inv2pi;
-    phi0 -= floor(phi0);
-    float hi, lo;
-    split_double(phi0, hi, lo);
-    h[fPhi0H] = hi; h[fPhi0L] = lo;
-    split_double((o.mdot + o.argpdot) * inv2pi, hi, lo);
-    h[fPhiDH] = hi; h[fPhiDL] = lo;
-    double m0r = m0 * inv2pi;       m0r -= floor(m0r);
-    double argp0r = argp0 * inv2pi; argp0r -= floor(argp0r);
-    double raan0r = raan0 * inv2pi; raan0r -= floor(raan0r);
-    h[fM0r] = f32_rn(m0r);
-    h[fMdr] = f32_rn(o.mdot * inv2pi);
-    h[fArgp0r] = f32_rn(argp0r);
-    h[fArgpdr] = f32_rn(o.argpdot * inv2pi);
-    h[fRaan0r] = f32_rn(raan0r);
-    h[fRaandr] = f32_rn(o.raandot * inv2pi);
-    h[fN0ppr] = f32_rn(sp.n0pp * inv2pi);
-    h[fXlcof] = f32_rn(o.xlcof); h[fAycof] = f32_rn(o.aycof);
+  if (w1) {
+    if (run) {
+      init_rates(g, sp, o);
+      if (kSplit) sh_x[1][lane] = o.raandot1;
+      f[kMdot * s + j] = o.mdot;   f[kArgpdot * s + j] = o.argpdot;
+      f[kRaandot * s + j] = o.raandot;
+      f[kXlcof * s + j] = o.xlcof; f[kAycof * s + j] = o.aycof;
+      // FP32 row: angles in revolutions, the argument-of-latitude phase as double-float.
+      double phi0 = (m0 + argp0) * inv2pi;
+      phi0 -= floor(phi0);
+      float hi, lo;
+      split_double(phi0, hi, lo);
+      h[fPhi0H] = hi; h[fPhi0L] = lo;
+      split_double((o.mdot + o.argpdot) * inv2pi, hi, lo);
+      h[fPhiDH] = hi; h[fPhiDL] = lo;
+      double m0r = m0 * inv2pi;       m0r -= floor(m0r);
+      double argp0r = argp0 * inv2pi; argp0r -= floor(argp0r);
+      double raan0r = raan0 * inv2pi; raan0r -= floor(raan0r);
+      h[fM0r] = f32_rn(m0r);
+      h[fMdr] = f32_rn(o.mdot * inv2pi);
+      h[fArgp0r] = f32_rn(argp0r);
+      h[fArgpdr] = f32_rn(o.argpdot * inv2pi);
+      h[fRaan0r] = f32_rn(raan0r);
+      h[fRaandr] = f32_rn(o.raandot * inv2pi);
+      h[fN0ppr] = f32_rn(sp.n0pp * inv2pi);
+      h[fXlcof] = f32_rn(o.xlcof); h[fAycof] = f32_rn(o.aycof);
+    }
+    if constexpr (kSplit) {
+      named_barrier_sync(1, 2 * kInitSats);   // warp 0's drag core is in shared memory
+      if (run) {
+        dc.ss = sh_dc[0][lane];    dc.xi = sh_dc[1][lane];   dc.eta = sh_dc[2][lane];
+        dc.ipsi2 = sh_dc[3][lane]; dc.coef = sh_dc[4][lane]; dc.coef1 = sh_dc[5][lane];
+        dc.isimp = sh_dc[6][lane] != 0.0;
+        init_drag_c(e7, g, sp, an, dc, o);
+        store_c();
+      }
+    }
   }
   if constexpr (kSplit) __syncthreads();
 

@@ -224,7 +224,10 @@ struct InitFields {
 // independent branches of it (drag terms; secular rates) in two warps:
 //   init_spine   inclination terms, beta0, the un-Kozai'd mean motion and a0'';
 //   init_angles  sin/cos of argp0 and M0 (independent of the spine);
-//   init_drag    atmosphere, C1 .. C5, D2 .. L5 and the drag rates (spine, angles);
+//   init_drag    atmosphere, C1 .. C5, D2 .. L5 and the drag rates (spine, angles), in
+//                three parts: init_drag_core (atmosphere, xi, eta, the C factors), then
+//                init_drag_c (C3, C4, C5 and their terms) and init_drag_d (C1, D, L),
+//                which are independent of each other;
 //   init_rates   secular rates and the J3 coefficients (spine);
 //   init_finish  the node drag term (drag and rates) and the element copies.
 // Reciprocals and square roots are formed from a few rsqrt and divisions and reused (on
@@ -277,45 +280,56 @@ __device__ __forceinline__ void init_angles(const S el[7], InitAngles<S>& an) {
   sincos(el[5], &an.sinm, &an.cosm);
 }
 
+// Atmosphere and the drag coefficients' common factors (spine).
 template <class S>
-__device__ __forceinline__ void init_drag(const S el[7], const Geo& g, const InitSpine<S>& sp,
-                                          const InitAngles<S>& an, InitFields<S>& o) {
-  const S e0 = el[1], bstar = el[6];
-  const double inv_re = g.inv_re;
-  const S a0pp = sp.a0pp, n0pp = sp.n0pp, b2 = sp.b2, x3thm1 = sp.x3thm1, x1mth2 = sp.x1mth2;
+struct DragCore {
+  S ss, xi, eta, ipsi2, coef, coef1;
+  bool isimp;
+};
 
+template <class S>
+__device__ __forceinline__ void init_drag_core(const S el[7], const Geo& g,
+                                               const InitSpine<S>& sp, DragCore<S>& dc) {
+  const S e0 = el[1];
+  const double inv_re = g.inv_re;
+  const S a0pp = sp.a0pp;
   // Atmosphere: s and (q0 - s)^4 by perigee height.
   const S rp_er = a0pp * (1.0 - e0);
   const S hp = (rp_er - 1.0) * g.re;
-  o.isimp = val(rp_er) < 1.0 + 220.0 * inv_re;
+  dc.isimp = val(rp_er) < 1.0 + 220.0 * inv_re;
   S s_km = 0.0 * hp + 78.0;
   if (val(hp) < 156.0) s_km = hp - 78.0;
   if (val(hp) < 98.0) s_km = 0.0 * hp + 20.0;
   const S qs = (120.0 - s_km) * inv_re;
   const S qs4 = qs * qs * qs * qs;
-  const S ss = 1.0 + s_km * inv_re;
+  dc.ss = 1.0 + s_km * inv_re;
+  dc.xi = 1.0 / (a0pp - dc.ss);
+  dc.eta = a0pp * e0 * dc.xi;
+  const S psi2 = fabs(1.0 - dc.eta * dc.eta);
+  const S rpsi = rsqrt(psi2);
+  dc.ipsi2 = rpsi * rpsi;                              // 1 / psi2
+  const S xi4 = dc.xi * dc.xi * dc.xi * dc.xi;
+  dc.coef = qs4 * xi4;
+  dc.coef1 = dc.coef * (dc.ipsi2 * dc.ipsi2 * dc.ipsi2 * rpsi);   // coef / psi2^3.5
+}
 
-  const S xi = 1.0 / (a0pp - ss);
-  const S eta = a0pp * e0 * xi;
+// C3, C4, C5 and the drag terms built on them: argp_cf, m_cf, B* C4, B* C5 (spine,
+// angles, core; none of them feeds the D and L coefficients).
+template <class S>
+__device__ __forceinline__ void init_drag_c(const S el[7], const Geo& g, const InitSpine<S>& sp,
+                                            const InitAngles<S>& an, const DragCore<S>& dc,
+                                            InitFields<S>& o) {
+  const S e0 = el[1], bstar = el[6];
+  const S a0pp = sp.a0pp, n0pp = sp.n0pp, b2 = sp.b2, x3thm1 = sp.x3thm1, x1mth2 = sp.x1mth2;
+  const S eta = dc.eta, xi = dc.xi, ipsi2 = dc.ipsi2, coef = dc.coef, coef1 = dc.coef1;
   const S eta2 = eta * eta;
   const S eeta = e0 * eta;
-  const S psi2 = fabs(1.0 - eta2);
-  const S rpsi = rsqrt(psi2);
-  const S ipsi2 = rpsi * rpsi;                // 1 / psi2
-  const S xi4 = xi * xi * xi * xi;
-  const S coef = qs4 * xi4;
-  const S coef1 = coef * (ipsi2 * ipsi2 * ipsi2 * rpsi);   // coef / psi2^3.5
-
-  const S C2 = coef1 * n0pp *
-               (a0pp * (1.0 + 1.5 * eta2 + eeta * (4.0 + eta2)) +
-                0.375 * g.j2 * xi * ipsi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
-  const S C1 = bstar * C2;
   const S cos2w = 2.0 * an.cosw * an.cosw - 1.0;
   // C3 and the mean-anomaly drag term divide by e0 and by e0 eta; one reciprocal of e0
   // serves both (1 / eta = (a0'' - s) / (a0'' e0)).
   const bool e_big = val(e0) > 1.0e-4;
   const S ie0 = e_big ? 1.0 / e0 : 0.0 * e0;
-  S C3 = 0.0 * C1;
+  S C3 = 0.0 * e0;
   if (e_big) C3 = -2.0 * coef * xi * g.j3oj2 * n0pp * sp.sini * ie0;
   const S C4 = 2.0 * n0pp * coef1 * a0pp * b2 *
                (eta * (2.0 + 0.5 * eta2) + e0 * (0.5 + 2.0 * eta2) -
@@ -323,17 +337,35 @@ __device__ __forceinline__ void init_drag(const S el[7], const Geo& g, const Ini
                     (-3.0 * x3thm1 * (1.0 - 2.0 * eeta + eta2 * (1.5 - 0.5 * eeta)) +
                      0.75 * x1mth2 * (2.0 * eta2 - eeta * (1.0 + eta2)) * cos2w));
   const S C5 = 2.0 * coef1 * a0pp * b2 * (1.0 + 2.75 * (eta2 + eeta) + eeta * eta2);
-
   o.argp_cf = bstar * C3 * an.cosw;
-  o.m_cf = 0.0 * C1;
-  if (e_big) o.m_cf = -(2.0 / 3.0) * coef * bstar * (ie0 * ie0) * ((a0pp - ss) * sp.ia0pp);
+  o.m_cf = 0.0 * e0;
+  if (e_big) o.m_cf = -(2.0 / 3.0) * coef * bstar * (ie0 * ie0) * ((a0pp - dc.ss) * sp.ia0pp);
+  o.bc4 = bstar * C4;
+  o.bc5 = bstar * C5;
+}
+
+// C1 (through C2), the l2 and D / L coefficients, (1 + eta cos M0)^3, sin M0 (spine,
+// angles, core).
+template <class S>
+__device__ __forceinline__ void init_drag_d(const S el[7], const Geo& g, const InitSpine<S>& sp,
+                                            const InitAngles<S>& an, const DragCore<S>& dc,
+                                            InitFields<S>& o) {
+  const S e0 = el[1], bstar = el[6];
+  const S a0pp = sp.a0pp, n0pp = sp.n0pp, x3thm1 = sp.x3thm1;
+  const S eta = dc.eta, xi = dc.xi, ss = dc.ss;
+  const S eta2 = eta * eta;
+  const S eeta = e0 * eta;
+  const S C2 = dc.coef1 * n0pp *
+               (a0pp * (1.0 + 1.5 * eta2 + eeta * (4.0 + eta2)) +
+                0.375 * g.j2 * xi * dc.ipsi2 * x3thm1 * (8.0 + 3.0 * eta2 * (8.0 + eta2)));
+  const S C1 = bstar * C2;
+  o.isimp = dc.isimp;
   o.l2 = 1.5 * C1;
   const S cm = 1.0 + eta * an.cosm;
   o.delm0 = cm * cm * cm;
   o.sinm0 = an.sinm;
-
   o.d2 = 0.0 * C1; o.d3 = o.d2; o.d4 = o.d2; o.l3 = o.d2; o.l4 = o.d2; o.l5 = o.d2;
-  if (!o.isimp) {
+  if (!dc.isimp) {
     const S c1sq = C1 * C1;
     o.d2 = 4.0 * a0pp * xi * c1sq;
     o.d3 = (4.0 / 3.0) * a0pp * xi * xi * (17.0 * a0pp + ss) * c1sq * C1;
@@ -343,7 +375,17 @@ __device__ __forceinline__ void init_drag(const S el[7], const Geo& g, const Ini
     o.l5 = 0.2 * (3.0 * o.d4 + 12.0 * C1 * o.d3 + 6.0 * o.d2 * o.d2 + 30.0 * c1sq * o.d2 +
                   15.0 * c1sq * c1sq);
   }
-  o.c1 = C1; o.bc4 = bstar * C4; o.bc5 = bstar * C5; o.eta = eta;
+  o.c1 = C1;
+  o.eta = eta;
+}
+
+template <class S>
+__device__ __forceinline__ void init_drag(const S el[7], const Geo& g, const InitSpine<S>& sp,
+                                          const InitAngles<S>& an, InitFields<S>& o) {
+  DragCore<S> dc;
+  init_drag_core(el, g, sp, dc);
+  init_drag_c(el, g, sp, an, dc, o);
+  init_drag_d(el, g, sp, an, dc, o);
 }
 
 template <class S>
