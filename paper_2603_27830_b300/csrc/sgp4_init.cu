@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(kSplit ? 64 : 32) init_kernel(const double* __
   __shared__ double sh_an[4][kInitSats];      // InitAngles
   __shared__ double sh_x[2][kInitSats];       // C1 (drag), first-order node rate (rates)
   __shared__ double sh_dc[7][kInitSats];      // DragCore (warp 0 -> warp 1)
+  __shared__ double sh_sa[6][kInitSats];      // SpineA (warp 1 -> warp 0)
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const bool w0 = !kSplit || w == 0;   // this thread runs the spine / drag branch
@@ -84,11 +85,35 @@ __global__ void __launch_bounds__(kSplit ? 64 : 32) init_kernel(const double* __
     init_status[j] = fatal;
   }
 
-  // Phase 1: the spine (warp 0) and the angles (warp 1).
+  // Phase 1: the spine (warp 0, its n0 / e0 terms from warp 1) and the angles (warp 1).
   InitSpine<double> sp;
   InitAngles<double> an;
-  if (run && w0) init_spine(e7, g, sp);
-  if (run && w1) init_angles(e7, an);
+  if constexpr (kSplit) {
+    // warp 1: the spine's terms in n0 and e0, published on named barrier 2, then the
+    // angles; warp 0: the inclination terms, then (barrier 2) the Kozai recovery
+    SpineA<double> sa;
+    if (w1) {
+      if (run) {
+        init_spine_a(e7, g, sa);
+        sh_sa[0][lane] = sa.n0k; sh_sa[1][lane] = sa.x1; sh_sa[2][lane] = sa.a1;
+        sh_sa[3][lane] = sa.b2;  sh_sa[4][lane] = sa.rb; sh_sa[5][lane] = sa.b;
+      }
+      __threadfence_block();
+      named_barrier_arrive(2, 2 * kInitSats);
+      if (run) init_angles(e7, an);
+    } else {
+      if (run) init_spine_i(e7, sp);
+      named_barrier_sync(2, 2 * kInitSats);
+      if (run) {
+        sa.n0k = sh_sa[0][lane]; sa.x1 = sh_sa[1][lane]; sa.a1 = sh_sa[2][lane];
+        sa.b2 = sh_sa[3][lane];  sa.rb = sh_sa[4][lane]; sa.b = sh_sa[5][lane];
+        init_spine_b(e7, g, sa, sp);
+      }
+    }
+  } else if (run) {
+    init_spine(e7, g, sp);
+    init_angles(e7, an);
+  }
   if constexpr (kSplit) {
     if (run && w0) {
       const double v[12] = {sp.cosi, sp.sini, sp.th2, sp.x3thm1, sp.x1mth2, sp.x7thm1,

@@ -222,7 +222,9 @@ struct InitFields {
 
 // The computation comes in phases, so that the record-build kernel can run the two
 // independent branches of it (drag terms; secular rates) in two warps:
-//   init_spine   inclination terms, beta0, the un-Kozai'd mean motion and a0'';
+//   init_spine   inclination terms, beta0, the un-Kozai'd mean motion and a0'' (in
+//                parts: init_spine_a, the terms in n0 and e0 alone; init_spine_i, the
+//                inclination terms; init_spine_b, the recovery, needing both);
 //   init_angles  sin/cos of argp0 and M0 (independent of the spine);
 //   init_drag    atmosphere, C1 .. C5, D2 .. L5 and the drag rates (spine, angles), in
 //                three parts: init_drag_core (atmosphere, xi, eta, the C factors), then
@@ -242,25 +244,43 @@ struct InitAngles {
   S sinw, cosw, sinm, cosm;
 };
 
+// The spine's terms in n0 and e0 alone: n0 / ke, its reciprocal, a1 = (ke/n0)^(2/3) and
+// beta0 (independent of the inclination, so a second warp can take them).
+template <class S>
+struct SpineA {
+  S n0k, x1, a1, b2, rb, b;
+};
+
 // Valid elements only (the caller screens non-finite input, e0 outside [0,1), n0 <= 0).
 template <class S>
-__device__ __forceinline__ void init_spine(const S el[7], const Geo& g, InitSpine<S>& sp) {
-  const S n0 = el[0], e0 = el[1], i0 = el[2];
-  const double k2 = 0.5 * g.j2;
-  sincos(i0, &sp.sini, &sp.cosi);
+__device__ __forceinline__ void init_spine_a(const S el[7], const Geo& g, SpineA<S>& sa) {
+  const S n0 = el[0], e0 = el[1];
+  sa.b2 = 1.0 - e0 * e0;
+  sa.rb = rsqrt(sa.b2);                       // 1 / beta0
+  sa.b = sa.b2 * sa.rb;
+  sa.n0k = n0 * g.inv_xke;                    // n0 / ke = 1 / x1
+  sa.x1 = 1.0 / sa.n0k;
+  sa.a1 = cbrt_pos(sa.x1 * sa.x1);            // (ke / n0)^(2/3); 1 / a1^2 = a1 (n0 / ke)^2
+}
+
+// The inclination terms, then the Kozai -> Brouwer recovery (needs SpineA).
+template <class S>
+__device__ __forceinline__ void init_spine_i(const S el[7], InitSpine<S>& sp) {
+  sincos(el[2], &sp.sini, &sp.cosi);
   sp.th2 = sp.cosi * sp.cosi;
   sp.x3thm1 = 3.0 * sp.th2 - 1.0;
   sp.x1mth2 = 1.0 - sp.th2;
   sp.x7thm1 = 7.0 * sp.th2 - 1.0;
-  sp.b2 = 1.0 - e0 * e0;
-  sp.rb = rsqrt(sp.b2);                       // 1 / beta0
-  sp.b = sp.b2 * sp.rb;
-  const double inv_xke = g.inv_xke;
+}
 
+template <class S>
+__device__ __forceinline__ void init_spine_b(const S el[7], const Geo& g, const SpineA<S>& sa,
+                                             InitSpine<S>& sp) {
+  const S n0 = el[0];
+  const double k2 = 0.5 * g.j2;
+  sp.b2 = sa.b2; sp.rb = sa.rb; sp.b = sa.b;
   // Kozai -> Brouwer mean motion and semi-major axis.
-  const S n0k = n0 * inv_xke;                 // n0 / ke = 1 / x1
-  const S x1 = 1.0 / n0k;
-  const S a1 = cbrt_pos(x1 * x1);             // (ke / n0)^(2/3); 1 / a1^2 = a1 (n0 / ke)^2
+  const S n0k = sa.n0k, a1 = sa.a1;
   const S c3b = 1.5 * k2 * sp.x3thm1 * (sp.rb * sp.rb * sp.rb);
   const S d1 = c3b * a1 * (n0k * n0k);
   const S a0 = a1 * (1.0 - d1 * (1.0 / 3.0) - d1 * d1 - (134.0 / 81.0) * d1 * d1 * d1);
@@ -268,10 +288,18 @@ __device__ __forceinline__ void init_spine(const S el[7], const Geo& g, InitSpin
   const S d0 = c3b * (ia0 * ia0);
   const S opd0 = 1.0 + d0;
   sp.n0pp = n0 / opd0;
-  const S xpp = x1 * opd0;                    // ke / n0''
+  const S xpp = sa.x1 * opd0;                 // ke / n0''
   sp.a0pp = cbrt_pos(xpp * xpp);              // (ke / n0'')^(2/3)
-  const S npk = sp.n0pp * inv_xke;
+  const S npk = sp.n0pp * g.inv_xke;
   sp.ia0pp = (sp.a0pp * sp.a0pp) * (npk * npk);   // 1 / a0'' = a0''^2 (n0'' / ke)^2
+}
+
+template <class S>
+__device__ __forceinline__ void init_spine(const S el[7], const Geo& g, InitSpine<S>& sp) {
+  SpineA<S> sa;
+  init_spine_a(el, g, sa);
+  init_spine_i(el, sp);
+  init_spine_b(el, g, sa, sp);
 }
 
 template <class S>
