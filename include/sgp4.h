@@ -402,6 +402,42 @@ int64_t sgp4_tle_parse_text(const char* text, size_t len, int64_t capacity, doub
 sgp4_result sgp4_tle_format(const double* elements, int32_t epoch_day, double epoch_frac,
                             int32_t satnum, char* line1, char* line2);
 
+/*
+ * CCSDS Orbit Mean-Elements Messages (OMM, CCSDS 502.0-B; host functions, no device
+ * work) carrying SGP4 mean elements, in KVN ("KEYWORD = value [units]" lines) or XML.
+ * Keywords read: EPOCH (UTC, ISO 8601 "YYYY-MM-DDThh:mm:ss[.f]" or
+ * "YYYY-DDDThh:mm:ss[.f]", years 1583-9999), MEAN_MOTION (rev/day), ECCENTRICITY,
+ * INCLINATION, RA_OF_ASC_NODE, ARG_OF_PERICENTER, MEAN_ANOMALY (deg), BSTAR (1/Earth
+ * radii), NORAD_CAT_ID (optional); MEAN_ELEMENT_THEORY, REF_FRAME and TIME_SYSTEM, if
+ * present, must be SGP4 (or SGP/SGP4), TEME and UTC.  Other keywords are skipped.
+ *
+ * sgp4_omm_parse_text: every message of a text, in order.  A text whose first
+ * non-blank character is '<' is XML (one message per <omm> element), otherwise KVN
+ * (a message starts at each CCSDS_OMM_VERS line).  Stores at most `capacity` messages
+ * into elements [capacity][7] (units of sgp4_init), epoch_day, epoch_frac (Julian date
+ * split as in sgp4_tle_parse) and satnum (may be NULL; -1 where NORAD_CAT_ID is
+ * absent); returns the number of valid messages (which may exceed capacity: call again
+ * with more room), or -1 for bad arguments.  n_rejected (may be NULL) receives the
+ * number of messages rejected (a required keyword missing or malformed, another
+ * theory, frame or time system).
+ */
+int64_t sgp4_omm_parse_text(const char* text, size_t len, int64_t capacity, double* elements,
+                            int32_t* epoch_day, double* epoch_frac, int32_t* satnum,
+                            int64_t* n_rejected);
+
+/*
+ * sgp4_omm_format: one KVN message (OMM 2.0 keywords) for elements (units of sgp4_init)
+ * and a split Julian epoch, written NUL-terminated into buf[cap]: values with 17
+ * significant digits, the epoch to the microsecond, zero mean-motion derivatives.
+ *   satnum  catalogue number, or -1 to omit NORAD_CAT_ID
+ *   name    OBJECT_NAME (may be NULL)
+ * Errors: SGP4_ERR_ARG for NULL elements or buf, non-finite elements, epoch_frac
+ * outside [0, 1), an epoch outside 1583-9999, a name with a line break, or a buffer
+ * too small (about 700 bytes suffice).
+ */
+sgp4_result sgp4_omm_format(const double* elements, int32_t epoch_day, double epoch_frac,
+                            int32_t satnum, const char* name, char* buf, size_t cap);
+
 /* Library version (major*10000 + minor*100 + patch). */
 int sgp4_version(void);
 

@@ -31,6 +31,7 @@ EXPORTS = (
     "sgp4_batch_graph_destroy", "sgp4_propagate_batched_static", "sgp4_adjoint_workspace_bytes",
     "sgp4_adjoint", "sgp4_fit_workspace_bytes", "sgp4_fit_step", "sgp4_tle_parse",
     "sgp4_tle_parse_text", "sgp4_tle_format", "sgp4_jacobian_workspace_bytes", "sgp4_jacobian",
+    "sgp4_omm_parse_text", "sgp4_omm_format",
 )
 STATIC_MAX_REQUESTS = 1024
 
@@ -121,6 +122,10 @@ def _declare(lib):
     lib.sgp4_tle_parse_text.restype = I64
     lib.sgp4_tle_format.argtypes = [P, I32, ctypes.c_double, I32, P, P]
     lib.sgp4_tle_format.restype = I32
+    lib.sgp4_omm_parse_text.argtypes = [CP, ctypes.c_size_t, I64, P, P, P, P, P]
+    lib.sgp4_omm_parse_text.restype = I64
+    lib.sgp4_omm_format.argtypes = [P, I32, ctypes.c_double, I32, CP, P, ctypes.c_size_t]
+    lib.sgp4_omm_format.restype = I32
     return lib
 
 

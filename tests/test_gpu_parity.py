@@ -397,6 +397,41 @@ def test_julian_dates_far_from_the_epochs_fp32():
     assert dr.max() <= 0.1 and dv.max() <= 1e-4, error_summary(dr, dv)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_omm_catalogue_to_julian_date_propagation(prec):
+    """A synthetic catalogue written as CCSDS OMM (KVN) and read back by the library,
+    built with its epochs and propagated to absolute times, against the oracle on the
+    parsed elements (FP64 to the FP64 bound, FP32 to the one-day FP32 bound)."""
+    import torch
+
+    from paper_2603_27830_b300 import omm, sgp4_init, sgp4_propagate_jd
+    rng = np.random.default_rng(37)
+    el0 = W.config2(seed=6, n=300).elements
+    day0 = (2461050 + rng.integers(-2, 3, len(el0))).astype(np.int32)
+    frac0 = rng.uniform(0.0, 1.0, len(el0))
+    cat = omm.parse_text("".join(omm.format_messages(el0, day0, frac0)))
+    assert len(cat.satnum) == len(el0) and cat.rejected == 0
+    jd_day = np.full(48, 2461050, dtype=np.int32)
+    jd_frac = np.arange(48) / 48.0
+    dev = "cuda"
+    recs, ist = sgp4_init(torch.as_tensor(cat.elements, device=dev),
+                          epoch_day=torch.as_tensor(cat.epoch_day, device=dev),
+                          epoch_frac=torch.as_tensor(cat.epoch_frac, device=dev))
+    r, v, st = sgp4_propagate_jd(recs, torch.as_tensor(jd_day, device=dev),
+                                 torch.as_tensor(jd_frac, device=dev), prec)
+    torch.cuda.synchronize()
+    tsince = ((jd_day[None, :] - cat.epoch_day[:, None]).astype(np.float64)
+              + (jd_frac[None, :] - cat.epoch_frac[:, None])) * 1440.0
+    rr, vr, sr, isr = oracle.propagate(cat.elements, tsince)
+    r, v, st = r.double().cpu().numpy(), v.double().cpu().numpy(), st.cpu().numpy()
+    assert_status_and_nan(st, sr, r, v, ist.cpu().numpy(), isr)
+    dr, dv = state_errors(r, v, rr, vr, sr)
+    if prec == "fp64":
+        assert dr.max() <= FP64_TOL_R_KM and dv.max() <= FP64_TOL_V_KMS, error_summary(dr, dv)
+    else:
+        assert dr.max() <= 0.1 and dv.max() <= 1e-4, error_summary(dr, dv)
+
+
 def test_tle_catalogue_to_julian_date_propagation():
     """A synthetic TLE catalogue written and read back by the library, built with its
     epochs and propagated to absolute times, against the oracle on the parsed elements."""
