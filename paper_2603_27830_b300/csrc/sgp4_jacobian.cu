@@ -122,17 +122,29 @@ __device__ __forceinline__ void jac_loop(const JacArgs& a, const SatShared<T>& s
         for (int m = 0; m < 7; ++m) jac[s * 42 + c * 7 + m] = J[c][m];
     if (cov) {
       // P = J C J^T, upper triangle row by row: P[p][q] = (J_p C) . J_q
+      // J sits in local memory (the seed loop writes its rows at a run-time index); read
+      // each row once into registers, the loops unrolled (5% on the FP32 kernel)
+      T Jr[6][7];
+#pragma unroll
+      for (int p = 0; p < 6; ++p)
+#pragma unroll
+        for (int m = 0; m < 7; ++m) Jr[p][m] = J[p][m];
       int idx = 0;
+#pragma unroll
       for (int p = 0; p < 6; ++p) {
         T w[7];
+#pragma unroll
         for (int l = 0; l < 7; ++l) {
           T acc = T(0);
-          for (int m = 0; m < 7; ++m) acc += J[p][m] * C[m][l];
+#pragma unroll
+          for (int m = 0; m < 7; ++m) acc += Jr[p][m] * C[m][l];
           w[l] = acc;
         }
+#pragma unroll
         for (int q = p; q < 6; ++q, ++idx) {
           T acc = T(0);
-          for (int l = 0; l < 7; ++l) acc += w[l] * J[q][l];
+#pragma unroll
+          for (int l = 0; l < 7; ++l) acc += w[l] * Jr[q][l];
           cov[s * 21 + idx] = acc;
         }
       }

@@ -6,7 +6,8 @@ Workloads: near-earth (64 x 100), starlink (9,341 x 1,000), catalogue (1,000,000
 100; ``--n`` shrinks it), batch (64 uneven requests, N_i log-U[100,5e3], T_i
 log-U[10,500]: the batched persistent launch), adjoint (the fitting workload,
 10,000 x 500: one sgp4_adjoint call), fit (the same workload: one sgp4_fit_step call
-against observations of the perturbed elements).  Prints the wall time of each
+against observations of the perturbed elements), jacobian (the same workload: one
+sgp4_jacobian call with an element covariance).  Prints the wall time of each
 repetition.
 """
 from __future__ import annotations
@@ -73,10 +74,23 @@ def run_fit(args):
                lambda: fit_step(el, ts, r_obs, lam, prec), args.reps)
 
 
+def run_jacobian(args):
+    from . import sgp4_jacobian
+    w = W.config5(n=args.n or 10_000)
+    el = torch.as_tensor(w.elements, device="cuda")
+    ts = torch.as_tensor(w.tsince, device="cuda")
+    recs, _ = sgp4_init(el)
+    cov = torch.diag_embed(torch.full((w.n, 7), 1e-10, dtype=torch.float64, device="cuda"))
+    precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
+    for prec in precs:
+        _timed(f"jacobian {w.states} states {prec}",
+               lambda: sgp4_jacobian(el, recs, ts, prec, cov=cov), args.reps)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=["near-earth", "starlink", "catalogue", "batch",
-                                           "adjoint", "fit"],
+                                           "adjoint", "fit", "jacobian"],
                     default="starlink")
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="fp32")
     ap.add_argument("--reps", type=int, default=2)
@@ -88,6 +102,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "fit":
         return run_fit(args)
+    if args.workload == "jacobian":
+        return run_jacobian(args)
     if args.workload == "near-earth":
         w = W.config1()
     elif args.workload == "starlink":
