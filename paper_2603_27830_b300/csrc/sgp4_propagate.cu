@@ -78,6 +78,7 @@ __device__ __forceinline__ void epoch_minutes(const RecordPtrs& rp, int64_t rec,
 // FP32, two states per thread (packed arithmetic, state32x2): unit u of [ubeg, uend)
 // is satellite j = u / Th, times i0 = u % Th and i1 = i0 + Th (Th = ceil(T / 2); i1 does
 // not exist for the last unit of an odd T), so both states share the record.
+template <bool kJd>
 __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
                                              const Range& rg, int64_t ubeg, int64_t uend,
                                              unsigned long long& nfix, const float2* split) {
@@ -105,7 +106,7 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
       const float2 a0 = split[it[0]], a1 = split[it[1]];
       th = make_float2(a0.x, a1.x);
       tl = make_float2(a0.y, a1.y);
-      if (rg.jd_day) {   // table of minutes from day jd0: subtract the record's epoch
+      if constexpr (kJd) {   // table of minutes from day jd0: subtract the record's epoch
         float eh, el;
         epoch_minutes(rp, rec, rg.jd0, eh, el);
         df_sub(a0.x, a0.y, eh, el, th.x, tl.x);
@@ -175,7 +176,7 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
 // read per state, no split table): the next unit's four times are loaded while this
 // unit computes (1 satellite x 1e7 times: 163 -> 126 us); a separate instantiation, as
 // the prefetch's registers slow the split-table path.
-template <bool kPre>
+template <bool kPre, bool kJd>
 __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
                                              const Range& rg, int64_t ubeg, int64_t uend,
                                              unsigned long long& nfix, const float2* split) {
@@ -227,14 +228,14 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
     };
     float th[4], tl[4];
     float eh = 0.0f, el = 0.0f;   // absolute times: the record's epoch from day jd0
-    if (split && rg.jd_day) epoch_minutes(rp, rec, rg.jd0, eh, el);
+    if (kJd && split) epoch_minutes(rp, rec, rg.jd0, eh, el);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (split) {
         const float2 a = split[it[k]];
         th[k] = a.x;
         tl[k] = a.y;
-        if (rg.jd_day) df_sub(a.x, a.y, eh, el, th[k], tl[k]);
+        if constexpr (kJd) df_sub(a.x, a.y, eh, el, th[k], tl[k]);
       } else {
         split_double(kPre ? tc[k] : tsince_at(it[k]), th[k], tl[k]);
       }
@@ -358,8 +359,10 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
 constexpr int kSplitMaxT = 6144;
 
 // kSpu: states per unit (FP32 2 or 4, FP64 1 or 2), chosen at launch; kPre: FP32
-// four-state units with times read per state, prefetched (run_range_x4).
-template <bool kFP32, int kSpu, bool kPre = false>
+// four-state units with times read per state, prefetched (run_range_x4); kJd: FP32 with
+// the split table of absolute times (each unit subtracts its record's epoch).  Separate
+// instantiations keep each path free of the others' code.
+template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
   extern __shared__ float2 s_split[];   // [t_count] when use_split
@@ -396,8 +399,9 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.status = a.status;
   unsigned long long nfix = 0;
   const float2* split = use_split ? s_split : nullptr;
-  if constexpr (kFP32 && kSpu == 4) run_range_x4<kPre>(a.rp, a.g, gf, rg, beg, end, nfix, split);
-  else if constexpr (kFP32) run_range_x2(a.rp, a.g, gf, rg, beg, end, nfix, split);
+  if constexpr (kFP32 && kSpu == 4)
+    run_range_x4<kPre, kJd>(a.rp, a.g, gf, rg, beg, end, nfix, split);
+  else if constexpr (kFP32) run_range_x2<kJd>(a.rp, a.g, gf, rg, beg, end, nfix, split);
   else run_units64<kSpu>(a.rp, a.g, rg, beg, end);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
@@ -452,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
     }
     rg.status = a.status + q.out_offset;
     // (no prefetch: tiles are short, and it measured 1% slower on the 256-request batch)
-    if constexpr (kFP32) run_range_x4<false>(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
+    if constexpr (kFP32) run_range_x4<false, false>(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
     else run_units64<2>(a.rp, a.g, rg, beg, end);
   }
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
@@ -467,7 +471,7 @@ int blocks_per_sm_of(K kernel, size_t dyn_smem = 0) {
   return bps > 0 ? bps : 1;
 }
 
-template <bool kFP32, int kSpu, bool kPre = false>
+template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false>
 cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   if (total == 0) return cudaSuccess;
@@ -477,13 +481,13 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   // split table so that the wave below is resident whatever the grid length.
   static int bps = 0;
   if (bps == 0)
-    bps = blocks_per_sm_of(propagate_kernel<kFP32, kSpu, kPre>,
+    bps = blocks_per_sm_of(propagate_kernel<kFP32, kSpu, kPre, kJd>,
                            kFP32 ? kSplitMaxT * sizeof(float2) : 0);
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
   const int64_t blocks = (total + chunk - 1) / chunk;
-  propagate_kernel<kFP32, kSpu, kPre><<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
+  propagate_kernel<kFP32, kSpu, kPre, kJd><<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
   return cudaGetLastError();
 }
 
@@ -495,8 +499,11 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
 bool fp32_units_of_four(int64_t T) { return T % 4 == 0 || T >= 48; }
 
 cudaError_t launch_fp32(const PropArgs& a, cudaStream_t stream) {
-  if (!fp32_units_of_four(a.t_count)) return launch_spu<true, 2>(a, stream);
-  const bool per_state = a.grid_per_sat || a.t_count > kSplitMaxT;   // minutes, no table
+  const bool per_state = a.grid_per_sat || a.t_count > kSplitMaxT;   // no split table
+  const bool jd_table = a.jd_day && !per_state;
+  if (!fp32_units_of_four(a.t_count))
+    return jd_table ? launch_spu<true, 2, false, true>(a, stream) : launch_spu<true, 2>(a, stream);
+  if (jd_table) return launch_spu<true, 4, false, true>(a, stream);
   if (per_state && !a.jd_day) return launch_spu<true, 4, true>(a, stream);
   return launch_spu<true, 4>(a, stream);
 }
