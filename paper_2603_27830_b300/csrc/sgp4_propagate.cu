@@ -1,9 +1,10 @@
 // Propagation kernels: independent (satellite, time) states (paper Sec. 2.2,
 // "Vectorisation": f(s, t) under a vmap over times composed with a vmap over
 // satellites).  A thread takes a unit of states of one satellite that share the
-// record: four (times i + k ceil(T/4)) in the FP32 kernels, as two pairs in packed FP32
-// arithmetic (run_range_x4, state32x2); two (times i and i + ceil(T/2)) in the FP64
-// kernels (run_units64, the two in turn on one load of the record).
+// record: in FP32 four (times i + k ceil(T/4)) as two pairs in packed arithmetic
+// (run_range_x4, state32x2), or one pair (run_range_x2) for short grids whose units of
+// four would be partly empty; in FP64 two (times i and i + ceil(T/2)) in turn on one
+// load of the record, or one for problems that fit one wave (run_units64).
 //   * a block walks a contiguous range of units, 128 per step, so consecutive steps of
 //     a thread stay on one satellite and its record stays in L1 (FP32) or registers
 //     (FP64);
@@ -38,7 +39,6 @@ constexpr int kThreads = 128;
 #define SGP4_MIN_BLOCKS_FP64 4
 #endif
 
-
 // One problem's view: its time grid, its first record and its output base.
 struct Range {
   const double* tsince;   // [T], or [n][T] when per_sat
@@ -52,7 +52,6 @@ struct Range {
   void* v;
   int32_t* status;
 };
-
 
 // a - b for double-floats (hi + lo, |lo| <= ulp(hi) / 2): Knuth's two-sum of the high
 // parts, the low parts added, the sum renormalised.  On the FP32 pipes; the absolute-time
@@ -97,7 +96,7 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
       if (rg.jd_day) {
         const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
         const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
-        return fma(1440.0, dfrac, (double)(dday * 1440));
+        return fma(1440.0, dfrac, (double)((long long)dday * 1440));
       }
       return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
     };
@@ -222,7 +221,7 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
       if (rg.jd_day) {
         const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
         const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
-        return fma(1440.0, dfrac, (double)(dday * 1440));
+        return fma(1440.0, dfrac, (double)((long long)dday * 1440));
       }
       return __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
     };
@@ -327,7 +326,7 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
       if (rg.jd_day) {
         const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
         const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
-        t = fma(1440.0, dfrac, (double)(dday * 1440));
+        t = fma(1440.0, dfrac, (double)((long long)dday * 1440));
       } else {
         t = __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
       }

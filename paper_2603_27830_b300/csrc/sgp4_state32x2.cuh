@@ -4,16 +4,18 @@
 // B300's FP32 instructions come in a packed form that applies one add, multiply or
 // FMA to a pair of floats (__fadd2_rn, __fmul2_rn, __ffma2_rn: two lanes of work per
 // issue slot, each lane rounded as its scalar instruction).  The FP32 propagation is
-// bound by instruction issue, so the kernel runs two states of the same satellite
-// (two times) per thread: the time-dependent values are pairs, the record's fields are
-// shared scalars, and every add, multiply and FMA of the state is one packed
-// instruction for both.  Transcendentals (SFU), compares, selects and the integer work
+// bound by instruction issue, so a pair of states of the same satellite (two times) is
+// computed together (the kernels run one or two pairs per thread): the time-dependent
+// values are pairs, the record's fields are shared scalars, and every add, multiply
+// and FMA of the state is one packed instruction for both.  Transcendentals (SFU), compares, selects and the integer work
 // stay per state.  The arithmetic is that of state32 (same formulation, guard bands and
 // status logic); the fusing of products into FMAs, the evaluation order of the drag
 // polynomials (Horner form) and the truncation of the small rotations and of the cosine
 // polynomial (each below 0.2 m) differ.  A record field enters a packed operation as a
-// pair of equal halves, so the formulas are arranged to need no negated fields and no
-// multiplications by -1 (each would be one more instruction per use).
+// pair of equal halves, so the formulas are arranged to avoid most negated fields and
+// multiplications by -1 (each is one more instruction per use); the few left are the
+// exact product error of the phase, the negated a_xN, a_yN and sin RAAN reused several
+// times, and two record fields.
 #pragma once
 
 #include "sgp4_device.cuh"
