@@ -223,7 +223,8 @@ __device__ __forceinline__ void fit_loop(const FitArgs& a, const SatShared<T>& s
       r[0] = T(slot[kNumAdj]); r[1] = T(slot[kNumAdj + 1]); r[2] = T(slot[kNumAdj + 2]);
     } else {
       const T rs = f.rk * sat.k.re;
-      r[0] = rs * f.Ux; r[1] = rs * f.Uy; r[2] = rs * f.Uz;
+      const Frame<T> fr = frame_get(f);
+      r[0] = rs * fr.Ux; r[1] = rs * fr.Uy; r[2] = rs * fr.Uz;
     }
     T res[3];
     for (int c = 0; c < 3; ++c) res[c] = r[c] - T(a.r_obs[s * 3 + c]);

@@ -81,14 +81,15 @@ __device__ __forceinline__ void jac_loop(const JacArgs& a, const SatShared<T>& s
       }
     } else {
       const T rs = f.rk * sat.k.re;
+      const Frame<T> fr = frame_get(f);
       if (r_out) {
-        r_out[s * 3 + 0] = rs * f.Ux; r_out[s * 3 + 1] = rs * f.Uy; r_out[s * 3 + 2] = rs * f.Uz;
+        r_out[s * 3 + 0] = rs * fr.Ux; r_out[s * 3 + 1] = rs * fr.Uy; r_out[s * 3 + 2] = rs * fr.Uz;
       }
       if (v_out) {
         const T vk = sat.k.vk;
-        v_out[s * 3 + 0] = vk * (f.rdotk * f.Ux + f.rfdotk * f.Vx);
-        v_out[s * 3 + 1] = vk * (f.rdotk * f.Uy + f.rfdotk * f.Vy);
-        v_out[s * 3 + 2] = vk * (f.rdotk * f.Uz + f.rfdotk * f.Vz);
+        v_out[s * 3 + 0] = vk * (f.rdotk * fr.Ux + f.rfdotk * fr.Vx);
+        v_out[s * 3 + 1] = vk * (f.rdotk * fr.Uy + f.rfdotk * fr.Vy);
+        v_out[s * 3 + 2] = vk * (f.rdotk * fr.Uz + f.rfdotk * fr.Vz);
       }
     }
     if (!jac && !cov) continue;

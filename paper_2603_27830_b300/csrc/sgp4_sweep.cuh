@@ -39,15 +39,32 @@ constexpr int kAdjMinBlocksFP32 = 6;
 // the propagation: a, e, a_xN, a_yN, E, p_L, r, u and the short-period terms).  The
 // FP32 kernels keep one per thread in shared memory (an odd number of 4-byte words, so
 // that the 32 threads of a warp hit 32 different banks).
+// The position and velocity unit vectors U, V and the rest of the output frame.
 template <class T>
-struct Fwd {
-  T tt, t2, t3, t4;
+struct Frame {
+  T mx, my, mz, Ux, Uy, Uz, Vx, Vy, Vz;
+};
+
+// Forward values that are cheap to recompute (the powers of t, the output frame): kept
+// by the FP64 sweeps (registers; their time is the FP64 unit's), recomputed by the FP32
+// ones (their time is the shared-memory traffic of the forward-value slot).
+template <class T>
+struct FwdKeep {};
+template <>
+struct FwdKeep<double> {
+  double t2, t3, t4;
+  Frame<double> fr;
+};
+
+template <class T>
+struct Fwd : FwdKeep<T> {
+  T tt;
   T sMdf, cMdf, c, sMM, cMM;   // sin/cos M_DF, 1 + eta cos M_DF, sin/cos(M_DF + dd)
   T tempa, templ, a, sqa, n, e, om, q, sw, cw, axn, ayn;
   T keep_e;                    // 0 where e was raised to 1e-6, else 1
   T sp, cp, ecosE, esinE, eL2, pL, rl, rdotl, sqp, rfdotl, betal, opb, w, aor, As, Ac;
   T sinu, cosu, sin2u, cos2u, k, kp, fac, rk, nk, rdotk, rfdotk;
-  T su, cu, sO, cO, si, ci, mx, my, mz, Ux, Uy, Uz, Vx, Vy, Vz;
+  T su, cu, sO, cO, si, ci;
   T pad;
 };
 static_assert(sizeof(Fwd<float>) % 8 == 4, "odd word count for conflict-free rows");
@@ -89,12 +106,29 @@ __device__ __forceinline__ RevC<float> rev_consts(const Rec32& rc, const GeoF& g
 __device__ __forceinline__ float inv_pos(float x) { return rcp_pos(x); }
 __device__ __forceinline__ double inv_pos(double x) { return 1.0 / x; }
 
-// The position and velocity unit vectors U, V and the rest of the output frame.
+// The output frame from the forward values' (sin, cos) pairs.
 template <class T>
-__device__ __forceinline__ void frame(Fwd<T>& f) {
-  f.mx = -f.sO * f.ci; f.my = f.cO * f.ci; f.mz = f.si;
-  f.Ux = f.mx * f.su + f.cO * f.cu; f.Uy = f.my * f.su + f.sO * f.cu; f.Uz = f.mz * f.su;
-  f.Vx = f.mx * f.cu - f.cO * f.su; f.Vy = f.my * f.cu - f.sO * f.su; f.Vz = f.mz * f.cu;
+__device__ __forceinline__ Frame<T> frame_of(const Fwd<T>& f) {
+  Frame<T> r;
+  r.mx = -f.sO * f.ci; r.my = f.cO * f.ci; r.mz = f.si;
+  r.Ux = r.mx * f.su + f.cO * f.cu; r.Uy = r.my * f.su + f.sO * f.cu; r.Uz = r.mz * f.su;
+  r.Vx = r.mx * f.cu - f.cO * f.su; r.Vy = r.my * f.cu - f.sO * f.su; r.Vz = r.mz * f.cu;
+  return r;
+}
+
+// The frame and the powers of t of a state, kept (FP64) or recomputed (FP32).
+template <class T>
+__device__ __forceinline__ Frame<T> frame_get(const Fwd<T>& f) {
+  if constexpr (sizeof(T) == 8) return f.fr;
+  else return frame_of(f);
+}
+template <class T>
+__device__ __forceinline__ void tpow_get(const Fwd<T>& f, T& t2, T& t3, T& t4) {
+  if constexpr (sizeof(T) == 8) {
+    t2 = f.t2; t3 = f.t3; t4 = f.t4;
+  } else {
+    t2 = f.tt * f.tt; t3 = t2 * f.tt; t4 = t3 * f.tt;
+  }
 }
 
 // Forward pass of one state in FP64: the formulation of state64 (angle reduction by
@@ -108,12 +142,13 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
   const bool isimp = rc.flags & kFlagIsimp;
   const double mdf = rc.m0 + rc.mdot * t;
   const double argpdf = rc.argp0 + rc.argpdot * t;
-  f.tt = t; f.t2 = t * t; f.t3 = f.t2 * t; f.t4 = f.t3 * t;
-  double raan = rc.raan0 + rc.raandot * t + rc.raan_cf * f.t2;
+  f.tt = t;
+  const auto t2 = t * t, t3 = t2 * t, t4 = t3 * t;
+  double raan = rc.raan0 + rc.raandot * t + rc.raan_cf * t2;
   double argp = argpdf;
   double tempa = 1.0 - rc.c1 * t;
   double tempe = rc.bc4 * t;
-  double templ = rc.l2 * f.t2;
+  double templ = rc.l2 * t2;
   f.sMdf = 0.0; f.cMdf = 0.0; f.c = 1.0; f.sMM = 0.0; f.cMM = 0.0;
   if (!isimp) {
     const double dargp = rc.argp_cf * t;
@@ -121,13 +156,13 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
     f.c = 1.0 + rc.eta * f.cMdf;
     const double dd = dargp + rc.m_cf * (f.c * f.c * f.c - rc.delm0);
     argp = argpdf - dd;
-    tempa = tempa - rc.d2 * f.t2 - rc.d3 * f.t3 - rc.d4 * f.t4;
+    tempa = tempa - rc.d2 * t2 - rc.d3 * t3 - rc.d4 * t4;
     double sdd, cdd;
     sincos_small64(dd, sdd, cdd);
     f.sMM = f.sMdf * cdd + f.cMdf * sdd;
     f.cMM = f.cMdf * cdd - f.sMdf * sdd;
     tempe = tempe + rc.bc5 * (f.sMM - rc.sinm0);
-    templ = templ + rc.l3 * f.t3 + f.t4 * (rc.l4 + t * rc.l5);
+    templ = templ + rc.l3 * t3 + t4 * (rc.l4 + t * rc.l5);
   }
   f.tempa = tempa;
   f.templ = templ;
@@ -199,7 +234,8 @@ __device__ __forceinline__ int forward64(const Rec64& rc, const Geo& g, double t
   rotate64(f.sO, f.cO, 1.5 * f.kp * rc.cosi * f.sin2u);
   f.si = rc.sini; f.ci = rc.cosi;
   rotate64(f.si, f.ci, 1.5 * f.kp * rc.cosi * rc.sini * f.cos2u);
-  frame(f);
+  f.t2 = t2; f.t3 = t3; f.t4 = t4;
+  f.fr = frame_of(f);
   return f.rk < 1.0 ? 6 : 0;
 }
 
@@ -213,10 +249,11 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
   if (rc.flags & kFlagN0ppNonPos) return 2;
   const bool isimp = rc.flags & kFlagIsimp;
   const float t = th;
-  f.tt = t; f.t2 = t * t; f.t3 = f.t2 * t; f.t4 = f.t3 * t;
+  f.tt = t;
+  const auto t2 = t * t, t3 = t2 * t, t4 = t3 * t;
   float tempa = 1.0f - rc.c1 * t;
   float tempe = rc.bc4 * t;
-  float templ = rc.l2 * f.t2;
+  float templ = rc.l2 * t2;
   float dd = 0.0f;
   f.sMdf = 0.0f; f.cMdf = 0.0f; f.c = 1.0f; f.sMM = 0.0f; f.cMM = 0.0f;
   if (!isimp) {
@@ -225,10 +262,10 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
     __sincosf(mdf, &f.sMdf, &f.cMdf);
     f.c = 1.0f + rc.eta * f.cMdf;
     dd = dargp + rc.mcf * (f.c * f.c * f.c - rc.delm0);
-    tempa = tempa - rc.d2 * f.t2 - rc.d3 * f.t3 - rc.d4 * f.t4;
+    tempa = tempa - rc.d2 * t2 - rc.d3 * t3 - rc.d4 * t4;
     __sincosf(mdf + dd, &f.sMM, &f.cMM);
     tempe = tempe + rc.bc5 * (f.sMM - rc.sinm0);
-    templ = templ + rc.l3 * f.t3 + f.t4 * (rc.l4 + t * rc.l5);
+    templ = templ + rc.l3 * t3 + t4 * (rc.l4 + t * rc.l5);
   }
   f.tempa = tempa;
   f.templ = templ;
@@ -252,7 +289,7 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
   y += s + rc.phi0l;
   y += wrap_rev(rc.n0ppr * templ);
   const float argp = wrap_rev(fmaf(rc.argpdr, t, rc.argp0r) - dd * kInvTwoPiF) * kTwoPiF;
-  const float raan = wrap_rev(fmaf(rc.raancfr, f.t2, fmaf(rc.raandr, t, rc.raan0r))) * kTwoPiF;
+  const float raan = wrap_rev(fmaf(rc.raancfr, t2, fmaf(rc.raandr, t, rc.raan0r))) * kTwoPiF;
 
   __sincosf(argp, &f.sw, &f.cw);
   f.axn = f.e * f.cw;
@@ -315,7 +352,6 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
   rotate_small(f.sO, f.cO, dO);
   f.si = rc.sini; f.ci = rc.cosi;
   rotate_small(f.si, f.ci, di);
-  frame(f);
   return f.rk < 1.0f ? 6 : 0;
 }
 
@@ -329,20 +365,23 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
                                         const T gv[3], Sink&& sink) {
   const T one = T(1), two = T(2), half = T(0.5), c15 = T(1.5);
   const T re = rc.re, vk = rc.vk;
+  T t2, t3, t4;
+  tpow_get(f, t2, t3, t4);
+  const Frame<T> fr = frame_get(f);
   // r = rk re U, v = vk (rdotk U + rfdotk V)
   const T Ubx = f.rk * re * gr[0] + vk * f.rdotk * gv[0];
   const T Uby = f.rk * re * gr[1] + vk * f.rdotk * gv[1];
   const T Ubz = f.rk * re * gr[2] + vk * f.rdotk * gv[2];
   const T Vbx = vk * f.rfdotk * gv[0], Vby = vk * f.rfdotk * gv[1], Vbz = vk * f.rfdotk * gv[2];
-  const T rkb = re * (gr[0] * f.Ux + gr[1] * f.Uy + gr[2] * f.Uz);
-  const T rdotkb = vk * (gv[0] * f.Ux + gv[1] * f.Uy + gv[2] * f.Uz);
-  const T rfdotkb = vk * (gv[0] * f.Vx + gv[1] * f.Vy + gv[2] * f.Vz);
+  const T rkb = re * (gr[0] * fr.Ux + gr[1] * fr.Uy + gr[2] * fr.Uz);
+  const T rdotkb = vk * (gv[0] * fr.Ux + gv[1] * fr.Uy + gv[2] * fr.Uz);
+  const T rfdotkb = vk * (gv[0] * fr.Vx + gv[1] * fr.Vy + gv[2] * fr.Vz);
   // U = M su + N cu, V = M cu - N su, M = (mx, my, mz), N = (cO, sO, 0)
   const T Mbx = Ubx * f.su + Vbx * f.cu, Mby = Uby * f.su + Vby * f.cu;
   const T Mbz = Ubz * f.su + Vbz * f.cu;
   const T Nbx = Ubx * f.cu - Vbx * f.su, Nby = Uby * f.cu - Vby * f.su;
-  const T sub = Ubx * f.mx + Uby * f.my + Ubz * f.mz - (Vbx * f.cO + Vby * f.sO);
-  const T cub = Ubx * f.cO + Uby * f.sO + (Vbx * f.mx + Vby * f.my + Vbz * f.mz);
+  const T sub = Ubx * fr.mx + Uby * fr.my + Ubz * fr.mz - (Vbx * f.cO + Vby * f.sO);
+  const T cub = Ubx * f.cO + Uby * f.sO + (Vbx * fr.mx + Vby * fr.my + Vbz * fr.mz);
   const T sOb = -Mbx * f.ci + Nby;
   const T cOb = Mby * f.ci + Nbx;
   const T cib = -Mbx * f.sO + Mby * f.cO;
@@ -460,15 +499,15 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
   const T tempab = ab * rc.a0pp * two * f.tempa;
   T mdfb = mm2b, argpdfb = argp1b;
   if (!rc.isimp) {
-    sink(aL3, templb * f.t3);
-    sink(aL4, templb * f.t4);
-    sink(aL5, templb * f.t4 * f.tt);
+    sink(aL3, templb * t3);
+    sink(aL4, templb * t4);
+    sink(aL5, templb * t4 * f.tt);
     sink(aBC5, tempeb * (f.sMM - rc.sinm0));
     const T sMMb = tempeb * rc.bc5;
     sink(aSinM0, -tempeb * rc.bc5);
-    sink(aD2, -tempab * f.t2);
-    sink(aD3, -tempab * f.t3);
-    sink(aD4, -tempab * f.t4);
+    sink(aD2, -tempab * t2);
+    sink(aD3, -tempab * t3);
+    sink(aD4, -tempab * t4);
     // mm1 = M_DF + dd carries sin(mm1); argp = argp_DF - dd; dd = argp_cf t + dm
     const T mm1b = mm2b + sMMb * f.cMM;
     mdfb = mm1b;
@@ -480,12 +519,12 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
     mdfb += -(cb * rc.eta) * f.sMdf;
     sink(aArgpCf, ddb * f.tt);
   }
-  sink(aL2, templb * f.t2);
+  sink(aL2, templb * t2);
   sink(aBC4, tempeb * f.tt);
   sink(aC1, -tempab * f.tt);
   sink(aRaan0, raankb);
   sink(aRaandot, raankb * f.tt);
-  sink(aRaanCf, raankb * f.t2);
+  sink(aRaanCf, raankb * t2);
   sink(aArgp0, argpdfb);
   sink(aArgpdot, argpdfb * f.tt);
   sink(aM0, mdfb);
@@ -516,15 +555,16 @@ static __device__ __noinline__ int adjoint_fallback(RecordPtrs rp, Geo g, int64_
   const double gv[3] = {gv0, gv1, gv2};
   for (int q = 0; q < kNumAdj; ++q) bar[q] = 0.0f;
   reverse(f, k, gr, gv, [&](int q, double v) { bar[q] = (float)v; });
+  const Frame<double> fr = frame_get(f);
   if (r) {
-    r[0] = (float)(f.rk * g.re * f.Ux);
-    r[1] = (float)(f.rk * g.re * f.Uy);
-    r[2] = (float)(f.rk * g.re * f.Uz);
+    r[0] = (float)(f.rk * g.re * fr.Ux);
+    r[1] = (float)(f.rk * g.re * fr.Uy);
+    r[2] = (float)(f.rk * g.re * fr.Uz);
   }
   if (v) {
-    v[0] = (float)(g.vkmps * (f.rdotk * f.Ux + f.rfdotk * f.Vx));
-    v[1] = (float)(g.vkmps * (f.rdotk * f.Uy + f.rfdotk * f.Vy));
-    v[2] = (float)(g.vkmps * (f.rdotk * f.Uz + f.rfdotk * f.Vz));
+    v[0] = (float)(g.vkmps * (f.rdotk * fr.Ux + f.rfdotk * fr.Vx));
+    v[1] = (float)(g.vkmps * (f.rdotk * fr.Uy + f.rfdotk * fr.Vy));
+    v[2] = (float)(g.vkmps * (f.rdotk * fr.Uz + f.rfdotk * fr.Vz));
   }
   return code;
 }
