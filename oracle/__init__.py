@@ -13,10 +13,14 @@ paper leaves open.
 Parity status of each part (pins live in ``tests/test_oracle_*.py``):
   * two-body geometry, Kepler solve, J2/J3/J4 periodics and secular rates: pinned
     (closed forms, bisection, numerical integration of the zonal force model);
-  * circular-orbit drag decay (C1 in the e=0, J2=0 limit): pinned by the power-law
-    density decay law;
-  * the eccentric drag terms C3, C4, C5, D2, D3, D4 and their t-polynomials:
-    parity unpinned beyond structure (no published values in reach).
+  * drag: C1 and the decay polynomials D2..D4, L2..L5 pinned as the Taylor
+    coefficients of the circular decay law; the e-dependence of C2 and the drag-only
+    part of C4 by orbit averages of Gauss's equations; C5 and the once-per-revolution
+    perigee/mean-anomaly term by harmonics of the same equations integrated along the
+    orbit; the quadratic node term by the chain rule on the J2 node rate;
+  * parity unpinned: C3 (drag with J3), the J2 part of C4, the second-order J2/J4
+    secular rates, the second-order Kozai->Brouwer recovery and the J3 long-period
+    mean-longitude term xlcof (no independent check reaches them).
 """
 from __future__ import annotations
 

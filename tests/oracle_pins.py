@@ -5,7 +5,9 @@ build in the mutation test) and returns a list of failure messages (empty = pass
 None of them re-types the oracle's formulas: they compare against textbook
 two-body motion, bisection, a numerical integration of the zonal (J2, J3, J4)
 gravity field, the decay law of a circular orbit in the power-law atmosphere the
-theory assumes, and physical invariants.
+theory assumes (its numerical integration and its Taylor series), Gauss's
+planetary equations for a tangential drag force averaged or integrated along the
+orbit, and physical invariants.
 """
 from __future__ import annotations
 
@@ -382,6 +384,253 @@ def pin_circular_drag_decay(lib):
     return fails
 
 
+# ---------------------------------------------------- drag on eccentric orbits (Gauss)
+def _orbit_samples(a, e, n_pts):
+    """Mean anomaly grid over one revolution (endpoint included), with the radius,
+    speed and cos(true anomaly) of the Keplerian ellipse at each point."""
+    M = np.linspace(0.0, 2.0 * math.pi, n_pts + 1)
+    E = M.copy()
+    for _ in range(50):
+        E = E - (E - e * np.sin(E) - M) / (1.0 - e * np.cos(E))
+    r = a * (1.0 - e * np.cos(E))
+    v = np.sqrt(XKE ** 2 * (2.0 / r - 1.0 / a))
+    cosf = (np.cos(E) - e) / (1.0 - e * np.cos(E))
+    return M, r, v, cosf
+
+
+def _gauss_drag_rates(a, e, bstar, s, q0, n_pts=40000):
+    """da/dt and de/dt of Gauss's equations for a purely tangential drag acceleration
+    -B* rho/rho0 |v| v, density ((q0 - s)/(r - s))^4 relative to rho0, along the
+    unperturbed ellipse: da/dt = 2 a^2 v T / mu and de/dt = 2 (e + cos f) T / v with
+    T = -B* rho/rho0 v^2.  Returns the instantaneous rates on the grid of
+    _orbit_samples and their averages over the mean anomaly (trapezoid rule on a
+    periodic integrand)."""
+    M, r, v, cosf = _orbit_samples(a, e, n_pts)
+    rho = ((q0 - s) / (r - s)) ** 4
+    dadt = -2.0 * a * a / XKE ** 2 * bstar * rho * v ** 3
+    dedt = -2.0 * bstar * rho * v * (e + cosf)
+    return M, dadt, dedt, dadt[:-1].mean(), dedt[:-1].mean()
+
+
+def pin_eccentric_drag_secular(lib):
+    """J2 = J3 = J4 = 0, small e: the theory's secular decay rates of the mean
+    semi-major axis and eccentricity agree with the orbit average of Gauss's
+    equations for its atmosphere to second order in e (the theory expands in
+    eta = a e / (a - s) and keeps the e-dependence of the density factor through
+    1/(1 - eta^2)^3.5)."""
+    fails = []
+    s = 1 + 78.0 / RE
+    q0 = 1 + 120.0 / RE
+    for alt_km in (500.0, 800.0):
+        a = 1 + alt_km / RE
+        n0 = XKE / a ** 1.5
+        P = 2.0 * math.pi / n0
+        for e in (0.001, 0.002, 0.004):
+            bstar = 1e-3
+            _, _, _, dadt_q, dedt_q = _gauss_drag_rates(a, e, bstar, s, q0)
+            el = np.array([[n0, e, 0.0, 0.0, 0.0, 0.0, bstar]])
+            mean = oracle.mean_elements(el, np.array([-1.0, 0.0, 1.0, P]), TWO_BODY, lib=lib)
+            am, em = mean[0, :, 0], mean[0, :, 1]
+            dadt = (am[2] - am[0]) / 2.0
+            dedt = (em[3] - em[1]) / P     # the periodic part returns after one period
+            ra, re_ = dadt / dadt_q - 1.0, dedt / dedt_q - 1.0
+            if abs(ra) > e * e + 2e-7:
+                fails.append(f"mean da/dt at {alt_km} km, e {e}: rel {ra:+.3e} from Gauss")
+            if abs(re_) > 0.5 * e * e + 1e-7:
+                fails.append(f"mean de/dt at {alt_km} km, e {e}: rel {re_:+.3e} from Gauss")
+    return fails
+
+
+def pin_drag_eccentricity_oscillation(lib):
+    """J2 = J3 = J4 = 0, small e: the once-per-revolution oscillation of the mean
+    eccentricity under drag (drag is strongest at perigee) matches the first
+    Fourier harmonic, in sin M, of e(M) integrated from Gauss's de/dt along the
+    orbit, to within 1.8 eta^2 relative (the size of the theory's own truncation)."""
+    fails = []
+    s = 1 + 78.0 / RE
+    q0 = 1 + 120.0 / RE
+    for alt_km in (500.0, 800.0):
+        a = 1 + alt_km / RE
+        n0 = XKE / a ** 1.5
+        P = 2.0 * math.pi / n0
+        for e in (0.0005, 0.001):
+            eta = a * e / (a - s)
+            bstar = 1e-4
+            M, _, dedt, _, _ = _gauss_drag_rates(a, e, bstar, s, q0, n_pts=20000)
+            de = np.concatenate([[0.0], np.cumsum(0.5 * (dedt[1:] + dedt[:-1]) * np.diff(M))])
+            de /= n0                                  # dM = n dt
+            per = de - de[-1] * M / (2.0 * math.pi)
+            amp = 2.0 * np.trapezoid(per * np.sin(M), M) / (2.0 * math.pi)
+            t = np.linspace(0.0, P, 401)
+            el = np.array([[n0, e, 0.0, 0.0, 0.0, 0.0, bstar]])
+            mean = oracle.mean_elements(el, t, TWO_BODY, lib=lib)
+            eo = mean[0, :, 1] - e
+            Mo = n0 * t
+            pero = eo - eo[-1] * t / P
+            amp_o = 2.0 * np.trapezoid(pero * np.sin(Mo), Mo) / (2.0 * math.pi)
+            rel = amp_o / amp - 1.0
+            if abs(rel) > 1.8 * eta * eta:
+                fails.append(f"e oscillation at {alt_km} km, e {e}: amplitude {amp_o:.6e} "
+                             f"vs {amp:.6e} (rel {rel:+.3e}, eta {eta:.4f})")
+    return fails
+
+
+def pin_drag_decay_series(lib):
+    """J2 = J3 = J4 = 0, e0 = 0: the theory's mean semi-major axis is a polynomial in
+    t (degree 4 inside the square) and its mean longitude one of degree 5.  Against a
+    tight numerical integration of the circular decay law da/dt = -2 B* sqrt(mu a)
+    ((q0 - s)/(a - s))^4 with dlambda/dt = sqrt(mu) a^-1.5, the residuals must be
+    the first omitted Taylor terms: growing as t^5 for a and t^6 for the longitude
+    (x32 and x64 per doubling of t).  A wrong t^2, t^3 or t^4 coefficient shows up
+    as a slower growth."""
+    from scipy.integrate import solve_ivp
+    fails = []
+    s = 1 + 78.0 / RE
+    q0 = 1 + 120.0 / RE
+    ts = np.array([500.0, 1000.0, 2000.0, 4000.0])
+    for alt_km, bstar in ((400.0, 5e-3), (600.0, 5e-2), (300.0, 1e-3)):
+        a0 = 1 + alt_km / RE
+        n0 = XKE / a0 ** 1.5
+        K = 2.0 * bstar * XKE * (q0 - s) ** 4
+
+        def rhs(_, y):
+            return [-K * math.sqrt(y[0]) / (y[0] - s) ** 4, XKE * y[0] ** -1.5 - n0]
+        sol = solve_ivp(rhs, (0.0, ts[-1]), [a0, 0.0], method="DOP853", rtol=1e-13,
+                        atol=1e-18, t_eval=ts)
+        el = np.array([[n0, 0.0, 0.0, 0.0, 0.0, 0.0, bstar]])
+        mean = oracle.mean_elements(el, ts, TWO_BODY, lib=lib)
+        res_a = mean[0, :, 0] - sol.y[0]
+        lam = mean[0, :, 3] + mean[0, :, 4] + mean[0, :, 5] - n0 * ts
+        res_l = np.array([math.remainder(x, 2.0 * math.pi) for x in lam]) - sol.y[1]
+        ga, gl = res_a[1:] / res_a[:-1], res_l[1:] / res_l[:-1]
+        if not np.all((ga > 26.0) & (ga < 40.0)):
+            fails.append(f"mean a residual growth at {alt_km} km: {ga} per doubling (t^5: 32)")
+        if not np.all((gl > 52.0) & (gl < 80.0)):
+            fails.append(f"mean longitude residual growth at {alt_km} km: {gl} (t^6: 64)")
+    return fails
+
+
+def pin_drag_decay_taylor(lib):
+    """J2 = J3 = J4 = 0, e0 = 0: the theory's decay coefficients are the Taylor
+    coefficients of the circular decay law.  a(t) = a0'' (1 - C1 t - D2 t^2 - D3 t^3
+    - D4 t^4)^2 must agree through t^4, and the mean longitude n0'' (t + L2 t^2 + ...
+    + L5 t^5) through t^5, with the Taylor series of the solution of
+    da/dt = f(a) = -2 B* sqrt(mu a) ((q0 - s)/(a - s))^4, dlambda/dt = sqrt(mu) a^-1.5.
+    For an autonomous equation the k-th time derivative of any g(a) is L^k g with
+    L g = g'(a) f(a); the derivatives are taken symbolically and evaluated in 40
+    digits (mpmath)."""
+    import mpmath
+    import sympy as sp
+    fails = []
+    A, B = sp.Symbol("A", positive=True), sp.Symbol("B")
+    digits = 40
+    s = sp.Integer(1) + sp.Integer(78) / sp.Float(RE, digits)
+    q0 = sp.Integer(1) + sp.Integer(120) / sp.Float(RE, digits)
+    xke = sp.Float(XKE, digits)
+    f = -2 * B * xke * sp.sqrt(A) * ((q0 - s) / (A - s)) ** 4
+    Lg, Lh = [], []
+    g = A                                  # L^k a  ->  k! * (t^k coefficient of a)
+    h = xke * A ** sp.Rational(-3, 2)      # L^k n  ->  (k+1)! * (t^(k+1) coeff of lambda)
+    for k in range(1, 6):
+        g = sp.diff(g, A) * f
+        Lg.append(sp.lambdify((A, B), g, "mpmath"))
+        Lh.append(sp.lambdify((A, B), h, "mpmath"))
+        h = sp.diff(h, A) * f
+    for alt_km, bstar in ((400.0, 5e-3), (600.0, 5e-2), (250.0, 1e-4), (900.0, 1e-1)):
+        a_er = 1 + alt_km / RE
+        n0 = XKE / a_er ** 1.5
+        el = np.array([[n0, 0.0, 0.0, 0.0, 0.0, 0.0, bstar]])
+        rec = oracle.records(el, TWO_BODY, lib=lib)
+        if rec["isimp"][0]:
+            fails.append(f"{alt_km} km: perigee above 220 km must take the full drag series")
+            continue
+        with mpmath.workdps(digits):
+            args = (mpmath.mpf(float(rec["a0pp"][0])), mpmath.mpf(bstar))
+            a_taylor = [float(Lg[k](*args)) / math.factorial(k + 1) for k in range(5)]
+            lam_taylor = [float(Lh[k](*args)) / math.factorial(k + 1) for k in range(5)]
+        a0pp, n0pp = float(rec["a0pp"][0]), float(rec["n0pp"][0])
+        C1, D2, D3, D4 = (float(rec[k][0]) for k in ("C1", "D2", "D3", "D4"))
+        tempa = np.polynomial.Polynomial([1.0, -C1, -D2, -D3, -D4])
+        model_a = (a0pp * tempa ** 2).coef
+        Ls = [1.0] + [float(rec[k][0]) for k in ("L2", "L3", "L4", "L5")]
+        for k in range(1, 5):
+            want = a_taylor[k - 1]
+            if abs(model_a[k] / want - 1) > 1e-9:
+                fails.append(f"{alt_km} km: t^{k} coefficient of a(t) {model_a[k]:.12e} "
+                             f"vs {want:.12e}")
+        for k in range(1, 6):
+            want, got = lam_taylor[k - 1], n0pp * Ls[k - 1]
+            if abs(got / want - 1) > 1e-9:
+                fails.append(f"{alt_km} km: t^{k} coefficient of the mean longitude {got:.12e} "
+                             f"vs {want:.12e}")
+    return fails
+
+def pin_drag_node_acceleration(lib):
+    """J2 only, e0 = 0: the first-order nodal rate -(3/2) J2 n cos i / p^2 goes as
+    a^-3.5, so while drag shrinks the mean orbit the node accelerates by
+    d2(RAAN)/dt2 = -(7/2) (RAAN rate / a) da/dt.  The theory's quadratic node term must
+    follow that chain rule applied to its own mean a(t) and node rate (within the
+    J2^2 part of the rate it does not carry over)."""
+    fails = []
+    h = 200.0
+    for alt_km, inc, bstar in ((400.0, 0.9, 1e-3), (600.0, 1.7, 1e-2), (300.0, 0.4, 2e-4)):
+        a_er = 1 + alt_km / RE
+        n0 = XKE / a_er ** 1.5
+        el = np.array([[n0, 0.0, inc, 1.0, 0.0, 0.0, bstar]])
+        mean = oracle.mean_elements(el, np.array([-h, 0.0, h]), J2_ONLY, lib=lib)
+        a, node = mean[0, :, 0], mean[0, :, 3]
+        rate = (node[2] - node[0]) / (2 * h)
+        dadt = (a[2] - a[0]) / (2 * h)
+        accel = (node[2] + node[0] - 2 * node[1]) / (h * h)
+        want = -3.5 * rate / a[1] * dadt
+        # the second-order J2 part of the rate, relative to the first-order one
+        tol = J2 * abs(4.0 - 19.0 * math.cos(inc) ** 2) / a[1] ** 2 + 2e-4
+        if abs(accel / want - 1) > tol:
+            fails.append(f"node acceleration at {alt_km} km, i {inc}: {accel:.6e} vs "
+                         f"{want:.6e} rad/min^2")
+    return fails
+
+
+def pin_drag_perigee_oscillation(lib):
+    """J2 = J3 = J4 = 0, small e: drag turns the perigee back and forth once per
+    revolution (Gauss: domega/dt = 2 sin f T / (e v) for a tangential force T), and
+    the theory moves the mean anomaly the opposite way by the same angle.  The cos M
+    harmonic of the theory's perigee must equal that of the integrated Gauss rate
+    times R_E / a: the theory's coefficient carries one Earth radius where the
+    Gauss estimate carries the semi-major axis.  The rest agrees to within 4 eta^2.
+    (The opposite shift of the mean anomaly leaves the mean longitude alone.)"""
+    fails = []
+    s = 1 + 78.0 / RE
+    q0 = 1 + 120.0 / RE
+    for alt_km in (500.0, 800.0):
+        a = 1 + alt_km / RE
+        n0 = XKE / a ** 1.5
+        P = 2.0 * math.pi / n0
+        for e in (0.0005, 0.001):
+            eta = a * e / (a - s)
+            bstar = 1e-4
+            M, r, v, cosf = _orbit_samples(a, e, 20000)
+            sinf = np.sqrt(1.0 - cosf * cosf) * np.sign(np.sin(M))
+            rho = ((q0 - s) / (r - s)) ** 4
+            dwdt = -2.0 * bstar * rho * v * sinf / e
+            dw = np.concatenate([[0.0], np.cumsum(0.5 * (dwdt[1:] + dwdt[:-1]) * np.diff(M))])
+            dw /= n0
+            per = dw - dw[-1] * M / (2.0 * math.pi)
+            amp = 2.0 * np.trapezoid(per * np.cos(M), M) / (2.0 * math.pi) / a
+            t = np.linspace(0.0, P, 401)
+            el = np.array([[n0, e, 0.0, 0.0, 0.0, 0.0, bstar]])
+            mean = oracle.mean_elements(el, t, TWO_BODY, lib=lib)
+            w = np.array([math.remainder(x, 2.0 * math.pi) for x in mean[0, :, 4]])
+            Mo = n0 * t
+            pero = w - w[-1] * t / P
+            amp_o = 2.0 * np.trapezoid(pero * np.cos(Mo), Mo) / (2.0 * math.pi)
+            rel = amp_o / amp - 1.0
+            if abs(rel) > 4.0 * eta * eta:
+                fails.append(f"perigee oscillation at {alt_km} km, e {e}: {amp_o:.6e} vs "
+                             f"{amp:.6e} (rel {rel:+.3e})")
+    return fails
+
+
 # ------------------------------------------------------------------ status codes
 def pin_status_codes(lib):
     """Constructed invalid inputs produce the documented codes, never a crash."""
@@ -423,9 +672,12 @@ def pin_status_codes(lib):
     return fails
 
 
+# cheapest first: the mutation test stops at the first pin that fails
 ALL_PINS = [
     pin_two_body, pin_two_body_invariants, pin_kepler, pin_first_order_rates,
-    pin_unkozai_critical_inclination, pin_zonal_integration, pin_secular_plane_drift,
-    pin_h_no_secular_trend, pin_circular_drag_decay, pin_status_codes,
-    pin_eccentricity_vector_evolution, pin_mean_a_third_law,
+    pin_unkozai_critical_inclination, pin_h_no_secular_trend, pin_circular_drag_decay,
+    pin_status_codes, pin_mean_a_third_law, pin_drag_eccentricity_oscillation,
+    pin_drag_decay_series, pin_eccentric_drag_secular, pin_drag_decay_taylor,
+    pin_drag_node_acceleration, pin_drag_perigee_oscillation,
+    pin_zonal_integration, pin_eccentricity_vector_evolution, pin_secular_plane_drift,
 ]

@@ -63,14 +63,28 @@ CAUGHT = [
     ("e validity", "if (m.e >= 1.0 || m.e < -0.001)", "if (m.e >= 1.0 || m.e < -0.1)"),
     ("decay code", "if (rk < 1.0) return 6;", "if (rk < 0.9) return 6;"),
     ("input e range", "(rc.e0 < 0.0 || rc.e0 >= 1.0)", "(rc.e0 < 0.0 || rc.e0 >= 2.0)"),
+    # drag on eccentric orbits and the higher-order decay polynomial
+    ("C2 eccentric term", "(1.0 + 1.5 * eta2 + e0eta", "(1.0 + 0.5 * eta2 + e0eta"),
+    ("C2 e0 eta term", "e0eta * (4.0 + eta2)", "e0eta * (3.0 + eta2)"),
+    ("psi^-3.5", "coef / pow(psi2, 3.5)", "coef / pow(psi2, 2.5)"),
+    ("C4 eta term", "rc.eta * (2.0 + 0.5 * eta2)", "rc.eta * (2.0 + 1.5 * eta2)"),
+    ("C4 e0 term", "rc.e0 * (0.5 + 2.0 * eta2)", "rc.e0 * (0.5 + 1.0 * eta2)"),
+    ("C5 factor", "(1.0 + 2.75 * (eta2 + e0eta)", "(1.0 + 1.75 * (eta2 + e0eta)"),
+    ("D2 factor", "rc.D2 = 4.0 * rc.a0pp", "rc.D2 = 3.0 * rc.a0pp"),
+    ("D3 factor", "(17.0 * rc.a0pp + rc.s)", "(7.0 * rc.a0pp + rc.s)"),
+    ("D4 s term", "(221.0 * rc.a0pp + 31.0 * rc.s)", "(221.0 * rc.a0pp + 13.0 * rc.s)"),
+    ("L3", "rc.L3 = rc.D2 + 2.0 * C1sq;", "rc.L3 = rc.D2 + 3.0 * C1sq;"),
+    ("L4", "10.0 * C1sq * rc.C1);", "12.0 * C1sq * rc.C1);"),
+    ("L5", "30.0 * C1sq * rc.D2", "20.0 * C1sq * rc.D2"),
+    ("raan drag factor", "rc.raan_cf = 3.5 * beta0sq", "rc.raan_cf = 2.5 * beta0sq"),
+    ("m_cf factor", "rc.m_cf = -(2.0 / 3.0) * coef", "rc.m_cf = -(1.0 / 3.0) * coef"),
+    ("drag M term sign", "R c = 1.0 + rc.eta * cos(M_df);", "R c = 1.0 - rc.eta * cos(M_df);"),
 ]
 
 # Terms that no independent check reaches (documented as parity-unpinned).
 UNPINNED = [
-    ("C2 eccentric term", "(1.0 + 1.5 * eta2 + e0eta", "(1.0 + 0.5 * eta2 + e0eta"),
+    # the J2 part of the drag eccentricity rate (the drag pins run without zonals)
     ("C4 cos 2w term", "* cos(2.0 * rc.argp0)));", "* sin(2.0 * rc.argp0)));"),
-    ("C5 factor", "(1.0 + 2.75 * (eta2 + e0eta)", "(1.0 + 1.75 * (eta2 + e0eta)"),
-    ("D3 factor", "(17.0 * rc.a0pp + rc.s)", "(7.0 * rc.a0pp + rc.s)"),
     ("Mdot second order", "(13.0 - 78.0 * theta2 + 137.0 * theta4)", "(13.0 - 78.0 * theta2 + 37.0 * theta4)"),
     # second-order terms of the Kozai -> Brouwer mean-motion recovery
     ("delta1 factor", "R delta1 = 1.5 * k2", "R delta1 = 0.75 * k2"),
@@ -81,6 +95,9 @@ UNPINNED = [
     ("xlcof (3+5cos)", "(3.0 + 5.0 * rc.cosi)", "(5.0 + 3.0 * rc.cosi)"),
     ("q = 1/(a(1-e^2))", "R q = 1.0 / (m.a * (1.0 - m.e * m.e));", "R q = 1.0 / (m.a * (1.0 + m.e * m.e));"),
     ("U drops long period", "+ q * rc.xlcof * axn;", ";"),
+    # the drag coupling with J3 (a secular perigee drift that needs J3, drag and e > 0
+    # together; the drag pins run without zonals)
+    ("C3 sign", "rc.C3 = -2.0 * coef", "rc.C3 = 2.0 * coef"),
 ]
 
 _BUILD_DIR = tempfile.mkdtemp(prefix="oracle_mutants_")
