@@ -18,9 +18,12 @@ Parity status of each part (pins live in ``tests/test_oracle_*.py``):
     part of C4 by orbit averages of Gauss's equations; C5 and the once-per-revolution
     perigee/mean-anomaly term by harmonics of the same equations integrated along the
     orbit; the quadratic node term by the chain rule on the J2 node rate;
-  * parity unpinned: C3 (drag with J3), the J2 part of C4, the second-order J2/J4
-    secular rates, the second-order Kozai->Brouwer recovery and the J3 long-period
-    mean-longitude term xlcof (no independent check reaches them).
+  * the node rate with its second-order J2 and J4 parts: pinned by the node of a
+    long numerical integration;
+  * parity unpinned: C3 (drag with J3), the J2 part of C4, the second-order J2 and
+    J4 parts of the mean-anomaly and perigee rates, the second-order Kozai->Brouwer
+    recovery and the J3 long-period mean-longitude term xlcof (no independent check
+    reaches them).
 """
 from __future__ import annotations
 

@@ -631,6 +631,45 @@ def pin_drag_perigee_oscillation(lib):
     return fails
 
 
+def pin_secular_node_rate(lib, days=2.0, tol=5e-5):
+    """B* = 0, e = 0.001: the mean nodal rate, with its second-order J2 and
+    first-order J4 parts (a few 1e-3 of the whole), equals the rate at which a
+    numerical integration of the zonal field started from the theory's state at
+    t = 0 moves its ascending node.  The node is read from the angular momentum at
+    each northward equator crossing, where the short-period node terms repeat, and a
+    straight line is fitted through the crossings."""
+    from scipy.integrate import solve_ivp
+    f = _zonal_accel_fn()
+    mu, R, j2, j3, j4 = ZONAL
+
+    def rhs(_t, y):
+        a = f(y[0], y[1], y[2], mu, R, j2, j3, j4)
+        return [y[3], y[4], y[5], a[0], a[1], a[2]]
+
+    def equator(_t, y):
+        return y[2]
+    equator.direction = 1.0
+
+    fails = []
+    for inc in (28.5, 97.6, 140.0):
+        el = np.array([[15.0 * REV_DAY, 0.001, math.radians(inc), 0.3, 1.0, 0.0, 0.0]])
+        r, v, st, _ = oracle.propagate(el, np.array([0.0]), ZONAL, threads=1, lib=lib)
+        if st[0, 0] != 0:
+            fails.append(f"node-rate case i={inc}: status {st[0, 0]}")
+            continue
+        sol = solve_ivp(rhs, (0.0, days * 86400.0), np.concatenate([r[0, 0], v[0, 0]]),
+                        method="DOP853", rtol=1e-12, atol=1e-9, events=equator)
+        tc, yc = sol.t_events[0] / 60.0, sol.y_events[0]
+        h = np.cross(yc[:, :3], yc[:, 3:])
+        node = np.unwrap(np.arctan2(h[:, 0], -h[:, 1]))
+        rate = np.polyfit(tc, node, 1)[0]
+        mean = oracle.mean_elements(el, np.array([0.0, 1440.0]), ZONAL, lib=lib)
+        rate_o = math.remainder(mean[0, 1, 3] - mean[0, 0, 3], 2 * math.pi) / 1440.0
+        if abs(rate_o / rate - 1) > tol:
+            fails.append(f"node rate i={inc}: {rate_o:.10e} vs integration {rate:.10e} rad/min")
+    return fails
+
+
 # ------------------------------------------------------------------ status codes
 def pin_status_codes(lib):
     """Constructed invalid inputs produce the documented codes, never a crash."""
@@ -680,4 +719,22 @@ ALL_PINS = [
     pin_drag_decay_series, pin_eccentric_drag_secular, pin_drag_decay_taylor,
     pin_drag_node_acceleration, pin_drag_perigee_oscillation,
     pin_zonal_integration, pin_eccentricity_vector_evolution, pin_secular_plane_drift,
+    pin_secular_node_rate,
 ]
+
+
+def first_failure(lib):
+    """Name and first message of the first pin that fails on ``lib``, else None."""
+    for pin in ALL_PINS:
+        try:
+            fails = pin(lib)
+        except Exception as exc:  # a crash counts as a failure
+            return f"{pin.__name__}: raised {exc!r}"
+        if fails:
+            return f"{pin.__name__}: {fails[0]}"
+    return None
+
+
+def first_failure_of_build(path):
+    """first_failure of the oracle library built at ``path`` (a worker-process entry)."""
+    return first_failure(oracle.load(path))
