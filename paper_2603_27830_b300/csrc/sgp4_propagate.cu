@@ -174,11 +174,16 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
 // pairs (k = 0, 2) and (k = 1, 3) on one load of the record.  kPre (grids in minutes
 // read per state, no split table): the next unit's four times are loaded while this
 // unit computes (1 satellite x 1e7 times: 163 -> 126 us); a separate instantiation, as
-// the prefetch's registers slow the split-table path.
-template <bool kPre, bool kJd>
+// the prefetch's registers slow the split-table path.  kCons (T a multiple of 4, a
+// split table, outputs 16-byte aligned): the unit's times are the consecutive
+// 4 i0 + k, so its r, v and status are 48, 48 and 16 contiguous bytes, written by
+// seven 16-byte stores instead of 28 scalar ones, and its four split times are two
+// 16-byte shared-memory loads.
+template <bool kPre, bool kJd, bool kCons = false>
 __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
                                              const Range& rg, int64_t ubeg, int64_t uend,
                                              unsigned long long& nfix, const float2* split) {
+  static_assert(!kCons || (!kPre && !kJd), "consecutive units take the minutes split table");
   const int tid = threadIdx.x;
   const int T = (int)rg.T;
   const int Tq = (T + 3) / 4;
@@ -201,10 +206,10 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
     int it[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const int i = i0 + k * Tq;
-      it[k] = i < T ? i : i0;
+      const int i = kCons ? 4 * i0 + k : i0 + k * Tq;
+      it[k] = kCons || i < T ? i : i0;
     }
-    const bool has3 = i0 + 3 * Tq < T;   // then all four exist
+    const bool has3 = kCons || i0 + 3 * Tq < T;   // then all four exist
     double tc[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) tc[k] = tn[k];
@@ -228,6 +233,12 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
     float th[4], tl[4];
     float eh = 0.0f, el = 0.0f;   // absolute times: the record's epoch from day jd0
     if (kJd && split) epoch_minutes(rp, rec, rg.jd0, eh, el);
+    if constexpr (kCons) {
+      const float4* s4 = reinterpret_cast<const float4*>(split) + 2 * i0;
+      const float4 a = s4[0], b = s4[1];
+      th[0] = a.x; tl[0] = a.y; th[1] = a.z; tl[1] = a.w;
+      th[2] = b.x; tl[2] = b.y; th[3] = b.z; tl[3] = b.w;
+    } else
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (split) {
@@ -245,8 +256,20 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
     state32x2(rc32, gf, make_float2(th[0], th[2]), make_float2(tl[0], tl[2]), rA, vA, cA);
     state32x2(rc32, gf, make_float2(th[1], th[3]), make_float2(tl[1], tl[3]), rB, vB, cB);
     auto ok = [](int c) { return (c == 0) | (c == 6); };
-    const int64_t idx0 = j * T + i0;
-    if (has3 & ok(cA[0]) & ok(cA[1]) & ok(cB[0]) & ok(cB[1])) {
+    const int64_t idx0 = j * T + (kCons ? 4 * i0 : i0);
+    const int64_t kstride = kCons ? 1 : Tq;   // index step between the unit's states
+    if (kCons && (ok(cA[0]) & ok(cA[1]) & ok(cB[0]) & ok(cB[1]))) {
+      // states k = 0..3 are (A.x, B.x, A.y, B.y): 12 floats of r, 12 of v, 4 codes
+      float4* gr = reinterpret_cast<float4*>(static_cast<float*>(rg.r) + idx0 * 3);
+      float4* gv = reinterpret_cast<float4*>(static_cast<float*>(rg.v) + idx0 * 3);
+      __stcs(gr + 0, make_float4(rA[0].x, rA[1].x, rA[2].x, rB[0].x));
+      __stcs(gr + 1, make_float4(rB[1].x, rB[2].x, rA[0].y, rA[1].y));
+      __stcs(gr + 2, make_float4(rA[2].y, rB[0].y, rB[1].y, rB[2].y));
+      __stcs(gv + 0, make_float4(vA[0].x, vA[1].x, vA[2].x, vB[0].x));
+      __stcs(gv + 1, make_float4(vB[1].x, vB[2].x, vA[0].y, vA[1].y));
+      __stcs(gv + 2, make_float4(vA[2].y, vB[0].y, vB[1].y, vB[2].y));
+      __stcs(reinterpret_cast<int4*>(rg.status + idx0), make_int4(cA[0], cB[0], cA[1], cB[1]));
+    } else if (!kCons && (has3 & ok(cA[0]) & ok(cA[1]) & ok(cB[0]) & ok(cB[1]))) {
       // all four present and valid (status 0 or 6): stores without branches or selects
       float* gr = static_cast<float*>(rg.r) + idx0 * 3;
       float* gv = static_cast<float*>(rg.v) + idx0 * 3;
@@ -266,12 +289,12 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
     } else {
       const float q = __int_as_float(0x7fc00000);
       for (int k = 0; k < 4; ++k) {
-        if (i0 + k * Tq >= T) break;
+        if (!kCons && i0 + k * Tq >= T) break;
         const float2* rr = (k & 1) ? rB : rA;
         const float2* vv = (k & 1) ? vB : vA;
         const bool hi = k >= 2;
         int cd = (k & 1) ? cB[hi] : cA[hi];
-        const int64_t idx = idx0 + k * Tq;
+        const int64_t idx = idx0 + k * kstride;
         float* gr = static_cast<float*>(rg.r) + idx * 3;
         float* gv = static_cast<float*>(rg.v) + idx * 3;
         if (cd == kRecomputeFP64) {
@@ -361,10 +384,10 @@ constexpr int kSplitMaxT = 6144;
 // four-state units with times read per state, prefetched (run_range_x4); kJd: FP32 with
 // the split table of absolute times (each unit subtracts its record's epoch).  Separate
 // instantiations keep each path free of the others' code.
-template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false>
+template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false, bool kCons = false>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
-  extern __shared__ float2 s_split[];   // [t_count] when use_split
+  extern __shared__ __align__(16) float2 s_split[];   // [t_count] when use_split
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
@@ -398,8 +421,9 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.status = a.status;
   unsigned long long nfix = 0;
   const float2* split = use_split ? s_split : nullptr;
+  if (kCons && !use_split) return;   // (the launch takes kCons only with a split table)
   if constexpr (kFP32 && kSpu == 4)
-    run_range_x4<kPre, kJd>(a.rp, a.g, gf, rg, beg, end, nfix, split);
+    run_range_x4<kPre, kJd, kCons>(a.rp, a.g, gf, rg, beg, end, nfix, split);
   else if constexpr (kFP32) run_range_x2<kJd>(a.rp, a.g, gf, rg, beg, end, nfix, split);
   else run_units64<kSpu>(a.rp, a.g, rg, beg, end);
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
@@ -470,7 +494,7 @@ int blocks_per_sm_of(K kernel, size_t dyn_smem = 0) {
   return bps > 0 ? bps : 1;
 }
 
-template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false>
+template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false, bool kCons = false>
 cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   if (total == 0) return cudaSuccess;
@@ -480,13 +504,14 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   // split table so that the wave below is resident whatever the grid length.
   static int bps = 0;
   if (bps == 0)
-    bps = blocks_per_sm_of(propagate_kernel<kFP32, kSpu, kPre, kJd>,
+    bps = blocks_per_sm_of(propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>,
                            kFP32 ? kSplitMaxT * sizeof(float2) : 0);
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
   const int64_t blocks = (total + chunk - 1) / chunk;
-  propagate_kernel<kFP32, kSpu, kPre, kJd><<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
+  propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>
+      <<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
   return cudaGetLastError();
 }
 
@@ -504,6 +529,10 @@ cudaError_t launch_fp32(const PropArgs& a, cudaStream_t stream) {
     return jd_table ? launch_spu<true, 2, false, true>(a, stream) : launch_spu<true, 2>(a, stream);
   if (jd_table) return launch_spu<true, 4, false, true>(a, stream);
   if (per_state && !a.jd_day) return launch_spu<true, 4, true>(a, stream);
+  auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+  if (!per_state && !a.jd_day && a.t_count % 4 == 0 && al16(a.r) && al16(a.v) &&
+      al16(a.status))
+    return launch_spu<true, 4, false, false, true>(a, stream);
   return launch_spu<true, 4>(a, stream);
 }
 
