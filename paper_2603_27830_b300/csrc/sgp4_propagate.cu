@@ -290,22 +290,28 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
       const float q = __int_as_float(0x7fc00000);
       for (int k = 0; k < 4; ++k) {
         if (!kCons && i0 + k * Tq >= T) break;
-        const float2* rr = (k & 1) ? rB : rA;
-        const float2* vv = (k & 1) ? vB : vA;
-        const bool hi = k >= 2;
-        int cd = (k & 1) ? cB[hi] : cA[hi];
+        // state k is lane k >> 1 of pair A (k even) or B (k odd), picked with selects:
+        // a run-time index into the register arrays would put them in local memory
+        const bool odd = k & 1, hi = k >= 2;
+        auto pick = [&](const float2& a, const float2& b) {
+          const float2 p = odd ? b : a;
+          return hi ? p.y : p.x;
+        };
+        int cd = odd ? (hi ? cB[1] : cB[0]) : (hi ? cA[1] : cA[0]);
+        const int ik = kCons ? 4 * i0 + k : i0 + k * Tq;
         const int64_t idx = idx0 + k * kstride;
         float* gr = static_cast<float*>(rg.r) + idx * 3;
         float* gv = static_cast<float*>(rg.v) + idx * 3;
         if (cd == kRecomputeFP64) {
-          cd = state64_fallback(rp, g, rec, tsince_at(it[k]), gr, gv);
+          cd = state64_fallback(rp, g, rec, tsince_at(ik), gr, gv);
           ++nfix;
           if (cd != 0 && cd != 6) { gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q; }
         } else {
           const bool bad = cd != 0 && cd != 6;
+#pragma unroll
           for (int c = 0; c < 3; ++c) {
-            __stcs(gr + c, bad ? q : (hi ? rr[c].y : rr[c].x));
-            __stcs(gv + c, bad ? q : (hi ? vv[c].y : vv[c].x));
+            __stcs(gr + c, bad ? q : pick(rA[c], rB[c]));
+            __stcs(gv + c, bad ? q : pick(vA[c], vB[c]));
           }
         }
         __stcs(rg.status + idx, cd);
