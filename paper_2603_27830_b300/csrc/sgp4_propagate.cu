@@ -174,16 +174,16 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
 // pairs (k = 0, 2) and (k = 1, 3) on one load of the record.  kPre (grids in minutes
 // read per state, no split table): the next unit's four times are loaded while this
 // unit computes (1 satellite x 1e7 times: 163 -> 126 us); a separate instantiation, as
-// the prefetch's registers slow the split-table path.  kCons (T a multiple of 4, a
-// split table, outputs 16-byte aligned): the unit's times are the consecutive
-// 4 i0 + k, so its r, v and status are 48, 48 and 16 contiguous bytes, written by
-// seven 16-byte stores instead of 28 scalar ones, and its four split times are two
-// 16-byte shared-memory loads.
+// the prefetch's registers slow the split-table path.  kCons (T a multiple of 4, grids
+// in minutes, 16-byte aligned arrays): the unit's times are the consecutive 4 i0 + k,
+// so its r, v and status are 48, 48 and 16 contiguous bytes, written by seven 16-byte
+// stores instead of 28 scalar ones, and its four times are two 16-byte loads (of the
+// split table, or of the grid with kPre).
 template <bool kPre, bool kJd, bool kCons = false>
 __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
                                              const Range& rg, int64_t ubeg, int64_t uend,
                                              unsigned long long& nfix, const float2* split) {
-  static_assert(!kCons || (!kPre && !kJd), "consecutive units take the minutes split table");
+  static_assert(!kCons || !kJd, "consecutive units take grids in minutes");
   const int tid = threadIdx.x;
   const int T = (int)rg.T;
   const int Tq = (T + 3) / 4;
@@ -191,10 +191,17 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
   int i0 = (int)((ubeg + tid) - j * Tq);
   const int jstep = kThreads / Tq, istep = kThreads - jstep * Tq;
   auto fetch = [&](int64_t jj, int ii0, double out[4]) {
+    if constexpr (kCons) {   // four consecutive times: two 16-byte loads
+      const double2* p = reinterpret_cast<const double2*>(
+          rg.per_sat ? rg.tsince + jj * T + 4 * ii0 : rg.tsince + 4 * ii0);
+      const double2 a = __ldg(p), b = __ldg(p + 1);
+      out[0] = a.x; out[1] = a.y; out[2] = b.x; out[3] = b.y;
+    } else {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int i = ii0 + k * Tq < T ? ii0 + k * Tq : ii0;
-      out[k] = __ldg(rg.per_sat ? rg.tsince + jj * T + i : rg.tsince + i);
+      for (int k = 0; k < 4; ++k) {
+        const int i = ii0 + k * Tq < T ? ii0 + k * Tq : ii0;
+        out[k] = __ldg(rg.per_sat ? rg.tsince + jj * T + i : rg.tsince + i);
+      }
     }
   };
   double tn[4] = {0.0, 0.0, 0.0, 0.0};
@@ -233,7 +240,7 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
     float th[4], tl[4];
     float eh = 0.0f, el = 0.0f;   // absolute times: the record's epoch from day jd0
     if (kJd && split) epoch_minutes(rp, rec, rg.jd0, eh, el);
-    if constexpr (kCons) {
+    if constexpr (kCons && !kPre) {
       const float4* s4 = reinterpret_cast<const float4*>(split) + 2 * i0;
       const float4 a = s4[0], b = s4[1];
       th[0] = a.x; tl[0] = a.y; th[1] = a.z; tl[1] = a.w;
@@ -427,7 +434,7 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   rg.status = a.status;
   unsigned long long nfix = 0;
   const float2* split = use_split ? s_split : nullptr;
-  if (kCons && !use_split) return;   // (the launch takes kCons only with a split table)
+  if (kCons && !kPre && !use_split) return;   // (the launch takes this only with a split table)
   if constexpr (kFP32 && kSpu == 4)
     run_range_x4<kPre, kJd, kCons>(a.rp, a.g, gf, rg, beg, end, nfix, split);
   else if constexpr (kFP32) run_range_x2<kJd>(a.rp, a.g, gf, rg, beg, end, nfix, split);
@@ -534,11 +541,13 @@ cudaError_t launch_fp32(const PropArgs& a, cudaStream_t stream) {
   if (!fp32_units_of_four(a.t_count))
     return jd_table ? launch_spu<true, 2, false, true>(a, stream) : launch_spu<true, 2>(a, stream);
   if (jd_table) return launch_spu<true, 4, false, true>(a, stream);
-  if (per_state && !a.jd_day) return launch_spu<true, 4, true>(a, stream);
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
-  if (!per_state && !a.jd_day && a.t_count % 4 == 0 && al16(a.r) && al16(a.v) &&
-      al16(a.status))
-    return launch_spu<true, 4, false, false, true>(a, stream);
+  const bool cons = !a.jd_day && a.t_count % 4 == 0 && al16(a.r) && al16(a.v) &&
+                    al16(a.status) && (!per_state || al16(a.tsince));
+  if (per_state && !a.jd_day)
+    return cons ? launch_spu<true, 4, true, false, true>(a, stream)
+                : launch_spu<true, 4, true>(a, stream);
+  if (cons) return launch_spu<true, 4, false, false, true>(a, stream);
   return launch_spu<true, 4>(a, stream);
 }
 

@@ -182,15 +182,54 @@ def test_partial_units(T, prec):
         _check_fp32(el, t, 1.0, 1e-3)
 
 
+@pytest.mark.parametrize("T", [77, 80])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_per_satellite_grid(prec):
+def test_per_satellite_grid(prec, T):
+    """Per-satellite grids: FP32 units of four strided times (T = 77) or four
+    consecutive times read as two 16-byte loads (T = 80)."""
     rng = np.random.default_rng(3)
     el = W.catalogue_elements(rng, 300, invalid_frac=0.02)
-    t = np.sort(rng.uniform(-720, 2880, (300, 77)), axis=1)
+    t = np.sort(rng.uniform(-720, 2880, (300, T)), axis=1)
     if prec == "fp64":
         _check_fp64(el, t)
     else:
         _check_fp32(el, t, 1.0, 1e-3)
+
+
+@pytest.mark.parametrize("T", [8192, 8194])
+def test_long_shared_grid_fp32(T):
+    """A shared grid longer than the per-block split table: times read per state with
+    the next unit's prefetched, in consecutive (T = 8192) or strided (T = 8194) units."""
+    rng = np.random.default_rng(T)
+    el = W.catalogue_elements(rng, 5, invalid_frac=0.0)
+    t = np.sort(rng.uniform(-720, 2880, T))
+    _check_fp32(el, t, 1.0, 1e-3)
+
+
+def test_unaligned_per_satellite_grid_fp32():
+    """A grid view 8 bytes off a 16-byte boundary takes the strided units (the
+    consecutive ones read the grid with 16-byte loads); against the oracle.  (The two
+    unit layouts pair different states, and a pair shares its Newton step count, so
+    their last bits may differ; the statuses may not.)"""
+    import torch
+
+    from paper_2603_27830_b300 import sgp4_init, sgp4_propagate
+    rng = np.random.default_rng(9)
+    el = W.catalogue_elements(rng, 40, invalid_frac=0.05)
+    t = np.sort(rng.uniform(-720, 2880, (40, 80)), axis=1)
+    flat = torch.empty(40 * 80 + 1, dtype=torch.float64, device="cuda")
+    flat[1:] = torch.as_tensor(t.ravel(), device="cuda")
+    tv = flat[1:].view(40, 80)
+    assert tv.data_ptr() % 16 == 8
+    recs, ist = sgp4_init(torch.as_tensor(el, device="cuda"))
+    r, v, st = sgp4_propagate(recs, tv, "fp32")
+    r_al, v_al, st_al = sgp4_propagate(recs, tv.clone(), "fp32")
+    rr, vr, sr, isr = oracle.propagate(el, t)
+    r, v, st = r.double().cpu().numpy(), v.double().cpu().numpy(), st.cpu().numpy()
+    assert_status_and_nan(st, sr, r, v, ist.cpu().numpy(), isr)
+    assert np.array_equal(st, st_al.cpu().numpy())
+    dr, dv = state_errors(r, v, rr, vr, sr)
+    assert dr.max() <= 1.0 and dv.max() <= 1e-3, error_summary(dr, dv)
 
 
 def test_empty_inputs():
@@ -458,7 +497,7 @@ def test_tle_catalogue_to_julian_date_propagation():
     tsince = ((jd_day[None, :] - cat.epoch_day[:, None]).astype(np.float64)
               + (jd_frac[None, :] - cat.epoch_frac[:, None])) * 1440.0
     rr, vr, sr, isr = oracle.propagate(cat.elements, tsince)
-    r, v, st = r.cpu().numpy(), v.cpu().numpy(), st.cpu().numpy()
+    r, v, st = r.double().cpu().numpy(), v.double().cpu().numpy(), st.cpu().numpy()
     assert_status_and_nan(st, sr, r, v, ist.cpu().numpy(), isr)
     dr, dv = state_errors(r, v, rr, vr, sr)
     # tsince rounds differently on the device (fma) and here: ~1e-12 min, ~1e-9 km
