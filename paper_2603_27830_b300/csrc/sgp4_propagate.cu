@@ -74,13 +74,86 @@ __device__ __forceinline__ void epoch_minutes(const RecordPtrs& rp, int64_t rec,
   split_double(fma(1440.0, __ldg(rp.f64 + kEpochFrac * rp.stride + rec), 1440.0 * d), h, l);
 }
 
+// Guard-band states (kRecomputeFP64) are not recomputed inside the FP32 loops: a call
+// of the out-of-line FP64 state there made the loops spill registers (7-13% of their
+// time).  The loop queues the state's index in shared memory and marks its status;
+// after the loop the block recomputes the queued states in FP64 (fix_queued).  A block
+// that met more than kFixCap of them rescans its own units for the mark instead.
+constexpr int kFixCap = 256;
+struct FixQueue {
+  int64_t idx[kFixCap];   // state index within the range, j * T + i
+  int n;                  // states queued (above kFixCap: the queue overflowed)
+};
+
+__device__ __forceinline__ void queue_fix(FixQueue* fq, int32_t* status, int64_t idx) {
+  const int slot = atomicAdd(&fq->n, 1);
+  if (slot < kFixCap) fq->idx[slot] = idx;
+  __stcs(status + idx, kRecomputeFP64);
+}
+
+// Index within the range of state k of unit u, or -1 where the unit has no state k:
+// kSpu = 4 with consecutive times (4 i0 + k) or strided ones (i0 + k ceil(T/4)), kSpu = 2
+// strided (i0 + k ceil(T/2)).
+template <int kSpu, bool kCons>
+struct UnitMap {
+  int T, Tu;   // times, units per satellite
+  __device__ int64_t operator()(int64_t u, int k) const {
+    const int64_t j = u / Tu;
+    const int i0 = (int)(u - j * Tu);
+    const int i = kCons ? 4 * i0 + k : i0 + k * Tu;
+    return i < T ? j * T + i : -1;
+  }
+};
+
+// After the FP32 loop over units [ubeg, uend) of range rg and a __syncthreads: the
+// queued guard-band states in FP64, their r, v (NaN for codes 1, 2, 4) and status.
+// Adds the block's count to nfix (thread 0).
+template <int kSpu, bool kCons>
+__device__ __noinline__ void fix_queued(const RecordPtrs& rp, const Geo& g, const Range& rg,
+                                        const FixQueue* fq, int64_t ubeg, int64_t uend,
+                                        unsigned long long& nfix) {
+  const int n = fq->n;
+  if (n == 0) return;
+  const int T = (int)rg.T;
+  const float q = __int_as_float(0x7fc00000);
+  auto fix = [&](int64_t idx) {
+    const int64_t j = idx / T;
+    const int i = (int)(idx - j * T);
+    const int64_t rec = rg.sat0 + j;
+    double t;
+    if (rg.jd_day) {
+      const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
+      const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
+      t = fma(1440.0, dfrac, (double)((long long)dday * 1440));
+    } else {
+      t = __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
+    }
+    float* gr = static_cast<float*>(rg.r) + idx * 3;
+    float* gv = static_cast<float*>(rg.v) + idx * 3;
+    const int cd = state64_fallback(rp, g, rec, t, gr, gv);
+    if (cd != 0 && cd != 6) { gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q; }
+    __stcs(rg.status + idx, cd);
+  };
+  if (n <= kFixCap) {
+    for (int e = threadIdx.x; e < n; e += kThreads) fix(fq->idx[e]);
+  } else {
+    const UnitMap<kSpu, kCons> um{T, (T + kSpu - 1) / kSpu};
+    for (int64_t u = ubeg + threadIdx.x; u < uend; u += kThreads)
+      for (int k = 0; k < kSpu; ++k) {
+        const int64_t idx = um(u, k);
+        if (idx >= 0 && __ldcg(rg.status + idx) == kRecomputeFP64) fix(idx);
+      }
+  }
+  if (threadIdx.x == 0) nfix += (unsigned long long)n;
+}
+
 // FP32, two states per thread (packed arithmetic, state32x2): unit u of [ubeg, uend)
 // is satellite j = u / Th, times i0 = u % Th and i1 = i0 + Th (Th = ceil(T / 2); i1 does
 // not exist for the last unit of an odd T), so both states share the record.
 template <bool kJd>
-__device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
+__device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const GeoF& gf,
                                              const Range& rg, int64_t ubeg, int64_t uend,
-                                             unsigned long long& nfix, const float2* split) {
+                                             FixQueue* fq, const float2* split) {
   const int tid = threadIdx.x;
   const int T = (int)rg.T;            // <= INT32_MAX (checked by the API)
   const int Th = (T + 1) / 2;
@@ -143,12 +216,12 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
       const int64_t idx = j * T + it[l];
       float* gr = static_cast<float*>(rg.r) + idx * 3;
       float* gv = static_cast<float*>(rg.v) + idx * 3;
-      int cd = code[l];
-      if (cd == kRecomputeFP64) {
-        cd = state64_fallback(rp, g, rec, tsince_at(it[l]), gr, gv);
-        ++nfix;
-        if (cd != 0 && cd != 6) { gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q; }
-      } else {
+      const int cd = code[l];
+      if (cd == kRecomputeFP64) {   // r, v and status written after the loop
+        queue_fix(fq, rg.status, idx);
+        continue;
+      }
+      {
         const bool bad = cd != 0 && cd != 6;
         const float rv[3] = {l ? r2[0].y : r2[0].x, l ? r2[1].y : r2[1].x, l ? r2[2].y : r2[2].x};
         const float vv[3] = {l ? v2[0].y : v2[0].x, l ? v2[1].y : v2[1].x, l ? v2[2].y : v2[2].x};
@@ -180,9 +253,9 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const Geo& g,
 // stores instead of 28 scalar ones, and its four times are two 16-byte loads (of the
 // split table, or of the grid with kPre).
 template <bool kPre, bool kJd, bool kCons = false>
-__device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g, const GeoF& gf,
+__device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const GeoF& gf,
                                              const Range& rg, int64_t ubeg, int64_t uend,
-                                             unsigned long long& nfix, const float2* split) {
+                                             FixQueue* fq, const float2* split) {
   static_assert(!kCons || !kJd, "consecutive units take grids in minutes");
   const int tid = threadIdx.x;
   const int T = (int)rg.T;
@@ -304,16 +377,15 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const Geo& g,
           const float2 p = odd ? b : a;
           return hi ? p.y : p.x;
         };
-        int cd = odd ? (hi ? cB[1] : cB[0]) : (hi ? cA[1] : cA[0]);
-        const int ik = kCons ? 4 * i0 + k : i0 + k * Tq;
+        const int cd = odd ? (hi ? cB[1] : cB[0]) : (hi ? cA[1] : cA[0]);
         const int64_t idx = idx0 + k * kstride;
+        if (cd == kRecomputeFP64) {   // r, v and status written after the loop
+          queue_fix(fq, rg.status, idx);
+          continue;
+        }
         float* gr = static_cast<float*>(rg.r) + idx * 3;
         float* gv = static_cast<float*>(rg.v) + idx * 3;
-        if (cd == kRecomputeFP64) {
-          cd = state64_fallback(rp, g, rec, tsince_at(ik), gr, gv);
-          ++nfix;
-          if (cd != 0 && cd != 6) { gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q; }
-        } else {
+        {
           const bool bad = cd != 0 && cd != 6;
 #pragma unroll
           for (int c = 0; c < 3; ++c) {
@@ -401,10 +473,12 @@ template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false, bool kCons 
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
   extern __shared__ __align__(16) float2 s_split[];   // [t_count] when use_split
+  __shared__ FixQueue s_fq;
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
+  if (kFP32 && threadIdx.x == 0) s_fq.n = 0;
   const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
   const int32_t jd0 = a.jd_day ? __ldg(a.jd_day) : 0;
   if (use_split) {
@@ -418,8 +492,8 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
       split_double(t, h, l);
       s_split[k] = make_float2(h, l);
     }
-    __syncthreads();
   }
+  if (kFP32) __syncthreads();   // the split table and the queue's count
   const GeoF gf = a.gf;
   Range rg;
   rg.tsince = a.tsince;
@@ -435,11 +509,15 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   unsigned long long nfix = 0;
   const float2* split = use_split ? s_split : nullptr;
   if (kCons && !kPre && !use_split) return;   // (the launch takes this only with a split table)
-  if constexpr (kFP32 && kSpu == 4)
-    run_range_x4<kPre, kJd, kCons>(a.rp, a.g, gf, rg, beg, end, nfix, split);
-  else if constexpr (kFP32) run_range_x2<kJd>(a.rp, a.g, gf, rg, beg, end, nfix, split);
-  else run_units64<kSpu>(a.rp, a.g, rg, beg, end);
-  if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
+  if constexpr (kFP32) {
+    if constexpr (kSpu == 4) run_range_x4<kPre, kJd, kCons>(a.rp, gf, rg, beg, end, &s_fq, split);
+    else run_range_x2<kJd>(a.rp, gf, rg, beg, end, &s_fq, split);
+    __syncthreads();
+    fix_queued<kSpu, kCons>(a.rp, a.g, rg, &s_fq, beg, end, nfix);
+    if (a.fixups && nfix) atomicAdd(a.fixups, nfix);
+  } else {
+    run_units64<kSpu>(a.rp, a.g, rg, beg, end);
+  }
 }
 
 // Persistent batched kernel: tiles of `tile_states` consecutive states of one
@@ -450,11 +528,15 @@ template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     batched_kernel(BatchArgs a) {
   __shared__ unsigned long long s_tile;
+  __shared__ FixQueue s_fq;
   const GeoF gf = a.gf;
   const int64_t total_tiles = a.tile_start[a.n_req];
   unsigned long long nfix = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(a.counter, 1ULL);
+    if (threadIdx.x == 0) {
+      s_tile = atomicAdd(a.counter, 1ULL);
+      s_fq.n = 0;
+    }
     __syncthreads();
     const int64_t tile = (int64_t)s_tile;
     __syncthreads();
@@ -492,8 +574,14 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
     }
     rg.status = a.status + q.out_offset;
     // (no prefetch: tiles are short, and it measured 1% slower on the 256-request batch)
-    if constexpr (kFP32) run_range_x4<false, false>(a.rp, a.g, gf, rg, beg, end, nfix, nullptr);
-    else run_units64<2>(a.rp, a.g, rg, beg, end);
+    if constexpr (kFP32) {
+      run_range_x4<false, false>(a.rp, gf, rg, beg, end, &s_fq, nullptr);
+      __syncthreads();
+      fix_queued<4, false>(a.rp, a.g, rg, &s_fq, beg, end, nfix);
+      __syncthreads();   // the queue is reset with the next tile
+    } else {
+      run_units64<2>(a.rp, a.g, rg, beg, end);
+    }
   }
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
 }
@@ -516,9 +604,16 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   // Resident blocks per SM of this kernel (same on every B300), taken with the largest
   // split table so that the wave below is resident whatever the grid length.
   static int bps = 0;
-  if (bps == 0)
+  if (bps == 0) {
+    if (kFP32) {   // the 48 KB split table beside the static guard-band queue
+      const cudaError_t e = cudaFuncSetAttribute(propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)(kSplitMaxT * sizeof(float2)));
+      if (e != cudaSuccess) return e;
+    }
     bps = blocks_per_sm_of(propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>,
                            kFP32 ? kSplitMaxT * sizeof(float2) : 0);
+  }
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;

@@ -88,6 +88,36 @@ def test_batched_against_oracle(precision):
             assert dr.max() <= tol, error_summary(dr, dv)
 
 
+def test_batched_guard_band_queue_overflow_fp32():
+    """Requests whose every state is a guard-band state (inclination within 1e-5 rad
+    of 180 degrees): tiles of 4,096 states overflow the block's 256-entry queue and are
+    rescanned; tiles of 512 do not."""
+    import math
+
+    from paper_2603_27830_b300 import make_batch
+    rng = np.random.default_rng(21)
+    probs = []
+    for k in range(6):
+        n = int(rng.integers(50, 200))
+        el = W.catalogue_elements(rng, n, invalid_frac=0.0)
+        if k % 2 == 0:
+            el[:, 2] = math.pi - 1e-5
+            el[:, 1] = rng.uniform(0.03, 0.08, n)
+        probs.append((el, np.sort(rng.uniform(-720.0, 2880.0, int(rng.integers(20, 120))))))
+    b = make_batch(probs)
+    for tile in (512, 4096):
+        r, v, st, _ = _run_batched(b, "fp32", tile=tile)
+        r, v, st = r.double().cpu().numpy(), v.double().cpu().numpy(), st.cpu().numpy()
+        for sat0, n, t0, T, out0 in b.requests:
+            rr, vr, sr, _ = oracle.propagate(b.elements[sat0:sat0 + n], b.tsince[t0:t0 + T])
+            sl = slice(out0, out0 + n * T)
+            rg, vg, sg = r[sl].reshape(n, T, 3), v[sl].reshape(n, T, 3), st[sl].reshape(n, T)
+            assert_status_and_nan(sg, sr, rg, vg)
+            dr, dv = state_errors(rg, vg, rr, vr, sr)
+            if dr.size:
+                assert dr.max() <= 1.0, error_summary(dr, dv)
+
+
 def test_tile_size_does_not_change_results():
     import torch
     b = _small_batch(seed=2)

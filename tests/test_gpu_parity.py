@@ -232,6 +232,42 @@ def test_unaligned_per_satellite_grid_fp32():
     assert dr.max() <= 1.0 and dv.max() <= 1e-3, error_summary(dr, dv)
 
 
+def _near_retrograde_equatorial(rng, n):
+    """Inclinations within 1e-5 rad of 180 degrees: the J3 long-period term of U
+    (factor 1 / (1 + cos i)) exceeds a radian, so the FP32 path recomputes every state
+    of these satellites in FP64."""
+    return np.column_stack([rng.uniform(14.0, 15.5, n) * 2 * math.pi / 1440.0,
+                            rng.uniform(0.03, 0.08, n), np.full(n, math.pi - 1e-5),
+                            rng.uniform(0, 2 * math.pi, (n, 3)), rng.uniform(1e-5, 1e-4, n)])
+
+
+@pytest.mark.parametrize("T,per_sat,n", [(7, False, 24000), (100, False, 600), (97, False, 600),
+                                         (80, True, 600)])
+def test_guard_band_queue_overflow_fp32(T, per_sat, n):
+    """Most states guard-band states: blocks queue more of them than the queue holds
+    (256) and rescan their units for the mark; units of two (T = 7; a block holds more
+    than 256 states only beyond one wave of units, hence the 24,000 satellites), four
+    consecutive (100) or strided (97) times, and a per-satellite grid (80)."""
+    rng = np.random.default_rng(T)
+    el = _near_retrograde_equatorial(rng, n)
+    t = (np.sort(rng.uniform(-720, 2880, (n, T)), axis=1) if per_sat
+         else np.linspace(0.0, 1440.0, T))
+    summ = _check_fp32(el, t, 1.0, 1e-3)
+    assert summ["fp64_fixups"] > 0.6 * n * T, summ
+
+
+def test_guard_band_states_mixed_into_a_catalogue_fp32():
+    """A few all-guard-band satellites among ordinary ones: queues that stay within
+    their capacity, next to blocks that overflow."""
+    rng = np.random.default_rng(11)
+    el = W.catalogue_elements(rng, 2000, invalid_frac=0.02)
+    pick = rng.choice(2000, 40, replace=False)
+    el[pick] = _near_retrograde_equatorial(rng, 40)
+    t = np.linspace(-100.0, 2000.0, 64)
+    summ = _check_fp32(el, t, 1.0, 1e-3)
+    assert summ["fp64_fixups"] >= 0.6 * 40 * 64, summ
+
+
 def test_empty_inputs():
     import torch
 
