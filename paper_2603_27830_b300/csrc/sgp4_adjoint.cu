@@ -52,11 +52,23 @@ struct AdjArgs {
 };
 
 
+// Guard-band states of the FP32 sweep are queued (their time index) and swept in FP64
+// after the loop: a call of the out-of-line FP64 sweep inside the loop made it spill
+// registers (472 bytes of spill stores).  With more than kAdjFixCap of them the block
+// runs the FP32 forward over the satellite's times again to find them.
+constexpr int kAdjFixCap = 256;
+struct AdjFixQueue {
+  int i[kAdjFixCap];
+  int n;   // states queued (above kAdjFixCap: the queue overflowed)
+};
+
 // The states of satellite j handled by this thread: forward, reverse sweep, and the
-// field adjoints summed into acc.  f is the thread's forward-value slot.
+// field adjoints summed into acc.  f is the thread's forward-value slot; fq the block's
+// guard-band queue (FP32).
 template <class T>
 __device__ __forceinline__ void prop_loop(const AdjArgs& a, const SatShared<T>& sat,
-                                          Fwd<T>& f, T (&acc)[kNumAdj], int64_t j) {
+                                          Fwd<T>& f, T (&acc)[kNumAdj], int64_t j,
+                                          AdjFixQueue* fq) {
   const T* gr = static_cast<const T*>(a.grad_r);
   const T* gv = static_cast<const T*>(a.grad_v);
   for (int64_t i = threadIdx.x; i < a.T; i += kAdjThreads) {
@@ -73,14 +85,9 @@ __device__ __forceinline__ void prop_loop(const AdjArgs& a, const SatShared<T>& 
       split_double(t, th, tl);
       const int code = forward32(sat.rc, a.gf, th, tl, f);
       reload_barrier();
-      if (code == kRecomputeFP64) {
-        float* bar = reinterpret_cast<float*>(&f);   // the slot holds the 33 adjoints
-        if (usable(adjoint_fallback(a.rp, a.g, j, t, g_r[0], g_r[1], g_r[2], g_v[0], g_v[1],
-                                    g_v[2], bar, nullptr))) {
-#pragma unroll
-          for (int q = 0; q < kNumAdj; ++q) acc[q] += bar[q];
-        }
-        reload_barrier();
+      if (code == kRecomputeFP64) {   // swept in FP64 after the loop (adj_fix_queued)
+        const int slot = atomicAdd(&fq->n, 1);
+        if (slot < kAdjFixCap) fq->i[slot] = (int)i;
       } else if (usable(code)) {
         reverse(f, sat.k, g_r, g_v, add);
       }
@@ -90,31 +97,69 @@ __device__ __forceinline__ void prop_loop(const AdjArgs& a, const SatShared<T>& 
   }
 }
 
+// After prop_loop, the thread's sums written to its row of the forward-value slots and
+// a __syncthreads: the FP64 sweeps of satellite j's queued guard-band states, added to
+// the row (nothing else is live across the out-of-line sweep, so the loop keeps its
+// registers).
+__device__ __forceinline__ void adj_fix_queued(const AdjArgs& a, const SatShared<float>& sat,
+                                               const AdjFixQueue* fq, float* row, int64_t j) {
+  const int n = fq->n;
+  if (n == 0) return;
+  const float* gr = static_cast<const float*>(a.grad_r);
+  const float* gv = static_cast<const float*>(a.grad_v);
+  const bool over = n > kAdjFixCap;
+  const int64_t cnt = over ? a.T : n;
+  for (int64_t e = threadIdx.x; e < cnt; e += kAdjThreads) {
+    const int64_t i = over ? e : fq->i[e];
+    const double t = a.per_sat ? __ldg(a.tsince + j * a.T + i) : __ldg(a.tsince + i);
+    if (over) {   // find the guard-band states again (a forward in a local slot)
+      Fwd<float> fl;
+      float th, tl;
+      split_double(t, th, tl);
+      if (forward32(sat.rc, a.gf, th, tl, fl) != kRecomputeFP64) continue;
+    }
+    const int64_t s = j * a.T + i;
+    float g_r[3], g_v[3];
+    for (int c = 0; c < 3; ++c) {
+      g_r[c] = gr ? gr[s * 3 + c] : 0.0f;
+      g_v[c] = gv ? gv[s * 3 + c] : 0.0f;
+    }
+    adjoint_fallback(a.rp, a.g, j, t, g_r[0], g_r[1], g_r[2], g_v[0], g_v[1], g_v[2], row,
+                     nullptr, nullptr, true);
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP32 : 1)
     adjoint_prop_kernel(AdjArgs a) {
   __shared__ T part[kNumAdj][kAdjWarps];
   __shared__ SatShared<T> sat;
   __shared__ Fwd<T> sfwd[FwdSlot<T>::kRows];
+  __shared__ AdjFixQueue s_fq;
   const int tid = threadIdx.x;
   const int64_t j = blockIdx.x;
-  if (tid == 0) load_sat(a.rp, a.g, a.gf, j, sat);
+  if (tid == 0) {
+    load_sat(a.rp, a.g, a.gf, j, sat);
+    s_fq.n = 0;
+  }
   __syncthreads();
   T acc[kNumAdj];
 #pragma unroll
   for (int q = 0; q < kNumAdj; ++q) acc[q] = T(0);
   if constexpr (sizeof(T) == 4) {
-    prop_loop(a, sat, sfwd[tid], acc, j);
+    prop_loop(a, sat, sfwd[tid], acc, j, &s_fq);
     // Block sum through the forward-value slots, free now: each thread writes its 33
-    // sums to its row, then 3 x 33 threads sum the columns in three interleaved parts
-    // (rows of 65 words: conflict-free).  A warp-shuffle tree cost 165 shuffles and adds
-    // per thread, spread over only T / 128 states.
+    // sums to its row (where the FP64 sweeps of the guard-band states add theirs), then
+    // 3 x 33 threads sum the columns in three interleaved parts (rows of 65 words:
+    // conflict-free).  A warp-shuffle tree cost 165 shuffles and adds per thread, spread
+    // over only T / 128 states.
     constexpr int kParts = 3;
     static_assert(kNumAdj * kParts <= kAdjThreads && kParts <= kAdjWarps, "reduction layout");
-    __syncthreads();
     float* row = reinterpret_cast<float*>(&sfwd[tid]);
 #pragma unroll
     for (int q = 0; q < kNumAdj; ++q) row[q] = acc[q];
+    __syncthreads();   // (also: every state queued)
+    adj_fix_queued(a, sat, &s_fq, row, j);
     __syncthreads();
     if (tid < kNumAdj * kParts) {
       const int c = tid % kNumAdj, p0 = tid / kNumAdj;
@@ -130,7 +175,7 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
     }
   } else {
     Fwd<T> f;
-    prop_loop(a, sat, f, acc, j);
+    prop_loop(a, sat, f, acc, j, nullptr);
 #pragma unroll
     for (int q = 0; q < kNumAdj; ++q) warp_partial(acc[q], q, part);
     __syncthreads();

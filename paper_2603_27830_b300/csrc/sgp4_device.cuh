@@ -309,8 +309,8 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   return rk < 1.0 ? 6 : 0;
 }
 
-// Out-of-line FP64 recomputation of one state for the FP32 path's guard band
-// (rarely taken; kept out of line so the FP32 kernel's registers stay small).
+// Out-of-line FP64 recomputation of one guard-band state (the record build's status at
+// t = 0; the propagation kernels queue theirs and recompute them after their loops).
 static __device__ __noinline__ int state64_fallback(RecordPtrs rp, Geo g, int64_t j, double t,
                                                     float r[3], float v[3]) {
   const Rec64 rc = load_rec64(rp, j);

@@ -540,12 +540,13 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, cons
 __device__ __forceinline__ bool usable(int code) { return code == 0 || code == 6; }
 
 // FP64 forward and reverse sweeps of one state for the FP32 kernels (guard-band
-// states), for the seed (g_r, g_v): writes the 33 field adjoints to bar and, if r and
-// v are not null, the position (km) and velocity (km/s).  Out of line: rarely taken.
+// states), for the seed (g_r, g_v): writes the 33 field adjoints to bar (adds them to
+// it with accumulate) and, if r and v are not null, the position (km) and velocity
+// (km/s).  Out of line: rarely taken.
 static __device__ __noinline__ int adjoint_fallback(RecordPtrs rp, Geo g, int64_t j, double t,
                                                     float gr0, float gr1, float gr2, float gv0,
                                                     float gv1, float gv2, float* bar, float* r,
-                                                    float* v = nullptr) {
+                                                    float* v = nullptr, bool accumulate = false) {
   const Rec64 rc = load_rec64(rp, j);
   Fwd<double> f;
   const int code = forward64(rc, g, t, f);
@@ -553,8 +554,9 @@ static __device__ __noinline__ int adjoint_fallback(RecordPtrs rp, Geo g, int64_
   const RevC<double> k = rev_consts(rc, g);
   const double gr[3] = {gr0, gr1, gr2};
   const double gv[3] = {gv0, gv1, gv2};
-  for (int q = 0; q < kNumAdj; ++q) bar[q] = 0.0f;
-  reverse(f, k, gr, gv, [&](int q, double v) { bar[q] = (float)v; });
+  if (!accumulate)
+    for (int q = 0; q < kNumAdj; ++q) bar[q] = 0.0f;
+  reverse(f, k, gr, gv, [&](int q, double v) { bar[q] += (float)v; });
   const Frame<double> fr = frame_get(f);
   if (r) {
     r[0] = (float)(f.rk * g.re * fr.Ux);

@@ -80,6 +80,28 @@ def test_adjoint_fp32_matches_oracle_jacobian(case):
     _compare(g, ref, 5e-3, 2e-4)
 
 
+@pytest.mark.parametrize("T", [100, 400])
+def test_adjoint_fp32_guard_band_states(T):
+    """Inclinations within 1e-5 rad of 180 degrees make most FP32 states guard-band
+    states, swept in FP64 after the block's loop: from its queue (T = 100) or, past the
+    queue's 256 entries, by finding them again (T = 400); against the oracle.  The i0
+    column is left out: its terms in d/di0 of 1 / (1 + cos i0) are not resolved by the
+    FP32 record build's dual numbers this close to the pole (1 + cos i0 rounds to 0 in
+    FP32), which is a property of the FP32 path, not of the sweeps tested here."""
+    rng = np.random.default_rng(30 + T)
+    n = 24
+    el = np.column_stack([rng.uniform(14.0, 15.5, n) * REV, rng.uniform(0.03, 0.08, n),
+                          np.full(n, math.pi - 1e-5), rng.uniform(0, 2 * math.pi, (n, 3)),
+                          rng.uniform(1e-5, 1e-4, n)])
+    t = np.linspace(0.0, 1440.0, T)
+    gr = rng.normal(size=(n, T, 3))
+    gv = rng.normal(size=(n, T, 3)) * 100.0
+    g = _gpu_adjoint(el, t, gr, gv, "fp32")
+    ref = _oracle_vjp(el, t, gr, gv)
+    cols = [0, 1, 3, 4, 5, 6]
+    _compare(g[:, cols], ref[:, cols], 5e-3, 2e-4)
+
+
 def test_adjoint_fp64_matches_central_differences():
     """Scalar loss sum(w . r) on a few satellites: adjoint vs central differences of
     the plain oracle (no dual numbers involved)."""
