@@ -81,6 +81,47 @@ def test_jacobian_and_covariance_match_the_oracle(case, prec):
     assert np.all(np.isnan(P[~ok]))
 
 
+@pytest.mark.parametrize("T", [100, 400])
+def test_jacobian_fp32_guard_band_states(T):
+    """Inclinations within 1e-5 rad of 180 degrees: most FP32 states are guard-band
+    states, done through the FP64 sweeps.  The i0 column is left out (and given no
+    variance): d/di0 of 1 / (1 + cos i0) is not resolved by the FP32 record build's dual
+    numbers this close to the pole."""
+    import math
+    rng = np.random.default_rng(50 + T)
+    n = 16
+    el = np.column_stack([rng.uniform(14.0, 15.5, n) * W.REV_PER_DAY,
+                          rng.uniform(0.03, 0.08, n), np.full(n, math.pi - 1e-5),
+                          rng.uniform(0, 2 * math.pi, (n, 3)), rng.uniform(1e-5, 1e-4, n)])
+    t = np.linspace(0.0, 1440.0, T)
+    cov = _covariances(n, rng)
+    cov[:, 2, :] = 0.0
+    cov[:, :, 2] = 0.0
+    out, ist = _run(el, t, "fp32", cov)
+    dr, dv, sj = oracle.jacobian(el, t)
+    rr, vr, sr, isr = oracle.propagate(el, t)
+    r, v, st = out["r"].astype(np.float64), out["v"].astype(np.float64), out["status"]
+    assert_status_and_nan(st, sr, r, v, ist, isr)
+    e_r, _ = state_errors(r, v, rr, vr, sr)
+    assert e_r.max() <= 1.0
+    ok = (sr == 0) | (sr == 6)
+    cols = [0, 1, 3, 4, 5, 6]
+    J = out["jac"].astype(np.float64)[..., cols]
+    Jref = np.concatenate([dr, dv], axis=2)[..., cols]
+    rel, floor = TOL["fp32"]
+    scale = np.abs(np.where(ok[..., None, None], Jref, 0.0)).max(axis=1, keepdims=True)
+    bad = ok[..., None, None] & (np.abs(J - Jref) > rel * np.abs(Jref) + floor * scale)
+    assert not bad.any(), f"{bad.sum()} Jacobian entries off"
+    Jfull = np.concatenate([dr, dv], axis=2)
+    Pref = np.einsum("ntpk,nkl,ntql->ntpq", Jfull, cov, Jfull)
+    iu = np.triu_indices(6)
+    P = out["cov"].astype(np.float64)
+    dref = np.sqrt(np.einsum("ntpp->ntp", Pref))
+    err = np.abs(P - Pref[..., iu[0], iu[1]]) / np.maximum(dref[..., iu[0]] * dref[..., iu[1]],
+                                                          1e-300)
+    assert np.all(err[ok] <= 2e-2), float(np.max(err[ok]))
+
+
 def test_jacobian_column_for_mean_anomaly_is_the_velocity_direction():
     """d r / d M0 at t = 0 with drag off is the velocity over the mean motion for a
     circular orbit (moving the satellite along its track), a check independent of the
