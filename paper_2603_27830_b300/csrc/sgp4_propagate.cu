@@ -254,8 +254,9 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const GeoF& g
 // pairs (k = 0, 2) and (k = 1, 3) on one load of the record.  kPre (grids in minutes
 // read per state, no split table): the next unit's four times are loaded while this
 // unit computes (1 satellite x 1e7 times: 163 -> 126 us); a separate instantiation, as
-// the prefetch's registers slow the split-table path.  kCons (T a multiple of 4, grids
-// in minutes, 16-byte aligned arrays): the unit's times are the consecutive 4 i0 + k,
+// the prefetch's registers slow the split-table path.  kCons (T a multiple of 4,
+// 16-byte aligned arrays; grids in minutes, or absolute times in the split table): the
+// unit's times are the consecutive 4 i0 + k,
 // so its r, v and status are 48, 48 and 16 contiguous bytes, written by seven 16-byte
 // stores instead of 28 scalar ones, and its four times are two 16-byte loads (of the
 // split table, or of the grid with kPre).
@@ -263,7 +264,7 @@ template <bool kPre, bool kJd, bool kCons = false>
 __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const GeoF& gf,
                                              const Range& rg, int64_t ubeg, int64_t uend,
                                              FixQueue* fq, const float2* split) {
-  static_assert(!kCons || !kJd, "consecutive units take grids in minutes");
+  static_assert(!kCons || !(kJd && kPre), "absolute times take the split table");
   const int tid = threadIdx.x;
   const int T = (int)rg.T;
   const int Tq = (T + 3) / 4;
@@ -325,6 +326,10 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const GeoF& g
       const float4 a = s4[0], b = s4[1];
       th[0] = a.x; tl[0] = a.y; th[1] = a.z; tl[1] = a.w;
       th[2] = b.x; tl[2] = b.y; th[3] = b.z; tl[3] = b.w;
+      if constexpr (kJd) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) df_sub(th[k], tl[k], eh, el, th[k], tl[k]);
+      }
     } else
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -642,7 +647,13 @@ cudaError_t launch_fp32(const PropArgs& a, cudaStream_t stream) {
   const bool jd_table = a.jd_day && !per_state;
   if (!fp32_units_of_four(a.t_count))
     return jd_table ? launch_spu<true, 2, false, true>(a, stream) : launch_spu<true, 2>(a, stream);
-  if (jd_table) return launch_spu<true, 4, false, true>(a, stream);
+  if (jd_table) {
+    const bool al = a.t_count % 4 == 0 && ((reinterpret_cast<uintptr_t>(a.r) |
+                                            reinterpret_cast<uintptr_t>(a.v) |
+                                            reinterpret_cast<uintptr_t>(a.status)) & 15) == 0;
+    return al ? launch_spu<true, 4, false, true, true>(a, stream)
+              : launch_spu<true, 4, false, true>(a, stream);
+  }
   auto al16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
   const bool cons = !a.jd_day && a.t_count % 4 == 0 && al16(a.r) && al16(a.v) &&
                     al16(a.status) && (!per_state || al16(a.tsince));

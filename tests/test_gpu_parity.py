@@ -437,7 +437,8 @@ def test_julian_date_grid_from_each_records_split_epoch(prec):
         assert dr.max() <= 0.1 and dv.max() <= 1e-4, error_summary(dr, dv)
 
 
-def test_julian_dates_far_from_the_epochs_fp32():
+@pytest.mark.parametrize("T", [97, 96])
+def test_julian_dates_far_from_the_epochs_fp32(T):
     """FP32 absolute times with epochs up to 120 days from the grid and arbitrary
     fractions (tsince up to 1.7e5 minutes): the grid is tabulated as minutes from its
     first day and each record's epoch subtracted in double-float arithmetic, which must
@@ -452,8 +453,8 @@ def test_julian_dates_far_from_the_epochs_fp32():
     n = len(el)
     eday = (2461040 + rng.integers(-120, 121, n)).astype(np.int32)
     efrac = rng.uniform(0.0, 1.0, n)
-    jd_day = np.full(97, 2461040, dtype=np.int32)
-    jd_frac = np.sort(rng.uniform(0.0, 1.0, 97))
+    jd_day = np.full(T, 2461040, dtype=np.int32)
+    jd_frac = np.sort(rng.uniform(0.0, 1.0, T))
     jd_day[60:] += 1                                        # the grid crosses a day
     tsince = ((jd_day[None, :] - eday[:, None]).astype(np.float64)
               + (jd_frac[None, :] - efrac[:, None])) * 1440.0
