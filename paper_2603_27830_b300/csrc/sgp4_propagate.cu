@@ -1,10 +1,12 @@
 // Propagation kernels: independent (satellite, time) states (paper Sec. 2.2,
 // "Vectorisation": f(s, t) under a vmap over times composed with a vmap over
 // satellites).  A thread takes a unit of states of one satellite that share the
-// record: in FP32 four (times i + k ceil(T/4)) as two pairs in packed arithmetic
-// (run_range_x4, state32x2), or one pair (run_range_x2) for short grids whose units of
-// four would be partly empty; in FP64 two (times i and i + ceil(T/2)) in turn on one
-// load of the record, or one for problems that fit one wave (run_units64).
+// record: in FP32 four (the consecutive times 4i..4i+3 when T is a multiple of 4, else
+// times i + k ceil(T/4)) as two pairs in packed arithmetic (run_range_x4, state32x2), or
+// one pair (run_range_x2) for short grids whose units of four would be partly empty; in
+// FP64 two (times i and i + ceil(T/2)) in turn on one load of the record, or one for
+// problems that fit one wave (run_units64).  FP32 guard-band states are queued and
+// recomputed in FP64 after the block's loop (fix_queued).
 //   * a block walks a contiguous range of units, 128 per step, so consecutive steps of
 //     a thread stay on one satellite and its record stays in L1 (FP32) or registers
 //     (FP64);
