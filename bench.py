@@ -40,8 +40,8 @@ BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
 # FP32 arithmetic + SFU operations per state of the FP32 formulation on the
 # Starlink-shaped workload, counted with ncu on the current kernel: each packed
 # instruction (FADD2, FMUL2, FFMA2) is two lane operations, one for each state of its
-# pair: FADD 37.1 + FMUL 97.1 + FFMA 67.1 + SFU 16.1 per state (the commands are in
-# profiles/propagate_fp32_starlink_9341x1000.md).
+# pair: FADD 37.1 + FMUL 97.1 + FFMA 67.1 + SFU 16.1 per state (ncu's per-pipe
+# instruction counts of one launch divided by the launch's states).
 ALG_OPS_FP32 = 217
 # DRAM bytes (read + write) of one launch of the FP32 propagate kernel on this workload,
 # from an ncu capture of the current kernel (dram__bytes_read.sum 2,256,640 +

@@ -201,7 +201,9 @@ size_t sgp4_batch_workspace_bytes(int32_t n_requests);
 
 /*
  * Validate a HOST request table, derive the tiling and copy the tables to the
- * workspace (stream-ordered; `requests` may be reused when the call returns).
+ * workspace (stream-ordered).  The call first takes its own pageable host copy of
+ * `requests`, validates that copy and uploads it, so `requests` (pageable or
+ * page-locked) may be reused as soon as the call returns.
  *   tile_states  states per tile, a positive multiple of 128 (chosen by the
  *                autotuner of the Python layer, e.g. 1024)
  *   grid_blocks  persistent grid size, 0 for one full wave
@@ -339,7 +341,9 @@ sgp4_result sgp4_jacobian(const double* elements, const sgp4_records* records,
  * the request table in a fixed array inside the library: about 48 KB held on every
  * GPU that loads the library, until the process exits.
  *   requests     HOST table of n_requests <= SGP4_STATIC_MAX_REQUESTS requests
- *                (same meaning as for sgp4_batch_plan_init; may be reused on return)
+ *                (same meaning as for sgp4_batch_plan_init).  The call copies it
+ *                into a per-thread host array, validates that copy and uploads it,
+ *                so the table (pageable or page-locked) may be reused on return.
  *   tile_states  states per work tile, a positive multiple of 128
  *   other arguments as in sgp4_propagate_batched (no fixup counter)
  * The first call on a device looks up the array's device address with that device
@@ -348,7 +352,8 @@ sgp4_result sgp4_jacobian(const double* elements, const sgp4_records* records,
  * different host threads) race and must be serialised by the caller.  Each call
  * rewrites the table and prefix sums and resets the counter before its launch.
  * Errors: SGP4_ERR_OOM if n_requests exceeds SGP4_STATIC_MAX_REQUESTS; SGP4_ERR_ARG
- * for bad sizes, offsets outside records / tsince / outputs, overlapping outputs,
+ * for bad or negative sizes (tsince_len, out_len included), offsets outside records /
+ * tsince / outputs, overlapping outputs,
  * a bad precision or tile size, NULL or misaligned arrays; SGP4_ERR_CUDA if the
  * address lookup, the copy or a launch fails.  Calls no allocation routine.
  */

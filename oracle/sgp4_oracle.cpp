@@ -16,7 +16,7 @@
 // fusion or reordering beyond the steps of the theory; every branch of the theory
 // is an ordinary `if` on the value.
 //
-// Readings of points the paper leaves open (each is listed in the design doc):
+// Readings of points the paper leaves open (the CUDA path takes the same ones):
 //  * WGS-72 with ke computed from mu and the Earth radius (not the rounded
 //    "WGS72old" ke literal).
 //  * a0'' = (ke / n0'')^(2/3) (2006 revision), not a0/(1 - delta0) (1980 report).

@@ -197,13 +197,17 @@ sgp4_result sgp4_batch_plan_init(const sgp4_request* requests, int32_t n_request
   if (n_requests > 0 && (!requests || !workspace || !aligned(workspace, 256))) return SGP4_ERR_ARG;
   if (n_requests > 0 && workspace_bytes < sgp4_batch_workspace_bytes(n_requests))
     return SGP4_ERR_OOM;
+  // One host copy of the caller's table: the checks and the device copy read it, so
+  // the device gets the table that was checked, and its pageable source is staged
+  // before return even when the caller's table is page-locked.
+  const std::vector<sgp4_request> table(requests, requests + n_requests);
   const int64_t kLimit = INT64_MAX / 4;
   std::vector<int64_t> tile_start((size_t)n_requests + 1, 0);
   std::vector<std::pair<int64_t, int64_t>> spans;
   spans.reserve((size_t)n_requests);
   int64_t sats = 0, ts = 0, outs = 0, total_states = 0;
   for (int32_t k = 0; k < n_requests; ++k) {
-    const sgp4_request& q = requests[k];
+    const sgp4_request& q = table[(size_t)k];
     if (q.n < 0 || q.t_count < 0 || q.sat_offset < 0 || q.t_offset < 0 || q.out_offset < 0)
       return SGP4_ERR_ARG;
     if (q.t_count > INT32_MAX) return SGP4_ERR_ARG;
@@ -239,7 +243,7 @@ sgp4_result sgp4_batch_plan_init(const sgp4_request* requests, int32_t n_request
   cudaError_t e = cudaMemcpyAsync(ws + ws_tile_start_off(), tile_start.data(),
                                   sizeof(int64_t) * tile_start.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ws + ws_reqs_off(n_requests), requests,
+    e = cudaMemcpyAsync(ws + ws_reqs_off(n_requests), table.data(),
                         sizeof(sgp4_request) * (size_t)n_requests, cudaMemcpyHostToDevice, s);
   return e == cudaSuccess ? SGP4_OK : SGP4_ERR_CUDA;
 }

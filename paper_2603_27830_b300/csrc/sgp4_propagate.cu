@@ -18,6 +18,7 @@
 // in one persistent launch; blocks take fixed-size tiles of units from a global
 // atomic counter, so uneven requests and uneven per-state cost balance themselves.
 #include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <type_traits>
 
@@ -609,25 +610,47 @@ int blocks_per_sm_of(K kernel, size_t dyn_smem = 0) {
   return bps > 0 ? bps : 1;
 }
 
+constexpr int kMaxDevices = 64;
+
+// Resident blocks per SM of `kernel` on the current device, found once per device and
+// cached in `cache` (zero = not yet known).  With `opt_in` the kernel's dynamic
+// shared-memory limit is first raised to `dyn_smem`; that attribute belongs to the
+// device, so it is set on each device the library launches on.
+template <typename K>
+cudaError_t device_bps(std::atomic<int> (&cache)[kMaxDevices], K kernel, size_t dyn_smem,
+                       bool opt_in, int* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  int b = cache[dev].load(std::memory_order_acquire);
+  if (b == 0) {
+    if (opt_in) {
+      e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)dyn_smem);
+      if (e != cudaSuccess) return e;
+    }
+    b = blocks_per_sm_of(kernel, dyn_smem);
+    cache[dev].store(b, std::memory_order_release);
+  }
+  *out = b;
+  return cudaSuccess;
+}
+
 template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false, bool kCons = false>
 cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   if (total == 0) return cudaSuccess;
   const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
   const size_t dyn = use_split ? (size_t)a.t_count * sizeof(float2) : 0;
-  // Resident blocks per SM of this kernel (same on every B300), taken with the largest
-  // split table so that the wave below is resident whatever the grid length.
-  static int bps = 0;
-  if (bps == 0) {
-    if (kFP32) {   // the 48 KB split table beside the static guard-band queue
-      const cudaError_t e = cudaFuncSetAttribute(propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)(kSplitMaxT * sizeof(float2)));
-      if (e != cudaSuccess) return e;
-    }
-    bps = blocks_per_sm_of(propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>,
-                           kFP32 ? kSplitMaxT * sizeof(float2) : 0);
-  }
+  // Resident blocks per SM of this kernel, taken with the largest split table so that
+  // the wave below is resident whatever the grid length.  FP32 opts in to the 48 KB
+  // split table beside the static guard-band queue.
+  static std::atomic<int> bps_dev[kMaxDevices];
+  int bps = 0;
+  const cudaError_t be = device_bps(bps_dev, propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>,
+                                    kFP32 ? kSplitMaxT * sizeof(float2) : 0, kFP32, &bps);
+  if (be != cudaSuccess) return be;
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
@@ -669,8 +692,10 @@ cudaError_t launch_fp32(const PropArgs& a, cudaStream_t stream) {
 // FP64: one state per thread while the two-state units would not fill one wave of the
 // kernel (148 SMs x 4 blocks x 128 threads), two otherwise.
 cudaError_t launch_fp64(const PropArgs& a, cudaStream_t stream) {
-  static int bps = 0;
-  if (bps == 0) bps = blocks_per_sm_of(propagate_kernel<false, 2>);
+  static std::atomic<int> bps_dev[kMaxDevices];
+  int bps = 0;
+  const cudaError_t be = device_bps(bps_dev, propagate_kernel<false, 2>, 0, false, &bps);
+  if (be != cudaSuccess) return be;
   const int64_t wave = (int64_t)device_sm_count() * bps * kThreads;
   return a.rp.n * units_per_sat(a.t_count, 2) < wave ? launch_spu<false, 1>(a, stream)
                                                      : launch_spu<false, 2>(a, stream);
@@ -678,8 +703,9 @@ cudaError_t launch_fp64(const PropArgs& a, cudaStream_t stream) {
 
 template <bool kFP32>
 int64_t grid_b(int64_t total_tiles, int grid_blocks) {
-  static int bps = 0;
-  if (bps == 0) bps = blocks_per_sm_of(batched_kernel<kFP32>);
+  static std::atomic<int> bps_dev[kMaxDevices];
+  int bps = 1;
+  if (device_bps(bps_dev, batched_kernel<kFP32>, 0, false, &bps) != cudaSuccess) bps = 1;
   int64_t grid = grid_blocks > 0 ? grid_blocks : (int64_t)device_sm_count() * bps;
   return std::max<int64_t>(1, std::min<int64_t>(grid, total_tiles));
 }

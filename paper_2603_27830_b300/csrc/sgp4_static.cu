@@ -11,6 +11,7 @@
 // The paper has no counterpart: it is a service feature of this library.
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "sgp4.h"
@@ -71,13 +72,21 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
   if (records->stride != sgp4::record_stride(records->n)) return SGP4_ERR_ARG;
   if (!(records->consts.mu_km3s2 > 0.0) || !(records->consts.radius_km > 0.0)) return SGP4_ERR_ARG;
   if (n_requests > 0 && !requests) return SGP4_ERR_ARG;
+  if (tsince_len < 0 || out_len < 0) return SGP4_ERR_ARG;
+
+  // The caller's table is copied once into this thread's own host array: the checks
+  // below and the copy to the device both read that copy, so the device gets exactly
+  // the table that was checked, and the copy's pageable source is staged before this
+  // call returns even when the caller's table is page-locked.
+  thread_local sgp4_request table[kMaxRequests];
+  std::memcpy(table, requests, sizeof(sgp4_request) * (size_t)n_requests);
 
   // Host checks of the table without any buffer: bounds, overflow, and pairwise
   // non-overlap of the output ranges (at most 1024 requests).
   const int64_t kLimit = INT64_MAX / 4;
   int64_t total_tiles = 0;
   for (int32_t k = 0; k < n_requests; ++k) {
-    const sgp4_request& q = requests[k];
+    const sgp4_request& q = table[k];
     if (q.n < 0 || q.t_count < 0 || q.sat_offset < 0 || q.t_offset < 0 || q.out_offset < 0)
       return SGP4_ERR_ARG;
     if (q.t_count > INT32_MAX) return SGP4_ERR_ARG;
@@ -89,7 +98,7 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
     total_tiles += sgp4::request_tiles(q.n, q.t_count, tile_states);
     if (st == 0) continue;
     for (int32_t m = 0; m < k; ++m) {
-      const sgp4_request& p = requests[m];
+      const sgp4_request& p = table[m];
       const int64_t sp = p.n * p.t_count;
       if (sp > 0 && q.out_offset < p.out_offset + sp && p.out_offset < q.out_offset + st)
         return SGP4_ERR_ARG;
@@ -120,9 +129,9 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
   char* scratch = static_cast<char*>(base);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // Request table into the scratch (the pageable source is staged before return),
-  // then the tile prefix sums on the device.
-  cudaError_t e = cudaMemcpyAsync(scratch + kCounterBytes + kTileStartBytes, requests,
+  // Request table into the scratch (the pageable copy is staged before return), then
+  // the tile prefix sums on the device.
+  cudaError_t e = cudaMemcpyAsync(scratch + kCounterBytes + kTileStartBytes, table,
                                   sizeof(sgp4_request) * (size_t)n_requests,
                                   cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return SGP4_ERR_CUDA;

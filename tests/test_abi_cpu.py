@@ -136,3 +136,32 @@ def test_batch_plan_rejects_bad_tables_before_any_copy():
     assert call([(0, 1 << 40, 0, 1 << 40, 0), ok[1]]) == _lib.SGP4_ERR_ARG    # overflow
     assert lib.sgp4_batch_plan_init(None, 0, 1024, 0, None, 0, ctypes.byref(plan), None) == 0
     assert plan.n_requests == 0 and plan.total_tiles == 0
+
+
+def test_static_batch_rejects_bad_tables_before_any_cuda_call():
+    lib = _lib.load()
+    rec = _lib.Sgp4Records()
+    assert lib.sgp4_records_bind(ctypes.c_void_p(1 << 20), lib.sgp4_records_bytes(20), 20, None,
+                                 ctypes.byref(rec)) == _lib.SGP4_OK
+    P = ctypes.c_void_p
+
+    def call(rows, tile=512, ts_len=100, out_len=1000, prec=_lib.SGP4_FP32):
+        n = len(rows)
+        table = (_lib.Sgp4Request * max(n, 1))(*[_lib.Sgp4Request(*r) for r in rows])
+        return lib.sgp4_propagate_batched_static(
+            ctypes.cast(table, ctypes.c_void_p), n, tile, ctypes.byref(rec), P(1 << 22), ts_len,
+            prec, P(1 << 24), P(1 << 25), P(1 << 26), out_len, None)
+
+    ok = [(0, 10, 0, 5, 0), (10, 4, 5, 3, 50)]
+    assert call(ok, ts_len=-1) == _lib.SGP4_ERR_ARG
+    assert call(ok, out_len=-1) == _lib.SGP4_ERR_ARG
+    assert call(ok, ts_len=-(1 << 62)) == _lib.SGP4_ERR_ARG
+    assert call(ok, tile=100) == _lib.SGP4_ERR_ARG
+    assert call(ok, prec=9) == _lib.SGP4_ERR_ARG
+    assert call([(0, 10, 0, 5, 0), (10, 4, 5, 3, 49)]) == _lib.SGP4_ERR_ARG   # outputs overlap
+    assert call([(15, 10, 0, 5, 0)]) == _lib.SGP4_ERR_ARG                     # past the records
+    assert call([(0, 10, 96, 5, 0)]) == _lib.SGP4_ERR_ARG                     # past tsince
+    assert call([(0, 10, 0, 5, 960)]) == _lib.SGP4_ERR_ARG                    # past the outputs
+    assert call([(0, 1 << 40, 0, 1 << 40, 0)]) == _lib.SGP4_ERR_ARG           # overflow
+    assert call([(0, 0, 0, 0, 0)] * (_lib.STATIC_MAX_REQUESTS + 1)) == _lib.SGP4_ERR_OOM
+    assert call([]) == _lib.SGP4_OK                                            # nothing to do

@@ -178,6 +178,39 @@ def test_graph_replay_equals_direct_launch():
     g.close()
 
 
+def test_plan_init_page_locked_table_reused_on_return():
+    """sgp4_batch_plan_init with a page-locked request table that the caller zeroes
+    right after the call, while the stream is still busy: the plan keeps the table it
+    was given (the call uploads its own checked copy)."""
+    import ctypes
+
+    import torch
+
+    from paper_2603_27830_b300 import _lib, sgp4_init, sgp4_propagate_batched
+    from paper_2603_27830_b300.api import BatchPlan
+    b = _small_batch(seed=6, n_req=24)
+    ref = _run_batched(b, "fp32", tile=512)
+    lib = _lib.load()
+    n = len(b.requests)
+    table = torch.as_tensor(np.asarray(b.requests, dtype=np.int64)).pin_memory()
+    nbytes = int(lib.sgp4_batch_workspace_bytes(n))
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    plan = _lib.Sgp4BatchPlan()
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    torch.cuda._sleep(20_000_000)             # keep the stream busy (about 10 ms)
+    code = lib.sgp4_batch_plan_init(ctypes.c_void_p(table.data_ptr()), n, 512, 0,
+                                    ctypes.c_void_p(ws.data_ptr()), nbytes, ctypes.byref(plan),
+                                    ctypes.c_void_p(stream.cuda_stream))
+    table.zero_()
+    assert code == _lib.SGP4_OK
+    r, v, st = sgp4_propagate_batched(BatchPlan(ws, plan, b.requests), ref[3],
+                                      torch.as_tensor(b.tsince, device="cuda"), "fp32")
+    torch.cuda.synchronize()
+    for x, y in zip((r, v, st), ref[:3]):
+        assert torch.equal(x.nan_to_num(7.0), y.nan_to_num(7.0))
+
+
 def test_plan_larger_than_buffers_is_rejected():
     import torch
 

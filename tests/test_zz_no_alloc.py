@@ -5,6 +5,10 @@ array inside the library.  This file is collected last on purpose.  The test cal
 the entry point through the C ABI twice in a row, on two different batches, and
 compares each result with the workspace-based sgp4_propagate_batched.  The second
 call checks that nothing left in the shared array by the first call leaks into it.
+Further cases: a table of exactly SGP4_STATIC_MAX_REQUESTS requests (every lane of
+the on-device prefix sum in use, empty requests among them), and a page-locked
+table that the caller overwrites as soon as the call returns, while the stream is
+still busy with earlier work.
 """
 from __future__ import annotations
 
@@ -31,15 +35,17 @@ def _batch(seed, n_req):
     return make_batch(probs)
 
 
-def _static_call(lib, b, recs, ts, precision, out, stream):
+def _static_call(lib, b, recs, ts, precision, out, stream, tile=512, table_ptr=None):
     from paper_2603_27830_b300 import _lib
     n = len(b.requests)
-    table = (_lib.Sgp4Request * max(n, 1))()
-    for k in range(n):
-        table[k] = _lib.Sgp4Request(*[int(x) for x in b.requests[k]])
+    if table_ptr is None:
+        table = (_lib.Sgp4Request * max(n, 1))()
+        for k in range(n):
+            table[k] = _lib.Sgp4Request(*[int(x) for x in b.requests[k]])
+        table_ptr = ctypes.cast(table, ctypes.c_void_p)
     r, v, st = out
     return lib.sgp4_propagate_batched_static(
-        ctypes.cast(table, ctypes.c_void_p), n, 512, ctypes.byref(recs.c),
+        table_ptr, n, tile, ctypes.byref(recs.c),
         ctypes.c_void_p(ts.data_ptr()), ts.numel(), _lib.SGP4_FP32 if precision == "fp32"
         else _lib.SGP4_FP64, ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(v.data_ptr()),
         ctypes.c_void_p(st.data_ptr()), st.numel(), ctypes.c_void_p(stream.cuda_stream))
@@ -86,3 +92,80 @@ def test_no_alloc_entry_rejects_more_requests_than_its_scratch_holds():
         ctypes.cast(table, ctypes.c_void_p), n, 512, ctypes.byref(recs.c), None, 0,
         _lib.SGP4_FP32, None, None, None, 0, None)
     assert code == _lib.SGP4_ERR_OOM
+
+
+def _compare(out, ref):
+    import torch
+    assert torch.equal(out[2], ref[2])
+    ok = (ref[2] == 0) | (ref[2] == 6)
+    dr = (out[0][ok].double() - ref[0][ok].double()).norm(dim=-1)
+    dv = (out[1][ok].double() - ref[1][ok].double()).norm(dim=-1)
+    if int(ok.sum()):
+        assert float(dr.max()) <= FP64_TOL_R_KM and float(dv.max()) <= FP64_TOL_V_KMS
+    assert torch.all(torch.isnan(out[0][~ok]))
+
+
+def _fresh_out(ref):
+    import torch
+    S = ref[2].numel()
+    dt = ref[0].dtype
+    return (torch.full((S, 3), 555.0, dtype=dt, device="cuda"),
+            torch.full((S, 3), 555.0, dtype=dt, device="cuda"),
+            torch.full((S,), 99, dtype=torch.int32, device="cuda"))
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_no_alloc_entry_at_its_request_limit(precision):
+    """SGP4_STATIC_MAX_REQUESTS small requests, some with no satellites or no times:
+    the one-block prefix sum then runs with every lane holding a request."""
+    import torch
+
+    from paper_2603_27830_b300 import _lib, make_batch, plan_batch, sgp4_init
+    from paper_2603_27830_b300 import sgp4_propagate_batched
+    from paper_2603_27830_b300 import workloads as W
+    lib = _lib.load()
+    rng = np.random.default_rng(21)
+    probs = []
+    for k in range(_lib.STATIC_MAX_REQUESTS):
+        n = 0 if k % 13 == 0 else int(rng.integers(1, 12))
+        T = 0 if k % 17 == 0 else int(rng.integers(1, 40))
+        el = W.catalogue_elements(rng, max(n, 1), invalid_frac=0.02)[:n]
+        probs.append((el, np.sort(rng.uniform(-720.0, 2880.0, T))))
+    b = make_batch(probs)
+    assert len(b.requests) == _lib.STATIC_MAX_REQUESTS
+    el = torch.as_tensor(b.elements, device="cuda")
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    recs, _ = sgp4_init(el)
+    ref = sgp4_propagate_batched(plan_batch(b.requests, 128), recs, ts, precision)
+    for tile in (128, 1024):
+        out = _fresh_out(ref)
+        assert _static_call(lib, b, recs, ts, precision, out, torch.cuda.current_stream(),
+                            tile=tile) == _lib.SGP4_OK
+        torch.cuda.synchronize()
+        _compare(out, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_no_alloc_entry_page_locked_table_reused_on_return(precision):
+    """The caller rewrites its page-locked table right after the call, while the
+    stream is still busy: the launch must still use the table it was given."""
+    import torch
+
+    from paper_2603_27830_b300 import _lib, plan_batch, sgp4_init, sgp4_propagate_batched
+    lib = _lib.load()
+    b = _batch(31, 60)
+    el = torch.as_tensor(b.elements, device="cuda")
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    recs, _ = sgp4_init(el)
+    ref = sgp4_propagate_batched(plan_batch(b.requests, 512), recs, ts, precision)
+    table = torch.as_tensor(np.asarray(b.requests, dtype=np.int64)).pin_memory()
+    assert table.is_pinned() and table.shape[1] == 5
+    out = _fresh_out(ref)
+    torch.cuda.synchronize()
+    torch.cuda._sleep(20_000_000)            # keep the stream busy (about 10 ms)
+    code = _static_call(lib, b, recs, ts, precision, out, torch.cuda.current_stream(),
+                        table_ptr=ctypes.c_void_p(table.data_ptr()))
+    table.zero_()                            # every request now empty
+    assert code == _lib.SGP4_OK
+    torch.cuda.synchronize()
+    _compare(out, ref)
