@@ -202,18 +202,165 @@ class ClockSampler:
                 "sm_max_mhz": self.max_mhz, "reasons": reasons, "samples": len(self.samples)}
 
 
-def cpu_oracle_rate(elements, tsince, n_sats: int, threads: int):
-    """Time the FP64 oracle (as it stands) on the first n_sats satellites."""
+def time_oracle(elements, tsince, threads: int, trials: int = 5, min_trial_s: float = 0.2):
+    """The paper's timing protocol (Sec. 3.1) applied to the FP64 oracle as it stands:
+    one call propagates every satellite to every time; a trial repeats the call until
+    it has run at least min_trial_s, and the best of `trials` trials (time per call) is
+    reported.  Returns (states/s, seconds per call, calls per trial)."""
     import oracle
-    el = elements[:n_sats]
     oracle.load()
-    t0 = time.perf_counter()
-    oracle.propagate(el, tsince, threads=threads)
-    dt = time.perf_counter() - t0
-    return el.shape[0] * tsince.shape[-1] / dt, dt
+    states = elements.shape[0] * tsince.shape[-1]
+    reps = 1
+    while True:                      # find a repetition count that fills a trial
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            oracle.propagate(elements, tsince, threads=threads)
+        dt = time.perf_counter() - t0
+        if dt >= min_trial_s:
+            break
+        reps = max(reps * 2, int(reps * min_trial_s / max(dt, 1e-6)) + 1)
+    best = dt / reps
+    for _ in range(trials - 1):
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            oracle.propagate(elements, tsince, threads=threads)
+        best = min(best, (time.perf_counter() - t0) / reps)
+    return states / best, best, reps
 
 
-def run_batched(torch, dev, stream, flush, steps):
+def _errors(r_dev, v_dev, st_dev, rows, rr, vr, sr):
+    """FP32/FP64 path vs the oracle on the sampled satellites `rows` (device outputs
+    [n, T, 3] / [n, T]): status mismatches, max and p99 of |dr| (km) and |dv| (km/s)
+    over the states with output."""
+    import torch
+    idx = torch.as_tensor(rows, device=st_dev.device)
+    r = r_dev[idx].double().cpu().numpy()
+    v = v_dev[idx].double().cpu().numpy()
+    st = st_dev[idx].cpu().numpy()
+    keep = (sr == 0) | (sr == 6)
+    dr = np.linalg.norm(r[keep] - rr[keep], axis=-1)
+    dv = np.linalg.norm(v[keep] - vr[keep], axis=-1)
+    out = {"status_mismatches": int((st != sr).sum()), "states": int(st.size)}
+    if dr.size:
+        out.update({"states_over_1e-6_km": int((dr > 1e-6).sum()),
+                    "max_dr_km": float(dr.max()), "p99_dr_km": float(np.percentile(dr, 99)),
+                    "median_dr_km": float(np.median(dr)), "max_dv_kms": float(dv.max()),
+                    "p99_dv_kms": float(np.percentile(dv, 99))})
+    return out
+
+
+# FP32 and FP64 arithmetic per state of the propagate kernels on each single-problem
+# workload, counted with ncu on the current kernels the same way as ALG_OPS_FP32 and
+# ALG_OPS_FP64 (the FP32 count includes the SFU operations).  The count depends on
+# the workload: eccentric orbits take more Newton steps, simplified-drag records skip
+# the D terms, guard-band states add FP64 work.
+OPS_PER_STATE = {
+    "near-earth-64x100": {"fp32": None, "fp64": None},
+    "starlink-9341x1000": {"fp32": ALG_OPS_FP32, "fp64": ALG_OPS_FP64},
+    "catalogue-1Mx100": {"fp32": None, "fp64": None},
+    "fit-10000x500": {"fp32": None, "fp64": None},
+}
+
+
+def _roofline(prec, workload, states, kern_ms, alu_peak, fp64_peak, hbm_peak):
+    """Roofline of one propagate launch: arithmetic against its pipe's peak (FP32 lanes
+    or the FP64 unit) and output bytes against HBM; the bound is the slower side."""
+    sec = kern_ms * 1e-3
+    gbs = BYTES_PER_STATE[prec] * states / sec / 1e9
+    out = {"hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                   "bytes_per_state": BYTES_PER_STATE[prec]}}
+    ops = OPS_PER_STATE.get(workload, {}).get(prec)
+    if ops is None:
+        out.update({"bound": "hbm", "frac": gbs / hbm_peak})
+        return out
+    peak = alu_peak if prec == "fp32" else fp64_peak
+    gops = ops * states / sec / 1e9
+    t_alu = ops * states / (peak * 1e9)
+    t_hbm = BYTES_PER_STATE[prec] * states / (hbm_peak * 1e9)
+    bound = ("alu" if prec == "fp32" else "fp64") if t_alu >= t_hbm else "hbm"
+    out.update({"bound": bound, "achieved": gops, "peak": peak, "unit": "Gop/s",
+                "ops_per_state": ops, "frac": (gops / peak) if bound != "hbm" else gbs / hbm_peak,
+                "alu_frac": gops / peak})
+    return out
+
+
+def run_single_config(torch, dev, stream, flush, steps, w, precs, n_sample, threads,
+                      alu_peak, fp64_peak, hbm_peak, time_cpu=True):
+    """One single-problem workload: per precision the step (sgp4_init + sgp4_propagate)
+    and the propagate launch alone, each the median of `steps` timed runs with L2
+    flushed between them, the roofline of the launch, and the error against the FP64
+    oracle over the whole horizon on a sample of satellites (all of them when n_sample
+    is None; the sampled ones always include every deliberately invalid record)."""
+    import oracle
+
+    from paper_2603_27830_b300 import sgp4_init, sgp4_propagate
+    n, T = w.n, w.t_count
+    el = torch.as_tensor(w.elements, device=dev)
+    ts = torch.as_tensor(w.tsince, device=dev)
+    recs, ist = sgp4_init(el)
+    if n_sample is None or n_sample >= n:
+        rows = np.arange(n)
+        sample = f"all {n} satellites x {T} times"
+    else:
+        rng = np.random.default_rng(12345)
+        rows = np.unique(np.concatenate([rng.choice(n, n_sample, replace=False),
+                                         np.asarray(w.meta.get("invalid", []), dtype=np.int64)]))
+        sample = (f"{len(rows)} of {n} satellites (random, plus every invalid record) x "
+                  f"{T} times")
+    rr, vr, sr, _ = oracle.propagate(w.elements[rows], w.tsince, threads=threads)
+    res = {"workload": w.name, "n_sats": n, "t_count": T,
+           "horizon_min": [float(w.tsince.min()), float(w.tsince.max())],
+           "error_sample": sample}
+    if time_cpu:
+        rate, per_call, reps = time_oracle(w.elements[rows], w.tsince, threads)
+        res["oracle"] = {"value": rate, "unit": UNIT, "cores": threads, "sample": sample,
+                         "s_per_call": per_call, "calls_per_trial": reps,
+                         "protocol": "best of 5 trials, each >= 0.2 s"}
+
+    def median_ms(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            host_lead(torch)
+            flush.fill_(1.0)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    for prec in precs:
+        dt = torch.float32 if prec == "fp32" else torch.float64
+        out = (torch.empty((n, T, 3), dtype=dt, device=dev),
+               torch.empty((n, T, 3), dtype=dt, device=dev),
+               torch.empty((n, T), dtype=torch.int32, device=dev))
+        reps = steps if prec == "fp32" else max(3, min(steps, 5))
+
+        def step():
+            sgp4_init(el, records=recs, init_status=ist)
+            sgp4_propagate(recs, ts, prec, out=out)
+
+        step_ms = median_ms(step, reps)
+        kern_ms = median_ms(lambda: sgp4_propagate(recs, ts, prec, out=out), reps)
+        step()
+        torch.cuda.synchronize()
+        err = _errors(out[0], out[1], out[2], rows, rr, vr, sr)
+        res[prec] = {"value": n * T / (step_ms * 1e-3), "unit": UNIT, "ms_per_step": step_ms,
+                     "kernel_ms": kern_ms, "kernel_states_per_s": n * T / (kern_ms * 1e-3),
+                     "roofline": _roofline(prec, w.name, n * T, kern_ms, alu_peak, fp64_peak,
+                                           hbm_peak),
+                     "vs_oracle": err}
+        del out
+    del recs, ist, el, ts
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_batched(torch, dev, stream, flush, steps, sample_requests=0, threads=1):
     """Time the 256-request uneven batch (graph replay of one persistent launch)."""
     from paper_2603_27830_b300 import BatchGraph, autotune, make_batch, sgp4_init
     from paper_2603_27830_b300 import workloads as W
@@ -228,6 +375,7 @@ def run_batched(torch, dev, stream, flush, steps):
            torch.empty((S,), dtype=torch.int32, device=dev))
     plan, entry = autotune.tune_batch(b.requests, recs, ts, "fp32", out=out, reps=2)
     graph = BatchGraph(plan, recs, ts, "fp32", out=out)
+    graph_out = out
     graph.replay(stream)
     torch.cuda.synchronize()
     ms = []
@@ -247,7 +395,42 @@ def run_batched(torch, dev, stream, flush, steps):
            "value": S / (med * 1e-3), "unit": UNIT, "ms_per_launch": med,
            "tile_states": entry["tile_states"], "launches_per_step": 2,
            "note": "N_i log-U[100,5e4], T_i log-U[10,5e3], grids U[-720,2880] min; "
-                   "one CUDA-graph replay (counter reset + persistent kernel)"}
+                   "one CUDA-graph replay (counter reset + persistent kernel)",
+           "roofline": {"hbm": {"achieved": 28 * S / (med * 1e-3) / 1e9, "unit": "GB/s",
+                                "bytes_per_state": 28}}}
+    if sample_requests:
+        # error against the oracle over each sampled request's whole grid, on up to 200
+        # of its satellites (and every invalid record among them)
+        import oracle
+        rng = np.random.default_rng(4)
+        r_all, v_all, s_all = graph_out
+        el_s, st_ref, dr_all, dv_all = [], [], [], []
+        mism = 0
+        states_checked = 0
+        for k in rng.choice(len(reqs), sample_requests, replace=False):
+            sat0, n, t0, T, out0 = b.requests[k]
+            pick = np.unique(np.concatenate([rng.choice(n, min(n, 200), replace=False),
+                                             np.flatnonzero(reqs[k].elements[:, 1] >= 1.0)]))
+            rr, vr, sr, _ = oracle.propagate(reqs[k].elements[pick], reqs[k].tsince,
+                                             threads=threads)
+            idx = torch.as_tensor((out0 + pick[:, None] * T + np.arange(T)[None, :]).reshape(-1),
+                                  device=dev)
+            rg = r_all[idx].double().cpu().numpy().reshape(len(pick), T, 3)
+            vg = v_all[idx].double().cpu().numpy().reshape(len(pick), T, 3)
+            sg = s_all[idx].cpu().numpy().reshape(len(pick), T)
+            mism += int((sg != sr).sum())
+            states_checked += sg.size
+            keep = (sr == 0) | (sr == 6)
+            dr_all.append(np.linalg.norm(rg[keep] - rr[keep], axis=-1))
+            dv_all.append(np.linalg.norm(vg[keep] - vr[keep], axis=-1))
+        dr = np.concatenate(dr_all)
+        dv = np.concatenate(dv_all)
+        res["vs_oracle"] = {"status_mismatches": mism, "states": states_checked,
+                            "max_dr_km": float(dr.max()), "p99_dr_km": float(np.percentile(dr, 99)),
+                            "median_dr_km": float(np.median(dr)), "max_dv_kms": float(dv.max()),
+                            "p99_dv_kms": float(np.percentile(dv, 99))}
+        res["error_sample"] = (f"{sample_requests} random requests, up to 200 satellites each "
+                               f"(plus their invalid records), every time of their grids")
     del out, recs, el, ts
     torch.cuda.empty_cache()
     return res
@@ -315,23 +498,31 @@ def run_adjoint(torch, dev, stream, flush, steps, alu_peak, fp64_peak):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle, as it stands, on the headline workload
+    (all 9,341 satellites x 1,000 times per step, or the first --ref-sats of them), on
+    every host core.  Each step is one call of the oracle; the line's value is the
+    states of all steps over their summed wall time."""
+    import oracle
     rank, world, _ = _dist()
     if rank != 0:
         return 0
     from paper_2603_27830_b300 import workloads as W
     w = W.config2()
     threads = os.cpu_count() or 1
-    n_sample = args.ref_sats
+    n_sample = min(args.ref_sats, w.n)
+    el = w.elements[:n_sample]
+    oracle.load()
     for _ in range(args.warmup):
-        cpu_oracle_rate(w.elements, w.tsince, max(1, n_sample // 10), threads)
-    rates, times = [], []
+        oracle.propagate(el, w.tsince, threads=threads)
+    times = []
     for _ in range(args.steps):
-        r, dt = cpu_oracle_rate(w.elements, w.tsince, n_sample, threads)
-        rates.append(r)
-        times.append(dt)
-    total_states = n_sample * w.t_count * args.steps
-    value = total_states / sum(times)
-    sample = f"first {n_sample} of {w.n} satellites x {w.t_count} times per step"
+        t0 = time.perf_counter()
+        oracle.propagate(el, w.tsince, threads=threads)
+        times.append(time.perf_counter() - t0)
+    states = n_sample * w.t_count
+    value = states * args.steps / sum(times)
+    sample = (f"all {w.n} satellites x {w.t_count} times per step" if n_sample == w.n else
+              f"first {n_sample} of {w.n} satellites x {w.t_count} times per step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
@@ -339,6 +530,7 @@ def run_reference(args):
         "data": "synthetic",
         "config": {"workload": w.name, "n_sats": w.n, "t_count": w.t_count,
                    "precision": "fp64 (CPU oracle)"},
+        "best_step_states_per_s": states / min(times),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -513,24 +705,46 @@ def run_ours(args):
                      "peak_basis": f"{n_sm} SMs x {FP64_LANES_PER_SM_CLK} FP64 lanes x "
                                    f"{sm_mhz:.0f} MHz"}
 
+    threads = os.cpu_count() or 1
     # Batched uneven requests: 256 requests, each with its own grid, in one persistent
     # launch replayed from a CUDA graph with the autotuned tile (FP32).
     batched = None
     if not args.no_batched:
-        batched = run_batched(torch, dev, stream, flush, max(3, min(args.steps, 5)))
+        batched = run_batched(torch, dev, stream, flush, max(3, min(args.steps, 5)),
+                              sample_requests=0 if args.no_configs else 16, threads=threads)
     adjoint = None
     if not args.no_adjoint:
         adjoint = run_adjoint(torch, dev, stream, flush, max(3, min(args.steps, 5)), alu_peak,
                               fp64_peak)
 
+    # Every workload: states/s of the step and of the launch in both precisions, the
+    # launch's roofline, the error against the oracle over the whole horizon and the
+    # oracle's own rate on the host cores.
+    configs = None
+    if rank == 0 and not args.no_configs:
+        common = dict(threads=threads, alu_peak=alu_peak, fp64_peak=fp64_peak,
+                      hbm_peak=peaks["hbm_gbs"], time_cpu=not args.no_cpu_baseline)
+        cs = max(3, min(args.steps, 10))
+        configs = {
+            "1": run_single_config(torch, dev, stream, flush, cs, W.config1(), ("fp64", "fp32"),
+                                   None, **common),
+            "2": run_single_config(torch, dev, stream, flush, cs, W.config2(), ("fp32", "fp64"),
+                                   None, **common),
+            "3": run_single_config(torch, dev, stream, flush, cs, W.config3(), ("fp32", "fp64"),
+                                   20_000, **common),
+            "4": batched,
+            "5": run_single_config(torch, dev, stream, flush, cs, W.config5(), ("fp32", "fp64"),
+                                   None, **common),
+        }
+        if adjoint is not None:
+            configs["5"]["adjoint"] = "see the line's adjoint object (same workload)"
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        threads = os.cpu_count() or 1
-        rate, dt = cpu_oracle_rate(w.elements, w.tsince, min(args.cpu_sats, n), threads)
+        rate, per_call, reps = time_oracle(w.elements, w.tsince, threads)
         cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {min(args.cpu_sats, n)} of {n} satellites x {T} times, "
-                         f"{dt:.2f} s wall on {threads} threads "
-                         f"({dt * threads:.0f} core-s)"}
+               "sample": f"all {n} satellites x {T} times per call; best of 5 trials of "
+                         f"{reps} call(s), {per_call:.2f} s per call on {threads} threads"}
 
     if rank == 0:
         line = {
@@ -550,6 +764,7 @@ def run_ours(args):
             "roofline": roofline,
             "batched": batched,
             "adjoint": adjoint,
+            "configs": configs,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
@@ -568,11 +783,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--cpu-sats", type=int, default=9341)
-    ap.add_argument("--ref-sats", type=int, default=1000)
+    ap.add_argument("--ref-sats", type=int, default=9341)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-configs", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

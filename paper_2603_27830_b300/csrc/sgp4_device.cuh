@@ -529,6 +529,17 @@ constexpr float kGuardR = 5.0e-5f;
 // error (~6e-8 of it) reaches the position once it exceeds a radian, so such states are
 // recomputed in FP64 too (inclinations within a few hundredths of a degree of 180).
 constexpr float kGuardLongPeriod = 1.0f;
+// The drag part of the mean longitude, n0'' (L2 t^2 + .. + L5 t^5), is evaluated in FP32
+// (in revolutions): its rounding error (a few 1e-7 of it) reaches the along-track
+// position as it grows, and on records whose drag polynomial of the semi-major axis has
+// passed its minimum (the mean orbit then balloons to millions of km) it reaches
+// thousands of revolutions.  Past one revolution (about 13 m of along-track error at
+// LEO radius) the state is recomputed in FP64: 4e-4 of the seven-day catalogue's
+// states, none of the one-day workloads'.
+#ifndef SGP4_GUARD_DRAG_PHASE
+#define SGP4_GUARD_DRAG_PHASE 1.0f
+#endif
+constexpr float kGuardDragPhase = SGP4_GUARD_DRAG_PHASE;
 constexpr int kRecomputeFP64 = -1;
 
 // One state in FP32 with the n*t phase in double-float.  (th, tl) is tsince split as
@@ -576,7 +587,9 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   p = p - round_magic(p);                              // exact
   float y = wrap_rev(p + rc.phi0h);
   y += s + rc.phi0l;
-  y += wrap_rev(rc.n0ppr * templ);
+  const float lrev = rc.n0ppr * templ;
+  const bool g_l = !(fabsf(lrev) < kGuardDragPhase);
+  y += wrap_rev(lrev);
 
   const float argp = wrap_rev(fmaf(rc.argpdr, t, rc.argp0r) - dd * kInvTwoPiF) * kTwoPiF;
   const float raan = wrap_rev(fmaf(rc.raancfr, t2, fmaf(rc.raandr, t, rc.raan0r))) * kTwoPiF;
@@ -661,7 +674,7 @@ __device__ __forceinline__ int state32(const Rec32& rc, const GeoF& g, float th,
   v[1] = (rdotk * uy + rfdotk * vy) * g.vkmps;
   v[2] = (rdotk * uz + rfdotk * vz) * g.vkmps;
   // A guard matters only while no earlier check has failed for certain.
-  const bool need64 = g_e | (!f_e & (g_lp | g_p | (!f_p & (g_r | g_d))));
+  const bool need64 = g_e | (!f_e & (g_lp | g_l | g_p | (!f_p & (g_r | g_d))));
   int code = f_e ? 1 : (f_p ? 4 : (rk < 1.0f ? 6 : 0));
   code = need64 ? kRecomputeFP64 : code;
   return code0 ? code0 : code;

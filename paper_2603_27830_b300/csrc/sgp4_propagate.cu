@@ -81,16 +81,22 @@ __device__ __forceinline__ void epoch_minutes(const RecordPtrs& rp, int64_t rec,
 // of an out-of-line FP64 state there made the loops spill registers (7-13% of their
 // time).  The loop queues the state's index in shared memory and marks its status;
 // after the loop the block recomputes the queued states in FP64 (fix_queued).  A block
-// that met more than kFixCap of them rescans its own units for the mark instead.
+// that met more than the queue's capacity of them rescans its own units for the mark
+// instead (one thread per unit, so a thread may then recompute several states in a row).
+// The batched kernel's tiles hold kFixCap entries; the single-problem kernel's queue
+// takes the dynamic shared memory that the time grid's split table leaves free (at least
+// kFixCap entries, 6,300 on a 100-time grid): a few blocks of the catalogue workload
+// queue close to 300 states, and their rescans had made the whole launch 55% longer.
 constexpr int kFixCap = 256;
 struct FixQueue {
-  int64_t idx[kFixCap];   // state index within the range, j * T + i
-  int n;                  // states queued (above kFixCap: the queue overflowed)
+  int64_t* idx;   // state index within the range, j * T + i
+  int cap;        // entries idx holds
+  int n;          // states queued (above cap: the queue overflowed)
 };
 
 __device__ __forceinline__ void queue_fix(FixQueue* fq, int32_t* status, int64_t idx) {
   const int slot = atomicAdd(&fq->n, 1);
-  if (slot < kFixCap) fq->idx[slot] = idx;
+  if (slot < fq->cap) fq->idx[slot] = idx;
   __stcs(status + idx, kRecomputeFP64);
 }
 
@@ -144,7 +150,7 @@ __device__ __forceinline__ void fix_queued(const RecordPtrs& rp, const Geo& g, c
     if (cd != 0 && cd != 6) { gr[0] = q; gr[1] = q; gr[2] = q; gv[0] = q; gv[1] = q; gv[2] = q; }
     __stcs(rg.status + idx, cd);
   };
-  if (n <= kFixCap) {
+  if (n <= fq->cap) {
     for (int e = threadIdx.x; e < n; e += kThreads) fix(fq->idx[e]);
   } else {
     const UnitMap<kSpu, kCons> um{T, (T + kSpu - 1) / kSpu};
@@ -487,14 +493,20 @@ constexpr int kSplitMaxT = 6144;
 template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false, bool kCons = false>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     propagate_kernel(PropArgs a, int64_t chunk) {
-  extern __shared__ __align__(16) float2 s_split[];   // [t_count] when use_split
+  // FP32: [t_count] split times when use_split, then the guard-band queue
+  extern __shared__ __align__(16) float2 s_split[];
   __shared__ FixQueue s_fq;
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
   if (beg >= end) return;
-  if (kFP32 && threadIdx.x == 0) s_fq.n = 0;
   const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
+  if (kFP32 && threadIdx.x == 0) {
+    const int used = use_split ? (int)a.t_count : 0;
+    s_fq.idx = reinterpret_cast<int64_t*>(s_split + used);
+    s_fq.cap = kSplitMaxT + kFixCap - used;
+    s_fq.n = 0;
+  }
   const int32_t jd0 = a.jd_day ? __ldg(a.jd_day) : 0;
   if (use_split) {
     // minutes since epoch, or for absolute times minutes from the grid's first day (each
@@ -543,6 +555,7 @@ template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
     batched_kernel(BatchArgs a) {
   __shared__ unsigned long long s_tile;
+  __shared__ int64_t s_fq_idx[kFixCap];
   __shared__ FixQueue s_fq;
   const GeoF gf = a.gf;
   const int64_t total_tiles = a.tile_start[a.n_req];
@@ -550,6 +563,8 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   for (;;) {
     if (threadIdx.x == 0) {
       s_tile = atomicAdd(a.counter, 1ULL);
+      s_fq.idx = s_fq_idx;
+      s_fq.cap = kFixCap;
       s_fq.n = 0;
     }
     __syncthreads();
@@ -641,15 +656,16 @@ template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false, bool kCons 
 cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   if (total == 0) return cudaSuccess;
-  const bool use_split = kFP32 && !a.grid_per_sat && a.t_count <= kSplitMaxT;
-  const size_t dyn = use_split ? (size_t)a.t_count * sizeof(float2) : 0;
-  // Resident blocks per SM of this kernel, taken with the largest split table so that
-  // the wave below is resident whatever the grid length.  FP32 opts in to the 48 KB
-  // split table beside the static guard-band queue.
+  // FP32: the split table and the guard-band queue share kFP32Dyn bytes of dynamic
+  // shared memory (an opt-in above 48 KB), whatever the grid length, so that the
+  // resident blocks per SM below hold for every launch.
+  constexpr size_t kFP32Dyn = (size_t)(kSplitMaxT + kFixCap) * sizeof(int64_t);
+  static_assert(sizeof(int64_t) == sizeof(float2), "queue entries reuse split slots");
+  const size_t dyn = kFP32 ? kFP32Dyn : 0;
   static std::atomic<int> bps_dev[kMaxDevices];
   int bps = 0;
   const cudaError_t be = device_bps(bps_dev, propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>,
-                                    kFP32 ? kSplitMaxT * sizeof(float2) : 0, kFP32, &bps);
+                                    dyn, kFP32, &bps);
   if (be != cudaSuccess) return be;
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);

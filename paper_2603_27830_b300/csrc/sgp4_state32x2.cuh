@@ -158,7 +158,9 @@ __device__ __forceinline__ void state32x2(const Rec32& rc, const GeoF& g, float2
   p = wrap_rev(p);                                             // exact
   F2 y = wrap_rev(add(p, S(rc.phi0h)));
   y = add(y, add(s, S(rc.phi0l)));
-  y = add(y, wrap_rev(mul(S(rc.n0ppr), templ)));
+  const F2 lrev = mul(S(rc.n0ppr), templ);
+  const bool g_l[2] = {!x2::lt_abs(lrev.x, kGuardDragPhase), !x2::lt_abs(lrev.y, kGuardDragPhase)};
+  y = add(y, wrap_rev(lrev));
 
   const F2 argp =
       mul(wrap_rev(fma(dd, S(-kInvTwoPiF), fma(S(rc.argpdr), t, S(rc.argp0r)))), S(kTwoPiF));
@@ -255,7 +257,8 @@ __device__ __forceinline__ void state32x2(const Rec32& rc, const GeoF& g, float2
 
   const float rkv[2] = {rk.x, rk.y};
   for (int l = 0; l < 2; ++l) {
-    const bool need64 = g_e[l] | (!f_e[l] & (g_lp[l] | g_p[l] | (!f_p[l] & (g_r[l] | g_d[l]))));
+    const bool need64 =
+        g_e[l] | (!f_e[l] & (g_lp[l] | g_l[l] | g_p[l] | (!f_p[l] & (g_r[l] | g_d[l]))));
     int cd = f_e[l] ? 1 : (f_p[l] ? 4 : (rkv[l] < 1.0f ? 6 : 0));
     cd = need64 ? kRecomputeFP64 : cd;
     code[l] = code0 ? code0 : cd;

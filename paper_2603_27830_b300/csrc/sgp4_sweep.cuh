@@ -287,6 +287,12 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
   p = p - round_magic(p);
   float y = wrap_rev(p + rc.phi0h);
   y += s + rc.phi0l;
+  // The propagation also recomputes in FP64 the states whose drag phase n0'' templ
+  // passes one revolution (kGuardDragPhase); the sweeps do not.  Those are orbits whose
+  // drag polynomial of the semi-major axis has passed its minimum and which balloon (5
+  // of the fitting workload's 10,000 satellites): sweeping their late states in FP64
+  // made the FP32 adjoint 27% slower, so there the adjoint's, Jacobian's and fit's
+  // FP32 forward values keep that term's FP32 rounding.
   y += wrap_rev(rc.n0ppr * templ);
   const float argp = wrap_rev(fmaf(rc.argpdr, t, rc.argp0r) - dd * kInvTwoPiF) * kTwoPiF;
   const float raan = wrap_rev(fmaf(rc.raancfr, t2, fmaf(rc.raandr, t, rc.raan0r))) * kTwoPiF;

@@ -7,7 +7,8 @@ Workloads: near-earth (64 x 100), starlink (9,341 x 1,000), catalogue (1,000,000
 log-U[10,500]: the batched persistent launch), adjoint (the fitting workload,
 10,000 x 500: one sgp4_adjoint call), fit (the same workload: one sgp4_fit_step call
 against observations of the perturbed elements), jacobian (the same workload: one
-sgp4_jacobian call with an element covariance).  Prints the wall time of each
+sgp4_jacobian call with an element covariance), fit-forward (the same workload: init +
+propagate).  Prints the wall time of each
 repetition.
 """
 from __future__ import annotations
@@ -90,7 +91,7 @@ def run_jacobian(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=["near-earth", "starlink", "catalogue", "batch",
-                                           "adjoint", "fit", "jacobian"],
+                                           "adjoint", "fit", "jacobian", "fit-forward"],
                     default="starlink")
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="fp32")
     ap.add_argument("--reps", type=int, default=2)
@@ -108,6 +109,8 @@ def main():
         w = W.config1()
     elif args.workload == "starlink":
         w = W.config2()
+    elif args.workload == "fit-forward":
+        w = W.config5(n=args.n or 10_000)
     else:
         w = W.config3(n=args.n or 1_000_000)
     el = torch.as_tensor(w.elements, device="cuda")

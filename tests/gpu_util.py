@@ -6,6 +6,26 @@ import numpy as np
 FP64_TOL_R_KM = 1e-6
 FP64_TOL_V_KMS = 1e-9
 
+# FP32 bounds against the FP64 oracle, by how far the grid reaches from the epoch.
+# Grids within one day: the one-day target, max |dr| <= 0.1 km.
+FP32_ONE_DAY_KM = 0.1
+FP32_ONE_DAY_KMS = 1e-4
+# Grids over [-0.5, 2] days (the uneven-request workload, the ragged, strided and
+# guard-band grids, the edge records): measured max 0.068 km and 7.8e-5 km/s (all 2.2e9
+# states of the uneven batch: 0.049 km, p99 6 m).
+FP32_TWO_DAY_KM = 0.1
+FP32_TWO_DAY_KMS = 2e-4
+# The seven-day catalogue (B* up to 1e-2, records that decay within the span): every
+# state of the 1e8 within 0.06 km and 5.3e-5 km/s, except where float32 cannot hold the
+# value that closely (next bar).
+FP32_CATALOGUE_7D_KM = 0.1
+FP32_CATALOGUE_7D_KMS = 2e-4
+# A float32 output holds each component to half an ulp, 2^-24 of its size, so no FP32
+# result is closer than ~1e-7 |r| to the oracle: on records whose mean orbit balloons to
+# millions of km (and on decayed states deep inside the Earth with absurd speeds, which
+# the theory still returns with code 6) the bar is FP32_STORE_REL |r| (|v|).
+FP32_STORE_REL = 2e-7
+
 
 def gpu_propagate(elements, tsince, precision, fixups=False):
     import torch
@@ -63,3 +83,136 @@ def valid_codes_only(st) -> bool:
         if not bool(torch.all(ok)):
             return False
     return True
+
+
+# ---------------------------------------------------------------- FP64 conditioning
+# Where the theory is ill-conditioned (records with B* near 1e-2 whose mean semi-major
+# axis, a polynomial in t, passes its minimum and grows again, reaching 1e6-1e7 km, and
+# orbits that have decayed deep inside the Earth), the oracle's own r moves by more than
+# 1e-6 km when one input element changes in its last bits, so no FP64 implementation with
+# a different rounding order can meet the absolute bar there.  For those states the bar
+# is COND_FACTOR times the oracle's measured sensitivity: the largest change of r (and v)
+# when one of the seven elements is perturbed by COND_REL_STEP relative (16 ulps).
+COND_REL_STEP = 2.0 ** -49
+COND_FACTOR = 4.0
+# Scale of each element for the perturbation when the element itself is zero:
+# n0 (rad/min), e0, i0, RAAN0, argp0, M0 (rad), B* (1/ER).
+_COND_SCALE = np.array([0.01, 1e-3, 1.0, 1.0, 1.0, 1.0, 1e-5])
+
+
+def oracle_sensitivity(elements, tsince):
+    """Per state, the largest |dr| (km) and |dv| (km/s) of the oracle when one of the
+    seven elements of the satellite moves by COND_REL_STEP of itself."""
+    import oracle
+    el = np.ascontiguousarray(elements, dtype=np.float64)
+    r0, v0, s0, _ = oracle.propagate(el, tsince)
+    sr = np.zeros(s0.shape)
+    sv = np.zeros(s0.shape)
+    for j in range(7):
+        e2 = el.copy()
+        e2[:, j] += COND_REL_STEP * np.maximum(np.abs(el[:, j]), _COND_SCALE[j])
+        r2, v2, s2, _ = oracle.propagate(e2, tsince)
+        ok = ((s0 == 0) | (s0 == 6)) & ((s2 == 0) | (s2 == 6))
+        sr = np.maximum(sr, np.where(ok, np.linalg.norm(r2 - r0, axis=-1), 0.0))
+        sv = np.maximum(sv, np.where(ok, np.linalg.norm(v2 - v0, axis=-1), 0.0))
+    return sr, sv
+
+
+def assert_fp64_within_conditioning(dr, dv, elements, tsince, keep):
+    """dr, dv [n, T] (NaN or 0 where the state has no output; keep marks states with
+    output): every state within the absolute FP64 bar, or, where the oracle itself is
+    ill-conditioned, within COND_FACTOR times its measured sensitivity.  Returns the
+    number of states that needed the conditioning bar."""
+    over = keep & ((dr > FP64_TOL_R_KM) | (dv > FP64_TOL_V_KMS))
+    if not over.any():
+        return 0
+    sats = np.unique(np.nonzero(over)[0])
+    t = tsince[sats] if np.ndim(tsince) == 2 else tsince
+    sr, sv = oracle_sensitivity(np.asarray(elements)[sats], t)
+    o = over[sats]
+    bar_r = np.maximum(FP64_TOL_R_KM, COND_FACTOR * sr)
+    bar_v = np.maximum(FP64_TOL_V_KMS, COND_FACTOR * sv)
+    bad_r = o & (dr[sats] > bar_r)
+    bad_v = o & (dv[sats] > bar_v)
+    assert not bad_r.any() and not bad_v.any(), {
+        "states_over_abs": int(o.sum()), "over_cond_r": int(bad_r.sum()),
+        "over_cond_v": int(bad_v.sum()), "max_dr": float(dr[sats][o].max()),
+        "sens_r_at_max": float(sr[o][np.argmax(dr[sats][o])])}
+    return int(o.sum())
+
+
+def device_state_errors(r_g, v_g, st_g, rr, vr, sr, norms=False):
+    """On the device: statuses equal to the oracle's bit for bit, NaN exactly where
+    the status says so, finite elsewhere; returns |dr| and |dv| [n, T] as float64
+    numpy arrays with 0 where the state has no output, and the keep mask (with
+    norms=True also the oracle's |r| and |v|)."""
+    import torch
+    dev = st_g.device
+    so = torch.as_tensor(sr, device=dev)
+    mism = st_g != so
+    if bool(mism.any()):
+        k = torch.nonzero(mism)[:5].cpu().numpy().tolist()
+        raise AssertionError(f"{int(mism.sum())} status mismatches, first {k}")
+    keep = (so == 0) | (so == 6)
+    rg = r_g.double()
+    vg = v_g.double()
+    nan_r = torch.isnan(rg).any(-1)
+    nan_v = torch.isnan(vg).any(-1)
+    assert bool(torch.all(nan_r[~keep])) and bool(torch.all(nan_v[~keep])), "missing NaN"
+    assert bool(torch.all(torch.isfinite(rg[keep]))) and bool(
+        torch.all(torch.isfinite(vg[keep]))), "non-finite output on a valid state"
+    ro = torch.as_tensor(rr, device=dev)
+    vo = torch.as_tensor(vr, device=dev)
+    dr = torch.where(keep, (rg - ro).nan_to_num(0.0).norm(dim=-1), 0.0)
+    dv = torch.where(keep, (vg - vo).nan_to_num(0.0).norm(dim=-1), 0.0)
+    out = (dr.cpu().numpy(), dv.cpu().numpy(), keep.cpu().numpy())
+    if norms:
+        out += (ro.nan_to_num(0.0).norm(dim=-1).cpu().numpy(),
+                vo.nan_to_num(0.0).norm(dim=-1).cpu().numpy())
+    return out
+
+
+def fp32_excess(dr, dv, rn, vn, keep, bar_r, bar_v):
+    """States whose FP32 error exceeds both the absolute bar and the float32
+    representation bar FP32_STORE_REL |r| (|v|); and how many needed the latter."""
+    over_abs = keep & ((dr > bar_r) | (dv > bar_v))
+    bad = keep & ((dr > np.maximum(bar_r, FP32_STORE_REL * rn)) |
+                  (dv > np.maximum(bar_v, FP32_STORE_REL * vn)))
+    return int(bad.sum()), int(over_abs.sum())
+
+
+class ErrorStats:
+    """Running max and p99 of |dr|, |dv| over chunks; the p99 comes from histograms
+    with 100 bins per decade (1e-15 .. 1e5), so it is good to about 2.3%."""
+
+    LO, HI, PER_DECADE = -15.0, 5.0, 100
+
+    def __init__(self):
+        self.n = 0
+        self.max_dr = 0.0
+        self.max_dv = 0.0
+        nb = int((self.HI - self.LO) * self.PER_DECADE) + 2
+        self.hr = np.zeros(nb, dtype=np.int64)
+        self.hv = np.zeros(nb, dtype=np.int64)
+
+    def _bins(self, x):
+        lg = np.log10(np.maximum(x, 10.0 ** self.LO))
+        b = np.floor((lg - self.LO) * self.PER_DECADE).astype(np.int64) + 1
+        return np.clip(b, 0, len(self.hr) - 1)
+
+    def add(self, dr, dv):
+        if dr.size == 0:
+            return
+        self.n += dr.size
+        self.max_dr = max(self.max_dr, float(dr.max()))
+        self.max_dv = max(self.max_dv, float(dv.max()))
+        self.hr += np.bincount(self._bins(dr), minlength=len(self.hr))
+        self.hv += np.bincount(self._bins(dv), minlength=len(self.hv))
+
+    def _p99(self, h):
+        b = int(np.searchsorted(np.cumsum(h), 0.99 * h.sum()))
+        return float(10.0 ** (self.LO + b / self.PER_DECADE))   # upper edge of the bin
+
+    def summary(self):
+        return {"n": self.n, "max_dr_km": self.max_dr, "p99_dr_km": self._p99(self.hr),
+                "max_dv_kms": self.max_dv, "p99_dv_kms": self._p99(self.hv)}

@@ -11,7 +11,8 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import valid_codes_only, FP64_TOL_R_KM, assert_status_and_nan, error_summary, state_errors
+from gpu_util import (FP32_TWO_DAY_KM, FP32_TWO_DAY_KMS, FP64_TOL_R_KM, ErrorStats,
+                      assert_status_and_nan, device_state_errors, error_summary, state_errors)
 from paper_2603_27830_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -83,7 +84,7 @@ def test_batched_against_oracle(precision):
         rg, vg, sg = r[sl].reshape(n, T, 3), v[sl].reshape(n, T, 3), st[sl].reshape(n, T)
         assert_status_and_nan(sg, sr, rg, vg)
         dr, dv = state_errors(rg, vg, rr, vr, sr)
-        tol = FP64_TOL_R_KM if precision == "fp64" else 1.0
+        tol = FP64_TOL_R_KM if precision == "fp64" else FP32_TWO_DAY_KM
         if dr.size:
             assert dr.max() <= tol, error_summary(dr, dv)
 
@@ -115,7 +116,7 @@ def test_batched_guard_band_queue_overflow_fp32():
             assert_status_and_nan(sg, sr, rg, vg)
             dr, dv = state_errors(rg, vg, rr, vr, sr)
             if dr.size:
-                assert dr.max() <= 1.0, error_summary(dr, dv)
+                assert dr.max() <= FP32_TWO_DAY_KM, error_summary(dr, dv)
 
 
 def test_tile_size_does_not_change_results():
@@ -226,8 +227,11 @@ def test_plan_larger_than_buffers_is_rejected():
 
 def test_uneven_requests_full_size_autotuned():
     """256 uneven requests (N log-U[100, 5e4], T log-U[10, 5e3], grids U[-720, 2880])
-    in one autotuned persistent launch, FP32; every invalid record and a sample of
-    each of 16 requests checked against the oracle."""
+    in one autotuned persistent launch, FP32, against the oracle on every state of
+    every request: statuses bit-exact, NaN where they say so, |dr| and |dv| within the
+    two-day FP32 bound."""
+    import json
+
     import torch
 
     from paper_2603_27830_b300 import autotune, make_batch, sgp4_init, sgp4_propagate_batched
@@ -244,19 +248,25 @@ def test_uneven_requests_full_size_autotuned():
                                       use_cache=False)
     r, v, st = sgp4_propagate_batched(plan, recs, ts, "fp32", out=out)
     torch.cuda.synchronize()
-    assert valid_codes_only(st)
-    rng = np.random.default_rng(0)
-    for k in rng.choice(len(reqs), 16, replace=False):
-        sat0, n, t0, T, out0 = b.requests[k]
-        pick = np.unique(np.concatenate([rng.choice(n, min(n, 40), replace=False),
-                                         np.flatnonzero(reqs[k].elements[:, 1] >= 1.0)]))
-        rr, vr, sr, _ = oracle.propagate(reqs[k].elements[pick], reqs[k].tsince)
-        idx = torch.as_tensor((out0 + pick[:, None] * T + np.arange(T)[None, :]).reshape(-1),
-                              device="cuda")
-        rg = r[idx].double().cpu().numpy().reshape(len(pick), T, 3)
-        vg = v[idx].double().cpu().numpy().reshape(len(pick), T, 3)
-        sg = st[idx].cpu().numpy().reshape(len(pick), T)
-        assert_status_and_nan(sg, sr, rg, vg)
-        dr, dv = state_errors(rg, vg, rr, vr, sr)
-        if dr.size:
-            assert dr.max() <= 1.0, (k, error_summary(dr, dv))
+    ist_h = ist.cpu().numpy()
+    stats = ErrorStats()
+    checked = 0
+    for k, (sat0, n, t0, T, out0) in enumerate(b.requests):
+        if n * T == 0:
+            continue
+        step = max(1, 4_000_000 // T)                # satellites per oracle chunk
+        for a in range(0, n, step):
+            m = min(n, a + step) - a
+            rr, vr, sr, isr = oracle.propagate(reqs[k].elements[a:a + m], reqs[k].tsince)
+            np.testing.assert_array_equal(ist_h[sat0 + a:sat0 + a + m], isr)
+            o = out0 + a * T
+            dr, dv, keep = device_state_errors(r[o:o + m * T].view(m, T, 3),
+                                               v[o:o + m * T].view(m, T, 3),
+                                               st[o:o + m * T].view(m, T), rr, vr, sr)
+            stats.add(dr[keep], dv[keep])
+            checked += m * T
+    assert checked == S
+    summ = {"case": "uneven-256-requests-fp32", **stats.summary(),
+            "tile_states": entry["tile_states"]}
+    print(json.dumps(summ))
+    assert summ["max_dr_km"] <= FP32_TWO_DAY_KM and summ["max_dv_kms"] <= FP32_TWO_DAY_KMS, summ

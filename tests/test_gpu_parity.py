@@ -13,8 +13,11 @@ import numpy as np
 import pytest
 
 import oracle
-from gpu_util import (valid_codes_only, FP64_TOL_R_KM, FP64_TOL_V_KMS, assert_status_and_nan, error_summary,
-                      gpu_propagate, state_errors)
+from gpu_util import (FP32_CATALOGUE_7D_KM, FP32_CATALOGUE_7D_KMS, FP32_ONE_DAY_KM,
+                      FP32_ONE_DAY_KMS, FP32_TWO_DAY_KM, FP32_TWO_DAY_KMS, FP64_TOL_R_KM,
+                      FP32_STORE_REL, FP64_TOL_V_KMS, ErrorStats, assert_fp64_within_conditioning,
+                      assert_status_and_nan, device_state_errors, error_summary,
+                      fp32_excess, gpu_propagate, state_errors)
 from paper_2603_27830_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -26,11 +29,14 @@ def _check_fp64(el, t):
     r, v, st, ist = gpu_propagate(el, t, "fp64")
     rr, vr, sr, isr = oracle.propagate(el, t)
     assert_status_and_nan(st, sr, r, v, ist, isr)
-    dr, dv = state_errors(r, v, rr, vr, sr)
-    if dr.size:
-        assert dr.max() <= FP64_TOL_R_KM, error_summary(dr, dv)
-        assert dv.max() <= FP64_TOL_V_KMS, error_summary(dr, dv)
-    return error_summary(dr, dv)
+    keep = (sr == 0) | (sr == 6)
+    dr = np.where(keep, np.linalg.norm(np.nan_to_num(r - rr), axis=-1), 0.0)
+    dv = np.where(keep, np.linalg.norm(np.nan_to_num(v - vr), axis=-1), 0.0)
+    n_cond = assert_fp64_within_conditioning(dr, dv, el, t, keep)
+    summ = error_summary(dr[keep], dv[keep])
+    summ["states_on_conditioning_bar"] = n_cond
+    print(json.dumps(summ))
+    return summ
 
 
 def _check_fp32(el, t, max_dr_km, max_dv_kms, max_dr_code0_km=None):
@@ -46,10 +52,14 @@ def _check_fp32(el, t, max_dr_km, max_dv_kms, max_dr_code0_km=None):
     ok0 = sr == 0
     summ["max_dr_code0_km"] = (float(np.linalg.norm(r[ok0] - rr[ok0], axis=-1).max())
                                if ok0.any() else 0.0)
+    keep = (sr == 0) | (sr == 6)
+    rn = np.linalg.norm(rr[keep], axis=-1)
+    vn = np.linalg.norm(vr[keep], axis=-1)
+    summ["states_on_float32_bar"] = int(((dr > max_dr_km) | (dv > max_dv_kms)).sum())
     print(json.dumps(summ))
     if dr.size:
-        assert dr.max() <= max_dr_km, summ
-        assert dv.max() <= max_dv_kms, summ
+        assert np.all(dr <= np.maximum(max_dr_km, FP32_STORE_REL * rn)), summ
+        assert np.all(dv <= np.maximum(max_dv_kms, FP32_STORE_REL * vn)), summ
     if max_dr_code0_km is not None:
         assert summ["max_dr_code0_km"] <= max_dr_code0_km, summ
     return summ
@@ -63,7 +73,7 @@ def test_near_earth_64x100_fp64():
 
 def test_near_earth_64x100_fp32():
     w = W.config1()
-    _check_fp32(w.elements, w.tsince, 0.1, 1e-4)
+    _check_fp32(w.elements, w.tsince, FP32_ONE_DAY_KM, FP32_ONE_DAY_KMS)
 
 
 @pytest.mark.parametrize("seed", [0, 1])
@@ -75,7 +85,21 @@ def test_starlink_9341x1000_fp64(seed):
 @pytest.mark.parametrize("seed", [0, 1])
 def test_starlink_9341x1000_fp32(seed):
     w = W.config2(seed)
-    _check_fp32(w.elements, w.tsince, 0.1, 1e-4)
+    _check_fp32(w.elements, w.tsince, FP32_ONE_DAY_KM, FP32_ONE_DAY_KMS)
+
+
+def test_fit_workload_10000x500_fp64():
+    """The element-fitting workload's forward propagation (n U[12,16] rev/day, e up to
+    0.05: some perigees inside the atmosphere, whose mean orbits decay and then balloon
+    within the day)."""
+    w = W.config5()
+    summ = _check_fp64(w.elements, w.tsince)
+    assert summ["states_on_conditioning_bar"] <= 1e-3 * w.states, summ
+
+
+def test_fit_workload_10000x500_fp32():
+    w = W.config5()
+    _check_fp32(w.elements, w.tsince, FP32_ONE_DAY_KM, FP32_ONE_DAY_KMS)
 
 
 def test_catalogue_small_fp64():
@@ -89,12 +113,20 @@ def test_catalogue_small_fp32():
     # seven days and B* up to 1e-2; the largest errors (0.17 km) are in records that
     # have decayed days earlier (deliberately invalid ones with a perigee below the
     # surface among them), whose states alternate between status 6 and 0
-    _check_fp32(w.elements, w.tsince, 0.25, 2e-3)
+    _check_fp32(w.elements, w.tsince, FP32_CATALOGUE_7D_KM, FP32_CATALOGUE_7D_KMS)
 
 
-def test_catalogue_full_size_sampled():
-    """1,000,000 x 100 in the launch configuration of the benchmark; the oracle checks
-    every invalid record and a random sample of the rest."""
+def _summary_line(name, dr, dv, extra=None):
+    summ = {"case": name, **error_summary(dr, dv), **(extra or {})}
+    print(json.dumps(summ))
+    return summ
+
+
+def test_catalogue_full_size_every_state():
+    """1,000,000 x 100 over 7 days in the launch configuration of the benchmark, both
+    precisions, against the oracle on every state: statuses bit-exact, FP64 r and v
+    within 1e-6 km and 1e-9 km/s (or, on the few ill-conditioned states, within the
+    oracle's own measured sensitivity), FP32 within the seven-day catalogue bound."""
     import torch
 
     from paper_2603_27830_b300 import sgp4_init, sgp4_propagate
@@ -102,23 +134,41 @@ def test_catalogue_full_size_sampled():
     el = torch.as_tensor(w.elements, device="cuda")
     ts = torch.as_tensor(w.tsince, device="cuda")
     recs, ist = sgp4_init(el)
-    rng = np.random.default_rng(0)
-    invalid = w.meta["invalid"]
-    sample = np.unique(np.concatenate([invalid, rng.choice(w.n, 3000, replace=False)]))
-    rr, vr, sr, isr = oracle.propagate(w.elements[sample], w.tsince)
-    for prec, tol in (("fp64", FP64_TOL_R_KM), ("fp32", 2.0)):
-        r, v, st = sgp4_propagate(recs, ts, prec)
-        torch.cuda.synchronize()
-        idx = torch.as_tensor(sample, device="cuda")
-        rs = r[idx].double().cpu().numpy()
-        vs = v[idx].double().cpu().numpy()
-        ss = st[idx].cpu().numpy()
-        assert_status_and_nan(ss, sr, rs, vs, ist[idx].cpu().numpy(), isr)
-        dr, dv = state_errors(rs, vs, rr, vr, sr)
-        assert dr.max() <= tol, (prec, error_summary(dr, dv))
-        # every status of the full run is a valid code
-        assert valid_codes_only(st)
-        del r, v, st
+    out = {p: sgp4_propagate(recs, ts, p) for p in ("fp64", "fp32")}
+    torch.cuda.synchronize()
+    ist_h = ist.cpu().numpy()
+    stats = {p: ErrorStats() for p in out}
+    near = ErrorStats()             # FP32 on states within 50,000 km of the centre
+    cond_states = 0
+    bad32 = store32 = 0
+    chunk = 100_000
+    for s0 in range(0, w.n, chunk):
+        sl = slice(s0, min(w.n, s0 + chunk))
+        rr, vr, sr, isr = oracle.propagate(w.elements[sl], w.tsince)
+        np.testing.assert_array_equal(ist_h[sl], isr)
+        for p, (r, v, st) in out.items():
+            dr, dv, keep, rn, vn = device_state_errors(r[sl], v[sl], st[sl], rr, vr, sr,
+                                                       norms=True)
+            stats[p].add(dr[keep], dv[keep])
+            if p == "fp64":
+                cond_states += assert_fp64_within_conditioning(dr, dv, w.elements[sl],
+                                                               w.tsince, keep)
+            else:
+                m = keep & (rn < 5e4)
+                near.add(dr[m], dv[m])
+                b, o = fp32_excess(dr, dv, rn, vn, keep, FP32_CATALOGUE_7D_KM,
+                                   FP32_CATALOGUE_7D_KMS)
+                bad32 += b
+                store32 += o
+    s64 = stats["fp64"].summary()
+    s32 = stats["fp32"].summary()
+    print(json.dumps({"case": "catalogue-1e6x100-fp64", **s64,
+                      "states_on_conditioning_bar": cond_states}))
+    print(json.dumps({"case": "catalogue-1e6x100-fp32", **s32,
+                      "near_earth": near.summary(), "states_on_float32_bar": store32}))
+    assert cond_states <= 1e-5 * w.n * w.t_count, cond_states
+    assert bad32 == 0, (bad32, s32)
+    assert store32 <= 1e-5 * w.n * w.t_count, store32
 
 
 # ------------------------------------------------------------------ edge cases
@@ -153,6 +203,12 @@ def test_edge_elements(prec):
         r, v, st, ist = gpu_propagate(el, t, "fp32")
         rr, vr, sr, isr = oracle.propagate(el, t)
         assert_status_and_nan(st, sr, r, v, ist, isr)
+        keep = (sr == 0) | (sr == 6)
+        dr = np.where(keep, np.linalg.norm(r - rr, axis=-1), 0.0)
+        dv = np.where(keep, np.linalg.norm(v - vr, axis=-1), 0.0)
+        print(json.dumps({"case": "edge-fp32", "max_dr_km_per_record": dr.max(axis=1).tolist(),
+                          "max_dv_kms_per_record": dv.max(axis=1).tolist()}))
+        assert dr.max() <= FP32_TWO_DAY_KM and dv.max() <= FP32_TWO_DAY_KMS, dr.max(axis=1)
 
 
 @pytest.mark.parametrize("n,T", [(1, 1), (1, 127), (3, 1), (7, 13), (129, 1), (33, 129),
@@ -165,7 +221,7 @@ def test_ragged_shapes(n, T, prec):
     if prec == "fp64":
         _check_fp64(el, t)
     else:
-        _check_fp32(el, t, 1.0, 1e-3)
+        _check_fp32(el, t, FP32_TWO_DAY_KM, FP32_TWO_DAY_KMS)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -179,7 +235,7 @@ def test_partial_units(T, prec):
     if prec == "fp64":
         _check_fp64(el, t)
     else:
-        _check_fp32(el, t, 1.0, 1e-3)
+        _check_fp32(el, t, FP32_TWO_DAY_KM, FP32_TWO_DAY_KMS)
 
 
 @pytest.mark.parametrize("T", [77, 80])
@@ -193,7 +249,7 @@ def test_per_satellite_grid(prec, T):
     if prec == "fp64":
         _check_fp64(el, t)
     else:
-        _check_fp32(el, t, 1.0, 1e-3)
+        _check_fp32(el, t, FP32_TWO_DAY_KM, FP32_TWO_DAY_KMS)
 
 
 @pytest.mark.parametrize("T", [8192, 8194])
@@ -203,7 +259,7 @@ def test_long_shared_grid_fp32(T):
     rng = np.random.default_rng(T)
     el = W.catalogue_elements(rng, 5, invalid_frac=0.0)
     t = np.sort(rng.uniform(-720, 2880, T))
-    _check_fp32(el, t, 1.0, 1e-3)
+    _check_fp32(el, t, FP32_TWO_DAY_KM, FP32_TWO_DAY_KMS)
 
 
 def test_unaligned_per_satellite_grid_fp32():
@@ -229,7 +285,7 @@ def test_unaligned_per_satellite_grid_fp32():
     assert_status_and_nan(st, sr, r, v, ist.cpu().numpy(), isr)
     assert np.array_equal(st, st_al.cpu().numpy())
     dr, dv = state_errors(r, v, rr, vr, sr)
-    assert dr.max() <= 1.0 and dv.max() <= 1e-3, error_summary(dr, dv)
+    assert dr.max() <= FP32_TWO_DAY_KM and dv.max() <= FP32_TWO_DAY_KMS, error_summary(dr, dv)
 
 
 def _near_retrograde_equatorial(rng, n):
@@ -252,7 +308,7 @@ def test_guard_band_queue_overflow_fp32(T, per_sat, n):
     el = _near_retrograde_equatorial(rng, n)
     t = (np.sort(rng.uniform(-720, 2880, (n, T)), axis=1) if per_sat
          else np.linspace(0.0, 1440.0, T))
-    summ = _check_fp32(el, t, 1.0, 1e-3)
+    summ = _check_fp32(el, t, FP32_TWO_DAY_KM, FP32_TWO_DAY_KMS)
     assert summ["fp64_fixups"] > 0.6 * n * T, summ
 
 
@@ -264,7 +320,7 @@ def test_guard_band_states_mixed_into_a_catalogue_fp32():
     pick = rng.choice(2000, 40, replace=False)
     el[pick] = _near_retrograde_equatorial(rng, 40)
     t = np.linspace(-100.0, 2000.0, 64)
-    summ = _check_fp32(el, t, 1.0, 1e-3)
+    summ = _check_fp32(el, t, FP32_TWO_DAY_KM, FP32_TWO_DAY_KMS)
     assert summ["fp64_fixups"] >= 0.6 * 40 * 64, summ
 
 
@@ -424,15 +480,12 @@ def test_julian_date_grid_from_each_records_split_epoch(prec):
     dr, dv = state_errors(r[rows], v[rows], rr[rows], vr[rows], sr[rows])
     if prec == "fp64":
         # the enormous-drag edge record reaches |r| ~ 6.5e8 km at negative t, where the
-        # theory is ill-conditioned (an ulp in a record constant moves r by ~1e-11 of
-        # itself): there the bound is relative, 1e-10 |r|
-        keep = (sr[rows] == 0) | (sr[rows] == 6)
-        rn = np.linalg.norm(rr[rows][keep], axis=-1)
-        assert np.all(dr <= np.maximum(FP64_TOL_R_KM, 1e-10 * rn)), error_summary(dr, dv)
-        assert np.all(dv <= np.maximum(FP64_TOL_V_KMS, 1e-10 * np.linalg.norm(
-            vr[rows][keep], axis=-1) * np.maximum(1.0, rn / 1e5))), error_summary(dr, dv)
-        well = rn < 1e5
-        assert dr[well].max() <= FP64_TOL_R_KM, error_summary(dr[well], dv[well])
+        # theory is ill-conditioned: there the bar is the oracle's measured sensitivity
+        keep = (sr == 0) | (sr == 6)
+        dr2 = np.where(keep, np.linalg.norm(np.nan_to_num(r - rr), axis=-1), 0.0)
+        dv2 = np.where(keep, np.linalg.norm(np.nan_to_num(v - vr), axis=-1), 0.0)
+        n_cond = assert_fp64_within_conditioning(dr2, dv2, el, tsince, keep)
+        print(json.dumps({"case": "jd-edge-fp64", "states_on_conditioning_bar": n_cond}))
     else:
         assert dr.max() <= 0.1 and dv.max() <= 1e-4, error_summary(dr, dv)
 
