@@ -10,7 +10,7 @@ no fast-math), which restates the near-Earth SGP4 theory that the paper implemen
 WGS-72 constants).  The comments in that file list every reading of a point the
 paper leaves open.
 
-Parity status of each part (pins live in ``tests/test_oracle_*.py``):
+Parity status of each part (pins live in ``tests/oracle_pins.py``):
   * two-body geometry, Kepler solve, J2/J3/J4 periodics and secular rates: pinned
     (closed forms, bisection, numerical integration of the zonal force model);
   * drag: C1 and the decay polynomials D2..D4, L2..L5 pinned as the Taylor
@@ -18,12 +18,20 @@ Parity status of each part (pins live in ``tests/test_oracle_*.py``):
     part of C4 by orbit averages of Gauss's equations; C5 and the once-per-revolution
     perigee/mean-anomaly term by harmonics of the same equations integrated along the
     orbit; the quadratic node term by the chain rule on the J2 node rate;
+  * drag with zonals: the J2 terms of C2 and C4 by an integration of J2 and the
+    theory's atmosphere, C3 (drag with J3) by the drift of the eccentricity vector in
+    an integration with J3 x10 and drag;
   * the node rate with its second-order J2 and J4 parts: pinned by the node of a
-    long numerical integration;
-  * parity unpinned: C3 (drag with J3), the J2 part of C4, the second-order J2 and
-    J4 parts of the mean-anomaly and perigee rates, the second-order Kozai->Brouwer
-    recovery and the J3 long-period mean-longitude term xlcof (no independent check
-    reaches them).
+    long numerical integration; the J4 part of the perigee rate by the orbit- and
+    perigee-averaged J4 potential through Lagrange's equations;
+  * the J3 long-period term of the mean longitude (xlcof, with its 1 / (a(1 - e^2))
+    factor): pinned by the evolution of node + argument of latitude in an
+    integration with J3 x10;
+  * parity unpinned: the cos 2w part of C4's J2 term, the second-order J2 parts of
+    the mean-anomaly and perigee rates and the second-order Kozai->Brouwer recovery
+    (delta1, the a0 series) -- each a second-order effect that no comparison with a
+    numerical integration started from the theory's first-order osculating state can
+    resolve.
 """
 from __future__ import annotations
 

@@ -84,25 +84,36 @@ CAUGHT = [
     ("raandot J4 term", "2.0 * T3 * (3.0 - 7.0 * theta2)", "2.0 * T3 * (3.0 - 5.0 * theta2)"),
     ("T3 factor", "R T3 = -0.46875 * g.j4", "R T3 = -0.9375 * g.j4"),
     ("drag M term sign", "R c = 1.0 + rc.eta * cos(M_df);", "R c = 1.0 - rc.eta * cos(M_df);"),
-]
-
-# Terms that no independent check reaches (documented as parity-unpinned).
-UNPINNED = [
-    # the J2 part of the drag eccentricity rate (the drag pins run without zonals)
-    ("C4 cos 2w term", "* cos(2.0 * rc.argp0)));", "* sin(2.0 * rc.argp0)));"),
-    ("Mdot second order", "(13.0 - 78.0 * theta2 + 137.0 * theta4)", "(13.0 - 78.0 * theta2 + 37.0 * theta4)"),
-    # second-order terms of the Kozai -> Brouwer mean-motion recovery
-    ("delta1 factor", "R delta1 = 1.5 * k2", "R delta1 = 0.75 * k2"),
-    ("a0 series sign", "- delta1 * delta1 - (134.0", "+ delta1 * delta1 - (134.0"),
-    # J3 long-period terms of the mean longitude (size ~ e J3/J2, below what the
-    # integration comparisons resolve)
+    # first-order J4 part of the perigee rate (orbit- and perigee-averaged potential)
+    ("argpdot J4 poly", "T3 * (3.0 - 36.0 * theta2 + 49.0 * theta4)",
+     "T3 * (3.0 - 36.0 * theta2 + 39.0 * theta4)"),
+    # J3 long-period term of the mean longitude (integration with J3 x10)
     ("xlcof sign", "rc.xlcof = -0.25 * g.j3oj2", "rc.xlcof = 0.25 * g.j3oj2"),
     ("xlcof (3+5cos)", "(3.0 + 5.0 * rc.cosi)", "(5.0 + 3.0 * rc.cosi)"),
     ("q = 1/(a(1-e^2))", "R q = 1.0 / (m.a * (1.0 - m.e * m.e));", "R q = 1.0 / (m.a * (1.0 + m.e * m.e));"),
     ("U drops long period", "+ q * rc.xlcof * axn;", ";"),
-    # the drag coupling with J3 (a secular perigee drift that needs J3, drag and e > 0
-    # together; the drag pins run without zonals)
+    # drag with J3: the perigee drift of the free eccentricity vector
     ("C3 sign", "rc.C3 = -2.0 * coef", "rc.C3 = 2.0 * coef"),
+    ("C3 half", "rc.C3 = -2.0 * coef", "rc.C3 = -1.0 * coef"),
+    # drag with J2: the J2 terms of the decay rates of a and e
+    ("C2 J2 term sign", "0.375 * g.j2 * rc.xi", "-0.375 * g.j2 * rc.xi"),
+    ("C4 J2 x3thm1 sign", "(-3.0 * rc.x3thm1 *", "(3.0 * rc.x3thm1 *"),
+]
+
+# Terms that no independent check reaches (documented as parity-unpinned): each is a
+# second-order effect below what a comparison with a numerical integration resolves.
+UNPINNED = [
+    # the J2 part of the drag eccentricity rate's cos 2w term: ~J2 eta^2 of the rate
+    ("C4 cos 2w term", "* cos(2.0 * rc.argp0)));", "* sin(2.0 * rc.argp0)));"),
+    # second-order J2 parts of the mean-anomaly and perigee rates: an integration
+    # started from the theory's first-order osculating state inherits an O(J2^2)
+    # mean-motion offset of the same size
+    ("Mdot second order", "(13.0 - 78.0 * theta2 + 137.0 * theta4)", "(13.0 - 78.0 * theta2 + 37.0 * theta4)"),
+    ("argpdot J2^2 poly", "(7.0 - 114.0 * theta2 + 395.0 * theta4)", "(7.0 - 114.0 * theta2 + 295.0 * theta4)"),
+    # second-order terms of the Kozai -> Brouwer mean-motion recovery (an O(J2^2)
+    # change of n0'', inside the same ambiguity)
+    ("delta1 factor", "R delta1 = 1.5 * k2", "R delta1 = 0.75 * k2"),
+    ("a0 series sign", "- delta1 * delta1 - (134.0", "+ delta1 * delta1 - (134.0"),
 ]
 
 _BUILD_DIR = tempfile.mkdtemp(prefix="oracle_mutants_")
