@@ -40,14 +40,14 @@ BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
 # FP32 arithmetic + SFU operations per state of the FP32 formulation on the
 # Starlink-shaped workload, counted with ncu on the current kernel: each packed
 # instruction (FADD2, FMUL2, FFMA2) is two lane operations, one for each state of its
-# pair: FADD 37.1 + FMUL 97.1 + FFMA 67.1 + SFU 16.1 per state (ncu's per-pipe
-# instruction counts of one launch divided by the launch's states).
-ALG_OPS_FP32 = 217
+# pair: FADD 39.1 + FMUL 98.1 + FFMA 65.1 + SFU 16.1 per state (ncu's per-opcode and
+# per-pipe instruction counts of one launch divided by the launch's states).
+ALG_OPS_FP32 = 218
 # DRAM bytes (read + write) of one launch of the FP32 propagate kernel on this workload,
-# from an ncu capture of the current kernel (dram__bytes_read.sum 2,256,640 +
-# dram__bytes_write.sum 203,543,808): below the 28 B/state written because L2 still
+# from an ncu capture of the current kernel (dram__bytes_read.sum 1,629,440 +
+# dram__bytes_write.sum 201,150,464): below the 28 B/state written because L2 still
 # holds the tail of the output when the kernel ends.
-TRAFFIC_FP32_BYTES = 203_354_624
+TRAFFIC_FP32_BYTES = 202_779_904
 # FP64 arithmetic (DADD + DMUL + DFMA thread instructions) per state of the FP64
 # propagation on the Starlink-shaped workload, counted with ncu (DADD 15.0, DMUL 140.0,
 # DFMA 210.0).
@@ -56,6 +56,12 @@ ALG_OPS_FP64 = 365
 # ncu: FP32 path FADD + FMUL + FFMA + SFU; FP64 path DADD + DMUL + DFMA.
 ALG_OPS_ADJ_FP32 = 531
 ALG_OPS_ADJ_FP64 = 707
+# DADD + DMUL + DFMA per state of the FP64 Jacobian kernel (one forward and six reverse
+# sweeps with the init Jacobian contraction and the covariance) and of the FP64 fit-step
+# kernel (one forward and three reverse sweeps, the normal-equation sums), counted with
+# ncu on 2,000 x 500 of the fitting workload.
+ALG_OPS_JAC_FP64 = 3564
+ALG_OPS_FIT_FP64 = 1823
 # B300's FP64 unit: 2 lanes per SM per clock (one warp instruction per 64 cycles per
 # SM sub-partition; ncu's fp64-pipe utilisation and instruction count give the rate).
 FP64_LANES_PER_SM_CLK = 2
@@ -86,7 +92,10 @@ def max_over_ranks(x: float, device) -> float:
 # kernel, outside the timed region) while the host enqueues the step, so that the
 # events time the GPU's work and not gaps in which the host had not yet submitted the
 # next launch (on a slow host those gaps made a kernel's time exceed the whole step's).
-HOST_LEAD_CYCLES = 400_000      # about 0.2 ms at 2 GHz
+# The lead must also cover the host while the NVML clock sampler's thread holds the
+# interpreter: with 0.2 ms the headline step measured 0.120 ms under the sampler
+# against 0.111 ms without it.
+HOST_LEAD_CYCLES = 2_000_000    # about 1 ms at 2 GHz
 
 
 def host_lead(torch) -> None:
@@ -254,11 +263,16 @@ def _errors(r_dev, v_dev, st_dev, rows, rr, vr, sr):
 # ALG_OPS_FP64 (the FP32 count includes the SFU operations).  The count depends on
 # the workload: eccentric orbits take more Newton steps, simplified-drag records skip
 # the D terms, guard-band states add FP64 work.
+# Counted per workload (packed FADD2 / FMUL2 / FFMA2 from the per-opcode table, two
+# lane operations each; scalar FADD / FMUL / FFMA and XU from the per-pipe counters):
+# near-earth 2 x 100.5 packed + 9.8 scalar + 20.5 XU; catalogue (100,000 x 100 of the
+# same draw) 2 x 103.9 + 9.9 + 21.6; fitting workload 2 x 100.5 + 9.2 + 19.1.  FP64:
+# DADD + DMUL + DFMA of the FP64 kernel.
 OPS_PER_STATE = {
-    "near-earth-64x100": {"fp32": None, "fp64": None},
+    "near-earth-64x100": {"fp32": 231, "fp64": 379},
     "starlink-9341x1000": {"fp32": ALG_OPS_FP32, "fp64": ALG_OPS_FP64},
-    "catalogue-1Mx100": {"fp32": None, "fp64": None},
-    "fit-10000x500": {"fp32": None, "fp64": None},
+    "catalogue-1Mx100": {"fp32": 239, "fp64": 406},
+    "fit-10000x500": {"fp32": 229, "fp64": 384},
 }
 
 
@@ -492,6 +506,14 @@ def run_adjoint(torch, dev, stream, flush, steps, alu_peak, fp64_peak):
                      "jacobian_ms": jac_ms, "jacobian_states_per_s": states / (jac_ms * 1e-3),
                      "jacobian_note": "sgp4_jacobian: r, v, status, 6x7 J and 6x6 J C J^T "
                                       "per state"}
+        if prec == "fp64":
+            for key, ops, ms_ in (("jacobian_roofline", ALG_OPS_JAC_FP64, jac_ms),
+                                  ("fit_step_roofline", ALG_OPS_FIT_FP64, fit_ms)):
+                ach = ops * states / (ms_ * 1e-3) / 1e9
+                res[prec][key] = {"bound": "fp64", "achieved": ach, "peak": peak,
+                                  "unit": "Gop/s", "frac": ach / peak, "ops_per_state": ops,
+                                  "timed": "whole call (its small init and solve kernels "
+                                           "included)"}
     del g64, r_obs, r_true, recs, truth, cov
     torch.cuda.empty_cache()
     return res
