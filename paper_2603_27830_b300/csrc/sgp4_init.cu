@@ -47,6 +47,9 @@ __global__ void __launch_bounds__(kSplit ? 64 : 32) init_kernel(const double* __
   __shared__ double sh_x[2][kInitSats];       // C1 (drag), first-order node rate (rates)
   __shared__ double sh_dc[7][kInitSats];      // DragCore (warp 0 -> warp 1)
   __shared__ double sh_sa[6][kInitSats];      // SpineA (warp 1 -> warp 0)
+  // A propagation launched after this build as its programmatic dependent may be
+  // scheduled now; it waits for this grid's completion before reading the records.
+  asm volatile("griddepcontrol.launch_dependents;");
   const int lane = threadIdx.x & 31;
   const int w = threadIdx.x >> 5;
   const bool w0 = !kSplit || w == 0;   // this thread runs the spine / drag branch

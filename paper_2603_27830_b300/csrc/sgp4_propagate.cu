@@ -38,6 +38,10 @@ constexpr int kThreads = 128;
 #ifndef SGP4_MIN_BLOCKS_FP32
 #define SGP4_MIN_BLOCKS_FP32 4
 #endif
+// Programmatic dependent launch of the propagation kernels (see propagate_kernel).
+#ifndef SGP4_PDL
+#define SGP4_PDL 1
+#endif
 #ifndef SGP4_MIN_BLOCKS_FP64
 #define SGP4_MIN_BLOCKS_FP64 4
 #endif
@@ -496,6 +500,12 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   // FP32: [t_count] split times when use_split, then the guard-band queue
   extern __shared__ __align__(16) float2 s_split[];
   __shared__ FixQueue s_fq;
+#if SGP4_PDL
+  // Launched as a programmatic dependent of the stream's previous kernel (the record
+  // build, in a step): the blocks are scheduled while it runs and wait here, before
+  // their first global access, until it has completed and its writes are visible.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
@@ -671,9 +681,23 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
   const int64_t blocks = (total + chunk - 1) / chunk;
+#if SGP4_PDL
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>, a, chunk);
+#else
   propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>
       <<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
   return cudaGetLastError();
+#endif
 }
 
 // FP32: four states per unit (on full units 0.94 of the time of two units of two) where
