@@ -44,10 +44,10 @@ BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
 # per-pipe instruction counts of one launch divided by the launch's states).
 ALG_OPS_FP32 = 218
 # DRAM bytes (read + write) of one launch of the FP32 propagate kernel on this workload,
-# from an ncu capture of the current kernel (dram__bytes_read.sum 1,629,440 +
-# dram__bytes_write.sum 201,150,464): below the 28 B/state written because L2 still
-# holds the tail of the output when the kernel ends.
-TRAFFIC_FP32_BYTES = 202_779_904
+# from an ncu capture of the current kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch after one warm-up launch): below the 28 B/state
+# written because L2 still holds the tail of the output when the kernel ends.
+TRAFFIC_FP32_BYTES = 203_413_504
 # FP64 arithmetic (DADD + DMUL + DFMA thread instructions) per state of the FP64
 # propagation on the Starlink-shaped workload, counted with ncu (DADD 15.0, DMUL 140.0,
 # DFMA 210.0).
@@ -265,14 +265,14 @@ def _errors(r_dev, v_dev, st_dev, rows, rr, vr, sr):
 # the D terms, guard-band states add FP64 work.
 # Counted per workload (packed FADD2 / FMUL2 / FFMA2 from the per-opcode table, two
 # lane operations each; scalar FADD / FMUL / FFMA and XU from the per-pipe counters):
-# near-earth 2 x 100.5 packed + 9.8 scalar + 20.5 XU; catalogue (100,000 x 100 of the
-# same draw) 2 x 103.9 + 9.9 + 21.6; fitting workload 2 x 100.5 + 9.2 + 19.1.  FP64:
-# DADD + DMUL + DFMA of the FP64 kernel.
+# near-earth 232, catalogue (100,000 x 100 of the same draw) 240, fitting workload 230
+# lane operations per state on the current kernel.  FP64: DADD + DMUL + DFMA of the
+# FP64 kernel.
 OPS_PER_STATE = {
-    "near-earth-64x100": {"fp32": 231, "fp64": 379},
+    "near-earth-64x100": {"fp32": 232, "fp64": 379},
     "starlink-9341x1000": {"fp32": ALG_OPS_FP32, "fp64": ALG_OPS_FP64},
-    "catalogue-1Mx100": {"fp32": 239, "fp64": 406},
-    "fit-10000x500": {"fp32": 229, "fp64": 384},
+    "catalogue-1Mx100": {"fp32": 240, "fp64": 406},
+    "fit-10000x500": {"fp32": 230, "fp64": 384},
 }
 
 
