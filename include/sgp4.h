@@ -353,9 +353,9 @@ sgp4_result sgp4_jacobian(const double* elements, const sgp4_records* records,
  * rewrites the table and prefix sums and resets the counter before its launch.
  * Errors: SGP4_ERR_OOM if n_requests exceeds SGP4_STATIC_MAX_REQUESTS; SGP4_ERR_ARG
  * for bad or negative sizes (tsince_len, out_len included), offsets outside records /
- * tsince / outputs, overlapping outputs,
- * a bad precision or tile size, NULL or misaligned arrays; SGP4_ERR_CUDA if the
- * address lookup, the copy or a launch fails.  Calls no allocation routine.
+ * tsince / outputs, overlapping outputs, a bad precision or tile size, NULL or
+ * misaligned arrays; SGP4_ERR_CUDA if the address lookup, the copy or a launch fails.
+ * Calls no allocation routine.
  */
 #define SGP4_STATIC_MAX_REQUESTS 1024
 sgp4_result sgp4_propagate_batched_static(const sgp4_request* requests, int32_t n_requests,
