@@ -58,8 +58,9 @@ TRAFFIC_FP32_BYTES = 203_413_504
 # DFMA 210.0).
 ALG_OPS_FP64 = 365
 # Per state of the adjoint sweep on the fitting workload (10,000 x 500), counted with
-# ncu: FP32 path FADD + FMUL + FFMA + SFU; FP64 path DADD + DMUL + DFMA.
-ALG_OPS_ADJ_FP32 = 531
+# ncu on the current kernels: FP32 path FADD 78.4 + FMUL 221.6 + FFMA 169.9 + SFU 29.8;
+# FP64 path DADD + DMUL + DFMA.
+ALG_OPS_ADJ_FP32 = 500
 ALG_OPS_ADJ_FP64 = 707
 # DADD + DMUL + DFMA per state of the FP64 Jacobian kernel (one forward and six reverse
 # sweeps with the init Jacobian contraction and the covariance) and of the FP64 fit-step
