@@ -534,12 +534,10 @@ constexpr float kGuardLongPeriod = 1.0f;
 // position as it grows, and on records whose drag polynomial of the semi-major axis has
 // passed its minimum (the mean orbit then balloons to millions of km) it reaches
 // thousands of revolutions.  Past one revolution (about 13 m of along-track error at
-// LEO radius) the state is recomputed in FP64: 4e-4 of the seven-day catalogue's
-// states, none of the one-day workloads'.
-#ifndef SGP4_GUARD_DRAG_PHASE
-#define SGP4_GUARD_DRAG_PHASE 1.0f
-#endif
-constexpr float kGuardDragPhase = SGP4_GUARD_DRAG_PHASE;
+// LEO radius) the state is recomputed in FP64: 3e-4 of the seven-day catalogue's
+// states, 2e-4 of the element-fitting set's (its orbits with a perigee inside the
+// atmosphere), none of the one-day Starlink-shaped set's.
+constexpr float kGuardDragPhase = 1.0f;
 constexpr int kRecomputeFP64 = -1;
 
 // One state in FP32 with the n*t phase in double-float.  (th, tl) is tsince split as
