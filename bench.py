@@ -45,14 +45,14 @@ BYTES_PER_STATE = {"fp32": 28, "fp64": 52}
 # FP32 arithmetic + SFU operations per state of the FP32 formulation on the
 # Starlink-shaped workload, counted with ncu on the current kernel: each packed
 # instruction (FADD2, FMUL2, FFMA2) is two lane operations, one for each state of its
-# pair: FADD 39.1 + FMUL 98.1 + FFMA 65.1 + SFU 16.1 per state (ncu's per-opcode and
+# pair: FADD 38.1 + FMUL 97.1 + FFMA 54.1 + SFU 18.1 per state (ncu's per-opcode and
 # per-pipe instruction counts of one launch divided by the launch's states).
-ALG_OPS_FP32 = 218
+ALG_OPS_FP32 = 207
 # DRAM bytes (read + write) of one launch of the FP32 propagate kernel on this workload,
 # from an ncu capture of the current kernel (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch after one warm-up launch): below the 28 B/state
 # written because L2 still holds the tail of the output when the kernel ends.
-TRAFFIC_FP32_BYTES = 203_413_504
+TRAFFIC_FP32_BYTES = 203_465_984
 # FP64 arithmetic (DADD + DMUL + DFMA thread instructions) per state of the FP64
 # propagation on the Starlink-shaped workload, counted with ncu (DADD 15.0, DMUL 140.0,
 # DFMA 210.0).
@@ -271,14 +271,14 @@ def _errors(r_dev, v_dev, st_dev, rows, rr, vr, sr):
 # the D terms, guard-band states add FP64 work.
 # Counted per workload (packed FADD2 / FMUL2 / FFMA2 from the per-opcode table, two
 # lane operations each; scalar FADD / FMUL / FFMA and XU from the per-pipe counters):
-# near-earth 232, catalogue (100,000 x 100 of the same draw) 240, fitting workload 230
+# near-earth 221, catalogue (100,000 x 100 of the same draw) 229, fitting workload 219
 # lane operations per state on the current kernel.  FP64: DADD + DMUL + DFMA of the
 # FP64 kernel.
 OPS_PER_STATE = {
-    "near-earth-64x100": {"fp32": 232, "fp64": 379},
+    "near-earth-64x100": {"fp32": 221, "fp64": 379},
     "starlink-9341x1000": {"fp32": ALG_OPS_FP32, "fp64": ALG_OPS_FP64},
-    "catalogue-1Mx100": {"fp32": 240, "fp64": 406},
-    "fit-10000x500": {"fp32": 230, "fp64": 384},
+    "catalogue-1Mx100": {"fp32": 229, "fp64": 406},
+    "fit-10000x500": {"fp32": 219, "fp64": 384},
 }
 
 
