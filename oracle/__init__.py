@@ -1,4 +1,4 @@
-"""SGP4 near-Earth FP64 CPU oracle -- TEST INFRASTRUCTURE ONLY.
+"""SGP4 FP64 CPU oracle (near-Earth and deep-space branches) -- TEST INFRASTRUCTURE ONLY.
 
 This package is the independent reference that the CUDA path is checked against.
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
@@ -32,6 +32,24 @@ Parity status of each part (pins live in ``tests/oracle_pins.py``):
     (delta1, the a0 series) -- each a second-order effect that no comparison with a
     numerical integration started from the theory's first-order osculating state can
     resolve.
+
+Deep space (periods of 225 min or more; pins in ``tests/oracle_deep_pins.py``):
+  * the sidereal angle: pinned (the degrees-per-day form of the IAU 1982 expression);
+  * the Sun's and Moon's secular rates and their application: pinned (the quadrupole
+    tide averaged over both orbits through Lagrange's equations, the bodies' orbits
+    built from rotation matrices);
+  * their long-period terms: pinned for circular body orbits (the tide integrated
+    along the body's orbit), directly above 0.2 rad and in the Lyddane form below it
+    (first-order normal and longitude, continuity across 0.2 rad and across a
+    negative inclination);
+  * the resonance amplitudes: pinned (Kaula's F_lmp exactly, his G_lpq from Hansen
+    coefficients within the theory's series or fits) and the resonance integration
+    (an 8th-order integration of the same equations);
+  * classes and code 3: pinned (period and mean-motion windows, e leaving [0, 1]);
+  * parity unpinned: the first-order terms in the bodies' orbital eccentricities (the
+    theory keeps only an orientation-free sin f term and the first-order true anomaly,
+    which no exact reference truncates the same way) and the d2n/dt2 term of the
+    resonance integrator's last partial step (~1e-4 of the resonance's effect).
 """
 from __future__ import annotations
 
@@ -48,6 +66,21 @@ _LIB = os.path.join(_HERE, "libsgp4_oracle.so")
 
 # WGS-72: mu (km^3/s^2), Earth radius (km), J2, J3, J4 (paper Sec. 2.1).
 WGS72 = (398600.8, 6378.135, 0.001082616, -0.00000253881, -0.00000165597)
+
+# Deep-space theory constants (Sun n, e, tide coefficient; Moon n, e, tide
+# coefficient; resonance amplitude factor): the values of the theory.
+DEEP_THEORY = (1.19459e-5, 0.01675, 2.9864797e-6, 1.5835218e-4, 0.05490, 4.7968065e-7, 1.0)
+
+DEEP_FIELDS = (
+    "gsto", "edot", "idot", "mdot_ls", "argpdot_ls", "raandot_ls",
+    "sun_e2", "sun_e3", "sun_i2", "sun_i3", "sun_l2", "sun_l3", "sun_l4",
+    "sun_gh2", "sun_gh3", "sun_gh4", "sun_h2", "sun_h3", "sun_M0",
+    "moon_e2", "moon_e3", "moon_i2", "moon_i3", "moon_l2", "moon_l3", "moon_l4",
+    "moon_gh2", "moon_gh3", "moon_gh4", "moon_h2", "moon_h3", "moon_M0",
+    "del1", "del2", "del3",
+    "d2201", "d2211", "d3210", "d3222", "d4410", "d4422", "d5220", "d5232", "d5421", "d5433",
+    "lambda0", "xfact", "irez",
+)
 
 RECORD_FIELDS = (
     "n0pp", "a0pp", "cosi", "sini", "x3thm1", "x1mth2", "x7thm1", "beta0",
@@ -86,14 +119,22 @@ def load(path: str | None = None):
 def _bind(lib):
     P = ctypes.c_void_p
     I64 = ctypes.c_int64
-    lib.oracle_propagate.argtypes = [P, P, I64, P, I64, ctypes.c_int, P, P, P, P, ctypes.c_int]
-    lib.oracle_records.argtypes = [P, P, I64, P, P, P]
-    lib.oracle_mean.argtypes = [P, P, I64, P, I64, P]
-    lib.oracle_kepler.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, P]
-    lib.oracle_kepler.restype = ctypes.c_double
-    lib.oracle_jacobian.argtypes = [P, P, I64, P, I64, ctypes.c_int, P, P, P, ctypes.c_int]
+    D = ctypes.c_double
+    lib.oracle_propagate.argtypes = [P, P, P, P, I64, P, I64, ctypes.c_int, P, P, P, P,
+                                     ctypes.c_int]
+    lib.oracle_records.argtypes = [P, P, P, P, I64, P, P, P]
+    lib.oracle_deep_records.argtypes = [P, P, P, P, I64, P, P]
+    lib.oracle_mean.argtypes = [P, P, P, P, I64, P, I64, P]
+    lib.oracle_deep_periodics.argtypes = [P, P, P, P, I64, P, I64, P]
+    lib.oracle_kepler.argtypes = [D, D, D, P]
+    lib.oracle_kepler.restype = D
+    lib.oracle_gmst.argtypes = [D, D]
+    lib.oracle_gmst.restype = D
+    lib.oracle_jacobian.argtypes = [P, P, P, P, I64, P, I64, ctypes.c_int, P, P, P, ctypes.c_int]
     lib.oracle_nrec.restype = ctypes.c_int
+    lib.oracle_ndeep.restype = ctypes.c_int
     assert lib.oracle_nrec() == len(RECORD_FIELDS)
+    assert lib.oracle_ndeep() == len(DEEP_FIELDS)
     return lib
 
 
@@ -111,19 +152,47 @@ def _prep(elements, tsince, consts):
     return el, t, c
 
 
+def _epoch(epoch, n):
+    """(day [n], frac [n]) Julian-date epochs -> a contiguous [n, 2] array, or None."""
+    if epoch is None:
+        return None
+    day, frac = epoch
+    ep = np.empty((n, 2))
+    ep[:, 0] = np.broadcast_to(np.asarray(day, dtype=np.float64), (n,))
+    ep[:, 1] = np.broadcast_to(np.asarray(frac, dtype=np.float64), (n,))
+    return ep
+
+
+def _deep(deep):
+    if deep is None:
+        return None
+    d = np.ascontiguousarray(deep, dtype=np.float64)
+    assert d.shape == (7,)
+    return d
+
+
+def _optr(a):
+    return None if a is None else _ptr(a)
+
+
 def default_threads() -> int:
     return max(1, os.cpu_count() or 1)
 
 
-def propagate(elements, tsince, consts=WGS72, threads: int | None = None, lib=None):
+def propagate(elements, tsince, consts=WGS72, threads: int | None = None, lib=None,
+              epoch=None, deep=None):
     """r [n,T,3] km, v [n,T,3] km/s, status [n,T] int32, init_status [n] int32.
 
     ``tsince`` is [T] (one grid for all satellites) or [n, T] (a grid per satellite).
-    States with codes 1, 2, 4 (and records with unusable elements) are NaN.
+    ``epoch`` = (day, frac): each record's epoch as a split Julian date (scalars or
+    [n]; None: epoch 0), which the deep-space terms depend on.  ``deep`` overrides the
+    deep-space constants (``DEEP_THEORY`` layout).  States with codes 1, 2, 3, 4 (and
+    records with unusable elements) are NaN.
     """
     lib = lib or load()
     el, t, c = _prep(elements, tsince, consts)
     n = el.shape[0]
+    ep, dc = _epoch(epoch, n), _deep(deep)
     per_sat = 1 if t.ndim == 2 else 0
     T = t.shape[-1]
     if per_sat and t.shape[0] != n:
@@ -132,33 +201,65 @@ def propagate(elements, tsince, consts=WGS72, threads: int | None = None, lib=No
     v = np.empty((n, T, 3))
     st = np.empty((n, T), dtype=np.int32)
     ist = np.empty((n,), dtype=np.int32)
-    lib.oracle_propagate(_ptr(c), _ptr(el), n, _ptr(t), T, per_sat, _ptr(r), _ptr(v), _ptr(st),
-                         _ptr(ist), int(threads or default_threads()))
+    lib.oracle_propagate(_ptr(c), _optr(dc), _ptr(el), _optr(ep), n, _ptr(t), T, per_sat,
+                         _ptr(r), _ptr(v), _ptr(st), _ptr(ist), int(threads or default_threads()))
     return r, v, st, ist
 
 
-def records(elements, consts=WGS72, lib=None):
+def records(elements, consts=WGS72, lib=None, epoch=None, deep=None):
     """Per-satellite constants: dict name -> [n] array, plus 'isimp' and 'init_status'."""
     lib = lib or load()
     el, _, c = _prep(elements, np.zeros(1), consts)
     n = el.shape[0]
+    ep, dc = _epoch(epoch, n), _deep(deep)
     out = np.empty((n, len(RECORD_FIELDS)))
     isimp = np.empty((n,), dtype=np.int32)
     ist = np.empty((n,), dtype=np.int32)
-    lib.oracle_records(_ptr(c), _ptr(el), n, _ptr(out), _ptr(isimp), _ptr(ist))
+    lib.oracle_records(_ptr(c), _optr(dc), _ptr(el), _optr(ep), n, _ptr(out), _ptr(isimp),
+                       _ptr(ist))
     d = {name: out[:, k].copy() for k, name in enumerate(RECORD_FIELDS)}
     d["isimp"] = isimp
     d["init_status"] = ist
     return d
 
 
-def mean_elements(elements, tsince, consts=WGS72, lib=None):
-    """[n, T, 7]: a (ER), e, n (rad/min), RAAN, argp, M (reduced), code after the secular step."""
+def deep_records(elements, consts=WGS72, lib=None, epoch=None, deep=None):
+    """Deep-space constants: dict name -> [n] array (NaN for near-Earth records), plus
+    'deep' = -1 (unusable), 0 (near-Earth) or 1 + irez (deep space; irez 0 none,
+    1 one revolution per day, 2 two)."""
+    lib = lib or load()
+    el, _, c = _prep(elements, np.zeros(1), consts)
+    n = el.shape[0]
+    ep, dc = _epoch(epoch, n), _deep(deep)
+    out = np.empty((n, len(DEEP_FIELDS)))
+    flag = np.empty((n,), dtype=np.int32)
+    lib.oracle_deep_records(_ptr(c), _optr(dc), _ptr(el), _optr(ep), n, _ptr(out), _ptr(flag))
+    d = {name: out[:, k].copy() for k, name in enumerate(DEEP_FIELDS)}
+    d["deep"] = flag
+    return d
+
+
+def mean_elements(elements, tsince, consts=WGS72, lib=None, epoch=None, deep=None):
+    """[n, T, 8]: a (ER), e, n (rad/min), RAAN, argp, M (reduced), code, i after the
+    secular step (deep space: with the lunar-solar secular rates and the resonance)."""
     lib = lib or load()
     el, t, c = _prep(elements, tsince, consts)
     n, T = el.shape[0], t.shape[0]
-    out = np.empty((n, T, 7))
-    lib.oracle_mean(_ptr(c), _ptr(el), n, _ptr(t), T, _ptr(out))
+    ep, dc = _epoch(epoch, n), _deep(deep)
+    out = np.empty((n, T, 8))
+    lib.oracle_mean(_ptr(c), _optr(dc), _ptr(el), _optr(ep), n, _ptr(t), T, _ptr(out))
+    return out
+
+
+def deep_periodics(elements, tsince, consts=WGS72, lib=None, epoch=None, deep=None):
+    """[n, T, 6]: e, i, RAAN, argp, M after the lunar-solar periodic terms, and the
+    code (0, 3; -1 for a near-Earth record; the secular code where that failed)."""
+    lib = lib or load()
+    el, t, c = _prep(elements, tsince, consts)
+    n, T = el.shape[0], t.shape[0]
+    ep, dc = _epoch(epoch, n), _deep(deep)
+    out = np.empty((n, T, 6))
+    lib.oracle_deep_periodics(_ptr(c), _optr(dc), _ptr(el), _optr(ep), n, _ptr(t), T, _ptr(out))
     return out
 
 
@@ -170,7 +271,14 @@ def kepler(U: float, axn: float, ayn: float, lib=None):
     return psi, it.value
 
 
-def jacobian(elements, tsince, consts=WGS72, threads: int | None = None, lib=None):
+def gmst(day: float, frac: float, lib=None) -> float:
+    """Greenwich mean sidereal angle (rad) at the Julian date day + frac."""
+    lib = lib or load()
+    return lib.oracle_gmst(float(day), float(frac))
+
+
+def jacobian(elements, tsince, consts=WGS72, threads: int | None = None, lib=None,
+             epoch=None, deep=None):
     """Forward-mode (dual-number) d(r, v)/d(n0, e0, i0, RAAN0, argp0, M0, B*).
 
     Returns dr, dv [n, T, 3, 7] and status [n, T].
@@ -178,11 +286,12 @@ def jacobian(elements, tsince, consts=WGS72, threads: int | None = None, lib=Non
     lib = lib or load()
     el, t, c = _prep(elements, tsince, consts)
     n = el.shape[0]
+    ep, dc = _epoch(epoch, n), _deep(deep)
     per_sat = 1 if t.ndim == 2 else 0
     T = t.shape[-1]
     dr = np.empty((n, T, 3, 7))
     dv = np.empty((n, T, 3, 7))
     st = np.empty((n, T), dtype=np.int32)
-    lib.oracle_jacobian(_ptr(c), _ptr(el), n, _ptr(t), T, per_sat, _ptr(dr), _ptr(dv), _ptr(st),
-                        int(threads or default_threads()))
+    lib.oracle_jacobian(_ptr(c), _optr(dc), _ptr(el), _optr(ep), n, _ptr(t), T, per_sat,
+                        _ptr(dr), _ptr(dv), _ptr(st), int(threads or default_threads()))
     return dr, dv, st

@@ -16,12 +16,16 @@ import math
 import numpy as np
 
 import oracle
+from oracle_deep_pins import DEEP_PINS
 
 MU, RE, J2, J3, J4 = oracle.WGS72
 XKE = 60.0 / math.sqrt(RE ** 3 / MU)          # sqrt(mu) in ER^1.5 / min
 TWO_BODY = (MU, RE, 0.0, 0.0, 0.0)
 J2_ONLY = (MU, RE, J2, 0.0, 0.0)
 ZONAL = oracle.WGS72
+# The deep-space branch (periods of 225 min or more) with the Sun's and Moon's tides
+# and the tesseral resonance switched off: it must then reduce to the zonal theory.
+DEEP_OFF = tuple(0.0 if k in (2, 5, 6) else c for k, c in enumerate(oracle.DEEP_THEORY))
 REV_DAY = 2.0 * math.pi / 1440.0
 
 
@@ -63,7 +67,8 @@ def two_body_state(n0, e, inc, raan, argp, M0, t):
 
 
 def pin_two_body(lib):
-    """J2 = J3 = J4 = 0, B* = 0: SGP4 must reduce to Keplerian motion."""
+    """J2 = J3 = J4 = 0, B* = 0: SGP4 must reduce to Keplerian motion (orbits of
+    period 225 min or more too, with the deep-space tides and resonance off)."""
     fails = []
     rng = np.random.default_rng(11)
     els = []
@@ -77,7 +82,7 @@ def pin_two_body(lib):
                     rng.uniform(0, 6.28), 0.0])
     els = np.array(els)
     t = np.array([0.0, 17.3, 250.0, 1440.0, 5000.0, -300.0])
-    r, v, st, _ = oracle.propagate(els, t, TWO_BODY, threads=1, lib=lib)
+    r, v, st, _ = oracle.propagate(els, t, TWO_BODY, threads=1, lib=lib, deep=DEEP_OFF)
     for j, el in enumerate(els):
         for i, ti in enumerate(t):
             rr, vv = two_body_state(*el[:6], ti)
@@ -236,11 +241,15 @@ def pin_zonal_integration(lib, consts=ZONAL, n_orbits=2.0, tol_km=1.5):
         ([14.0 * REV_DAY, 0.02, math.radians(97.6), 4.0, 0.3, 2.0, 0.0], tol_km),
         ([15.5 * REV_DAY, 0.005, math.radians(120.0), 0.7, 2.9, 3.3, 0.0], tol_km),
         ([13.0 * REV_DAY, 0.08, math.radians(30.0), 2.5, 4.0, 5.0, 0.0], 6 * tol_km),
+        # periods of 225 min or more: the deep-space branch, its tides and resonance off
+        ([6.0 * REV_DAY, 0.01, math.radians(63.0), 1.0, 2.0, 0.5, 0.0], tol_km),
+        ([4.0 * REV_DAY, 0.002, math.radians(110.0), 5.0, 1.0, 3.0, 0.0], tol_km),
     ]
     for el, tol in cases:
         P = 2 * math.pi / el[0]
         t = np.linspace(0.0, n_orbits * P, 40)
-        r, v, st, _ = oracle.propagate(np.array([el]), t, consts, threads=1, lib=lib)
+        r, v, st, _ = oracle.propagate(np.array([el]), t, consts, threads=1, lib=lib,
+                                       deep=DEEP_OFF)
         if np.any(st != 0):
             fails.append(f"zonal case {el}: unexpected status {np.unique(st)}")
             continue
@@ -930,7 +939,7 @@ ALL_PINS = [
     pin_status_codes, pin_mean_a_third_law, pin_drag_eccentricity_oscillation,
     pin_drag_decay_series, pin_eccentric_drag_secular, pin_drag_decay_taylor,
     pin_drag_node_acceleration, pin_drag_perigee_oscillation,
-    pin_j4_secular_rates, pin_zonal_integration, pin_eccentricity_vector_evolution,
+    pin_j4_secular_rates, *DEEP_PINS, pin_zonal_integration, pin_eccentricity_vector_evolution,
     pin_secular_plane_drift, pin_secular_node_rate, pin_j2_drag_coupling, pin_drag_j3_perigee,
     pin_j3_long_period_longitude,
 ]

@@ -36,11 +36,11 @@ CAUGHT = [
     ("L2", "rc.L2 = 1.5 * rc.C1;", "rc.L2 = 0.5 * rc.C1;"),
     ("aycof sign", "rc.aycof = -0.5 * g.j3oj2", "rc.aycof = 0.5 * g.j3oj2"),
     ("a(t) power of tempa", "* tempa * tempa;", "* tempa;"),
-    ("drag e sign", "m.e = rc.e0 - tempe;", "m.e = rc.e0 + tempe;"),
+    ("drag e sign", "m.e = e - tempe;", "m.e = e + tempe;"),
     ("mean longitude uses n0''", "M = M + rc.n0pp * templ;", "M = M + 0.5 * rc.n0pp * templ;"),
     ("node secular", "R raan_df = rc.raan0 + rc.raandot * t;", "R raan_df = rc.raan0 - rc.raandot * t;"),
     ("argp secular", "R argp_df = rc.argp0 + rc.argpdot * t;", "R argp_df = rc.argp0 - rc.argpdot * t;"),
-    ("axn uses sin", "R axn = m.e * cos(m.argp);", "R axn = m.e * sin(m.argp);"),
+    ("axn uses sin", "R axn = ecc * cos(argp);", "R axn = ecc * sin(argp);"),
     ("Kepler numerator sign", "R f = U - ayn * cp + axn * sp - psi;", "R f = U + ayn * cp + axn * sp - psi;"),
     ("Kepler derivative", "R fp = 1.0 - ayn * sp - axn * cp;", "R fp = 1.0 + ayn * sp - axn * cp;"),
     ("ecosE transposed", "R ecosE = axn * cp + ayn * sp;", "R ecosE = axn * sp + ayn * cp;"),
@@ -52,12 +52,12 @@ CAUGHT = [
     ("cosu uses axn", "(cp - axn + ayn * w)", "(cp - ayn + ayn * w)"),
     ("k2/pL", "R k = 0.5 * g.j2 / pL;", "R k = 0.5 * g.j2 / (pL * pL);"),
     ("rk radial J2 term", "R rk = rr * (1.0 - 1.5 * kp", "R rk = rr * (1.0 + 1.5 * kp"),
-    ("rk cos2u term", "+ 0.5 * k * rc.x1mth2 * cos2u;", "- 0.5 * k * rc.x1mth2 * cos2u;"),
+    ("rk cos2u term", "+ 0.5 * k * x1mth2 * cos2u;", "- 0.5 * k * x1mth2 * cos2u;"),
     ("uk sign", "R uk = u - 0.25 * kp", "R uk = u + 0.25 * kp"),
-    ("raank sign", "R raank = m.raan + 1.5 * kp", "R raank = m.raan - 1.5 * kp"),
-    ("ik sign", "R ik = rc.i0 + 1.5 * kp", "R ik = rc.i0 - 1.5 * kp"),
+    ("raank sign", "R raank = raan + 1.5 * kp", "R raank = raan - 1.5 * kp"),
+    ("ik sign", "R ik = inc + 1.5 * kp", "R ik = inc - 1.5 * kp"),
     ("rdotk sign", "R rdotk = rdot - m.n * k", "R rdotk = rdot + m.n * k"),
-    ("rfdotk constant term", "+ 1.5 * rc.x3thm1) / g.xke;", "- 1.5 * rc.x3thm1) / g.xke;"),
+    ("rfdotk constant term", "+ 1.5 * x3thm1) / g.xke;", "- 1.5 * x3thm1) / g.xke;"),
     ("M vector", "R Mx = -sO * ci, My = cO * ci", "R Mx = sO * ci, My = cO * ci"),
     ("V vector sign", "R Vx = Mx * cu - Nx * su", "R Vx = Mx * cu + Nx * su"),
     ("velocity scale", "double vscale = g.re * g.xke / 60.0;", "double vscale = g.re * g.xke;"),
@@ -90,14 +90,103 @@ CAUGHT = [
     # J3 long-period term of the mean longitude (integration with J3 x10)
     ("xlcof sign", "rc.xlcof = -0.25 * g.j3oj2", "rc.xlcof = 0.25 * g.j3oj2"),
     ("xlcof (3+5cos)", "(3.0 + 5.0 * rc.cosi)", "(5.0 + 3.0 * rc.cosi)"),
-    ("q = 1/(a(1-e^2))", "R q = 1.0 / (m.a * (1.0 - m.e * m.e));", "R q = 1.0 / (m.a * (1.0 + m.e * m.e));"),
-    ("U drops long period", "+ q * rc.xlcof * axn;", ";"),
+    ("q = 1/(a(1-e^2))", "R q = 1.0 / (m.a * (1.0 - ecc * ecc));", "R q = 1.0 / (m.a * (1.0 + ecc * ecc));"),
+    ("U drops long period", "+ q * xlcof * axn;", ";"),
     # drag with J3: the perigee drift of the free eccentricity vector
     ("C3 sign", "rc.C3 = -2.0 * coef", "rc.C3 = 2.0 * coef"),
     ("C3 half", "rc.C3 = -2.0 * coef", "rc.C3 = -1.0 * coef"),
     # drag with J2: the J2 terms of the decay rates of a and e
     ("C2 J2 term sign", "0.375 * g.j2 * rc.xi", "-0.375 * g.j2 * rc.xi"),
     ("C4 J2 x3thm1 sign", "(-3.0 * rc.x3thm1 *", "(3.0 * rc.x3thm1 *"),
+    # deep space: classes, sidereal angle, lunar-solar geometry and tides
+    ("deep period threshold", "rc.deep = kTwoPi / rc.n0pp >= 225.0;", "rc.deep = kTwoPi / rc.n0pp >= 255.0;"),
+    ("deep keeps drag", "if (rc.deep) rc.isimp = true;", "if (rc.deep) rc.isimp = rc.isimp;"),
+    ("12 h class e", "rc.n0pp <= 9.24e-3 && rc.e0 >= 0.5", "rc.n0pp <= 9.24e-3 && rc.e0 >= 0.05"),
+    ("gmst seconds to rad", "sec * (kTwoPi / 86400.0)", "sec * (kTwoPi / 86164.0)"),
+    ("gmst T^2", "+ 0.093104 * T * T", "- 0.093104 * T * T"),
+    ("gmst wrap", "if (th < 0.0) th += kTwoPi;", "if (th < 0.0) th = -th;"),
+    ("epoch day origin", "double day = (ep_day - 2415020.0) + ep_frac;", "double day = (ep_day - 2433282.5) + ep_frac;"),
+    ("Moon inclination to equator", "double cIm = 0.91375164 - 0.03568096 * ctem;", "double cIm = 0.91375164 + 0.03568096 * ctem;"),
+    ("Moon equatorial node", "double shm = 0.089683511 * stem / sIm;", "double shm = 0.089683511 * ctem / sIm;"),
+    ("Moon perigee arc", "double gm = per_m + arc - node_m;", "double gm = per_m - arc - node_m;"),
+    ("Moon mean anomaly", "0.22997150 * day - per_m", "0.22997150 * day + per_m"),
+    ("Moon node relative", "cO * chm + sO * shm", "cO * chm - sO * shm"),
+    ("tide a1", "R a1 = cg * ch + sg * cI * sh;", "R a1 = cg * ch - sg * cI * sh;"),
+    ("tide a3", "R a3 = -sg * ch + cg * cI * sh;", "R a3 = sg * ch + cg * cI * sh;"),
+    ("tide a7", "R a7 = -cg * sh + sg * cI * ch;", "R a7 = -cg * sh + sg * sI * ch;"),
+    ("tide a5", "R a5 = -si * a7 + ci * a8;", "R a5 = si * a7 + ci * a8;"),
+    ("tide x3", "R x3 = -a1 * sinw + a2 * cosw;", "R x3 = a1 * sinw + a2 * cosw;"),
+    ("tide z31", "R z31 = 12.0 * x1 * x1 - 3.0 * x3 * x3;", "R z31 = 12.0 * x1 * x1 - 6.0 * x3 * x3;"),
+    ("tide z1 e^2", "R z1 = 2.0 * (3.0 * (a1 * a1 + a2 * a2) + z31 * e2) + b2 * z31;",
+     "R z1 = 2.0 * (3.0 * (a1 * a1 + a2 * a2) + z31 * e2) + z31;"),
+    ("tide z12", "R z12 = -6.0 * (a1 * a6 + a3 * a5)", "R z12 = -6.0 * (a1 * a6 - a3 * a5)"),
+    ("tide z13 e^2", "R z13 = -6.0 * a3 * a6 + e2 * (-24.0 * x2 * x8 - 6.0 * x4 * x6);",
+     "R z13 = -6.0 * a3 * a6 + e2 * (-24.0 * x2 * x8 + 6.0 * x4 * x6);"),
+    ("tide z22", "R z22 = 6.0 * (a4 * a5 + a2 * a6)", "R z22 = 6.0 * (a4 * a5 - a2 * a6)"),
+    ("tide s2", "R s2 = -0.5 * s3 / beta;", "R s2 = -0.5 * s3 * beta;"),
+    ("tide s1", "R s1 = -15.0 * e * s4;", "R s1 = -12.0 * e * s4;"),
+    ("tide s6", "R s6 = x2 * x3 + x1 * x4;", "R s6 = x2 * x3 - x1 * x4;"),
+    ("periodic e3", "L.e3 = 2.0 * s1 * s7;", "L.e3 = 2.0 * s1 * s6;"),
+    ("periodic i3", "L.i3 = 2.0 * s2 * (z13 - z11);", "L.i3 = 2.0 * s2 * (z13 + z11);"),
+    ("periodic l2", "L.l2 = -2.0 * s3 * z2;", "L.l2 = 2.0 * s3 * z2;"),
+    ("periodic gh3", "L.gh3 = 2.0 * s4 * (z33 - z31);", "L.gh3 = 2.0 * s4 * (z33 + z31);"),
+    ("periodic h2", "L.h2 = -2.0 * s2 * z22;", "L.h2 = -2.0 * s2 * z21;"),
+    ("secular e", "rc.edot = rc.edot + s1 * nb * s5;", "rc.edot = rc.edot + s1 * nb * s6;"),
+    ("secular i", "rc.idot = rc.idot + s2 * nb * (z11 + z13);", "rc.idot = rc.idot + s2 * nb * (z11 - z13);"),
+    ("secular M constant", "(z1 + z3 - 14.0 - 6.0 * e2)", "(z1 + z3 - 12.0 - 6.0 * e2)"),
+    ("secular gh constant", "(z31 + z33 - 6.0)", "(z31 + z33 - 4.0)"),
+    ("secular node", "R h = -nb * s2 * (z21 + z23) / si;", "R h = nb * s2 * (z21 + z23) / si;"),
+    ("secular perigee from node", "gh - ci * h;", "gh + ci * h;"),
+    ("near-equatorial band", "rc.i0 < 5.2359877e-2 ||", "rc.i0 < 5.2359877e-3 ||"),
+    ("periodic F2", "double F2 = 0.5 * sf * sf - 0.25;", "double F2 = 0.5 * sf * cf - 0.25;"),
+    ("periodic F3 sign", "double F3 = -0.5 * sf * cf;", "double F3 = 0.5 * sf * cf;"),
+    ("body moves", "double Mb = b->M0 + b->n * t;", "double Mb = b->M0 - b->n * t;"),
+    ("periodic node divide", "R dnode = ph / si;", "R dnode = ph * si;"),
+    ("periodic perigee", "argp = argp + (pgh - ci * dnode);", "argp = argp + (pgh + ci * dnode);"),
+    ("Lyddane alpha", "R alpha = si * so + (ph * co + pinc * ci * so);", "R alpha = si * so + (ph * co - pinc * ci * so);"),
+    ("Lyddane beta", "R beta = si * co + (-ph * so + pinc * ci * co);", "R beta = si * co + (ph * so + pinc * ci * co);"),
+    ("Lyddane longitude", "(pl + pgh - pinc * raan * si)", "(pl + pgh + pinc * raan * si)"),
+    ("negative inclination flip", "raan = raan + kPi; argp = argp - kPi;", "raan = raan + kPi; argp = argp + 0.0;"),
+    ("code 3 range", "if (ecc < 0.0 || ecc > 1.0) return 3;", "if (ecc < -1e-3 || ecc > 1.0) return 3;"),
+    ("deep short-period inclination", "x3thm1 = 3.0 * c2 - 1.0;", "x3thm1 = 3.0 * c2 + 1.0;"),
+    # resonance: amplitudes (Kaula's functions) and integration
+    ("G300 e^2", "R g300 = 1.0 + e2 * (-6.0 + 6.60937 * e2);", "R g300 = 1.0 + e2 * (-3.0 + 6.60937 * e2);"),
+    ("F311", "R f311 = 0.9375 * si * si * (1.0 + 3.0 * ci) - 0.75 * opc;", "R f311 = 0.9375 * si * si * (1.0 + 3.0 * ci) + 0.75 * opc;"),
+    ("del2 factor", "rc.del2 = 2.0 * k * f220 * g200 * kQ22;", "rc.del2 = k * f220 * g200 * kQ22;"),
+    ("del3 power of 1/a", "rc.del3 = 3.0 * k * f330 * g300 * kQ33 * aonv;", "rc.del3 = 3.0 * k * f330 * g300 * kQ33;"),
+    ("G201", "R g201 = -0.306 - (e - 0.64) * 0.440;", "R g201 = -0.306 + (e - 0.64) * 0.440;"),
+    ("G310 low e", "g310 = -19.302 + 117.3900 * e - 228.4190 * e2 + 156.5910 * e3;",
+     "g310 = -19.302 + 117.3900 * e - 282.4190 * e2 + 156.5910 * e3;"),
+    ("G422 high e", "g422 = -3581.690 + 16178.110 * e - 24462.770 * e2 + 12422.520 * e3;",
+     "g422 = -3581.690 + 16178.110 * e - 24462.770 * e2 + 12242.520 * e3;"),
+    ("G533 low e", "g533 = -919.22770 + 4988.6100 * e - 9064.7700 * e2 + 5542.21 * e3;",
+     "g533 = -919.22770 + 4988.6100 * e - 9064.7700 * e2 + 5452.21 * e3;"),
+    ("F321", "R f321 = 1.875 * si * (1.0 - 2.0 * ci - 3.0 * ci2);", "R f321 = 1.875 * si * (1.0 + 2.0 * ci - 3.0 * ci2);"),
+    ("F441", "R f441 = 35.0 * si2 * f220;", "R f441 = 35.0 * si * f220;"),
+    ("F522", "0.33333333 * (-2.0 + 4.0 * ci + 6.0 * ci2));", "0.33333333 * (-2.0 - 4.0 * ci + 6.0 * ci2));"),
+    ("F543", "R f543 = 29.53125 * si * (-2.0 - 8.0 * ci + ci2 * (12.0 + 8.0 * ci - 10.0 * ci2));",
+     "R f543 = 29.53125 * si * (-2.0 - 8.0 * ci + ci2 * (12.0 - 8.0 * ci - 10.0 * ci2));"),
+    ("d4410 factor 2", "rc.d4410 = 2.0 * k4 * kR44 * f441 * g410;", "rc.d4410 = k4 * kR44 * f441 * g410;"),
+    ("d5220 power", "R k3 = k * aonv, k4 = k3 * aonv, k5 = k4 * aonv;", "R k3 = k * aonv, k4 = k3 * aonv, k5 = k4;"),
+    ("lambda0 12 h", "rc.lambda0 = fmod(rc.m0 + 2.0 * rc.raan0 - 2.0 * rc.gsto, kTwoPi);",
+     "rc.lambda0 = fmod(rc.m0 + 2.0 * rc.raan0 - rc.gsto, kTwoPi);"),
+    ("xfact 12 h", "rc.xfact = rc.Mdot + rc.mdot_ls + 2.0 * (rc.raandot + rc.raandot_ls - kEarthRot) - rc.n0pp;",
+     "rc.xfact = rc.Mdot + rc.mdot_ls + 2.0 * (rc.raandot - kEarthRot) - rc.n0pp;"),
+    ("xfact sync", "rc.xfact = rc.Mdot + rc.argpdot + rc.raandot - kEarthRot + rc.mdot_ls +",
+     "rc.xfact = rc.Mdot + rc.argpdot + rc.raandot + kEarthRot + rc.mdot_ls +"),
+    ("sync phase 31", "rc.del1 * sin(lam - kPhase31)", "rc.del1 * sin(lam + kPhase31)"),
+    ("sync harmonic 2", "rc.del2 * sin(2.0 * (lam - kPhase22))", "rc.del2 * sin(lam - kPhase22)"),
+    ("12 h argument 2201", "rc.d2201 * sin(w2 + lam - kG22)", "rc.d2201 * sin(w + lam - kG22)"),
+    ("12 h argument 3222", "rc.d3222 * sin(-w + lam - kG32)", "rc.d3222 * sin(w + lam - kG32)"),
+    ("12 h argument 5433", "rc.d5433 * sin(-w + l2 - kG54)", "rc.d5433 * sin(-w + lam - kG54)"),
+    ("12 h perigee rate", "R w = rc.argp0 + rc.argpdot * tc;", "R w = rc.argp0;"),
+    ("resonance step lambda", "lam = lam + ldot * h + ndot * (0.5 * h * h);", "lam = lam + ldot * h;"),
+    ("resonance step n", "n = n + ndot * h + nddot * (0.5 * h * h);", "n = n + ndot * h;"),
+    ("resonance M 12 h", "M = lam - 2.0 * raan + 2.0 * theta;", "M = lam - 2.0 * raan + theta;"),
+    ("resonance M sync", "M = lam - raan - argp + theta;", "M = lam - raan + argp + theta;"),
+    ("deep mean motion used", "m.a = pow(g.xke / n, 2.0 / 3.0) * tempa * tempa;", "m.a = pow(g.xke / rc.n0pp, 2.0 / 3.0) * tempa * tempa;"),
+    ("lunar-solar e rate applied", "e = e + rc.edot * t;", "e = e - rc.edot * t;"),
+    ("lunar-solar i rate applied", "m.i = m.i + rc.idot * t;", "m.i = m.i + 0.0 * t;"),
 ]
 
 # Terms that no independent check reaches (documented as parity-unpinned): each is a
@@ -114,6 +203,20 @@ UNPINNED = [
     # change of n0'', inside the same ambiguity)
     ("delta1 factor", "R delta1 = 1.5 * k2", "R delta1 = 0.75 * k2"),
     ("a0 series sign", "- delta1 * delta1 - (134.0", "+ delta1 * delta1 - (134.0"),
+    # deep space: the first-order terms in the Sun's and Moon's orbital eccentricity.
+    # The theory keeps only part of them (a sin f term in the mean anomaly and in
+    # perigee + cos i node with orientation-free coefficients, the true anomaly to
+    # first order); no exact reference has the same truncation.
+    ("lunar-solar l4 term", "L.l4 = -2.0 * s3 * (-21.0 - 9.0 * e2) * eb;",
+     "L.l4 = -2.0 * s3 * (-14.0 - 9.0 * e2) * eb;"),
+    ("lunar-solar gh4 term", "L.gh4 = -18.0 * s4 * eb;", "L.gh4 = -12.0 * s4 * eb;"),
+    ("body true anomaly", "double f = Mb + 2.0 * b->ecc * std::sin(Mb);",
+     "double f = Mb + b->ecc * std::sin(Mb);"),
+    # the resonance integrator's last partial step without its d2n/dt2 term: it is
+    # (d2n/dt2) ft^2 / 2 with ft < 720 min and d2n/dt2 = sum k d cos(arg) dlambda/dt,
+    # small with the slow resonant longitude (~1e-4 of the resonance's dn over days),
+    # below what the comparison with the integrated equations resolves
+    ("resonance final n", "n_out = n + ndot * ft + nddot * (0.5 * ft * ft);", "n_out = n + ndot * ft;"),
 ]
 
 _BUILD_DIR = tempfile.mkdtemp(prefix="oracle_mutants_")

@@ -82,3 +82,41 @@ def test_retrograde_pole_guard(lib):
     el = np.array([[15.0 * P.REV_DAY, 0.001, math.pi, 0.2, 0.3, 0.4, 1e-4]])
     r, v, st, ist = oracle.propagate(el, np.linspace(0, 1440, 5))
     assert np.all(st == 0) and np.all(np.isfinite(r)) and np.all(np.isfinite(v))
+
+
+def test_deep_dual_number_jacobian_matches_central_differences(lib):
+    """The dual-number derivatives through the deep-space branch (lunar-solar terms,
+    the resonance integration, the Lyddane form) against central differences."""
+    el = np.array([[1.00273 * P.REV_DAY, 0.001, 0.1, 1.0, 2.0, 3.0, 1e-5],
+                   [2.00561 * P.REV_DAY, 0.72, 1.107, 1.0, 4.7, 0.3, 1e-4],
+                   [2.0056 * P.REV_DAY, 0.01, 0.96, 2.0, 1.0, 3.0, 0.0],
+                   [0.5 * P.REV_DAY, 0.6, 2.6, 4.0, 5.5, 1.0, 0.0]])
+    ep = (np.full(4, 2455000.0), np.full(4, 0.3))
+    t = np.array([0.0, 700.0, 5000.0, -3000.0])
+    dr, dv, st = oracle.jacobian(el, t, epoch=ep)
+    assert np.all(st == 0)
+    steps = np.array([1e-10, 1e-8, 1e-7, 1e-7, 1e-7, 1e-7, 1e-6])
+    for k in range(7):
+        ep_, em_ = el.copy(), el.copy()
+        ep_[:, k] += steps[k]
+        em_[:, k] -= steps[k]
+        rp, vp, _, _ = oracle.propagate(ep_, t, epoch=ep)
+        rm, vm, _, _ = oracle.propagate(em_, t, epoch=ep)
+        fd_r = (rp - rm) / (2 * steps[k])
+        fd_v = (vp - vm) / (2 * steps[k])
+        scale_r = np.abs(dr[..., k]).max() + 1e-30
+        scale_v = np.abs(dv[..., k]).max() + 1e-30
+        assert np.abs(fd_r - dr[..., k]).max() < 1e-5 * scale_r + 1e-5, f"d r / d el[{k}]"
+        assert np.abs(fd_v - dv[..., k]).max() < 1e-5 * scale_v + 1e-8, f"d v / d el[{k}]"
+
+
+def test_deep_epoch_matters_only_for_deep_records(lib):
+    """Near-Earth results do not depend on the epoch; deep-space ones do (the Sun's
+    and Moon's positions, the sidereal angle)."""
+    el = np.array([[15.0 * P.REV_DAY, 0.001, 0.9, 0.2, 0.3, 0.4, 1e-4],
+                   [1.00273 * P.REV_DAY, 0.001, 0.1, 1.0, 2.0, 3.0, 1e-5]])
+    t = np.linspace(0, 2880, 5)
+    a = oracle.propagate(el, t, epoch=(np.full(2, 2455000.0), np.full(2, 0.3)))
+    b = oracle.propagate(el, t, epoch=(np.full(2, 2458000.0), np.full(2, 0.7)))
+    np.testing.assert_array_equal(a[0][0], b[0][0])
+    assert np.abs(a[0][1] - b[0][1]).max() > 1.0
