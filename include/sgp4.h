@@ -1,11 +1,14 @@
 /*
- * sgp4.h -- C ABI of the B300 (sm_103a) near-Earth SGP4 propagation library.
+ * sgp4.h -- C ABI of the B300 (sm_103a) SGP4 propagation library.
  *
  * The problem is the paper's f(s, t) -> (r, v), batched over satellites s and
  * times t (Priestley & Handley, "jaxsgp4", Sec. 2.2 "Vectorisation"): near-Earth
  * SGP4 (Spacetrack Report #3 equations as revised in 2006, WGS-72 constants,
  * Sec. 2.1), with invalid physical states flagged by integer codes instead of
- * aborting (Sec. 2.2 "Control Flow").
+ * aborting (Sec. 2.2 "Control Flow").  Records with a period of 225 min or more take
+ * the same revision's deep-space branch (SDP4: the Sun's and Moon's perturbations and
+ * tesseral resonance), which the paper names as future work (Sec. 6, 7); those
+ * states are computed in FP64 in both precisions and depend on the record's epoch.
  *
  * Conventions for every entry point:
  *  - All array arguments are DEVICE pointers unless stated otherwise, owned by the
@@ -26,11 +29,15 @@
  *   0  ok
  *   1  eccentricity out of range: input e0 outside [0,1) or a non-finite input
  *      element (fatal for the record), or mean e(t) >= 1 or < -0.001 after drag
- *   2  mean motion <= 0 (input n0 fatal for the record, or n0'' <= 0)
+ *   2  mean motion <= 0 (input n0 fatal for the record, or n0'' <= 0); deep space
+ *      with resonance: also |tsince| > 1e7 min or a non-finite tsince (the resonance
+ *      integration covers |tsince| <= 1e7 min)
+ *   3  deep space: eccentricity outside [0, 1] after the lunar-solar periodic terms
  *   4  semi-latus rectum p_L < 0
+ *   5  sgp4_jacobian only: a deep-space record, which it does not differentiate
  *   6  decayed: osculating radius below one Earth radius (r, v are still written)
- * Codes 1, 2 and 4 write NaN to r and v.  The first failing check in this order
- * wins: 2, 1, 4, 6.  3 and 5 are reserved (deep-space codes, not implemented).
+ * Codes 1 to 5 write NaN to r and v.  The first failing check in this order wins:
+ * 2, 1, 3, 4, 6.
  */
 #ifndef SGP4_B300_SGP4_H
 #define SGP4_B300_SGP4_H
@@ -61,7 +68,9 @@ enum {
   SGP4_STATUS_OK = 0,
   SGP4_STATUS_ECCENTRICITY = 1,
   SGP4_STATUS_MEAN_MOTION = 2,
+  SGP4_STATUS_DEEP_ECCENTRICITY = 3,
   SGP4_STATUS_SEMI_LATUS = 4,
+  SGP4_STATUS_NOT_DIFFERENTIATED = 5,
   SGP4_STATUS_DECAYED = 6
 };
 
@@ -110,8 +119,9 @@ sgp4_result sgp4_records_bind(void* arena, size_t bytes, int64_t n, const sgp4_c
  *   epoch_day    [n] int32 and epoch_frac [n] double: epoch as Julian date split
  *                into an integer day and a fraction in [0, 1) (paper Sec. 6: a split
  *                epoch avoids the FP32 epoch rounding).  Both may be NULL (epoch 0).
- *                Stored in the records; sgp4_propagate_jd measures time from them,
- *                tsince-based propagation does not use them.
+ *                Stored in the records; sgp4_propagate_jd measures time from them;
+ *                the deep-space terms of records with a period of 225 min or more
+ *                (the Sun's and Moon's positions, the sidereal angle) depend on it.
  *   init_status  [n] int32 out: 1/2 for unusable input (fatal for the record),
  *                otherwise the status of the state at tsince = 0.
  * Errors: SGP4_ERR_ARG for NULL elements/records/init_status with n > 0, a record
@@ -266,7 +276,8 @@ sgp4_result sgp4_batch_graph_destroy(void* graph);
  *   grad_elements  [n][7] double out
  *   workspace  device, sgp4_adjoint_workspace_bytes(n) bytes, 8-byte aligned
  * States with status 1, 2 or 4 contribute nothing; records with unusable elements
- * get a zero gradient.  Errors: SGP4_ERR_ARG for NULL / misaligned arrays, a record
+ * and deep-space records (period 225 min or more, not differentiated) get a zero
+ * gradient.  Errors: SGP4_ERR_ARG for NULL / misaligned arrays, a record
  * set of another size, bad precision or t_count < 0; SGP4_ERR_OOM for a small
  * workspace; SGP4_ERR_CUDA for a failed launch.
  */
@@ -295,7 +306,8 @@ sgp4_result sgp4_adjoint(const double* elements, const sgp4_records* records,
  *                 during the call)
  * SGP4_FP32 runs the sweeps in FP32 as sgp4_adjoint does and forms A and b per thread
  * in FP32 (sums over warps in FP64); the Cholesky solve is FP64 in both precisions.
- * Unusable records keep their elements and get sse 0.  Errors as sgp4_adjoint.
+ * Unusable records and deep-space records (not fitted) keep their elements and get
+ * sse 0.  Errors as sgp4_adjoint.
  */
 size_t sgp4_fit_workspace_bytes(int64_t n);
 sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
@@ -319,7 +331,8 @@ sgp4_result sgp4_fit_step(const double* elements, const sgp4_records* records,
  *   cov_out     [n][t_count][21] out (may be NULL): upper triangle of P, row by row
  *               ((0,0), (0,1) .. (0,5), (1,1) .. (5,5)), precision's type
  *   workspace   device, sgp4_jacobian_workspace_bytes(n) bytes, 8-byte aligned
- * States with status 1, 2 or 4 get NaN in r, v, jac and cov_out.  Errors:
+ * States with status 1, 2 or 4 get NaN in r, v, jac and cov_out; deep-space records
+ * (period 225 min or more) are not differentiated: status 5 and NaN.  Errors:
  * SGP4_ERR_ARG for NULL elements / tsince / status, cov_out without cov, misaligned
  * arrays, a bad precision or sizes; SGP4_ERR_OOM for a small workspace; SGP4_ERR_CUDA
  * for a failed launch.

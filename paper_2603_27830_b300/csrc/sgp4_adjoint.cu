@@ -143,6 +143,10 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
     s_fq.n = 0;
   }
   __syncthreads();
+  if (sat.rc.flags & kFlagDeep) {   // deep-space records are not differentiated: zero
+    if (tid < kNumAdj) a.field_bar[j * kNumAdj + tid] = 0.0;
+    return;
+  }
   T acc[kNumAdj];
 #pragma unroll
   for (int q = 0; q < kNumAdj; ++q) acc[q] = T(0);
@@ -333,6 +337,12 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
     (&Ji[0][0])[q] = static_cast<const T*>(a.jac)[j * kNumAdj * 7 + q];
   __syncthreads();
   if (!s_ok) return;   // fit_solve_kernel keeps the elements of unusable records
+  if (sat.rc.flags & kFlagDeep) {
+    // deep-space records are not fitted: zero normal equations leave their elements
+    // unchanged, with zero residual
+    if (tid < 36) a.normal[j * 36 + tid] = 0.0;
+    return;
+  }
   T A[28], b[7], sse = T(0);
 #pragma unroll
   for (int q = 0; q < 28; ++q) A[q] = T(0);

@@ -24,8 +24,24 @@ enum F64Field {
   kEta, kDelM0, kSinM0, kXlcof, kAycof,
   kCosi, kSini, kX3thm1, kX1mth2, kX7thm1,
   kEpochFrac,
+  // Deep space (period >= 225 min; written for deep-space records only): Greenwich
+  // sidereal angle at the epoch, the lunar-solar secular rates, each body's long-period
+  // amplitudes and mean anomaly at the epoch, the resonance amplitudes (one rev/day:
+  // kDel1..3; two: kD2201..kD5433), the resonant longitude at the epoch and its rate
+  // minus the mean motion.
+  kGsto, kEdotLs, kIdotLs, kMdotLs, kArgpdotLs, kRaandotLs,
+  kSunE2, kSunE3, kSunI2, kSunI3, kSunL2, kSunL3, kSunL4, kSunGh2, kSunGh3, kSunGh4,
+  kSunH2, kSunH3, kSunM0,
+  kMoonE2, kMoonE3, kMoonI2, kMoonI3, kMoonL2, kMoonL3, kMoonL4, kMoonGh2, kMoonGh3,
+  kMoonGh4, kMoonH2, kMoonH3, kMoonM0,
+  kDel1, kDel2, kDel3,
+  kD2201, kD2211, kD3210, kD3222, kD4410, kD4422, kD5220, kD5232, kD5421, kD5433,
+  kLambda0, kXfact,
   kNumF64
 };
+// Amplitudes of one body's long-period terms, in plane order from kSunE2 / kMoonE2.
+constexpr int kBodyPlanes = kSunM0 - kSunE2 + 1;
+static_assert(kMoonM0 - kMoonE2 + 1 == kBodyPlanes, "body plane blocks differ");
 
 // FP32-path record: one 160-byte row of 40 floats per satellite (array of
 // structures), read with ten 16-byte loads per state.  Angles and their rates are
@@ -50,6 +66,10 @@ static_assert(kNumF32Used <= kF32Row, "FP32 record row too small");
 // flags word
 constexpr int kFlagIsimp = 1;        // perigee below 220 km: truncated drag terms
 constexpr int kFlagN0ppNonPos = 2;   // n0'' <= 0 -> code 2 at every t
+constexpr int kFlagDeep = 4;         // deep space: FP64 deep-space state (the FP32 row's a0''
+                                     // is NaN, which sends every FP32 state to FP64)
+constexpr int kFlagRez1 = 16;        // deep space, one-revolution-per-day resonance
+constexpr int kFlagRez2 = 32;        // deep space, two-revolutions-per-day resonance
 constexpr int kFatalShift = 8;       // bits 8..15: fatal input code (1 or 2)
 
 __host__ __device__ inline int64_t record_stride(int64_t n) { return ((n + 63) / 64) * 64; }
@@ -186,63 +206,28 @@ __device__ __forceinline__ int newton_steps64(double eL2) {
        : eL2 <= 0.25 ? 5 : 10;
 }
 
-// One state in FP64.  Returns the status code; r (km) and v (km/s) are written
-// for codes 0 and 6 only.  Same theory and status decisions as the FP32 path and the
-// textbook form: atan2 and the sin/cos of u_k, RAAN_k, i_k are replaced by small
-// rotations of (sin, cos) pairs by the short-period corrections.
-__device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, double r[3],
-                                       double v[3]) {
-  const int fatal = (rc.flags >> kFatalShift) & 0xff;
-  if (fatal) return fatal;
-  const bool isimp = rc.flags & kFlagIsimp;
-
-  // Secular gravity and drag (mean elements at t).
-  const double mdf = rc.m0 + rc.mdot * t;
-  const double argpdf = rc.argp0 + rc.argpdot * t;
-  const double raandf = rc.raan0 + rc.raandot * t;
-  const double t2 = t * t;
-  double raan = raandf + rc.raan_cf * t2;
-  double argp = argpdf;
-  double tempa = 1.0 - rc.c1 * t;
-  double tempe = rc.bc4 * t;
-  double templ = rc.l2 * t2;
-  if (!isimp) {
-    const double dargp = rc.argp_cf * t;
-    double sm, cm;
-    sincos(wrap_2pi(mdf), &sm, &cm);
-    const double c = 1.0 + rc.eta * cm;
-    const double dm = rc.m_cf * (c * c * c - rc.delm0);
-    const double dd = dargp + dm;
-    argp = argpdf - dd;
-    const double t3 = t2 * t, t4 = t3 * t;
-    tempa = tempa - rc.d2 * t2 - rc.d3 * t3 - rc.d4 * t4;
-    double sdd, cdd;
-    sincos_small64(dd, sdd, cdd);   // the drag shift dd is usually small
-    tempe = tempe + rc.bc5 * (sm * cdd + cm * sdd - rc.sinm0);   // sin(M_DF + dd)
-    templ = templ + rc.l3 * t3 + t4 * (rc.l4 + t * rc.l5);
-  }
-  if (rc.flags & kFlagN0ppNonPos) return 2;
-  const double a = rc.a0pp * tempa * tempa;
+// From the mean elements after all secular (and, in deep space, lunar-solar) terms to
+// r, v: a (Earth radii), e, node, perigee, M + perigee (mpa), the J3 coefficients and
+// the inclination's functions (x3thm1 = 3 cos^2 i - 1, x1mth2 = 1 - cos^2 i, x7thm1 =
+// 7 cos^2 i - 1).
+__device__ __forceinline__ int state64_tail(const Geo& g, double a, double e, double raan,
+                                            double argp, double mpa, double xlcof,
+                                            double aycof, double cosi, double sini,
+                                            double x3thm1, double x1mth2, double x7thm1,
+                                            double r[3], double v[3]) {
   // square roots and reciprocals through rsqrt (one FP64-unit sequence instead of a
   // square root and a division)
   const double ra = rsqrt(a);
   const double sa = a * ra;
   const double ia15 = ra * ra * ra;                    // n / ke
-  double e = rc.e0 - tempe;
-  if (e >= 1.0 || e < -0.001) return 1;
-  if (e < 1.0e-6) e = 1.0e-6;
-  raan = wrap_2pi(raan);
-  argp = wrap_2pi(argp);
-  // M + argp: the drag corrections of M and argp cancel.
-  const double mpa = mdf + argpdf + rc.n0pp * templ;
 
   // Long-period periodics (J3).
   double sw, cw;
   sincos(argp, &sw, &cw);
   const double axn = e * cw;
   const double q = 1.0 / (a * (1.0 - e * e));
-  const double ayn = e * sw + q * rc.aycof;
-  const double U = wrap_2pi(mpa + q * rc.xlcof * axn);
+  const double ayn = e * sw + q * aycof;
+  const double U = wrap_2pi(mpa + q * xlcof * axn);
   const double eL2 = axn * axn + ayn * ayn;
 
   // Kepler's equation: Newton with clamped steps, count from the e_L bound.
@@ -283,20 +268,20 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   const double invp = rpl * rpl;
   const double k = 0.5 * g.j2 * invp;
   const double kp = k * invp;
-  const double rk = rl * (1.0 - 1.5 * kp * betal * rc.x3thm1) + 0.5 * k * rc.x1mth2 * cos2u;
+  const double rk = rl * (1.0 - 1.5 * kp * betal * x3thm1) + 0.5 * k * x1mth2 * cos2u;
   const double nk = ia15 * k;          // n k / ke
-  const double rdotk = rdotl - nk * rc.x1mth2 * sin2u;
-  const double rfdotk = rfdotl + nk * (rc.x1mth2 * cos2u + 1.5 * rc.x3thm1);
+  const double rdotk = rdotl - nk * x1mth2 * sin2u;
+  const double rfdotk = rfdotl + nk * (x1mth2 * cos2u + 1.5 * x3thm1);
 
   // u_k, RAAN_k and i_k as rotations of (sin, cos) pairs.
   const double nrm = rsqrt(sinu * sinu + cosu * cosu);
   double su = sinu * nrm, cu = cosu * nrm;
-  rotate64(su, cu, -0.25 * kp * rc.x7thm1 * sin2u);
+  rotate64(su, cu, -0.25 * kp * x7thm1 * sin2u);
   double sO, cO;
   sincos(raan, &sO, &cO);
-  rotate64(sO, cO, 1.5 * kp * rc.cosi * sin2u);
-  double si = rc.sini, ci = rc.cosi;
-  rotate64(si, ci, 1.5 * kp * rc.cosi * rc.sini * cos2u);
+  rotate64(sO, cO, 1.5 * kp * cosi * sin2u);
+  double si = sini, ci = cosi;
+  rotate64(si, ci, 1.5 * kp * cosi * sini * cos2u);
 
   const double mx = -sO * ci, my = cO * ci, mz = si;
   const double ux = mx * su + cO * cu, uy = my * su + sO * cu, uz = mz * su;
@@ -309,18 +294,52 @@ __device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, 
   return rk < 1.0 ? 6 : 0;
 }
 
-// Out-of-line FP64 recomputation of one guard-band state (the record build's status at
-// t = 0; the propagation kernels queue theirs and recompute them after their loops).
-static __device__ __noinline__ int state64_fallback(RecordPtrs rp, Geo g, int64_t j, double t,
-                                                    float r[3], float v[3]) {
-  const Rec64 rc = load_rec64(rp, j);
-  double r64[3], v64[3];
-  const int code = state64(rc, g, t, r64, v64);
-  for (int c = 0; c < 3; ++c) {
-    r[c] = (float)r64[c];
-    v[c] = (float)v64[c];
+// One state in FP64.  Returns the status code; r (km) and v (km/s) are written
+// for codes 0 and 6 only.  Same theory and status decisions as the FP32 path and the
+// textbook form: atan2 and the sin/cos of u_k, RAAN_k, i_k are replaced by small
+// rotations of (sin, cos) pairs by the short-period corrections.
+__device__ __forceinline__ int state64(const Rec64& rc, const Geo& g, double t, double r[3],
+                                       double v[3]) {
+  const int fatal = (rc.flags >> kFatalShift) & 0xff;
+  if (fatal) return fatal;
+  const bool isimp = rc.flags & kFlagIsimp;
+
+  // Secular gravity and drag (mean elements at t).
+  const double mdf = rc.m0 + rc.mdot * t;
+  const double argpdf = rc.argp0 + rc.argpdot * t;
+  const double raandf = rc.raan0 + rc.raandot * t;
+  const double t2 = t * t;
+  double raan = raandf + rc.raan_cf * t2;
+  double argp = argpdf;
+  double tempa = 1.0 - rc.c1 * t;
+  double tempe = rc.bc4 * t;
+  double templ = rc.l2 * t2;
+  if (!isimp) {
+    const double dargp = rc.argp_cf * t;
+    double sm, cm;
+    sincos(wrap_2pi(mdf), &sm, &cm);
+    const double c = 1.0 + rc.eta * cm;
+    const double dm = rc.m_cf * (c * c * c - rc.delm0);
+    const double dd = dargp + dm;
+    argp = argpdf - dd;
+    const double t3 = t2 * t, t4 = t3 * t;
+    tempa = tempa - rc.d2 * t2 - rc.d3 * t3 - rc.d4 * t4;
+    double sdd, cdd;
+    sincos_small64(dd, sdd, cdd);   // the drag shift dd is usually small
+    tempe = tempe + rc.bc5 * (sm * cdd + cm * sdd - rc.sinm0);   // sin(M_DF + dd)
+    templ = templ + rc.l3 * t3 + t4 * (rc.l4 + t * rc.l5);
   }
-  return code;
+  if (rc.flags & kFlagN0ppNonPos) return 2;
+  const double a = rc.a0pp * tempa * tempa;
+  double e = rc.e0 - tempe;
+  if (e >= 1.0 || e < -0.001) return 1;
+  if (e < 1.0e-6) e = 1.0e-6;
+  raan = wrap_2pi(raan);
+  argp = wrap_2pi(argp);
+  // M + argp: the drag corrections of M and argp cancel.
+  const double mpa = mdf + argpdf + rc.n0pp * templ;
+  return state64_tail(g, a, e, raan, argp, mpa, rc.xlcof, rc.aycof, rc.cosi, rc.sini,
+                      rc.x3thm1, rc.x1mth2, rc.x7thm1, r, v);
 }
 
 // ============================================================== FP32 state

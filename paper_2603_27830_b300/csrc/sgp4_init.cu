@@ -4,6 +4,7 @@
 // double-float row of the mixed-precision path and the init status.
 #include <cmath>
 
+#include "sgp4_deep.cuh"
 #include "sgp4_device.cuh"
 #include "sgp4_init_math.cuh"
 #include "sgp4_kernels.cuh"
@@ -202,6 +203,11 @@ __global__ void __launch_bounds__(kSplit ? 64 : 32) init_kernel(const double* __
       int flags = 0;
       if (isimp) flags |= kFlagIsimp;
       if (sp.n0pp <= 0.0) flags |= kFlagN0ppNonPos;
+      if (is_deep(sp.n0pp)) {
+        const int rez = resonance_class(sp.n0pp, e0);
+        flags |= kFlagDeep | (rez == 1 ? kFlagRez1 : 0) | (rez == 2 ? kFlagRez2 : 0);
+        h[fA0pp] = __int_as_float(0x7fc00000);   // NaN: every FP32 state goes to FP64
+      }
       rp.flags[j] = flags;
       h[fFlags] = __int_as_float(flags);
       for (int k = kNumF32Used; k < kF32Row; ++k) h[k] = 0.0f;
@@ -256,6 +262,14 @@ __global__ void __launch_bounds__(kSplit ? 64 : 32) init_kernel(const double* __
     h[fRaanCfr] = f32_rn(raan_cf * inv2pi);
   }
   if constexpr (kSplit) __syncthreads();
+
+  // Deep space: the lunar-solar and resonance constants, from the near-Earth fields
+  // written above (the secular rates by warp 1, visible after the barrier).
+  if (run && w0 && is_deep(sp.n0pp)) {
+    const DeepIn in = {e0, i0, raan0, argp0, m0, sp.n0pp, sp.cosi, sp.sini,
+                       f[kMdot * s + j], f[kArgpdot * s + j], f[kRaandot * s + j], g.xke};
+    deep_record_init(in, rp.epoch_day[j], f[kEpochFrac * s + j], f, s, j);
+  }
 
   // Init status: the status of the state at tsince = 0, from the FP32 state with its
   // FP64 recomputation inside the guard bands (so it equals the FP64 decision).

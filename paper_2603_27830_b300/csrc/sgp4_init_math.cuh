@@ -324,7 +324,9 @@ __device__ __forceinline__ void init_drag_core(const S el[7], const Geo& g,
   // Atmosphere: s and (q0 - s)^4 by perigee height.
   const S rp_er = a0pp * (1.0 - e0);
   const S hp = (rp_er - 1.0) * g.re;
-  dc.isimp = val(rp_er) < 1.0 + 220.0 * inv_re;
+  // Truncated drag: perigee below 220 km, and every deep-space orbit (period 2 pi / n0''
+  // of 225 min or more).
+  dc.isimp = val(rp_er) < 1.0 + 220.0 * inv_re || kTwoPi / val(sp.n0pp) >= 225.0;
   S s_km = 0.0 * hp + 78.0;
   if (val(hp) < 156.0) s_km = hp - 78.0;
   if (val(hp) < 98.0) s_km = 0.0 * hp + 20.0;

@@ -9,7 +9,8 @@
 // component (six seeds e_rx .. e_vz), each contracted with the record-field Jacobian
 // of sgp4init (computed once per satellite by launch_init_jacobian) into a row of
 // J = d(r, v)/d(elements).  Guard-band states of the FP32 path use the FP64 sweep.
-// States with status 1, 2 or 4 get NaN outputs, like their r and v.
+// States with status 1, 2 or 4 get NaN outputs, like their r and v.  Deep-space
+// records are not differentiated: their states get status 5 and NaN outputs.
 #include <cmath>
 #include <cstdint>
 
@@ -168,18 +169,21 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
     for (int k = 0; k < 7; ++k) e7[k] = a.el[j * 7 + k];
     s_ok = elements_usable(e7) ? 1 : 0;
     load_sat(a.rp, a.g, a.gf, j, sat);
+    if (sat.rc.flags & kFlagDeep) s_ok = 0;
   }
   for (int q = tid; q < kNumAdj * 7; q += kAdjThreads)
     (&Ji[0][0])[q] = static_cast<const T*>(a.jinit)[j * kNumAdj * 7 + q];
   if (a.out.cov && tid < 49) (&C[0][0])[tid] = T(a.out.cov[j * 49 + tid]);
   __syncthreads();
   if (!s_ok) {
-    // unusable elements: the record's fatal status with NaN outputs, as propagation
+    // unusable elements: the record's fatal status with NaN outputs, as propagation;
+    // deep-space records (not differentiated here): status 5, NaN outputs
     const T qnan = T(__longlong_as_double(0x7ff8000000000000LL));
     const int fatal = (sat.rc.flags >> kFatalShift) & 0xff;
+    const int code = (sat.rc.flags & kFlagDeep) ? 5 : fatal ? fatal : 1;
     for (int64_t i = tid; i < a.T; i += kAdjThreads) {
       const int64_t s = j * a.T + i;
-      a.out.status[s] = fatal ? fatal : 1;
+      a.out.status[s] = code;
       for (int c = 0; c < 3; ++c) {
         if (a.out.r) static_cast<T*>(a.out.r)[s * 3 + c] = qnan;
         if (a.out.v) static_cast<T*>(a.out.v)[s * 3 + c] = qnan;

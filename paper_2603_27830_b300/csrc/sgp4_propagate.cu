@@ -22,6 +22,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "sgp4_deep.cuh"
 #include "sgp4_device.cuh"
 #include "sgp4_kernels.cuh"
 #include "sgp4_state32x2.cuh"
@@ -120,6 +121,9 @@ struct UnitMap {
 
 // After the FP32 loop over units [ubeg, uend) of range rg and a __syncthreads: the
 // queued guard-band states in FP64, their r, v (NaN for codes 1, 2, 4) and status.
+// States of deep-space records (queued too: their FP32 row's a0'' is NaN) stay marked:
+// deep_fix_kernel recomputes them after the launch, which keeps the deep-space code
+// and the call it needs out of the FP32 kernels (with it the headline kernel spilled).
 // Adds the block's count to nfix (thread 0).  Inlined, FP64 state included: a kernel
 // with no call at all ran 0.4-2.4% faster than one calling it out of line.
 template <int kSpu, bool kCons>
@@ -142,6 +146,8 @@ __device__ __forceinline__ void fix_queued(const RecordPtrs& rp, const Geo& g, c
     } else {
       t = __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
     }
+    // deep-space states are left marked for deep_fix_kernel
+    if (__ldg(rp.flags + rec) & kFlagDeep) return;
     float* gr = static_cast<float*>(rg.r) + idx * 3;
     float* gv = static_cast<float*>(rg.v) + idx * 3;
     const Rec64 rc = load_rec64(rp, rec);
@@ -463,6 +469,7 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
       } else {
         t = __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
       }
+      if (rc.flags & kFlagDeep) continue;   // deep_fix_kernel's
       double r[3], v[3];
       const int code = state64(rc, g, t, r, v);
       const bool bad = code != 0 && code != 6;
@@ -505,6 +512,9 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   // build, in a step): the blocks are scheduled while it runs and wait here, before
   // their first global access, until it has completed and its writes are visible.
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // (No early trigger for deep_fix_kernel, launched after this one as its dependent:
+  // it starts as this grid's blocks exit.  Triggered here, its blocks waiting on the
+  // SMs made the record build + propagation step 3-4 us longer on Starlink.)
 #endif
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
@@ -624,6 +634,109 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
     }
   }
   if (kFP32 && a.fixups && nfix) atomicAdd(a.fixups, nfix);
+}
+
+// Deep-space states of satellites [j0, j1) (at most kThreads) and times [i0, i1) of
+// range rg, in FP64, by one block: the block gathers the slice's deep-space
+// satellites in shared memory (none: it is done), then its threads share their
+// states.  Outputs of type Out.
+template <typename Out>
+__device__ __forceinline__ void deep_slice(const RecordPtrs& rp, const Geo& g, const Range& rg,
+                                           int64_t j0, int64_t j1, int i0, int i1, int* s_sel,
+                                           int* s_n) {
+  if (threadIdx.x == 0) *s_n = 0;
+  __syncthreads();
+  const int64_t j = j0 + threadIdx.x;
+  if (j < j1 && (__ldg(rp.flags + rg.sat0 + j) & kFlagDeep)) s_sel[atomicAdd(s_n, 1)] = threadIdx.x;
+  __syncthreads();
+  const int nd = *s_n;
+  const int64_t T = rg.T;
+  const int nt = i1 - i0;
+  const Out q = (Out)__longlong_as_double(0x7ff8000000000000LL);
+  for (int64_t k = threadIdx.x; k < (int64_t)nd * nt; k += kThreads) {
+    const int64_t jj = j0 + s_sel[k / nt];
+    const int i = i0 + (int)(k % nt);
+    const int64_t rec = rg.sat0 + jj;
+    double t;
+    if (rg.jd_day) {
+      const int dday = __ldg(rg.jd_day + i) - __ldg(rp.epoch_day + rec);
+      const double dfrac = __ldg(rg.jd_frac + i) - __ldg(rp.f64 + kEpochFrac * rp.stride + rec);
+      t = fma(1440.0, dfrac, (double)((long long)dday * 1440));
+    } else {
+      t = __ldg(rg.per_sat ? rg.tsince + jj * T + i : rg.tsince + i);
+    }
+    double r64[3], v64[3];
+    const int cd = state64_deep(rp, rec, g, t, r64, v64);
+    const bool keep = cd == 0 || cd == 6;
+    const int64_t idx = jj * T + i;
+    Out* gr = static_cast<Out*>(rg.r) + idx * 3;
+    Out* gv = static_cast<Out*>(rg.v) + idx * 3;
+    for (int c = 0; c < 3; ++c) {
+      gr[c] = keep ? (Out)r64[c] : q;
+      gv[c] = keep ? (Out)v64[c] : q;
+    }
+    rg.status[idx] = cd;
+  }
+  __syncthreads();
+}
+
+// After a single-problem launch, as its programmatic dependent: the deep-space states
+// it left to this kernel, in FP64.  Without deep-space records its blocks read their
+// satellites' flags and exit.
+template <bool kFP32>
+__global__ void __launch_bounds__(kThreads) deep_fix_kernel(PropArgs a, int chunks) {
+  __shared__ int s_sel[kThreads];
+  __shared__ int s_n;
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  Range rg;
+  rg.tsince = a.tsince;
+  rg.jd_day = a.jd_day;
+  rg.jd_frac = a.jd_frac;
+  rg.jd0 = 0;
+  rg.T = a.t_count;
+  rg.per_sat = a.grid_per_sat;
+  rg.sat0 = 0;
+  rg.r = a.r;
+  rg.v = a.v;
+  rg.status = a.status;
+  // work items: (slice of kThreads satellites, one of `chunks` parts of the grid)
+  const int64_t n = a.rp.n;
+  const int T = (int)a.t_count;
+  const int per = (T + chunks - 1) / chunks;
+  const int64_t items = (n + kThreads - 1) / kThreads * chunks;
+  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    const int64_t j0 = w / chunks * kThreads;
+    const int i0 = (int)(w % chunks) * per;
+    deep_slice<std::conditional_t<kFP32, float, double>>(
+        a.rp, a.g, rg, j0, min(n, j0 + kThreads), i0, min(T, i0 + per), s_sel, &s_n);
+  }
+}
+
+// The same after a batched launch, request by request.
+template <bool kFP32>
+__global__ void __launch_bounds__(kThreads) deep_fix_batched_kernel(BatchArgs a) {
+  __shared__ int s_sel[kThreads];
+  __shared__ int s_n;
+  for (int k = 0; k < a.n_req; ++k) {
+    const sgp4_request q = a.reqs[k];
+    if (q.n == 0 || q.t_count == 0) continue;
+    Range rg;
+    rg.tsince = a.tsince + q.t_offset;
+    rg.jd_day = nullptr;
+    rg.jd_frac = nullptr;
+    rg.jd0 = 0;
+    rg.T = q.t_count;
+    rg.per_sat = 0;
+    rg.sat0 = q.sat_offset;
+    using Out = std::conditional_t<kFP32, float, double>;
+    rg.r = static_cast<Out*>(a.r) + q.out_offset * 3;
+    rg.v = static_cast<Out*>(a.v) + q.out_offset * 3;
+    rg.status = a.status + q.out_offset;
+    for (int64_t j0 = (int64_t)blockIdx.x * kThreads; j0 < q.n;
+         j0 += (int64_t)gridDim.x * kThreads)
+      deep_slice<Out>(a.rp, a.g, rg, j0, min(q.n, j0 + kThreads), 0, (int)q.t_count, s_sel,
+                      &s_n);
+  }
 }
 
 template <typename K>
@@ -759,12 +872,48 @@ int device_sm_count() {
   return sms > 0 ? sms : 1;
 }
 
+namespace {
+
+// The deep-space states after a single-problem launch, as the launch's programmatic
+// dependent: work items of kThreads satellites x a part of the grid (parts of at least
+// 32 times, as many as give four items per SM), at most four blocks per SM.
+template <bool kFP32>
+cudaError_t launch_deep_fix(const PropArgs& a, cudaStream_t stream) {
+  const int64_t slices = (a.rp.n + kThreads - 1) / kThreads;
+  const int64_t want = 4 * (int64_t)device_sm_count();
+  const int chunks = (int)std::max<int64_t>(
+      1, std::min<int64_t>((a.t_count + 31) / 32, (want + slices - 1) / slices));
+  const int64_t blocks = std::min<int64_t>(slices * chunks, want);
+#if SGP4_PDL
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, deep_fix_kernel<kFP32>, a, chunks);
+#else
+  deep_fix_kernel<kFP32><<<(unsigned)blocks, kThreads, 0, stream>>>(a, chunks);
+  return cudaGetLastError();
+#endif
+}
+
+}  // namespace
+
 cudaError_t launch_propagate64(const PropArgs& a, cudaStream_t stream) {
-  return launch_fp64(a, stream);
+  if (a.rp.n == 0 || a.t_count == 0) return cudaSuccess;
+  const cudaError_t e = launch_fp64(a, stream);
+  return e != cudaSuccess ? e : launch_deep_fix<false>(a, stream);
 }
 
 cudaError_t launch_propagate32(const PropArgs& a, cudaStream_t stream) {
-  return launch_fp32(a, stream);
+  if (a.rp.n == 0 || a.t_count == 0) return cudaSuccess;
+  const cudaError_t e = launch_fp32(a, stream);
+  return e != cudaSuccess ? e : launch_deep_fix<true>(a, stream);
 }
 
 int64_t batched_grid(bool fp32, int64_t total_tiles, int grid_blocks) {
@@ -776,8 +925,15 @@ cudaError_t launch_batched(const BatchArgs& a, bool fp32, int64_t total_tiles, i
   if (total_tiles == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return e;
-  if (fp32) batched_kernel<true><<<(unsigned)grid, kThreads, 0, stream>>>(a);
-  else batched_kernel<false><<<(unsigned)grid, kThreads, 0, stream>>>(a);
+  // then the deep-space states the batched kernel left to deep_fix_batched_kernel
+  const unsigned fix_grid = (unsigned)std::min<int64_t>(grid, 4 * (int64_t)device_sm_count());
+  if (fp32) {
+    batched_kernel<true><<<(unsigned)grid, kThreads, 0, stream>>>(a);
+    deep_fix_batched_kernel<true><<<fix_grid, kThreads, 0, stream>>>(a);
+  } else {
+    batched_kernel<false><<<(unsigned)grid, kThreads, 0, stream>>>(a);
+    deep_fix_batched_kernel<false><<<fix_grid, kThreads, 0, stream>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -8,7 +8,8 @@ log-U[10,500]: the batched persistent launch), adjoint (the fitting workload,
 10,000 x 500: one sgp4_adjoint call), fit (the same workload: one sgp4_fit_step call
 against observations of the perturbed elements), jacobian (the same workload: one
 sgp4_jacobian call with an element covariance), fit-forward (the same workload: init +
-propagate).  Prints the wall time of each
+propagate), deep-space (10,000 deep-space satellites with their own epochs x 1,000 times
+over seven days; ``--n`` shrinks it).  Prints the wall time of each
 repetition.
 """
 from __future__ import annotations
@@ -91,7 +92,8 @@ def run_jacobian(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", choices=["near-earth", "starlink", "catalogue", "batch",
-                                           "adjoint", "fit", "jacobian", "fit-forward"],
+                                           "adjoint", "fit", "jacobian", "fit-forward",
+                                           "deep-space"],
                     default="starlink")
     ap.add_argument("--precision", choices=["fp32", "fp64", "both"], default="fp32")
     ap.add_argument("--reps", type=int, default=2)
@@ -111,16 +113,22 @@ def main():
         w = W.config2()
     elif args.workload == "fit-forward":
         w = W.config5(n=args.n or 10_000)
+    elif args.workload == "deep-space":
+        w = W.deep_space(n=args.n or 10_000)
     else:
         w = W.config3(n=args.n or 1_000_000)
     el = torch.as_tensor(w.elements, device="cuda")
     ts = torch.as_tensor(w.tsince, device="cuda")
+    ep = {}
+    if "epoch_day" in w.meta:
+        ep = {"epoch_day": torch.as_tensor(w.meta["epoch_day"], device="cuda"),
+              "epoch_frac": torch.as_tensor(w.meta["epoch_frac"], device="cuda")}
     precs = ["fp32", "fp64"] if args.precision == "both" else [args.precision]
     for prec in precs:
         for k in range(args.reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            recs, _ = sgp4_init(el)
+            recs, _ = sgp4_init(el, **ep)
             r, v, st = sgp4_propagate(recs, ts, prec)
             torch.cuda.synchronize()
             print(f"{w.name} {prec} rep {k}: {1e3 * (time.perf_counter() - t0):.3f} ms")

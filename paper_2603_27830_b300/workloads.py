@@ -186,3 +186,64 @@ def config5(seed: int = 0, n: int = 10_000, t_count: int = 500):
 
     return Workload("fit-10000x500", base, t, "elements fit, truth = base (1 + N(0,1e-4))",
                     meta={"truth": truth, "noise": noise})
+
+
+def deep_space_elements(rng: np.random.Generator, n: int):
+    """Deep-space catalogue draw (periods of 225 min or more) in five classes:
+    geosynchronous 35% (n U[0.99, 1.01] rev/day, e |N(0, 5e-4)|, i U[0, 15] deg),
+    Molniya 15% (n U[2.0, 2.02], e U[0.6, 0.75], i N(63.4, 1) deg), navigation 20%
+    (n U[1.7, 2.01], e U[0, 0.02], i U[50, 65] deg), transfer orbits 20% (n U[2.2,
+    2.4], e U[0.65, 0.73], i U[0, 30] deg, perigee above 6,578 km) and others 10%
+    (period U[225 min, 3 days], e U[0, 0.5], perigee above 6,578 km); node, perigee and
+    mean anomaly U[0, 360) deg; B* log-U[1e-6, 1e-3]."""
+    cls = rng.choice(5, size=n, p=[0.35, 0.15, 0.20, 0.20, 0.10])
+    out = np.empty((n, 7))
+    for c in range(5):
+        k = np.nonzero(cls == c)[0]
+        m = k.size
+        if m == 0:
+            continue
+        if c == 0:
+            nr, e, i = rng.uniform(0.99, 1.01, m), np.minimum(np.abs(rng.normal(0, 5e-4, m)),
+                                                               0.01), rng.uniform(0, 15, m)
+        elif c == 1:
+            nr, e, i = rng.uniform(2.0, 2.02, m), rng.uniform(0.6, 0.75, m), rng.normal(63.4, 1, m)
+        elif c == 2:
+            nr, e, i = rng.uniform(1.7, 2.01, m), rng.uniform(0, 0.02, m), rng.uniform(50, 65, m)
+        else:
+            nr = np.empty(m)
+            e = np.empty(m)
+            filled = 0
+            while filled < m:
+                q = 2 * (m - filled) + 16
+                if c == 3:
+                    nq, eq = rng.uniform(2.2, 2.4, q), rng.uniform(0.65, 0.73, q)
+                else:
+                    nq, eq = 1440.0 / rng.uniform(225.0, 4320.0, q), rng.uniform(0.0, 0.5, q)
+                ok = _semi_major_km(nq * REV_PER_DAY) * (1.0 - eq) > 6578.0
+                take = min(int(ok.sum()), m - filled)
+                nr[filled:filled + take] = nq[ok][:take]
+                e[filled:filled + take] = eq[ok][:take]
+                filled += take
+            i = rng.uniform(0, 30, m) if c == 3 else rng.uniform(0, 180, m)
+        out[k, 0] = nr * REV_PER_DAY
+        out[k, 1] = e
+        out[k, 2] = np.clip(i, 0.0, 180.0) * DEG
+    out[:, 3] = rng.uniform(0.0, 360.0, n) * DEG
+    out[:, 4] = rng.uniform(0.0, 360.0, n) * DEG
+    out[:, 5] = rng.uniform(0.0, 360.0, n) * DEG
+    out[:, 6] = np.exp(rng.uniform(math.log(1e-6), math.log(1e-3), n))
+    return out
+
+
+def deep_space(seed: int = 0, n: int = 10_000, t_count: int = 1000) -> Workload:
+    """Deep-space catalogue: n satellites of deep_space_elements x t_count times over
+    seven days, each with its own epoch (Julian day U{2458000..2461999} + U[0, 1))."""
+    rng = np.random.default_rng(6000 + seed)
+    el = deep_space_elements(rng, n)
+    day = rng.integers(2458000, 2462000, n).astype(np.int32)
+    frac = rng.uniform(0.0, 1.0, n)
+    return Workload(f"deep-space-{n}x{t_count}", el, np.linspace(0.0, 10080.0, t_count),
+                    "deep-space classes (geosynchronous, Molniya, navigation, transfer, "
+                    "other), own epochs, tsince 0..10080 min",
+                    meta={"epoch_day": day, "epoch_frac": frac})

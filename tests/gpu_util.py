@@ -100,25 +100,26 @@ COND_FACTOR = 4.0
 _COND_SCALE = np.array([0.01, 1e-3, 1.0, 1.0, 1.0, 1.0, 1e-5])
 
 
-def oracle_sensitivity(elements, tsince):
+def oracle_sensitivity(elements, tsince, epoch=None):
     """Per state, the largest |dr| (km) and |dv| (km/s) of the oracle when one of the
-    seven elements of the satellite moves by COND_REL_STEP of itself."""
+    seven elements of the satellite moves by COND_REL_STEP of itself (``epoch``: the
+    records' (day, frac) epochs, as oracle.propagate takes them)."""
     import oracle
     el = np.ascontiguousarray(elements, dtype=np.float64)
-    r0, v0, s0, _ = oracle.propagate(el, tsince)
+    r0, v0, s0, _ = oracle.propagate(el, tsince, epoch=epoch)
     sr = np.zeros(s0.shape)
     sv = np.zeros(s0.shape)
     for j in range(7):
         e2 = el.copy()
         e2[:, j] += COND_REL_STEP * np.maximum(np.abs(el[:, j]), _COND_SCALE[j])
-        r2, v2, s2, _ = oracle.propagate(e2, tsince)
+        r2, v2, s2, _ = oracle.propagate(e2, tsince, epoch=epoch)
         ok = ((s0 == 0) | (s0 == 6)) & ((s2 == 0) | (s2 == 6))
         sr = np.maximum(sr, np.where(ok, np.linalg.norm(r2 - r0, axis=-1), 0.0))
         sv = np.maximum(sv, np.where(ok, np.linalg.norm(v2 - v0, axis=-1), 0.0))
     return sr, sv
 
 
-def assert_fp64_within_conditioning(dr, dv, elements, tsince, keep):
+def assert_fp64_within_conditioning(dr, dv, elements, tsince, keep, epoch=None):
     """dr, dv [n, T] (NaN or 0 where the state has no output; keep marks states with
     output): every state within the absolute FP64 bar, or, where the oracle itself is
     ill-conditioned, within COND_FACTOR times its measured sensitivity.  Returns the
@@ -128,7 +129,8 @@ def assert_fp64_within_conditioning(dr, dv, elements, tsince, keep):
         return 0
     sats = np.unique(np.nonzero(over)[0])
     t = tsince[sats] if np.ndim(tsince) == 2 else tsince
-    sr, sv = oracle_sensitivity(np.asarray(elements)[sats], t)
+    ep = None if epoch is None else (np.asarray(epoch[0])[sats], np.asarray(epoch[1])[sats])
+    sr, sv = oracle_sensitivity(np.asarray(elements)[sats], t, ep)
     o = over[sats]
     bar_r = np.maximum(FP64_TOL_R_KM, COND_FACTOR * sr)
     bar_v = np.maximum(FP64_TOL_V_KMS, COND_FACTOR * sv)

@@ -373,7 +373,7 @@ def test_fp32_time_split_keeps_minute_fractions():
 
 # The record layout of the C ABI (sgp4.h): FP64 planes, then one row of 40 floats per
 # satellite.  Plane and row indices of the fields the FP32 row carries unscaled.
-_N_PLANES, _ROW = 35, 40
+_N_PLANES, _ROW = 82, 40   # FP64 planes (near-Earth 35, deep space 47), floats per row
 _PLANE_ROW = {"a0pp": (1, 12), "e0": (2, 13), "c1": (14, 14), "bc4": (15, 15), "bc5": (16, 16),
               "d2": (17, 17), "d3": (18, 18), "d4": (19, 19), "l2": (20, 20), "l3": (21, 21),
               "l4": (22, 22), "l5": (23, 23), "eta": (24, 24), "delm0": (25, 25),
