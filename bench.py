@@ -217,7 +217,8 @@ class ClockSampler:
                 "sm_max_mhz": self.max_mhz, "reasons": reasons, "samples": len(self.samples)}
 
 
-def time_oracle(elements, tsince, threads: int, trials: int = 5, min_trial_s: float = 0.2):
+def time_oracle(elements, tsince, threads: int, trials: int = 5, min_trial_s: float = 0.2,
+                epoch=None):
     """The paper's timing protocol (Sec. 3.1) applied to the FP64 oracle as it stands:
     one call propagates every satellite to every time; a trial repeats the call until
     it has run at least min_trial_s, and the best of `trials` trials (time per call) is
@@ -229,7 +230,7 @@ def time_oracle(elements, tsince, threads: int, trials: int = 5, min_trial_s: fl
     while True:                      # find a repetition count that fills a trial
         t0 = time.perf_counter()
         for _ in range(reps):
-            oracle.propagate(elements, tsince, threads=threads)
+            oracle.propagate(elements, tsince, threads=threads, epoch=epoch)
         dt = time.perf_counter() - t0
         if dt >= min_trial_s:
             break
@@ -238,7 +239,7 @@ def time_oracle(elements, tsince, threads: int, trials: int = 5, min_trial_s: fl
     for _ in range(trials - 1):
         t0 = time.perf_counter()
         for _ in range(reps):
-            oracle.propagate(elements, tsince, threads=threads)
+            oracle.propagate(elements, tsince, threads=threads, epoch=epoch)
         best = min(best, (time.perf_counter() - t0) / reps)
     return states / best, best, reps
 
@@ -273,12 +274,15 @@ def _errors(r_dev, v_dev, st_dev, rows, rr, vr, sr):
 # lane operations each; scalar FADD / FMUL / FFMA and XU from the per-pipe counters):
 # near-earth 221, catalogue (100,000 x 100 of the same draw) 229, fitting workload 219
 # lane operations per state on the current kernel.  FP64: DADD + DMUL + DFMA of the
-# FP64 kernel.
+# FP64 kernel.  Deep space: the FP64 DADD + DMUL + DFMA of deep_fix_kernel, which
+# computes every deep-space state in both precisions (2,000 x 1,000 of the same draw:
+# 149.1 M + 549.8 M + 1191.7 M thread instructions for 2e6 states = 945 per state).
 OPS_PER_STATE = {
     "near-earth-64x100": {"fp32": 221, "fp64": 379},
     "starlink-9341x1000": {"fp32": ALG_OPS_FP32, "fp64": ALG_OPS_FP64},
     "catalogue-1Mx100": {"fp32": 229, "fp64": 406},
     "fit-10000x500": {"fp32": 219, "fp64": 384},
+    "deep-space-10000x1000": {"fp32": 945, "fp64": 945},
 }
 
 
@@ -293,11 +297,13 @@ def _roofline(prec, workload, states, kern_ms, alu_peak, fp64_peak, hbm_peak):
     if ops is None:
         out.update({"bound": "hbm", "frac": gbs / hbm_peak})
         return out
-    peak = alu_peak if prec == "fp32" else fp64_peak
+    # deep-space states run on the FP64 unit in both precisions
+    fp64_unit = prec == "fp64" or workload.startswith("deep-space")
+    peak = fp64_peak if fp64_unit else alu_peak
     gops = ops * states / sec / 1e9
     t_alu = ops * states / (peak * 1e9)
     t_hbm = BYTES_PER_STATE[prec] * states / (hbm_peak * 1e9)
-    bound = ("alu" if prec == "fp32" else "fp64") if t_alu >= t_hbm else "hbm"
+    bound = ("fp64" if fp64_unit else "alu") if t_alu >= t_hbm else "hbm"
     out.update({"bound": bound, "achieved": gops, "peak": peak, "unit": "Gop/s",
                 "ops_per_state": ops, "frac": (gops / peak) if bound != "hbm" else gbs / hbm_peak,
                 "alu_frac": gops / peak})
@@ -317,7 +323,14 @@ def run_single_config(torch, dev, stream, flush, steps, w, precs, n_sample, thre
     n, T = w.n, w.t_count
     el = torch.as_tensor(w.elements, device=dev)
     ts = torch.as_tensor(w.tsince, device=dev)
-    recs, ist = sgp4_init(el)
+    # records with their own epochs (the deep-space workload): the deep-space terms
+    # depend on them
+    ep_dev, ep_host = {}, None
+    if "epoch_day" in w.meta:
+        ep_dev = {"epoch_day": torch.as_tensor(w.meta["epoch_day"], device=dev),
+                  "epoch_frac": torch.as_tensor(w.meta["epoch_frac"], device=dev)}
+        ep_host = (w.meta["epoch_day"].astype(np.float64), w.meta["epoch_frac"])
+    recs, ist = sgp4_init(el, **ep_dev)
     if n_sample is None or n_sample >= n:
         rows = np.arange(n)
         sample = f"all {n} satellites x {T} times"
@@ -327,12 +340,13 @@ def run_single_config(torch, dev, stream, flush, steps, w, precs, n_sample, thre
                                          np.asarray(w.meta.get("invalid", []), dtype=np.int64)]))
         sample = (f"{len(rows)} of {n} satellites (random, plus every invalid record) x "
                   f"{T} times")
-    rr, vr, sr, _ = oracle.propagate(w.elements[rows], w.tsince, threads=threads)
+    ep_rows = None if ep_host is None else (ep_host[0][rows], ep_host[1][rows])
+    rr, vr, sr, _ = oracle.propagate(w.elements[rows], w.tsince, threads=threads, epoch=ep_rows)
     res = {"workload": w.name, "n_sats": n, "t_count": T,
            "horizon_min": [float(w.tsince.min()), float(w.tsince.max())],
            "error_sample": sample}
     if time_cpu:
-        rate, per_call, reps = time_oracle(w.elements[rows], w.tsince, threads)
+        rate, per_call, reps = time_oracle(w.elements[rows], w.tsince, threads, epoch=ep_rows)
         res["oracle"] = {"value": rate, "unit": UNIT, "cores": threads, "sample": sample,
                          "s_per_call": per_call, "calls_per_trial": reps,
                          "protocol": "best of 5 trials, each >= 0.2 s"}
@@ -361,7 +375,7 @@ def run_single_config(torch, dev, stream, flush, steps, w, precs, n_sample, thre
         reps = steps if prec == "fp32" else max(3, min(steps, 5))
 
         def step():
-            sgp4_init(el, records=recs, init_status=ist)
+            sgp4_init(el, records=recs, init_status=ist, **ep_dev)
             sgp4_propagate(recs, ts, prec, out=out)
 
         step_ms = median_ms(step, reps)
@@ -717,6 +731,8 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved_gops, "peak": alu_peak, "unit": "Gop/s",
                 "frac": achieved_gops / alu_peak, "traffic": TRAFFIC_FP32_BYTES,
                 "kernel": "propagate_kernel<fp32>", "kernel_ms": kern_ms,
+                "timed": "the sgp4_propagate call: propagate_kernel<fp32> and the deep-space "
+                         "pass after it (no deep-space records here: it reads their flags)",
                 "ops_per_state": ALG_OPS_FP32,
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
                 "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -765,6 +781,10 @@ def run_ours(args):
             "4": batched,
             "5": run_single_config(torch, dev, stream, flush, cs, W.config5(), ("fp32", "fp64"),
                                    None, **common),
+            # deep space (SDP4), the branch the paper leaves for future work: FP64 states
+            # in both precisions
+            "deep": run_single_config(torch, dev, stream, flush, cs, W.deep_space(),
+                                      ("fp64", "fp32"), 2_000, **common),
         }
         if adjoint is not None:
             configs["5"]["adjoint"] = "see the line's adjoint object (same workload)"
@@ -803,7 +823,8 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": 2 * args.steps,
+            # per step: the record build, the FP32 propagation and the deep-space pass
+            "gpu_launches": 3 * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

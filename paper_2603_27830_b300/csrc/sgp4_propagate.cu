@@ -684,10 +684,22 @@ __device__ __forceinline__ void deep_slice(const RecordPtrs& rp, const Geo& g, c
 // it left to this kernel, in FP64.  Without deep-space records its blocks read their
 // satellites' flags and exit.
 template <bool kFP32>
-__global__ void __launch_bounds__(kThreads) deep_fix_kernel(PropArgs a, int chunks) {
+__global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int chunks) {
   __shared__ int s_sel[kThreads];
   __shared__ int s_n;
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // Most record sets hold no deep-space record: each thread looks at its satellite of
+  // every item of this block first, and the block leaves if none is one.
+  {
+    const int64_t n = a.rp.n;
+    const int64_t items = (n + kThreads - 1) / kThreads * chunks;
+    bool any = false;
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+      const int64_t j = w / chunks * kThreads + threadIdx.x;
+      any |= j < n && (__ldg(a.rp.flags + j) & kFlagDeep);
+    }
+    if (!__syncthreads_or(any)) return;
+  }
   Range rg;
   rg.tsince = a.tsince;
   rg.jd_day = a.jd_day;
@@ -714,7 +726,7 @@ __global__ void __launch_bounds__(kThreads) deep_fix_kernel(PropArgs a, int chun
 
 // The same after a batched launch, request by request.
 template <bool kFP32>
-__global__ void __launch_bounds__(kThreads) deep_fix_batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kThreads, 4) deep_fix_batched_kernel(BatchArgs a) {
   __shared__ int s_sel[kThreads];
   __shared__ int s_n;
   for (int k = 0; k < a.n_req; ++k) {
