@@ -276,13 +276,15 @@ def _errors(r_dev, v_dev, st_dev, rows, rr, vr, sr):
 # lane operations per state on the current kernel.  FP64: DADD + DMUL + DFMA of the
 # FP64 kernel.  Deep space: the FP64 DADD + DMUL + DFMA of deep_fix_kernel, which
 # computes every deep-space state in both precisions (2,000 x 1,000 of the same draw:
-# 149.1 M + 549.8 M + 1191.7 M thread instructions for 2e6 states = 945 per state).
+# 93.3 M + 427.1 M + 780.7 M thread instructions for 2e6 states = 651 per state; with
+# the comparisons, conversions and roundings the FP64 pipe issues 1,069 per state and
+# is 86% busy).
 OPS_PER_STATE = {
     "near-earth-64x100": {"fp32": 221, "fp64": 379},
     "starlink-9341x1000": {"fp32": ALG_OPS_FP32, "fp64": ALG_OPS_FP64},
     "catalogue-1Mx100": {"fp32": 229, "fp64": 406},
     "fit-10000x500": {"fp32": 219, "fp64": 384},
-    "deep-space-10000x1000": {"fp32": 945, "fp64": 945},
+    "deep-space-10000x1000": {"fp32": 651, "fp64": 651},
 }
 
 

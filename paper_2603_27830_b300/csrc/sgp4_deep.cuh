@@ -274,46 +274,79 @@ __device__ __forceinline__ void shift(double sx, double cx, double sp, double cp
   c = cx * cp + sx * sp;
 }
 
-// Resonance: the resonant longitude lambda and mean motion n at t from the epoch values,
-// fixed 720-min steps of the second-order Taylor series (dlambda/dt = n + xfact, dn/dt
-// from the resonance terms, d2n/dt2 their derivative along lambda), then a partial
-// step.  The terms' sines come from one sincos of lambda (and of the perigee, which
-// moves at its J2 rate in the two-per-day terms) per step and angle addition.  Returns
-// false for a non-finite t or |t| > kMaxT.
+// sin and cos of the resonance terms' phases: [0, 3) the one-revolution-per-day terms'
+// (phase31, 2 phase22, 3 phase33), [3, 8) the two-per-day terms' (g22 .. g54).
+struct DeepPhases {
+  double s[8], c[8];
+};
+
+__device__ __forceinline__ void deep_phase(int k, DeepPhases& p) {
+  using namespace deep;
+  const double ph[8] = {kPh31, 2.0 * kPh22, 3.0 * kPh33, kG22, kG32, kG44, kG52, kG54};
+  sincos(ph[k], &p.s[k], &p.c[k]);
+}
+
+// One thread's resonance integration between states of one satellite: the last full
+// step point (tc, lambda, n) of record j.  Continuing from it takes the same steps, so
+// gives the same result, as starting from the epoch; like the revision's own cache it
+// restarts at the epoch when t changes sign or moves back towards the epoch.
+struct ResCache {
+  int64_t j;
+  double tc, lam, n;
+  double ndot, dsum;   // the rates at that point
+};
+
+// Resonance: the resonant longitude lambda and mean motion n at t, fixed 720-min steps
+// of the second-order Taylor series (dlambda/dt = n + xfact, dn/dt from the resonance
+// terms, d2n/dt2 their derivative along lambda) from the epoch values or the cached step
+// point, then a partial step.  The terms' sines come from one sincos of lambda (and of
+// the perigee, which moves at its J2 rate in the two-per-day terms) per step and angle
+// addition.  Returns false for a non-finite t or |t| > kMaxT.
 __device__ __forceinline__ bool deep_resonance(const RecordPtrs& rp, int64_t j, int rez,
                                                double n0pp, double argp0, double argpdot,
-                                               double t, double& n_out, double& lam_out) {
+                                               double t, double& n_out, double& lam_out,
+                                               const DeepPhases& ph, ResCache& cache) {
   using namespace deep;
   if (!(fabs(t) <= kMaxT)) return false;
   const double* f = rp.f64;
   const int64_t s = rp.stride;
   const double xfact = __ldg(f + kXfact * s + j);
-  double lam = __ldg(f + kLambda0 * s + j);
-  double n = n0pp;
-  const double h = t > 0.0 ? kStep : -kStep;
-  double tc = 0.0;
-  // rates at the current step: ndot and sum of k amp cos(argument)
+  double tc = 0.0, lam, n;
+  // rates at the current step: ndot and sum of k amp cos(argument); `known`: they are
+  // the cached ones of this step point
   double ndot = 0.0, dsum = 0.0;
+  bool known = false;
+  if (cache.j == j && cache.tc != 0.0 && t * cache.tc > 0.0 && fabs(t) >= fabs(cache.tc)) {
+    tc = cache.tc;
+    lam = cache.lam;
+    n = cache.n;
+    ndot = cache.ndot;
+    dsum = cache.dsum;
+    known = true;
+  } else {
+    lam = __ldg(f + kLambda0 * s + j);
+    n = n0pp;
+  }
+  const double h = t > 0.0 ? kStep : -kStep;
   if (rez == 1) {
     const double d1 = __ldg(f + kDel1 * s + j), d2 = __ldg(f + kDel2 * s + j),
                  d3 = __ldg(f + kDel3 * s + j);
-    double sp1, cp1, sp2, cp2, sp3, cp3;
-    sincos(kPh31, &sp1, &cp1);
-    sincos(2.0 * kPh22, &sp2, &cp2);
-    sincos(3.0 * kPh33, &sp3, &cp3);
-    for (;;) {
-      double s1, c1;
-      sincos(lam, &s1, &c1);
-      const double s2 = 2.0 * s1 * c1, c2 = c1 * c1 - s1 * s1;
-      const double s3 = s2 * c1 + c2 * s1, c3 = c2 * c1 - s2 * s1;
-      double a, b, x, y, u, w;
-      shift(s1, c1, sp1, cp1, a, b);
-      shift(s2, c2, sp2, cp2, x, y);
-      shift(s3, c3, sp3, cp3, u, w);
-      ndot = d1 * a + d2 * x + d3 * u;
-      dsum = d1 * b + 2.0 * d2 * y + 3.0 * d3 * w;
+    for (;; known = false) {
+      if (!known) {
+        double s1, c1;
+        sincos(lam, &s1, &c1);
+        const double s2 = 2.0 * s1 * c1, c2 = c1 * c1 - s1 * s1;
+        const double s3 = s2 * c1 + c2 * s1, c3 = c2 * c1 - s2 * s1;
+        double a, b, x, y, u, w;
+        shift(s1, c1, ph.s[0], ph.c[0], a, b);
+        shift(s2, c2, ph.s[1], ph.c[1], x, y);
+        shift(s3, c3, ph.s[2], ph.c[2], u, w);
+        ndot = d1 * a + d2 * x + d3 * u;
+        dsum = d1 * b + 2.0 * d2 * y + 3.0 * d3 * w;
+      }
       const double ldot = n + xfact;
       if (!(fabs(t - tc) >= kStep)) {
+        cache = ResCache{j, tc, lam, n, ndot, dsum};
         const double ft = t - tc;
         n_out = n + ndot * ft + dsum * ldot * (0.5 * ft * ft);
         lam_out = lam + ldot * ft + ndot * (0.5 * ft * ft);
@@ -325,47 +358,47 @@ __device__ __forceinline__ bool deep_resonance(const RecordPtrs& rp, int64_t j, 
     }
   }
   const double* d = f + kD2201 * s + j;   // ten planes kD2201 .. kD5433
-  double s22, c22, s32, c32, s44, c44, s52, c52, s54, c54;
-  sincos(kG22, &s22, &c22);
-  sincos(kG32, &s32, &c32);
-  sincos(kG44, &s44, &c44);
-  sincos(kG52, &s52, &c52);
-  sincos(kG54, &s54, &c54);
-  for (;;) {
-    double sl, cl, sw, cw;
-    sincos(lam, &sl, &cl);
-    sincos(argp0 + argpdot * tc, &sw, &cw);
-    const double sl2 = 2.0 * sl * cl, cl2 = cl * cl - sl * sl;
-    const double sw2 = 2.0 * sw * cw, cw2 = cw * cw - sw * sw;
-    // sin, cos of lambda + w, lambda - w, lambda + 2w, 2 lambda + w, 2 lambda - w,
-    // 2 lambda + 2 w
-    const double slpw = sl * cw + cl * sw, clpw = cl * cw - sl * sw;
-    const double slmw = sl * cw - cl * sw, clmw = cl * cw + sl * sw;
-    const double slp2w = sl * cw2 + cl * sw2, clp2w = cl * cw2 - sl * sw2;
-    const double s2lpw = sl2 * cw + cl2 * sw, c2lpw = cl2 * cw - sl2 * sw;
-    const double s2lmw = sl2 * cw - cl2 * sw, c2lmw = cl2 * cw + sl2 * sw;
-    const double s2lp2w = sl2 * cw2 + cl2 * sw2, c2lp2w = cl2 * cw2 - sl2 * sw2;
-    double a, b;
-    ndot = 0.0;
-    dsum = 0.0;
-    auto add = [&](int k, double sx, double cx, double sp, double cp, double weight) {
-      shift(sx, cx, sp, cp, a, b);
-      const double amp = __ldg(d + (int64_t)k * s);
-      ndot = fma(amp, a, ndot);
-      dsum = fma(amp * weight, b, dsum);
-    };
-    add(0, slp2w, clp2w, s22, c22, 1.0);     // 2w + lambda  (2,2,0,-1)
-    add(1, sl, cl, s22, c22, 1.0);           // lambda       (2,2,1,1)
-    add(2, slpw, clpw, s32, c32, 1.0);       // w + lambda   (3,2,1,0)
-    add(3, slmw, clmw, s32, c32, 1.0);       // lambda - w   (3,2,2,2)
-    add(4, s2lp2w, c2lp2w, s44, c44, 2.0);   // 2w + 2lambda (4,4,1,0)
-    add(5, sl2, cl2, s44, c44, 2.0);         // 2 lambda     (4,4,2,2)
-    add(6, slpw, clpw, s52, c52, 1.0);       // w + lambda   (5,2,2,0)
-    add(7, slmw, clmw, s52, c52, 1.0);       // lambda - w   (5,2,3,2)
-    add(8, s2lpw, c2lpw, s54, c54, 2.0);     // w + 2 lambda (5,4,2,1)
-    add(9, s2lmw, c2lmw, s54, c54, 2.0);     // 2 lambda - w (5,4,3,3)
+  const double s22 = ph.s[3], c22 = ph.c[3], s32 = ph.s[4], c32 = ph.c[4];
+  const double s44 = ph.s[5], c44 = ph.c[5], s52 = ph.s[6], c52 = ph.c[6];
+  const double s54 = ph.s[7], c54 = ph.c[7];
+  for (;; known = false) {
     const double ldot = n + xfact;
+    if (!known) {
+      double sl, cl, sw, cw;
+      sincos(lam, &sl, &cl);
+      sincos(argp0 + argpdot * tc, &sw, &cw);
+      const double sl2 = 2.0 * sl * cl, cl2 = cl * cl - sl * sl;
+      const double sw2 = 2.0 * sw * cw, cw2 = cw * cw - sw * sw;
+      // sin, cos of lambda + w, lambda - w, lambda + 2w, 2 lambda + w, 2 lambda - w,
+      // 2 lambda + 2 w
+      const double slpw = sl * cw + cl * sw, clpw = cl * cw - sl * sw;
+      const double slmw = sl * cw - cl * sw, clmw = cl * cw + sl * sw;
+      const double slp2w = sl * cw2 + cl * sw2, clp2w = cl * cw2 - sl * sw2;
+      const double s2lpw = sl2 * cw + cl2 * sw, c2lpw = cl2 * cw - sl2 * sw;
+      const double s2lmw = sl2 * cw - cl2 * sw, c2lmw = cl2 * cw + sl2 * sw;
+      const double s2lp2w = sl2 * cw2 + cl2 * sw2, c2lp2w = cl2 * cw2 - sl2 * sw2;
+      double a, b;
+      ndot = 0.0;
+      dsum = 0.0;
+      auto add = [&](int k, double sx, double cx, double sp, double cp, double weight) {
+        shift(sx, cx, sp, cp, a, b);
+        const double amp = __ldg(d + (int64_t)k * s);
+        ndot = fma(amp, a, ndot);
+        dsum = fma(amp * weight, b, dsum);
+      };
+      add(0, slp2w, clp2w, s22, c22, 1.0);     // 2w + lambda  (2,2,0,-1)
+      add(1, sl, cl, s22, c22, 1.0);           // lambda       (2,2,1,1)
+      add(2, slpw, clpw, s32, c32, 1.0);       // w + lambda   (3,2,1,0)
+      add(3, slmw, clmw, s32, c32, 1.0);       // lambda - w   (3,2,2,2)
+      add(4, s2lp2w, c2lp2w, s44, c44, 2.0);   // 2w + 2lambda (4,4,1,0)
+      add(5, sl2, cl2, s44, c44, 2.0);         // 2 lambda     (4,4,2,2)
+      add(6, slpw, clpw, s52, c52, 1.0);       // w + lambda   (5,2,2,0)
+      add(7, slmw, clmw, s52, c52, 1.0);       // lambda - w   (5,2,3,2)
+      add(8, s2lpw, c2lpw, s54, c54, 2.0);     // w + 2 lambda (5,4,2,1)
+      add(9, s2lmw, c2lmw, s54, c54, 2.0);     // 2 lambda - w (5,4,3,3)
+    }
     if (!(fabs(t - tc) >= kStep)) {
+      cache = ResCache{j, tc, lam, n, ndot, dsum};
       const double ft = t - tc;
       n_out = n + ndot * ft + dsum * ldot * (0.5 * ft * ft);
       lam_out = lam + ldot * ft + ndot * (0.5 * ft * ft);
@@ -389,10 +422,21 @@ __device__ __forceinline__ void deep_periodics(const RecordPtrs& rp, int64_t j, 
   double pe = 0.0, pi = 0.0, pl = 0.0, pgh = 0.0, ph = 0.0;
   for (int b = 0; b < 2; ++b) {
     const double* o = f + (int64_t)(b ? kMoonE2 : kSunE2) * s + j;
+    // true anomaly f = M + d, d = 2 e sin M (|d| <= 0.11): sin f, cos f by rotating
+    // (sin M, cos M) by d, whose sine and cosine are Taylor series to d^11 and d^12
+    // (truncation below 1e-22)
     const double mb = __ldg(o + 12 * s) + (b ? kMoonN : kSunN) * t;
-    const double fb = mb + 2.0 * (b ? kMoonE : kSunE) * sin(mb);
-    double sf, cf;
-    sincos(fb, &sf, &cf);
+    double sm, cm;
+    sincos(mb, &sm, &cm);
+    const double d = 2.0 * (b ? kMoonE : kSunE) * sm, d2 = d * d;
+    const double sd =
+        d * (1.0 - d2 * (1.0 / 6.0) * (1.0 - d2 * (1.0 / 20.0) * (1.0 - d2 * (1.0 / 42.0) *
+             (1.0 - d2 * (1.0 / 72.0) * (1.0 - d2 * (1.0 / 110.0))))));
+    const double cd =
+        1.0 - d2 * 0.5 * (1.0 - d2 * (1.0 / 12.0) * (1.0 - d2 * (1.0 / 30.0) *
+              (1.0 - d2 * (1.0 / 56.0) * (1.0 - d2 * (1.0 / 90.0) * (1.0 - d2 * (1.0 / 132.0))))));
+    const double sf = sm * cd + cm * sd;
+    const double cf = cm * cd - sm * sd;
     const double F2 = 0.5 * sf * sf - 0.25;
     const double F3 = -0.5 * sf * cf;
     pe += __ldg(o + 0 * s) * F2 + __ldg(o + 1 * s) * F3;
@@ -416,7 +460,7 @@ __device__ __forceinline__ void deep_periodics(const RecordPtrs& rp, int64_t j, 
   sincos(raan, &so, &co);
   const double alpha = si * so + (ph * co + pi * ci * so);
   const double beta = si * co + (pi * ci * co - ph * so);
-  raan = fmod(raan, kTwoPi);
+  raan = wrap_2pi(raan);
   const double L = M + argp + ci * raan + (pl + pgh - pi * raan * si);
   const double mean_node = raan;
   raan = atan2(alpha, beta);
@@ -433,7 +477,8 @@ __device__ __forceinline__ void deep_periodics(const RecordPtrs& rp, int64_t j, 
 #define SGP4_DEEP_INLINE __noinline__
 #endif
 static __device__ SGP4_DEEP_INLINE int state64_deep(const RecordPtrs rp, int64_t j, const Geo g,
-                                             double t, double* r, double* v) {
+                                             double t, double* r, double* v,
+                                             const DeepPhases* ph, ResCache* cache) {
   const Rec64 rc = load_rec64(rp, j);
   const double* f = rp.f64;
   const int64_t s = rp.stride;
@@ -452,8 +497,9 @@ static __device__ SGP4_DEEP_INLINE int state64_deep(const RecordPtrs rp, int64_t
   const int rez = (rc.flags & kFlagRez1) ? 1 : (rc.flags & kFlagRez2) ? 2 : 0;
   if (rez) {
     double lam;
-    if (!deep_resonance(rp, j, rez, rc.n0pp, rc.argp0, rc.argpdot, t, n, lam)) return 2;
-    const double theta = fmod(__ldg(f + kGsto * s + j) + t * deep::kEarthRot, kTwoPi);
+    if (!deep_resonance(rp, j, rez, rc.n0pp, rc.argp0, rc.argpdot, t, n, lam, *ph, *cache))
+      return 2;
+    const double theta = wrap_2pi(__ldg(f + kGsto * s + j) + t * deep::kEarthRot);
     M = rez == 1 ? lam - raan - argp + theta : lam - 2.0 * raan + 2.0 * theta;
   }
   if (n <= 0.0) return 2;
@@ -462,11 +508,12 @@ static __device__ SGP4_DEEP_INLINE int state64_deep(const RecordPtrs rp, int64_t
   if (e >= 1.0 || e < -0.001) return 1;
   if (e < 1.0e-6) e = 1.0e-6;
   M += rc.n0pp * templ;
-  // mean angles reduced as in the near-Earth theory (C fmod, sign kept)
-  const double L = fmod(M + argp + raan, kTwoPi);
-  raan = fmod(raan, kTwoPi);
-  argp = fmod(argp, kTwoPi);
-  M = fmod(L - argp - raan, kTwoPi);
+  // mean angles reduced as in the near-Earth theory (the sign kept; wrap_2pi equals C
+  // fmod to rounding without its iterative remainder)
+  const double L = wrap_2pi(M + argp + raan);
+  raan = wrap_2pi(raan);
+  argp = wrap_2pi(argp);
+  M = wrap_2pi(L - argp - raan);
 
   deep_periodics(rp, j, t, e, inc, raan, argp, M);
   if (inc < 0.0) {
@@ -492,10 +539,16 @@ static __device__ SGP4_DEEP_INLINE int state64_deep(const RecordPtrs rp, int64_t
   return code;
 }
 
-// Any record in FP64: the deep-space state for deep-space records, else state64.
+// Any record in FP64: the deep-space state for deep-space records (phases computed
+// here, no cache), else state64.
 __device__ __forceinline__ int state64_any(const RecordPtrs& rp, int64_t j, const Rec64& rc,
                                            const Geo& g, double t, double r[3], double v[3]) {
-  if (rc.flags & kFlagDeep) return state64_deep(rp, j, g, t, r, v);
+  if (rc.flags & kFlagDeep) {
+    DeepPhases ph;
+    for (int k = 0; k < 8; ++k) deep_phase(k, ph);
+    ResCache cache{-1, 0.0, 0.0, 0.0};
+    return state64_deep(rp, j, g, t, r, v, &ph, &cache);
+  }
   return state64(rc, g, t, r, v);
 }
 

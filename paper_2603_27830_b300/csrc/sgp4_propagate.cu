@@ -638,12 +638,13 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
 
 // Deep-space states of satellites [j0, j1) (at most kThreads) and times [i0, i1) of
 // range rg, in FP64, by one block: the block gathers the slice's deep-space
-// satellites in shared memory (none: it is done), then its threads share their
-// states.  Outputs of type Out.
+// satellites in shared memory (none: it is done), then each thread takes a run of
+// consecutive states (satellite-major), so that it carries its resonance integration
+// from one time of a satellite to the next.  Outputs of type Out.
 template <typename Out>
 __device__ __forceinline__ void deep_slice(const RecordPtrs& rp, const Geo& g, const Range& rg,
                                            int64_t j0, int64_t j1, int i0, int i1, int* s_sel,
-                                           int* s_n) {
+                                           int* s_n, const DeepPhases* ph) {
   if (threadIdx.x == 0) *s_n = 0;
   __syncthreads();
   const int64_t j = j0 + threadIdx.x;
@@ -653,7 +654,11 @@ __device__ __forceinline__ void deep_slice(const RecordPtrs& rp, const Geo& g, c
   const int64_t T = rg.T;
   const int nt = i1 - i0;
   const Out q = (Out)__longlong_as_double(0x7ff8000000000000LL);
-  for (int64_t k = threadIdx.x; k < (int64_t)nd * nt; k += kThreads) {
+  const int64_t S = nt > 0 ? (int64_t)nd * nt : 0;
+  const int64_t per = (S + kThreads - 1) / kThreads;
+  const int64_t k0 = threadIdx.x * per, k1 = min(S, k0 + per);
+  ResCache cache{-1, 0.0, 0.0, 0.0};
+  for (int64_t k = k0; k < k1; ++k) {
     const int64_t jj = j0 + s_sel[k / nt];
     const int i = i0 + (int)(k % nt);
     const int64_t rec = rg.sat0 + jj;
@@ -666,7 +671,7 @@ __device__ __forceinline__ void deep_slice(const RecordPtrs& rp, const Geo& g, c
       t = __ldg(rg.per_sat ? rg.tsince + jj * T + i : rg.tsince + i);
     }
     double r64[3], v64[3];
-    const int cd = state64_deep(rp, rec, g, t, r64, v64);
+    const int cd = state64_deep(rp, rec, g, t, r64, v64, ph, &cache);
     const bool keep = cd == 0 || cd == 6;
     const int64_t idx = jj * T + i;
     Out* gr = static_cast<Out*>(rg.r) + idx * 3;
@@ -687,6 +692,7 @@ template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int chunks) {
   __shared__ int s_sel[kThreads];
   __shared__ int s_n;
+  __shared__ DeepPhases s_ph;
   asm volatile("griddepcontrol.wait;" ::: "memory");
   // Most record sets hold no deep-space record: each thread looks at its satellite of
   // every item of this block first, and the block leaves if none is one.
@@ -700,6 +706,7 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int c
     }
     if (!__syncthreads_or(any)) return;
   }
+  if (threadIdx.x < 8) deep_phase(threadIdx.x, s_ph);   // visible after deep_slice's barrier
   Range rg;
   rg.tsince = a.tsince;
   rg.jd_day = a.jd_day;
@@ -720,7 +727,7 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int c
     const int64_t j0 = w / chunks * kThreads;
     const int i0 = (int)(w % chunks) * per;
     deep_slice<std::conditional_t<kFP32, float, double>>(
-        a.rp, a.g, rg, j0, min(n, j0 + kThreads), i0, min(T, i0 + per), s_sel, &s_n);
+        a.rp, a.g, rg, j0, min(n, j0 + kThreads), i0, min(T, i0 + per), s_sel, &s_n, &s_ph);
   }
 }
 
@@ -729,6 +736,8 @@ template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, 4) deep_fix_batched_kernel(BatchArgs a) {
   __shared__ int s_sel[kThreads];
   __shared__ int s_n;
+  __shared__ DeepPhases s_ph;
+  if (threadIdx.x < 8) deep_phase(threadIdx.x, s_ph);   // visible after deep_slice's barrier
   for (int k = 0; k < a.n_req; ++k) {
     const sgp4_request q = a.reqs[k];
     if (q.n == 0 || q.t_count == 0) continue;
@@ -747,7 +756,7 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_batched_kernel(BatchArgs
     for (int64_t j0 = (int64_t)blockIdx.x * kThreads; j0 < q.n;
          j0 += (int64_t)gridDim.x * kThreads)
       deep_slice<Out>(a.rp, a.g, rg, j0, min(q.n, j0 + kThreads), 0, (int)q.t_count, s_sel,
-                      &s_n);
+                      &s_n, &s_ph);
   }
 }
 
