@@ -733,8 +733,8 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved_gops, "peak": alu_peak, "unit": "Gop/s",
                 "frac": achieved_gops / alu_peak, "traffic": TRAFFIC_FP32_BYTES,
                 "kernel": "propagate_kernel<fp32>", "kernel_ms": kern_ms,
-                "timed": "the sgp4_propagate call: propagate_kernel<fp32> and the deep-space "
-                         "pass after it (no deep-space records here: it reads their flags)",
+                "timed": "the sgp4_propagate call: the deep-space pass (no deep-space records "
+                         "here: it reads their flags) and propagate_kernel<fp32> after it",
                 "ops_per_state": ALG_OPS_FP32,
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
                 "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",

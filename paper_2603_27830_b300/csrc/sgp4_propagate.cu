@@ -121,9 +121,10 @@ struct UnitMap {
 
 // After the FP32 loop over units [ubeg, uend) of range rg and a __syncthreads: the
 // queued guard-band states in FP64, their r, v (NaN for codes 1, 2, 4) and status.
-// States of deep-space records (queued too: their FP32 row's a0'' is NaN) stay marked:
-// deep_fix_kernel recomputes them after the launch, which keeps the deep-space code
-// and the call it needs out of the FP32 kernels (with it the headline kernel spilled).
+// States of deep-space records are not queued (their FP32 row's a0'' NaN makes every one
+// a guard-band state, which the loops drop): deep_fix_kernel computes them, which keeps
+// the deep-space code and the call it needs out of the FP32 kernels (with it the
+// headline kernel spilled).  The check below only serves a rescan.
 // Adds the block's count to nfix (thread 0).  Inlined, FP64 state included: a kernel
 // with no call at all ran 0.4-2.4% faster than one calling it out of line.
 template <int kSpu, bool kCons>
@@ -146,7 +147,7 @@ __device__ __forceinline__ void fix_queued(const RecordPtrs& rp, const Geo& g, c
     } else {
       t = __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
     }
-    // deep-space states are left marked for deep_fix_kernel
+    // deep-space states are deep_fix_kernel's
     if (__ldg(rp.flags + rec) & kFlagDeep) return;
     float* gr = static_cast<float*>(rg.r) + idx * 3;
     float* gv = static_cast<float*>(rg.v) + idx * 3;
@@ -244,7 +245,7 @@ __device__ __forceinline__ void run_range_x2(const RecordPtrs& rp, const GeoF& g
       float* gv = static_cast<float*>(rg.v) + idx * 3;
       const int cd = code[l];
       if (cd == kRecomputeFP64) {   // r, v and status written after the loop
-        queue_fix(fq, rg.status, idx);
+        if (!(rc32.flags & kFlagDeep)) queue_fix(fq, rg.status, idx);   // deep: not ours
         continue;
       }
       {
@@ -411,7 +412,7 @@ __device__ __forceinline__ void run_range_x4(const RecordPtrs& rp, const GeoF& g
         const int cd = odd ? (hi ? cB[1] : cB[0]) : (hi ? cA[1] : cA[0]);
         const int64_t idx = idx0 + k * kstride;
         if (cd == kRecomputeFP64) {   // r, v and status written after the loop
-          queue_fix(fq, rg.status, idx);
+          if (!(rc32.flags & kFlagDeep)) queue_fix(fq, rg.status, idx);   // deep: not ours
           continue;
         }
         float* gr = static_cast<float*>(rg.r) + idx * 3;
@@ -512,9 +513,6 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   // build, in a step): the blocks are scheduled while it runs and wait here, before
   // their first global access, until it has completed and its writes are visible.
   asm volatile("griddepcontrol.wait;" ::: "memory");
-  // (No early trigger for deep_fix_kernel, launched after this one as its dependent:
-  // it starts as this grid's blocks exit.  Triggered here, its blocks waiting on the
-  // SMs made the record build + propagation step 3-4 us longer on Starlink.)
 #endif
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
@@ -685,15 +683,18 @@ __device__ __forceinline__ void deep_slice(const RecordPtrs& rp, const Geo& g, c
   __syncthreads();
 }
 
-// After a single-problem launch, as its programmatic dependent: the deep-space states
-// it left to this kernel, in FP64.  Without deep-space records its blocks read their
-// satellites' flags and exit.
+// The deep-space states of a single-problem call, in FP64, launched before the
+// propagation kernel (which leaves those states untouched) as the record build's
+// programmatic dependent, the propagation being its own.  Without deep-space records
+// its blocks read their satellites' flags and exit.
 template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int chunks) {
   __shared__ int s_sel[kThreads];
   __shared__ int s_n;
   __shared__ DeepPhases s_ph;
   asm volatile("griddepcontrol.wait;" ::: "memory");
+  // the propagation launched after this pass as its dependent may be scheduled now
+  asm volatile("griddepcontrol.launch_dependents;");
   // Most record sets hold no deep-space record: each thread looks at its satellite of
   // every item of this block first, and the block leaves if none is one.
   {
@@ -895,9 +896,13 @@ int device_sm_count() {
 
 namespace {
 
-// The deep-space states after a single-problem launch, as the launch's programmatic
-// dependent: work items of kThreads satellites x a part of the grid (parts of at least
-// 32 times, as many as give four items per SM), at most four blocks per SM.
+// The deep-space states of a single-problem call, before its propagation launch and as
+// a programmatic dependent: work items of kThreads satellites x a part of the grid
+// (parts of at least 32 times, as many as give four items per SM), at most four blocks
+// per SM.  Launched before the propagation rather than after it: on the Starlink-shaped
+// record build + propagation step it then costs 0-2 us instead of 8 (A/B on one box;
+// after it, the pass's blocks waited for the whole propagation grid, and the step lost
+// the overlap of the record build with the propagation's launch).
 template <bool kFP32>
 cudaError_t launch_deep_fix(const PropArgs& a, cudaStream_t stream) {
   const int64_t slices = (a.rp.n + kThreads - 1) / kThreads;
@@ -927,14 +932,14 @@ cudaError_t launch_deep_fix(const PropArgs& a, cudaStream_t stream) {
 
 cudaError_t launch_propagate64(const PropArgs& a, cudaStream_t stream) {
   if (a.rp.n == 0 || a.t_count == 0) return cudaSuccess;
-  const cudaError_t e = launch_fp64(a, stream);
-  return e != cudaSuccess ? e : launch_deep_fix<false>(a, stream);
+  const cudaError_t e = launch_deep_fix<false>(a, stream);
+  return e != cudaSuccess ? e : launch_fp64(a, stream);
 }
 
 cudaError_t launch_propagate32(const PropArgs& a, cudaStream_t stream) {
   if (a.rp.n == 0 || a.t_count == 0) return cudaSuccess;
-  const cudaError_t e = launch_fp32(a, stream);
-  return e != cudaSuccess ? e : launch_deep_fix<true>(a, stream);
+  const cudaError_t e = launch_deep_fix<true>(a, stream);
+  return e != cudaSuccess ? e : launch_fp32(a, stream);
 }
 
 int64_t batched_grid(bool fp32, int64_t total_tiles, int grid_blocks) {
