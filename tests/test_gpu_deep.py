@@ -263,3 +263,63 @@ def test_differentiable_entry_points_leave_deep_records_out():
                                                            device="cuda"), precision)
         assert torch.equal(el_out[1], elt[1]) and float(sse[1]) == 0.0
         assert float(sse[0]) > 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_deep_graph_replay_and_no_alloc_entry(precision):
+    """Batches holding deep-space records: a CUDA-graph replay of the batched launch
+    (batched kernel + deep-space pass captured together) and the no-allocation entry
+    point both equal the direct workspace launch, bit for bit."""
+    import ctypes
+
+    import torch
+
+    from paper_2603_27830_b300 import (BatchGraph, _lib, make_batch, plan_batch, sgp4_init,
+                                       sgp4_propagate_batched)
+    rng = np.random.default_rng(12)
+    problems = []
+    for k in range(5):
+        el = (W.deep_space_elements(rng, 30 + 20 * k) if k % 2 == 0
+              else W.catalogue_elements(rng, 40 + 10 * k))
+        problems.append((el, np.sort(rng.uniform(-720.0, 4000.0, 15 + 6 * k))))
+    b = make_batch(problems)
+    n = b.elements.shape[0]
+    day = torch.as_tensor(rng.integers(2458000, 2462000, n).astype(np.int32), device="cuda")
+    frac = torch.as_tensor(rng.uniform(0.0, 1.0, n), device="cuda")
+    recs, _ = sgp4_init(torch.as_tensor(b.elements, device="cuda"), epoch_day=day,
+                        epoch_frac=frac)
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    ref = sgp4_propagate_batched(plan_batch(b.requests, 512), recs, ts, precision)
+    torch.cuda.synchronize()
+    assert bool((ref[2] != -1).all())   # every state written, none left marked
+
+    g = BatchGraph(plan_batch(b.requests, 512), recs, ts, precision)
+    for x in g.out:
+        x.fill_(0)
+    out = g.replay()
+    torch.cuda.synchronize()
+    for x, y in zip(out, ref[:3]):
+        assert torch.equal(x.nan_to_num(7.0), y.nan_to_num(7.0))
+    g.close()
+
+    lib = _lib.load()
+    nreq = len(b.requests)
+    table = (_lib.Sgp4Request * nreq)()
+    for k in range(nreq):
+        table[k] = _lib.Sgp4Request(*[int(x) for x in b.requests[k]])
+    S = ref[2].numel()
+    dt = ref[0].dtype
+    o = (torch.full((S, 3), 555.0, dtype=dt, device="cuda"),
+         torch.full((S, 3), 555.0, dtype=dt, device="cuda"),
+         torch.full((S,), 99, dtype=torch.int32, device="cuda"))
+    stream = torch.cuda.current_stream()
+    rc = lib.sgp4_propagate_batched_static(
+        ctypes.cast(table, ctypes.c_void_p), nreq, 512, ctypes.byref(recs.c),
+        ctypes.c_void_p(ts.data_ptr()), ts.numel(),
+        _lib.SGP4_FP32 if precision == "fp32" else _lib.SGP4_FP64,
+        ctypes.c_void_p(o[0].data_ptr()), ctypes.c_void_p(o[1].data_ptr()),
+        ctypes.c_void_p(o[2].data_ptr()), S, ctypes.c_void_p(stream.cuda_stream))
+    assert rc == _lib.SGP4_OK
+    torch.cuda.synchronize()
+    for x, y in zip(o, ref[:3]):
+        assert torch.equal(x.nan_to_num(7.0), y.nan_to_num(7.0))
