@@ -58,7 +58,10 @@ TRAFFIC_FP32_BYTES = 203_465_984
 # DFMA 210.0).
 ALG_OPS_FP64 = 365
 # Per state of the adjoint sweep on the fitting workload (10,000 x 500), counted with
-# ncu on the current kernels: FP32 path FADD 78.4 + FMUL 221.6 + FFMA 169.9 + SFU 29.8;
+# ncu: FP32 path FADD 78.4 + FMUL 221.6 + FFMA 169.9 + SFU 29.8 lane operations, the mix
+# of the scalar sweep (one state per thread).  The packed sweep now run (two states per
+# thread) executes 536 (FADD2/FMUL2/FFMA2 x 2 lanes + scalar FADD/FMUL/FFMA + SFU: the
+# negations and sums of its packed form add some); the smaller count is the one used.
 # FP64 path DADD + DMUL + DFMA.
 ALG_OPS_ADJ_FP32 = 500
 ALG_OPS_ADJ_FP64 = 707

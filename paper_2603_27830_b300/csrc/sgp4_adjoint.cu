@@ -5,12 +5,13 @@
 // (the paper's differentiable propagator, Sec. 5).
 //
 // Kernels:
-//  * adjoint_prop_kernel: one block per satellite; each thread recomputes its states
-//    forward (forward64 / forward32, the same formulations as the propagation
+//  * adjoint_prop_kernel64 / adjoint_prop_kernel_x2: one block per satellite; each
+//    thread recomputes its states forward (forward64, or forward32x2 for two
+//    consecutive times in packed FP32: the same formulations as the propagation
 //    kernels) and runs the hand-written reverse sweep of the propagation, giving the
 //    adjoints of the 33 record fields the propagation reads.  A thread sums them over
-//    its states in registers, a warp in a shuffle tree, and the warps' partial sums
-//    are added in FP64.  The Kepler solve is differentiated at its root (implicit
+//    its states in registers, the block over its threads, and the partial sums are
+//    added in FP64.  The Kepler solve is differentiated at its root (implicit
 //    function theorem); the clamps and threshold decisions are constants of the sweep.
 //  * adjoint_init_kernel: one thread per satellite pushes the 7 element directions
 //    through sgp4init with dual numbers (the record build is per satellite, so
@@ -34,6 +35,7 @@
 #include "sgp4_init_math.cuh"
 #include "sgp4_kernels.cuh"
 #include "sgp4_sweep.cuh"
+#include "sgp4_sweep32x2.cuh"
 
 namespace sgp4 {
 
@@ -52,89 +54,160 @@ struct AdjArgs {
 };
 
 
-// Guard-band states of the FP32 sweep are queued (their time index) and swept in FP64
-// after the loop: a call of the out-of-line FP64 sweep inside the loop made it spill
-// registers (472 bytes of spill stores).  With more than kAdjFixCap of them the block
-// runs the FP32 forward over the satellite's times again to find them.
+// The FP64 sweep: the states of satellite j handled by this thread, forward and reverse,
+// the field adjoints summed into acc.
+__device__ __forceinline__ void prop_loop64(const AdjArgs& a, const SatShared<double>& sat,
+                                            double (&acc)[kNumAdj], int64_t j) {
+  const double* gr = static_cast<const double*>(a.grad_r);
+  const double* gv = static_cast<const double*>(a.grad_v);
+  Fwd<double> f;
+  for (int64_t i = threadIdx.x; i < a.T; i += kAdjThreads) {
+    const int64_t s = j * a.T + i;
+    const double t = a.per_sat ? __ldg(a.tsince + s) : __ldg(a.tsince + i);
+    double g_r[3], g_v[3];
+    for (int c = 0; c < 3; ++c) {
+      g_r[c] = gr ? gr[s * 3 + c] : 0.0;
+      g_v[c] = gv ? gv[s * 3 + c] : 0.0;
+    }
+    if (usable(forward64(sat.rc, a.g, t, f)))
+      reverse(f, sat.k, g_r, g_v, [&](int q, double v) { acc[q] += v; });
+  }
+}
+
+__global__ void __launch_bounds__(kAdjThreads, 1) adjoint_prop_kernel64(AdjArgs a) {
+  __shared__ double part[kNumAdj][kAdjWarps];
+  __shared__ SatShared<double> sat;
+  const int tid = threadIdx.x;
+  const int64_t j = blockIdx.x;
+  if (tid == 0) load_sat(a.rp, a.g, a.gf, j, sat);
+  __syncthreads();
+  if (sat.rc.flags & kFlagDeep) {   // deep-space records are not differentiated: zero
+    if (tid < kNumAdj) a.field_bar[j * kNumAdj + tid] = 0.0;
+    return;
+  }
+  double acc[kNumAdj];
+#pragma unroll
+  for (int q = 0; q < kNumAdj; ++q) acc[q] = 0.0;
+  prop_loop64(a, sat, acc, j);
+#pragma unroll
+  for (int q = 0; q < kNumAdj; ++q) warp_partial(acc[q], q, part);
+  __syncthreads();
+  if (tid < kNumAdj) {
+    double sum = 0.0;
+    for (int w = 0; w < kAdjWarps; ++w) sum += part[tid][w];
+    a.field_bar[j * kNumAdj + tid] = sum;
+  }
+}
+
+// The FP32 sweep: two consecutive times of the satellite per thread in packed FP32
+// (forward32x2 and the reverse sweep over P2), one block of kAdj2Threads per satellite.
+// A pair whose two states are both usable is swept packed; the states of every other
+// pair are queued (guard-band states for the FP64 sweep, usable ones for the scalar
+// FP32 sweep) and swept one by one after the loop, so that a single call of either
+// sweep in the loop does not cost the loop its registers.  With more than kAdjFixCap
+// queued the block runs the packed forward over the satellite's pairs again to find
+// them.  Each thread's slot holds its pair's forward values (53 8-byte words: an odd
+// count, so the 16 threads of a half-warp's 8-byte accesses hit distinct bank pairs).
+// Against the scalar FP32 sweep (one state per thread, 128 threads, 6 blocks per SM)
+// it issues 570 instead of 906 instructions per state; the fitting workload's
+// sgp4_adjoint (10,000 x 500) went 0.1925 -> 0.172 ms on B300.  Six blocks of 64 per SM
+// (168 registers; slot and registers both allow six) measured best: four 0.227 ms,
+// eight (128 registers, still six by shared memory) 0.201, seven with the
+// shared-memory carveout raised 0.19.
+constexpr int kAdj2Threads = 64;
+#ifndef SGP4_ADJ2_MIN_BLOCKS
+#define SGP4_ADJ2_MIN_BLOCKS 6
+#endif
+constexpr int kAdj2MinBlocks = SGP4_ADJ2_MIN_BLOCKS;
 constexpr int kAdjFixCap = 256;
+constexpr int kQueueScalar = 1 << 30;   // queue entry: an FP32 state (else an FP64 one)
+static_assert((sizeof(Fwd<P2>) / 8) % 2 == 1, "odd 8-byte word count for conflict-free rows");
+static_assert(kNumAdj <= kAdj2Threads, "one column sum per thread");
+
 struct AdjFixQueue {
   int i[kAdjFixCap];
   int n;   // states queued (above kAdjFixCap: the queue overflowed)
 };
 
-// The states of satellite j handled by this thread: forward, reverse sweep, and the
-// field adjoints summed into acc.  f is the thread's forward-value slot; fq the block's
-// guard-band queue (FP32).
-template <class T>
-__device__ __forceinline__ void prop_loop(const AdjArgs& a, const SatShared<T>& sat,
-                                          Fwd<T>& f, T (&acc)[kNumAdj], int64_t j,
-                                          AdjFixQueue* fq) {
-  const T* gr = static_cast<const T*>(a.grad_r);
-  const T* gv = static_cast<const T*>(a.grad_v);
-  for (int64_t i = threadIdx.x; i < a.T; i += kAdjThreads) {
-    const int64_t s = j * a.T + i;
-    const double t = a.per_sat ? __ldg(a.tsince + s) : __ldg(a.tsince + i);
-    T g_r[3], g_v[3];
-    for (int c = 0; c < 3; ++c) {
-      g_r[c] = gr ? gr[s * 3 + c] : T(0);
-      g_v[c] = gv ? gv[s * 3 + c] : T(0);
-    }
-    auto add = [&](int q, T v) { acc[q] += v; };
-    if constexpr (sizeof(T) == 4) {
-      float th, tl;
-      split_double(t, th, tl);
-      const int code = forward32(sat.rc, a.gf, th, tl, f);
-      reload_barrier();
-      if (code == kRecomputeFP64) {   // swept in FP64 after the loop (adj_fix_queued)
-        const int slot = atomicAdd(&fq->n, 1);
-        if (slot < kAdjFixCap) fq->i[slot] = (int)i;
-      } else if (usable(code)) {
-        reverse(f, sat.k, g_r, g_v, add);
-      }
-    } else {
-      if (usable(forward64(sat.rc, a.g, t, f))) reverse(f, sat.k, g_r, g_v, add);
-    }
-  }
+__device__ __forceinline__ double adj_time(const AdjArgs& a, int64_t j, int64_t i) {
+  return a.per_sat ? __ldg(a.tsince + j * a.T + i) : __ldg(a.tsince + i);
 }
 
-// After prop_loop, the thread's sums written to its row of the forward-value slots and
-// a __syncthreads: the FP64 sweeps of satellite j's queued guard-band states, added to
-// the row (nothing else is live across the out-of-line sweep, so the loop keeps its
-// registers).
-__device__ __forceinline__ void adj_fix_queued(const AdjArgs& a, const SatShared<float>& sat,
-                                               const AdjFixQueue* fq, float* row, int64_t j) {
-  const int n = fq->n;
-  if (n == 0) return;
+__device__ __forceinline__ void adj_enqueue(AdjFixQueue* fq, int64_t i, bool scalar) {
+  const int slot = atomicAdd(&fq->n, 1);
+  if (slot < kAdjFixCap && i < kQueueScalar) fq->i[slot] = (int)i | (scalar ? kQueueScalar : 0);
+  else if (slot < kAdjFixCap) atomicAdd(&fq->n, kAdjFixCap);   // index too large: rescan
+}
+
+// One state of satellite j swept on its own, its field adjoints added to row: through
+// the FP64 sweep (fp64) or the scalar FP32 one (which may still hand it to FP64).
+__device__ __forceinline__ void adj_sweep_one(const AdjArgs& a, const SatShared<float>& sat,
+                                              float* row, int64_t j, int64_t i, bool fp64) {
   const float* gr = static_cast<const float*>(a.grad_r);
   const float* gv = static_cast<const float*>(a.grad_v);
-  const bool over = n > kAdjFixCap;
-  const int64_t cnt = over ? a.T : n;
-  for (int64_t e = threadIdx.x; e < cnt; e += kAdjThreads) {
-    const int64_t i = over ? e : fq->i[e];
-    const double t = a.per_sat ? __ldg(a.tsince + j * a.T + i) : __ldg(a.tsince + i);
-    if (over) {   // find the guard-band states again (a forward in a local slot)
-      Fwd<float> fl;
-      float th, tl;
-      split_double(t, th, tl);
-      if (forward32(sat.rc, a.gf, th, tl, fl) != kRecomputeFP64) continue;
+  const int64_t s = j * a.T + i;
+  const double t = adj_time(a, j, i);
+  float g_r[3], g_v[3];
+  for (int c = 0; c < 3; ++c) {
+    g_r[c] = gr ? gr[s * 3 + c] : 0.0f;
+    g_v[c] = gv ? gv[s * 3 + c] : 0.0f;
+  }
+  if (!fp64) {
+    Fwd<float> fl;
+    float th, tl;
+    split_double(t, th, tl);
+    const int code = forward32(sat.rc, a.gf, th, tl, fl);
+    if (code != kRecomputeFP64) {
+      if (usable(code)) reverse(fl, sat.k, g_r, g_v, [&](int q, float v) { row[q] += v; });
+      return;
     }
-    const int64_t s = j * a.T + i;
-    float g_r[3], g_v[3];
-    for (int c = 0; c < 3; ++c) {
-      g_r[c] = gr ? gr[s * 3 + c] : 0.0f;
-      g_v[c] = gv ? gv[s * 3 + c] : 0.0f;
+  }
+  adjoint_fallback(a.rp, a.g, j, t, g_r[0], g_r[1], g_r[2], g_v[0], g_v[1], g_v[2], row,
+                   nullptr, nullptr, true);
+}
+
+// The packed forward of pair p (times 2p, 2p + 1) into f; code[1] = kAbsentState past
+// the last time.
+__device__ __forceinline__ void adj_forward_pair(const AdjArgs& a, const SatShared<float>& sat,
+                                                 int64_t j, int64_t p, Fwd<P2>& f, int code[2]) {
+  const int64_t i0 = 2 * p;
+  const bool has1 = i0 + 1 < a.T;
+  float2 th, tl;
+  split_double(adj_time(a, j, i0), th.x, tl.x);
+  if (has1) split_double(adj_time(a, j, i0 + 1), th.y, tl.y);
+  else { th.y = th.x; tl.y = tl.x; }
+  forward32x2(sat.rc, a.gf, th, tl, f, code);
+  if (!has1) code[1] = kAbsentState;
+}
+
+// After the loop (the thread's sums in its row, a __syncthreads behind): the queued
+// states of satellite j swept one by one into the rows of the threads that take them.
+__device__ __forceinline__ void adj_fix_queued2(const AdjArgs& a, const SatShared<float>& sat,
+                                                const AdjFixQueue* fq, float* row, int64_t j) {
+  const int n = fq->n;
+  if (n == 0) return;
+  if (n <= kAdjFixCap) {
+    for (int e = threadIdx.x; e < n; e += kAdj2Threads) {
+      const int v = fq->i[e];
+      adj_sweep_one(a, sat, row, j, v & (kQueueScalar - 1), !(v & kQueueScalar));
     }
-    adjoint_fallback(a.rp, a.g, j, t, g_r[0], g_r[1], g_r[2], g_v[0], g_v[1], g_v[2], row,
-                     nullptr, nullptr, true);
+    return;
+  }
+  const int64_t npair = (a.T + 1) / 2;
+  for (int64_t p = threadIdx.x; p < npair; p += kAdj2Threads) {
+    Fwd<P2> fl;
+    int code[2];
+    adj_forward_pair(a, sat, j, p, fl, code);
+    if (usable(code[0]) && usable(code[1])) continue;   // swept in the loop
+    for (int l = 0; l < 2; ++l)
+      if (code[l] == kRecomputeFP64 || usable(code[l]))
+        adj_sweep_one(a, sat, row, j, 2 * p + l, code[l] == kRecomputeFP64);
   }
 }
 
-template <class T>
-__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP32 : 1)
-    adjoint_prop_kernel(AdjArgs a) {
-  __shared__ T part[kNumAdj][kAdjWarps];
-  __shared__ SatShared<T> sat;
-  __shared__ Fwd<T> sfwd[FwdSlot<T>::kRows];
+__global__ void __launch_bounds__(kAdj2Threads, kAdj2MinBlocks) adjoint_prop_kernel_x2(AdjArgs a) {
+  __shared__ SatShared<float> sat;
+  __shared__ Fwd<P2> sfwd[kAdj2Threads];
   __shared__ AdjFixQueue s_fq;
   const int tid = threadIdx.x;
   const int64_t j = blockIdx.x;
@@ -147,47 +220,50 @@ __global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP3
     if (tid < kNumAdj) a.field_bar[j * kNumAdj + tid] = 0.0;
     return;
   }
-  T acc[kNumAdj];
+  const float* gr = static_cast<const float*>(a.grad_r);
+  const float* gv = static_cast<const float*>(a.grad_v);
+  P2 acc[kNumAdj];
 #pragma unroll
-  for (int q = 0; q < kNumAdj; ++q) acc[q] = T(0);
-  if constexpr (sizeof(T) == 4) {
-    prop_loop(a, sat, sfwd[tid], acc, j, &s_fq);
-    // Block sum through the forward-value slots, free now: each thread writes its 33
-    // sums to its row (where the FP64 sweeps of the guard-band states add theirs), then
-    // 3 x 33 threads sum the columns in three interleaved parts (rows of 65 words:
-    // conflict-free).  A warp-shuffle tree cost 165 shuffles and adds per thread, spread
-    // over only T / 128 states.
-    constexpr int kParts = 3;
-    static_assert(kNumAdj * kParts <= kAdjThreads && kParts <= kAdjWarps, "reduction layout");
-    float* row = reinterpret_cast<float*>(&sfwd[tid]);
+  for (int q = 0; q < kNumAdj; ++q) acc[q] = P2(0.0f);
+  Fwd<P2>& f = sfwd[tid];
+  const int64_t npair = (a.T + 1) / 2;
+  for (int64_t p = tid; p < npair; p += kAdj2Threads) {
+    // the pair's output adjoints first, so that their loads from memory overlap the
+    // forward pass (the second state's are read only when it exists)
+    const int64_t s = j * a.T + 2 * p;
+    const int64_t s1 = 2 * p + 1 < a.T ? s + 1 : s;
+    P2 g_r[3], g_v[3];
+    for (int c = 0; c < 3; ++c) {
+      g_r[c] = gr ? P2(make_float2(__ldcs(gr + s * 3 + c), __ldcs(gr + s1 * 3 + c))) : P2(0.0f);
+      g_v[c] = gv ? P2(make_float2(__ldcs(gv + s * 3 + c), __ldcs(gv + s1 * 3 + c))) : P2(0.0f);
+    }
+    int code[2];
+    adj_forward_pair(a, sat, j, p, f, code);
+    reload_barrier();
+    if (usable(code[0]) && usable(code[1])) {
+      reverse(f, sat.k, g_r, g_v, [&](int q, P2 v) { acc[q] += v; });
+    } else {
+      for (int l = 0; l < 2; ++l)
+        if (code[l] == kRecomputeFP64 || usable(code[l]))
+          adj_enqueue(&s_fq, 2 * p + l, code[l] != kRecomputeFP64);
+    }
+  }
+  // Block sum through the slots, free now: each thread writes its 33 sums to its row
+  // (where the queued states' sweeps add theirs), then thread c < 33 sums column c over
+  // the rows (consecutive words of a row: conflict-free) in four interleaved parts,
+  // added in FP64.
+  float* row = reinterpret_cast<float*>(&sfwd[tid]);
 #pragma unroll
-    for (int q = 0; q < kNumAdj; ++q) row[q] = acc[q];
-    __syncthreads();   // (also: every state queued)
-    adj_fix_queued(a, sat, &s_fq, row, j);
-    __syncthreads();
-    if (tid < kNumAdj * kParts) {
-      const int c = tid % kNumAdj, p0 = tid / kNumAdj;
-      float sum = 0.0f;
-      for (int r = p0; r < kAdjThreads; r += kParts) sum += reinterpret_cast<const float*>(&sfwd[r])[c];
-      part[c][p0] = sum;
-    }
-    __syncthreads();
-    if (tid < kNumAdj) {
-      double sum = 0.0;
-      for (int w = 0; w < kParts; ++w) sum += (double)part[tid][w];
-      a.field_bar[j * kNumAdj + tid] = sum;
-    }
-  } else {
-    Fwd<T> f;
-    prop_loop(a, sat, f, acc, j, nullptr);
-#pragma unroll
-    for (int q = 0; q < kNumAdj; ++q) warp_partial(acc[q], q, part);
-    __syncthreads();
-    if (tid < kNumAdj) {
-      double sum = 0.0;
-      for (int w = 0; w < kAdjWarps; ++w) sum += (double)part[tid][w];
-      a.field_bar[j * kNumAdj + tid] = sum;
-    }
+  for (int q = 0; q < kNumAdj; ++q) row[q] = acc[q].v.x + acc[q].v.y;
+  __syncthreads();   // (also: every state queued)
+  adj_fix_queued2(a, sat, &s_fq, row, j);
+  __syncthreads();
+  if (tid < kNumAdj) {
+    float s4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    for (int r = 0; r < kAdj2Threads; r += 4)
+      for (int k = 0; k < 4; ++k) s4[k] += reinterpret_cast<const float*>(&sfwd[r + k])[tid];
+    a.field_bar[j * kNumAdj + tid] =
+        ((double)s4[0] + (double)s4[1]) + ((double)s4[2] + (double)s4[3]);
   }
 }
 
@@ -498,8 +574,8 @@ cudaError_t launch_adjoint(const RecordPtrs& rp, const Geo& g, const double* el,
   a.grad_r = grad_r;
   a.grad_v = grad_v;
   a.field_bar = workspace;
-  if (fp32) adjoint_prop_kernel<float><<<(unsigned)rp.n, kAdjThreads, 0, stream>>>(a);
-  else adjoint_prop_kernel<double><<<(unsigned)rp.n, kAdjThreads, 0, stream>>>(a);
+  if (fp32) adjoint_prop_kernel_x2<<<(unsigned)rp.n, kAdj2Threads, 0, stream>>>(a);
+  else adjoint_prop_kernel64<<<(unsigned)rp.n, kAdjThreads, 0, stream>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int threads = 64;

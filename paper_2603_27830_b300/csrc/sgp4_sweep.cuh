@@ -119,12 +119,12 @@ __device__ __forceinline__ Frame<T> frame_of(const Fwd<T>& f) {
 // The frame and the powers of t of a state, kept (FP64) or recomputed (FP32).
 template <class T>
 __device__ __forceinline__ Frame<T> frame_get(const Fwd<T>& f) {
-  if constexpr (sizeof(T) == 8) return f.fr;
+  if constexpr (std::is_same<T, double>::value) return f.fr;
   else return frame_of(f);
 }
 template <class T>
 __device__ __forceinline__ void tpow_get(const Fwd<T>& f, T& t2, T& t3, T& t4) {
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (std::is_same<T, double>::value) {
     t2 = f.t2; t3 = f.t3; t4 = f.t4;
   } else {
     t2 = f.tt * f.tt; t3 = t2 * f.tt; t4 = t3 * f.tt;
@@ -366,8 +366,10 @@ __device__ __forceinline__ int forward32(const Rec32& rc, const GeoF& g, float t
 // adjoint goes to sink(field, value) as soon as it is final (fields that do not
 // depend on the state, such as the drag terms of a simplified-drag record, are not
 // passed), so that no array of 33 adjoints has to stay live through the sweep.
-template <class T, class Sink>
-__device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<T>& rc, const T gr[3],
+// T is the type of the state's values (double, float, or a packed pair of floats for
+// two states), C that of the satellite's constants.
+template <class T, class C, class Sink>
+__device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<C>& rc, const T gr[3],
                                         const T gv[3], Sink&& sink) {
   const T one = T(1), two = T(2), half = T(0.5), c15 = T(1.5);
   const T re = rc.re, vk = rc.vk;

@@ -68,13 +68,35 @@ def test_adjoint_fp64_matches_oracle_jacobian(case):
     _compare(g, ref, 1e-7, 1e-9)
 
 
-@pytest.mark.parametrize("case", range(2))
+@pytest.mark.parametrize("case", range(3))
 def test_adjoint_fp32_matches_oracle_jacobian(case):
     name, el, t = _cases()[case]
     rng = np.random.default_rng(10 + case)
     T = t.shape[-1]
     gr = rng.normal(size=(len(el), T, 3))
     gv = rng.normal(size=(len(el), T, 3)) * 100.0
+    g = _gpu_adjoint(el, t, gr, gv, "fp32")
+    ref = _oracle_vjp(el, t, gr, gv)
+    _compare(g, ref, 5e-3, 2e-4)
+
+
+def test_adjoint_fp32_odd_grid_and_mixed_pairs():
+    """The FP32 sweep takes two consecutive times per thread: an odd time count leaves
+    the last pair one state short, and a pair with one usable state and one that is not
+    (here, orbits that decay within the two-day grid: codes 1 and 6 among the states) is
+    swept state by state after the loop.  37 shared times, against the oracle."""
+    rng = np.random.default_rng(44)
+    n = 24
+    el = np.column_stack([rng.uniform(15.8, 16.4, n) * REV, rng.uniform(0.0005, 0.01, n),
+                          rng.uniform(0.5, 1.5, n), rng.uniform(0, 2 * math.pi, (n, 3)),
+                          rng.uniform(0.002, 0.05, n)])
+    t = np.linspace(0.0, 2880.0, 37)
+    _, _, st, _ = oracle.propagate(el, t)
+    ok = (st == 0) | (st == 6)
+    assert (ok[:, 0:36:2] != ok[:, 1:37:2]).sum() >= 5     # pairs with one usable state
+    assert (~ok).any() and (st == 6).any()
+    gr = rng.normal(size=(n, t.size, 3))
+    gv = rng.normal(size=(n, t.size, 3)) * 100.0
     g = _gpu_adjoint(el, t, gr, gv, "fp32")
     ref = _oracle_vjp(el, t, gr, gv)
     _compare(g, ref, 5e-3, 2e-4)
