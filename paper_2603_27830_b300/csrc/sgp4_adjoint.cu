@@ -168,16 +168,28 @@ __device__ __forceinline__ void adj_sweep_one(const AdjArgs& a, const SatShared<
 
 // The packed forward of pair p (times 2p, 2p + 1) into f; code[1] = kAbsentState past
 // the last time.
+// The times of pair p (the first one twice past the last time).
+__device__ __forceinline__ void adj_pair_times(const AdjArgs& a, int64_t j, int64_t p,
+                                               double& t0, double& t1) {
+  t0 = adj_time(a, j, 2 * p);
+  t1 = 2 * p + 1 < a.T ? adj_time(a, j, 2 * p + 1) : t0;
+}
+
+__device__ __forceinline__ void adj_forward_times(const AdjArgs& a, const SatShared<float>& sat,
+                                                  int64_t p, double t0, double t1, Fwd<P2>& f,
+                                                  int code[2]) {
+  float2 th, tl;
+  split_double(t0, th.x, tl.x);
+  split_double(t1, th.y, tl.y);
+  forward32x2(sat.rc, a.gf, th, tl, f, code);
+  if (2 * p + 1 >= a.T) code[1] = kAbsentState;
+}
+
 __device__ __forceinline__ void adj_forward_pair(const AdjArgs& a, const SatShared<float>& sat,
                                                  int64_t j, int64_t p, Fwd<P2>& f, int code[2]) {
-  const int64_t i0 = 2 * p;
-  const bool has1 = i0 + 1 < a.T;
-  float2 th, tl;
-  split_double(adj_time(a, j, i0), th.x, tl.x);
-  if (has1) split_double(adj_time(a, j, i0 + 1), th.y, tl.y);
-  else { th.y = th.x; tl.y = tl.x; }
-  forward32x2(sat.rc, a.gf, th, tl, f, code);
-  if (!has1) code[1] = kAbsentState;
+  double t0, t1;
+  adj_pair_times(a, j, p, t0, t1);
+  adj_forward_times(a, sat, p, t0, t1, f, code);
 }
 
 // After the loop (the thread's sums in its row, a __syncthreads behind): the queued
@@ -227,7 +239,11 @@ __global__ void __launch_bounds__(kAdj2Threads, kAdj2MinBlocks) adjoint_prop_ker
   for (int q = 0; q < kNumAdj; ++q) acc[q] = P2(0.0f);
   Fwd<P2>& f = sfwd[tid];
   const int64_t npair = (a.T + 1) / 2;
+  double tn0 = 0.0, tn1 = 0.0;   // the times of the thread's next pair, loaded ahead
+  if (tid < npair) adj_pair_times(a, j, tid, tn0, tn1);
   for (int64_t p = tid; p < npair; p += kAdj2Threads) {
+    const double t0 = tn0, t1 = tn1;
+    if (p + kAdj2Threads < npair) adj_pair_times(a, j, p + kAdj2Threads, tn0, tn1);
     // the pair's output adjoints first, so that their loads from memory overlap the
     // forward pass (the second state's are read only when it exists)
     const int64_t s = j * a.T + 2 * p;
@@ -238,7 +254,7 @@ __global__ void __launch_bounds__(kAdj2Threads, kAdj2MinBlocks) adjoint_prop_ker
       g_v[c] = gv ? P2(make_float2(__ldcs(gv + s * 3 + c), __ldcs(gv + s1 * 3 + c))) : P2(0.0f);
     }
     int code[2];
-    adj_forward_pair(a, sat, j, p, f, code);
+    adj_forward_times(a, sat, p, t0, t1, f, code);
     reload_barrier();
     if (usable(code[0]) && usable(code[1])) {
       reverse(f, sat.k, g_r, g_v, [&](int q, P2 v) { acc[q] += v; });
