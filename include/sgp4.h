@@ -360,14 +360,17 @@ sgp4_result sgp4_jacobian(const double* elements, const sgp4_records* records,
  *   tile_states  states per work tile, a positive multiple of 128
  *   other arguments as in sgp4_propagate_batched (no fixup counter)
  * The first call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  All calls on a device
+ * current.  The call cannot be captured into a CUDA graph (its table copy reads a
+ * host array that later calls rewrite): under an active stream capture it returns
+ * SGP4_ERR_ARG and enqueues nothing; graphs use sgp4_batch_graph_*.  All calls on a device
  * share the array: two calls whose work overlaps on the GPU (different streams, or
  * different host threads) race and must be serialised by the caller.  Each call
  * rewrites the table and prefix sums and resets the counter before its launch.
  * Errors: SGP4_ERR_OOM if n_requests exceeds SGP4_STATIC_MAX_REQUESTS; SGP4_ERR_ARG
  * for bad or negative sizes (tsince_len, out_len included), offsets outside records /
  * tsince / outputs, overlapping outputs, a bad precision or tile size, NULL or
- * misaligned arrays; SGP4_ERR_CUDA if the address lookup, the copy or a launch fails.
+ * misaligned arrays, a stream under capture; SGP4_ERR_CUDA if the address lookup, the
+ * capture query, the copy or a launch fails.
  * Calls no allocation routine.
  */
 #define SGP4_STATIC_MAX_REQUESTS 1024

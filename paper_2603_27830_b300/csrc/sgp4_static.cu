@@ -109,6 +109,17 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
   if (!aligned(tsince, 8) || !aligned(r, 16) || !aligned(v, 16) || !aligned(status, 16))
     return SGP4_ERR_ARG;
 
+  // A capture would record the copy from this thread's host table, which a graph
+  // replay would read long after the call returned (and later calls rewrote it); it is
+  // refused before any other CUDA call, so that nothing breaks the caller's capture.
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return SGP4_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return SGP4_ERR_ARG;
+
   // Device address of the scratch array, looked up once per device with that device
   // current (in host code the array's name is not a device address).
   int dev = 0;
@@ -127,7 +138,6 @@ extern "C" sgp4_result sgp4_propagate_batched_static(
     base = g_addr[dev];
   }
   char* scratch = static_cast<char*>(base);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   // Request table into the scratch (the pageable copy is staged before return), then
   // the tile prefix sums on the device.

@@ -169,3 +169,33 @@ def test_no_alloc_entry_page_locked_table_reused_on_return(precision):
     assert code == _lib.SGP4_OK
     torch.cuda.synchronize()
     _compare(out, ref)
+
+
+def test_no_alloc_entry_refuses_stream_capture():
+    """Under an active stream capture the entry point returns SGP4_ERR_ARG and enqueues
+    nothing (its table copy reads a host array that a replay would read too late); the
+    capture itself stays valid, and the same call outside it runs."""
+    import torch
+
+    from paper_2603_27830_b300 import _lib, plan_batch, sgp4_init, sgp4_propagate_batched
+    lib = _lib.load()
+    b = _batch(13, 30)
+    el = torch.as_tensor(b.elements, device="cuda")
+    ts = torch.as_tensor(b.tsince, device="cuda")
+    recs, _ = sgp4_init(el)
+    ref = sgp4_propagate_batched(plan_batch(b.requests, 512), recs, ts, "fp32")
+    out = _fresh_out(ref)
+    dummy = torch.zeros(4, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        rc = _static_call(lib, b, recs, ts, "fp32", out, torch.cuda.current_stream())
+        dummy.add_(1.0)                  # the capture holds some work of its own
+    assert rc == _lib.SGP4_ERR_ARG
+    g.replay()
+    torch.cuda.synchronize()
+    assert float(dummy.sum()) == 4.0     # the capture ended valid and replays
+    assert bool((out[2] == 99).all())    # nothing of the refused call ran
+    assert _static_call(lib, b, recs, ts, "fp32", out, torch.cuda.current_stream()) == _lib.SGP4_OK
+    torch.cuda.synchronize()
+    _compare(out, ref)
