@@ -71,6 +71,11 @@ ALG_OPS_ADJ_FP64 = 707
 # ncu on 2,000 x 500 of the fitting workload.
 ALG_OPS_JAC_FP64 = 3564
 ALG_OPS_FIT_FP64 = 1823
+# The same kernels in FP32 (FADD + FMUL + FFMA thread instructions and the SFU's, ncu on
+# 2,000 x 500): Jacobian FADD 115.3, FMUL 1049.8, FFMA 2345.6, SFU 75.0; fit step FADD
+# 130.5, FMUL 549.8, FFMA 1091.2, SFU 47.8.
+ALG_OPS_JAC_FP32 = 3586
+ALG_OPS_FIT_FP32 = 1819
 # B300's FP64 unit: 2 lanes per SM per clock (one warp instruction per 64 cycles per
 # SM sub-partition; ncu's fp64-pipe utilisation and instruction count give the rate).
 FP64_LANES_PER_SM_CLK = 2
@@ -531,14 +536,15 @@ def run_adjoint(torch, dev, stream, flush, steps, alu_peak, fp64_peak):
                      "jacobian_ms": jac_ms, "jacobian_states_per_s": states / (jac_ms * 1e-3),
                      "jacobian_note": "sgp4_jacobian: r, v, status, 6x7 J and 6x6 J C J^T "
                                       "per state"}
-        if prec == "fp64":
-            for key, ops, ms_ in (("jacobian_roofline", ALG_OPS_JAC_FP64, jac_ms),
-                                  ("fit_step_roofline", ALG_OPS_FIT_FP64, fit_ms)):
-                ach = ops * states / (ms_ * 1e-3) / 1e9
-                res[prec][key] = {"bound": "fp64", "achieved": ach, "peak": peak,
-                                  "unit": "Gop/s", "frac": ach / peak, "ops_per_state": ops,
-                                  "timed": "whole call (its small init and solve kernels "
-                                           "included)"}
+        jac_ops, fit_ops = ((ALG_OPS_JAC_FP64, ALG_OPS_FIT_FP64) if prec == "fp64"
+                            else (ALG_OPS_JAC_FP32, ALG_OPS_FIT_FP32))
+        for key, ops, ms_ in (("jacobian_roofline", jac_ops, jac_ms),
+                              ("fit_step_roofline", fit_ops, fit_ms)):
+            ach = ops * states / (ms_ * 1e-3) / 1e9
+            res[prec][key] = {"bound": unit_kind, "achieved": ach, "peak": peak,
+                              "unit": "Gop/s", "frac": ach / peak, "ops_per_state": ops,
+                              "timed": "whole call (its small init and solve kernels "
+                                       "included)"}
     del g64, r_obs, r_true, recs, truth, cov
     torch.cuda.empty_cache()
     return res
