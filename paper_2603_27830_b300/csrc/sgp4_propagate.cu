@@ -642,13 +642,39 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
 template <typename Out>
 __device__ __forceinline__ void deep_slice(const RecordPtrs& rp, const Geo& g, const Range& rg,
                                            int64_t j0, int64_t j1, int i0, int i1, int* s_sel,
-                                           int* s_n, const DeepPhases* ph) {
+                                           int* s_key, int* s_n, const DeepPhases* ph) {
   if (threadIdx.x == 0) *s_n = 0;
   __syncthreads();
   const int64_t j = j0 + threadIdx.x;
-  if (j < j1 && (__ldg(rp.flags + rg.sat0 + j) & kFlagDeep)) s_sel[atomicAdd(s_n, 1)] = threadIdx.x;
+  if (j < j1) {
+    const int64_t rec = rg.sat0 + j;
+    const int fl = __ldg(rp.flags + rec);
+    if (fl & kFlagDeep) {
+      // The branches of the deep-space state follow the record's class: the resonance
+      // (none, one or two revolutions per day), the Lyddane form of the periodics (the
+      // epoch inclination below 0.2 rad stands in for the perturbed one) and the
+      // Newton step count (from e0).  B300's FP64 unit charges a warp instruction
+      // whatever the number of its active lanes, so the block orders its satellites by
+      // that class (then by index), and its warps take mostly uniform branches.
+      const int rez = (fl & kFlagRez1) ? 1 : (fl & kFlagRez2) ? 2 : 0;
+      const float inc = (float)__ldg(rp.f64 + kI0 * rp.stride + rec);
+      const float e0 = (float)__ldg(rp.f64 + kE0 * rp.stride + rec);
+      const float e2 = e0 * e0;
+      const int eb = (e2 > 1.5876e-10f) + (e2 > 9.3e-5f) + (e2 > 0.01664f) + (e2 > 0.1347f) +
+                     (e2 > 0.25f);
+      const int key = ((rez * 2 + (inc < 0.2f ? 1 : 0)) * 8 + eb) * 256 + threadIdx.x;
+      s_key[atomicAdd(s_n, 1)] = key;
+    }
+  }
   __syncthreads();
   const int nd = *s_n;
+  if (threadIdx.x < nd) {   // rank of this entry among the block's keys (all distinct)
+    const int mine = s_key[threadIdx.x];
+    int rank = 0;
+    for (int q = 0; q < nd; ++q) rank += s_key[q] < mine;
+    s_sel[rank] = mine & 255;
+  }
+  __syncthreads();
   const int64_t T = rg.T;
   const int nt = i1 - i0;
   const Out q = (Out)__longlong_as_double(0x7ff8000000000000LL);
@@ -690,6 +716,7 @@ __device__ __forceinline__ void deep_slice(const RecordPtrs& rp, const Geo& g, c
 template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int chunks) {
   __shared__ int s_sel[kThreads];
+  __shared__ int s_key[kThreads];
   __shared__ int s_n;
   __shared__ DeepPhases s_ph;
   asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -728,7 +755,8 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int c
     const int64_t j0 = w / chunks * kThreads;
     const int i0 = (int)(w % chunks) * per;
     deep_slice<std::conditional_t<kFP32, float, double>>(
-        a.rp, a.g, rg, j0, min(n, j0 + kThreads), i0, min(T, i0 + per), s_sel, &s_n, &s_ph);
+        a.rp, a.g, rg, j0, min(n, j0 + kThreads), i0, min(T, i0 + per), s_sel, s_key, &s_n,
+        &s_ph);
   }
 }
 
@@ -736,6 +764,7 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int c
 template <bool kFP32>
 __global__ void __launch_bounds__(kThreads, 4) deep_fix_batched_kernel(BatchArgs a) {
   __shared__ int s_sel[kThreads];
+  __shared__ int s_key[kThreads];
   __shared__ int s_n;
   __shared__ DeepPhases s_ph;
   if (threadIdx.x < 8) deep_phase(threadIdx.x, s_ph);   // visible after deep_slice's barrier
@@ -757,7 +786,7 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_batched_kernel(BatchArgs
     for (int64_t j0 = (int64_t)blockIdx.x * kThreads; j0 < q.n;
          j0 += (int64_t)gridDim.x * kThreads)
       deep_slice<Out>(a.rp, a.g, rg, j0, min(q.n, j0 + kThreads), 0, (int)q.t_count, s_sel,
-                      &s_n, &s_ph);
+                      s_key, &s_n, &s_ph);
   }
 }
 
@@ -898,18 +927,22 @@ namespace {
 
 // The deep-space states of a single-problem call, before its propagation launch and as
 // a programmatic dependent: work items of kThreads satellites x a part of the grid
-// (parts of at least 32 times, as many as give four items per SM), at most four blocks
-// per SM.  Launched before the propagation rather than after it: on the Starlink-shaped
+// (parts of at least 32 times, as many as give SGP4_DEEP_ITEMS_PER_SM items per SM),
+// at most four blocks per SM, each taking items round-robin.  Launched before the propagation rather than after it: on the Starlink-shaped
 // record build + propagation step it then costs 0-2 us instead of 8 (A/B on one box;
 // after it, the pass's blocks waited for the whole propagation grid, and the step lost
 // the overlap of the record build with the propagation's launch).
+#ifndef SGP4_DEEP_ITEMS_PER_SM
+#define SGP4_DEEP_ITEMS_PER_SM 16
+#endif
 template <bool kFP32>
 cudaError_t launch_deep_fix(const PropArgs& a, cudaStream_t stream) {
   const int64_t slices = (a.rp.n + kThreads - 1) / kThreads;
-  const int64_t want = 4 * (int64_t)device_sm_count();
+  const int64_t sms = device_sm_count();
+  const int64_t want = SGP4_DEEP_ITEMS_PER_SM * sms;
   const int chunks = (int)std::max<int64_t>(
       1, std::min<int64_t>((a.t_count + 31) / 32, (want + slices - 1) / slices));
-  const int64_t blocks = std::min<int64_t>(slices * chunks, want);
+  const int64_t blocks = std::min<int64_t>(slices * chunks, 4 * sms);
 #if SGP4_PDL
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
