@@ -106,14 +106,13 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_prop_kernel64(AdjArgs 
 // FP32 sweep) and swept one by one after the loop, so that a single call of either
 // sweep in the loop does not cost the loop its registers.  With more than kAdjFixCap
 // queued the block runs the packed forward over the satellite's pairs again to find
-// them.  Each thread's slot holds its pair's forward values (53 8-byte words: an odd
+// them.  Each thread's slot holds its pair's forward values (49 8-byte words: an odd
 // count, so the 16 threads of a half-warp's 8-byte accesses hit distinct bank pairs).
 // Against the scalar FP32 sweep (one state per thread, 128 threads, 6 blocks per SM)
 // it issues 570 instead of 906 instructions per state; the fitting workload's
-// sgp4_adjoint (10,000 x 500) went 0.1925 -> 0.172 ms on B300.  Six blocks of 64 per SM
-// (168 registers; slot and registers both allow six) measured best: four 0.227 ms,
-// eight (128 registers, still six by shared memory) 0.201, seven with the
-// shared-memory carveout raised 0.19.
+// sgp4_adjoint (10,000 x 500) went 0.1925 -> 0.170 ms on B300.  Six blocks of 64 per SM
+// (168 registers) measured best: four 0.227 ms; eight, with the slot cut to 49 words so
+// that eight fit in shared memory, 0.186 (128 registers, their spills in the loop).
 constexpr int kAdj2Threads = 64;
 #ifndef SGP4_ADJ2_MIN_BLOCKS
 #define SGP4_ADJ2_MIN_BLOCKS 6

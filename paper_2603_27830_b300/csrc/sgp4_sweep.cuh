@@ -69,6 +69,18 @@ struct Fwd : FwdKeep<T> {
 };
 static_assert(sizeof(Fwd<float>) % 8 == 4, "odd word count for conflict-free rows");
 
+// Forward values the reverse sweep reads through these accessors: kept in the slot by
+// the scalar sweeps, recomputed from other slot values by the packed one (whose slot
+// leaves them out).
+template <class T>
+__device__ __forceinline__ T fwd_om(const Fwd<T>& f) { return f.om; }
+template <class T>
+__device__ __forceinline__ T fwd_opb(const Fwd<T>& f) { return f.opb; }
+template <class T>
+__device__ __forceinline__ T fwd_ecosE(const Fwd<T>& f) { return f.ecosE; }
+template <class T, class K>
+__device__ __forceinline__ T fwd_c(const Fwd<T>& f, const K&) { return f.c; }
+
 // Per-satellite constants of the reverse sweep.
 template <class T>
 struct RevC {
@@ -444,7 +456,7 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<C>& rc, cons
   T aynb = -Asb + Acb * f.w;
   T axnb = -Asb * f.w - Acb;
   const T wb = -Asb * f.axn + Acb * f.ayn;
-  const T irl = inv_pos(f.rl), iopb = inv_pos(f.opb);
+  const T irl = inv_pos(f.rl), iopb = inv_pos(fwd_opb(f));
   T ab = aorb * irl;
   rlb += -aorb * f.aor * irl;
   T esinEb = wb * iopb;
@@ -456,7 +468,7 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<C>& rc, cons
   const T sqab = rdotkb * f.esinE * irl;
   esinEb += rdotkb * f.sqa * irl;
   rlb += -rdotkb * f.rdotl * irl;
-  ab += rlb * (one - f.ecosE);
+  ab += rlb * (one - fwd_ecosE(f));
   const T ecosEb = -rlb * f.a;
   ab += pLb * (one - f.eL2);
   eL2b += -pLb * f.a;
@@ -487,7 +499,7 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<C>& rc, cons
   sink(aAycof, aynb * f.q);
   // q = 1 / (a (1 - e^2))
   const T qab = -qb * f.q * f.q;
-  ab += qab * f.om;
+  ab += qab * fwd_om(f);
   eb += -two * f.e * (qab * f.a);
   // a_xN = e cos argp
   eb += axnb * f.cw;
@@ -520,8 +532,9 @@ __device__ __forceinline__ void reverse(const Fwd<T>& f, const RevC<C>& rc, cons
     const T mm1b = mm2b + sMMb * f.cMM;
     mdfb = mm1b;
     const T ddb = mm1b - argp1b;
-    sink(aMCf, ddb * (f.c * f.c * f.c - rc.delm0));
-    const T cb = ddb * rc.mcf * T(3) * f.c * f.c;
+    const T c = fwd_c(f, rc);
+    sink(aMCf, ddb * (c * c * c - rc.delm0));
+    const T cb = ddb * rc.mcf * T(3) * c * c;
     sink(aDelM0, -ddb * rc.mcf);
     sink(aEta, cb * f.cMdf);
     mdfb += -(cb * rc.eta) * f.sMdf;

@@ -59,6 +59,28 @@ __device__ __forceinline__ P2 operator-(P2 a) { return P2(0.0f) - a; }
 __device__ __forceinline__ P2& operator+=(P2& a, P2 b) { return a = a + b; }
 __device__ __forceinline__ P2 inv_pos(P2 x) { return P2(x2::rcp_pos(x.v)); }
 
+// The packed sweep's slot: the forward values of Fwd, less four that its reverse sweep
+// recomputes (1 - e^2, 1 + beta_L, 1 + eta cos M_DF and e_L cos E), so that the slot is
+// 49 8-byte words (an odd count: conflict-free rows) and eight 64-thread blocks' slots
+// fit in an SM's shared memory.
+template <>
+struct Fwd<P2> {
+  P2 tt;
+  P2 sMdf, cMdf, sMM, cMM;
+  P2 tempa, templ, a, sqa, n, e, q, sw, cw, axn, ayn;
+  P2 keep_e;
+  P2 sp, cp, esinE, eL2, pL, rl, rdotl, sqp, rfdotl, betal, w, aor, As, Ac;
+  P2 sinu, cosu, sin2u, cos2u, k, kp, fac, rk, nk, rdotk, rfdotk;
+  P2 su, cu, sO, cO, si, ci;
+  P2 pad;
+};
+__device__ __forceinline__ P2 fwd_om(const Fwd<P2>& f) { return P2(1.0f) - f.e * f.e; }
+__device__ __forceinline__ P2 fwd_opb(const Fwd<P2>& f) { return P2(1.0f) + f.betal; }
+__device__ __forceinline__ P2 fwd_ecosE(const Fwd<P2>& f) { return f.axn * f.cp + f.ayn * f.sp; }
+__device__ __forceinline__ P2 fwd_c(const Fwd<P2>& f, const RevC<float>& rc) {
+  return P2(1.0f) + rc.eta * f.cMdf;
+}
+
 // Per-state status of a packed forward pass where the second time is absent (an odd
 // number of times): neither swept nor queued.
 constexpr int kAbsentState = -2;
@@ -99,7 +121,6 @@ __device__ __forceinline__ void forward32x2(const Rec32& rc, const GeoF& g, floa
     f.sMdf = P2(s);
     f.cMdf = P2(c);
     const F2 cc = fma(S(rc.eta), c, S(1.0f));
-    f.c = P2(cc);
     dd = fma(S(rc.mcf), sub(mul(mul(cc, cc), cc), S(rc.delm0)), mul(S(rc.argpcf), t));
     sincos_sfu(add(mdf, dd), s, c);
     f.sMM = P2(s);
@@ -156,7 +177,6 @@ __device__ __forceinline__ void forward32x2(const Rec32& rc, const GeoF& g, floa
   const F2 q = rcp_pos(mul(a, om));
   const F2 ayn = fma(e, sw, mul(q, S(rc.aycof)));
   f.axn = P2(axn);
-  f.om = P2(om);
   f.q = P2(q);
   f.ayn = P2(ayn);
   const F2 lpt = mul(mul(q, S(rc.xlcof)), axn);
@@ -187,7 +207,6 @@ __device__ __forceinline__ void forward32x2(const Rec32& rc, const GeoF& g, floa
   // Short-period preliminaries.
   const F2 ecosE = fma(axn, cp, mul(ayn, sp));
   const F2 esinE = fma(axn, sp, mul(nayn, cp));
-  f.ecosE = P2(ecosE);
   f.esinE = P2(esinE);
   const F2 omel = sub(S(1.0f), eL2);
   const F2 pL = mul(a, omel);
@@ -206,7 +225,6 @@ __device__ __forceinline__ void forward32x2(const Rec32& rc, const GeoF& g, floa
   const F2 betal = mul(omel, rsqrt(omel));
   f.betal = P2(betal);
   const F2 opb = add(S(1.0f), betal);
-  f.opb = P2(opb);
   const F2 w = mul(esinE, rcp_pos(opb));
   f.w = P2(w);
   const F2 aor = mul(a, invr);
