@@ -132,10 +132,16 @@ __device__ __forceinline__ double adj_time(const AdjArgs& a, int64_t j, int64_t 
   return a.per_sat ? __ldg(a.tsince + j * a.T + i) : __ldg(a.tsince + i);
 }
 
+// Past the capacity (or for an index the entry cannot hold) the block rescans its pairs
+// after the loop anyway, so the count stops there: it stays within kAdjFixCap plus the
+// block's threads, however many states a satellite has.
 __device__ __forceinline__ void adj_enqueue(AdjFixQueue* fq, int64_t i, bool scalar) {
+  if (i >= kQueueScalar || *reinterpret_cast<volatile int*>(&fq->n) > kAdjFixCap) {
+    atomicMax(&fq->n, kAdjFixCap + 1);
+    return;
+  }
   const int slot = atomicAdd(&fq->n, 1);
-  if (slot < kAdjFixCap && i < kQueueScalar) fq->i[slot] = (int)i | (scalar ? kQueueScalar : 0);
-  else if (slot < kAdjFixCap) atomicAdd(&fq->n, kAdjFixCap);   // index too large: rescan
+  if (slot < kAdjFixCap) fq->i[slot] = (int)i | (scalar ? kQueueScalar : 0);
 }
 
 // One state of satellite j swept on its own, its field adjoints added to row: through
