@@ -728,6 +728,7 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int c
     const int64_t n = a.rp.n;
     const int64_t items = (n + kThreads - 1) / kThreads * chunks;
     bool any = false;
+#pragma unroll 8
     for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
       const int64_t j = w / chunks * kThreads + threadIdx.x;
       any |= j < n && (__ldg(a.rp.flags + j) & kFlagDeep);
@@ -846,6 +847,14 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
   const int64_t blocks = (total + chunk - 1) / chunk;
 #if SGP4_PDL
+  // A programmatic dependent's blocks are placed as the previous kernel's blocks leave
+  // their SMs, so a grid of less than one wave can land several blocks on the first SMs
+  // to free up (an FP64 call of 1e4 states: 33 us instead of 21).  Such grids launch
+  // after the previous kernel has ended; grids of nine tenths of a wave or more (the
+  // chunking leaves a wave-capped grid a few blocks short) and single blocks keep the
+  // overlap.
+  const int64_t wave = (int64_t)device_sm_count() * bps;
+  const bool pdl = blocks * 10 >= wave * 9 || blocks == 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kThreads);
@@ -853,7 +862,7 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>, a, chunk);
@@ -935,6 +944,9 @@ namespace {
 #ifndef SGP4_DEEP_ITEMS_PER_SM
 #define SGP4_DEEP_ITEMS_PER_SM 16
 #endif
+#ifndef SGP4_DEEP_BLOCKS_PER_SM
+#define SGP4_DEEP_BLOCKS_PER_SM 4
+#endif
 template <bool kFP32>
 cudaError_t launch_deep_fix(const PropArgs& a, cudaStream_t stream) {
   const int64_t slices = (a.rp.n + kThreads - 1) / kThreads;
@@ -942,7 +954,7 @@ cudaError_t launch_deep_fix(const PropArgs& a, cudaStream_t stream) {
   const int64_t want = SGP4_DEEP_ITEMS_PER_SM * sms;
   const int chunks = (int)std::max<int64_t>(
       1, std::min<int64_t>((a.t_count + 31) / 32, (want + slices - 1) / slices));
-  const int64_t blocks = std::min<int64_t>(slices * chunks, 4 * sms);
+  const int64_t blocks = std::min<int64_t>(slices * chunks, SGP4_DEEP_BLOCKS_PER_SM * sms);
 #if SGP4_PDL
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
