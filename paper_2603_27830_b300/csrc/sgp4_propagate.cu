@@ -849,12 +849,13 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
 #if SGP4_PDL
   // A programmatic dependent's blocks are placed as the previous kernel's blocks leave
   // their SMs, so a grid of less than one wave can land several blocks on the first SMs
-  // to free up (an FP64 call of 1e4 states: 33 us instead of 21).  Such grids launch
-  // after the previous kernel has ended; grids of nine tenths of a wave or more (the
-  // chunking leaves a wave-capped grid a few blocks short) and single blocks keep the
-  // overlap.
+  // to free up.  For the FP64 kernel, bound by each SM's small FP64 unit, that cost an
+  // FP64 call of 1e4 states 33 us instead of 21: its grids under nine tenths of a wave
+  // (the chunking leaves a wave-capped grid a few blocks short) launch after the previous
+  // kernel has ended.  The FP32 kernel keeps the overlap at every size (without it small
+  // calls took 1-2 us longer).
   const int64_t wave = (int64_t)device_sm_count() * bps;
-  const bool pdl = blocks * 10 >= wave * 9 || blocks == 1;
+  const bool pdl = kFP32 || blocks * 10 >= wave * 9 || blocks == 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(kThreads);
