@@ -282,8 +282,9 @@ def _errors(r_dev, v_dev, st_dev, rows, rr, vr, sr):
 # lane operations each; scalar FADD / FMUL / FFMA and XU from the per-pipe counters):
 # near-earth 221, catalogue (100,000 x 100 of the same draw) 229, fitting workload 219
 # lane operations per state on the current kernel.  FP64: DADD + DMUL + DFMA of the
-# FP64 kernel.  Deep space: the FP64 DADD + DMUL + DFMA of deep_fix_kernel, which
-# computes every deep-space state in both precisions (2,000 x 1,000 of the same draw:
+# FP64 kernel.  Deep space: the FP64 DADD + DMUL + DFMA of the deep-space pass (the
+# propagation launch's last blocks), which computes every deep-space state in both
+# precisions (2,000 x 1,000 of the same draw:
 # 93.3 M + 427.1 M + 780.7 M thread instructions for 2e6 states = 651 per state; with
 # the comparisons, conversions and roundings the FP64 pipe issues 1,069 per state and
 # is 86% busy).
@@ -742,8 +743,9 @@ def run_ours(args):
     roofline = {"bound": "alu", "achieved": achieved_gops, "peak": alu_peak, "unit": "Gop/s",
                 "frac": achieved_gops / alu_peak, "traffic": TRAFFIC_FP32_BYTES,
                 "kernel": "propagate_kernel<fp32>", "kernel_ms": kern_ms,
-                "timed": "the sgp4_propagate call: the deep-space pass (no deep-space records "
-                         "here: it reads their flags) and propagate_kernel<fp32> after it",
+                "timed": "the sgp4_propagate call: one launch of propagate_kernel<fp32>, whose "
+                         "last blocks are the deep-space pass (no deep-space records here: "
+                         "they read their flags)",
                 "ops_per_state": ALG_OPS_FP32,
                 "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x {sm_mhz:.0f} MHz",
                 "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -834,8 +836,9 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            # per step: the record build, the FP32 propagation and the deep-space pass
-            "gpu_launches": 3 * args.steps,
+            # per step: the record build and the FP32 propagation (whose launch also
+            # carries the deep-space pass)
+            "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -122,7 +122,7 @@ struct UnitMap {
 // After the FP32 loop over units [ubeg, uend) of range rg and a __syncthreads: the
 // queued guard-band states in FP64, their r, v (NaN for codes 1, 2, 4) and status.
 // States of deep-space records are not queued (their FP32 row's a0'' NaN makes every one
-// a guard-band state, which the loops drop): deep_fix_kernel computes them, which keeps
+// a guard-band state, which the loops drop): deep_pass_block computes them, which keeps
 // the deep-space code and the call it needs out of the FP32 kernels (with it the
 // headline kernel spilled).  The check below only serves a rescan.
 // Adds the block's count to nfix (thread 0).  Inlined, FP64 state included: a kernel
@@ -147,7 +147,7 @@ __device__ __forceinline__ void fix_queued(const RecordPtrs& rp, const Geo& g, c
     } else {
       t = __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
     }
-    // deep-space states are deep_fix_kernel's
+    // deep-space states are the deep-space pass's
     if (__ldg(rp.flags + rec) & kFlagDeep) return;
     float* gr = static_cast<float*>(rg.r) + idx * 3;
     float* gv = static_cast<float*>(rg.v) + idx * 3;
@@ -470,7 +470,7 @@ __device__ __forceinline__ void run_units64(const RecordPtrs& rp, const Geo& g, 
       } else {
         t = __ldg(rg.per_sat ? rg.tsince + j * T + i : rg.tsince + i);
       }
-      if (rc.flags & kFlagDeep) continue;   // deep_fix_kernel's
+      if (rc.flags & kFlagDeep) continue;   // the deep-space pass's
       double r[3], v[3];
       const int code = state64(rc, g, t, r, v);
       const bool bad = code != 0 && code != 6;
@@ -502,9 +502,18 @@ constexpr int kSplitMaxT = 6144;
 // four-state units with times read per state, prefetched (run_range_x4); kJd: FP32 with
 // the split table of absolute times (each unit subtracts its record's epoch).  Separate
 // instantiations keep each path free of the others' code.
+template <typename Out>
+static __device__ __noinline__ void deep_pass_block(const PropArgs a, int chunks, int64_t bid,
+                                                    int64_t nblocks);
+
+// The last `deep_blocks` blocks run the deep-space pass (deep_pass_block, work items of
+// `deep_chunks` parts of the grid); the others propagate `chunk` units each.  Last, so
+// that the propagation's blocks are the ones resident while the record build that this
+// launch depends on runs (first, the pass's blocks held the SMs then: 2 us more on the
+// Starlink-shaped step).
 template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false, bool kCons = false>
 __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_MIN_BLOCKS_FP64)
-    propagate_kernel(PropArgs a, int64_t chunk) {
+    propagate_kernel(PropArgs a, int64_t chunk, int deep_blocks, int deep_chunks) {
   // FP32: [t_count] split times when use_split, then the guard-band queue
   extern __shared__ __align__(16) float2 s_split[];
   __shared__ FixQueue s_fq;
@@ -514,6 +523,12 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   // their first global access, until it has completed and its writes are visible.
   asm volatile("griddepcontrol.wait;" ::: "memory");
 #endif
+  const int64_t prop_blocks = (int64_t)gridDim.x - deep_blocks;
+  if ((int64_t)blockIdx.x >= prop_blocks) {
+    deep_pass_block<std::conditional_t<kFP32, float, double>>(
+        a, deep_chunks, (int64_t)blockIdx.x - prop_blocks, deep_blocks);
+    return;
+  }
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   const int64_t beg = (int64_t)blockIdx.x * chunk;
   const int64_t end = min(total, beg + chunk);
@@ -709,19 +724,18 @@ __device__ __forceinline__ void deep_slice(const RecordPtrs& rp, const Geo& g, c
   __syncthreads();
 }
 
-// The deep-space states of a single-problem call, in FP64, launched before the
-// propagation kernel (which leaves those states untouched) as the record build's
-// programmatic dependent, the propagation being its own.  Without deep-space records
-// its blocks read their satellites' flags and exit.
-template <bool kFP32>
-__global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int chunks) {
+// The deep-space states of a single-problem call, in FP64, by the last `nblocks` blocks
+// of its propagation launch (block `bid` of them; the other blocks propagate and leave
+// deep-space states untouched).  Out of line: one copy for every instantiation of the
+// propagation kernel, and none of its registers in the propagation's loops.  Without
+// deep-space records the blocks read their satellites' flags and leave.
+template <typename Out>
+static __device__ __noinline__ void deep_pass_block(const PropArgs a, int chunks, int64_t bid,
+                                                    int64_t nblocks) {
   __shared__ int s_sel[kThreads];
   __shared__ int s_key[kThreads];
   __shared__ int s_n;
   __shared__ DeepPhases s_ph;
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  // the propagation launched after this pass as its dependent may be scheduled now
-  asm volatile("griddepcontrol.launch_dependents;");
   // Most record sets hold no deep-space record: each thread looks at its satellite of
   // every item of this block first, and the block leaves if none is one.
   {
@@ -729,7 +743,7 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int c
     const int64_t items = (n + kThreads - 1) / kThreads * chunks;
     bool any = false;
 #pragma unroll 8
-    for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+    for (int64_t w = bid; w < items; w += nblocks) {
       const int64_t j = w / chunks * kThreads + threadIdx.x;
       any |= j < n && (__ldg(a.rp.flags + j) & kFlagDeep);
     }
@@ -752,12 +766,11 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_kernel(PropArgs a, int c
   const int T = (int)a.t_count;
   const int per = (T + chunks - 1) / chunks;
   const int64_t items = (n + kThreads - 1) / kThreads * chunks;
-  for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+  for (int64_t w = bid; w < items; w += nblocks) {
     const int64_t j0 = w / chunks * kThreads;
     const int i0 = (int)(w % chunks) * per;
-    deep_slice<std::conditional_t<kFP32, float, double>>(
-        a.rp, a.g, rg, j0, min(n, j0 + kThreads), i0, min(T, i0 + per), s_sel, s_key, &s_n,
-        &s_ph);
+    deep_slice<Out>(a.rp, a.g, rg, j0, min(n, j0 + kThreads), i0, min(T, i0 + per), s_sel,
+                    s_key, &s_n, &s_ph);
   }
 }
 
@@ -827,6 +840,28 @@ cudaError_t device_bps(std::atomic<int> (&cache)[kMaxDevices], K kernel, size_t 
   return cudaSuccess;
 }
 
+// The deep-space pass's share of a single-problem launch: work items of kThreads
+// satellites x a part of the grid (parts of at least 32 times, as many as give
+// SGP4_DEEP_ITEMS_PER_SM items per SM), taken round-robin by the launch's first blocks,
+// SGP4_DEEP_BLOCKS_PER_SM per SM.  Measured on the 10,000 x 1,000 deep-space workload:
+// 16 items per SM 19.0 ms, 4 items 22.4 (the last wave's items ran alone), 32 or 64
+// items 19.9; one block per SM 22.2.  The pass runs in the propagation's own launch (its
+// last blocks) rather than in a launch of its own, which cost every call about 2 us.
+#ifndef SGP4_DEEP_ITEMS_PER_SM
+#define SGP4_DEEP_ITEMS_PER_SM 16
+#endif
+#ifndef SGP4_DEEP_BLOCKS_PER_SM
+#define SGP4_DEEP_BLOCKS_PER_SM 4
+#endif
+void deep_share(const PropArgs& a, int per_sm, int* chunks, int* blocks) {
+  const int64_t slices = (a.rp.n + kThreads - 1) / kThreads;
+  const int64_t sms = device_sm_count();
+  const int64_t want = SGP4_DEEP_ITEMS_PER_SM * sms;
+  *chunks = (int)std::max<int64_t>(
+      1, std::min<int64_t>((a.t_count + 31) / 32, (want + slices - 1) / slices));
+  *blocks = (int)std::min<int64_t>(slices * *chunks, per_sm * sms);
+}
+
 template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false, bool kCons = false>
 cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
@@ -846,18 +881,24 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
   const int64_t chunk = ((tiles + grid - 1) / grid) * kThreads;
   const int64_t blocks = (total + chunk - 1) / chunk;
+  // The deep-space blocks: with an FP64 grid under nine tenths of a wave one per SM, so
+  // that they are resident beside the propagation's blocks (in a launch of their own
+  // before the propagation, the propagation's blocks were placed as theirs left and
+  // piled onto the first SMs to free up; the FP64 kernel is bound by each SM's FP64
+  // unit: 1e5 states 124 us instead of 96).
+  const int64_t wave = (int64_t)device_sm_count() * bps;
+  const bool full = blocks * 10 >= wave * 9;
+  int deep_chunks = 1, deep_blocks = 0;
+  deep_share(a, kFP32 || full ? SGP4_DEEP_BLOCKS_PER_SM : 1, &deep_chunks, &deep_blocks);
 #if SGP4_PDL
   // A programmatic dependent's blocks are placed as the previous kernel's blocks leave
   // their SMs, so a grid of less than one wave can land several blocks on the first SMs
-  // to free up.  For the FP64 kernel, bound by each SM's small FP64 unit, that cost an
-  // FP64 call of 1e4 states 33 us instead of 21: its grids under nine tenths of a wave
-  // (the chunking leaves a wave-capped grid a few blocks short) launch after the previous
-  // kernel has ended.  The FP32 kernel keeps the overlap at every size (without it small
-  // calls took 1-2 us longer).
-  const int64_t wave = (int64_t)device_sm_count() * bps;
-  const bool pdl = kFP32 || blocks * 10 >= wave * 9 || blocks == 1;
+  // to free up; FP64 grids under nine tenths of a wave (the chunking leaves a wave-capped
+  // grid a few blocks short) launch after the previous kernel has ended.  The FP32 kernel
+  // keeps the overlap at every size (without it small calls took 1-2 us longer).
+  const bool pdl = kFP32 || full || blocks == 1;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.gridDim = dim3((unsigned)(blocks + deep_blocks));
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = dyn;
   cfg.stream = stream;
@@ -866,10 +907,12 @@ cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>, a, chunk);
+  return cudaLaunchKernelEx(&cfg, propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>, a, chunk,
+                            deep_blocks, deep_chunks);
 #else
   propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>
-      <<<(unsigned)blocks, kThreads, dyn, stream>>>(a, chunk);
+      <<<(unsigned)(blocks + deep_blocks), kThreads, dyn, stream>>>(a, chunk, deep_blocks,
+                                                                   deep_chunks);
   return cudaGetLastError();
 #endif
 }
@@ -933,59 +976,14 @@ int device_sm_count() {
   return sms > 0 ? sms : 1;
 }
 
-namespace {
-
-// The deep-space states of a single-problem call, before its propagation launch and as
-// a programmatic dependent: work items of kThreads satellites x a part of the grid
-// (parts of at least 32 times, as many as give SGP4_DEEP_ITEMS_PER_SM items per SM),
-// at most four blocks per SM, each taking items round-robin.  Launched before the propagation rather than after it: on the Starlink-shaped
-// record build + propagation step it then costs 0-2 us instead of 8 (A/B on one box;
-// after it, the pass's blocks waited for the whole propagation grid, and the step lost
-// the overlap of the record build with the propagation's launch).
-#ifndef SGP4_DEEP_ITEMS_PER_SM
-#define SGP4_DEEP_ITEMS_PER_SM 16
-#endif
-#ifndef SGP4_DEEP_BLOCKS_PER_SM
-#define SGP4_DEEP_BLOCKS_PER_SM 4
-#endif
-template <bool kFP32>
-cudaError_t launch_deep_fix(const PropArgs& a, cudaStream_t stream) {
-  const int64_t slices = (a.rp.n + kThreads - 1) / kThreads;
-  const int64_t sms = device_sm_count();
-  const int64_t want = SGP4_DEEP_ITEMS_PER_SM * sms;
-  const int chunks = (int)std::max<int64_t>(
-      1, std::min<int64_t>((a.t_count + 31) / 32, (want + slices - 1) / slices));
-  const int64_t blocks = std::min<int64_t>(slices * chunks, SGP4_DEEP_BLOCKS_PER_SM * sms);
-#if SGP4_PDL
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)blocks);
-  cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = 0;
-  cfg.stream = stream;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, deep_fix_kernel<kFP32>, a, chunks);
-#else
-  deep_fix_kernel<kFP32><<<(unsigned)blocks, kThreads, 0, stream>>>(a, chunks);
-  return cudaGetLastError();
-#endif
-}
-
-}  // namespace
-
 cudaError_t launch_propagate64(const PropArgs& a, cudaStream_t stream) {
   if (a.rp.n == 0 || a.t_count == 0) return cudaSuccess;
-  const cudaError_t e = launch_deep_fix<false>(a, stream);
-  return e != cudaSuccess ? e : launch_fp64(a, stream);
+  return launch_fp64(a, stream);
 }
 
 cudaError_t launch_propagate32(const PropArgs& a, cudaStream_t stream) {
   if (a.rp.n == 0 || a.t_count == 0) return cudaSuccess;
-  const cudaError_t e = launch_deep_fix<true>(a, stream);
-  return e != cudaSuccess ? e : launch_fp32(a, stream);
+  return launch_fp32(a, stream);
 }
 
 int64_t batched_grid(bool fp32, int64_t total_tiles, int grid_blocks) {
