@@ -781,26 +781,39 @@ __global__ void __launch_bounds__(kThreads, 4) deep_fix_batched_kernel(BatchArgs
   __shared__ int s_key[kThreads];
   __shared__ int s_n;
   __shared__ DeepPhases s_ph;
+  __shared__ sgp4_request s_req[kThreads];
   if (threadIdx.x < 8) deep_phase(threadIdx.x, s_ph);   // visible after deep_slice's barrier
-  for (int k = 0; k < a.n_req; ++k) {
-    const sgp4_request q = a.reqs[k];
-    if (q.n == 0 || q.t_count == 0) continue;
-    Range rg;
-    rg.tsince = a.tsince + q.t_offset;
-    rg.jd_day = nullptr;
-    rg.jd_frac = nullptr;
-    rg.jd0 = 0;
-    rg.T = q.t_count;
-    rg.per_sat = 0;
-    rg.sat0 = q.sat_offset;
-    using Out = std::conditional_t<kFP32, float, double>;
-    rg.r = static_cast<Out*>(a.r) + q.out_offset * 3;
-    rg.v = static_cast<Out*>(a.v) + q.out_offset * 3;
-    rg.status = a.status + q.out_offset;
-    for (int64_t j0 = (int64_t)blockIdx.x * kThreads; j0 < q.n;
-         j0 += (int64_t)gridDim.x * kThreads)
-      deep_slice<Out>(a.rp, a.g, rg, j0, min(q.n, j0 + kThreads), 0, (int)q.t_count, s_sel,
-                      s_key, &s_n, &s_ph);
+  using Out = std::conditional_t<kFP32, float, double>;
+  // The request table kThreads entries at a time through shared memory (one load each,
+  // in parallel, instead of one dependent load per request per block); request k's
+  // slices of kThreads satellites start at block k mod gridDim, so that the first slices
+  // of the many small requests spread over the blocks instead of all going to block 0.
+  for (int k0 = 0; k0 < a.n_req; k0 += kThreads) {
+    const int nk = min(kThreads, a.n_req - k0);
+    __syncthreads();   // the previous chunk's requests are no longer read
+    if ((int)threadIdx.x < nk) s_req[threadIdx.x] = a.reqs[k0 + threadIdx.x];
+    __syncthreads();
+    for (int kk = 0; kk < nk; ++kk) {
+      const sgp4_request q = s_req[kk];
+      if (q.n == 0 || q.t_count == 0) continue;
+      const int64_t first =
+          ((int64_t)blockIdx.x + gridDim.x - (int64_t)((k0 + kk) % gridDim.x)) % gridDim.x;
+      if (first * kThreads >= q.n) continue;
+      Range rg;
+      rg.tsince = a.tsince + q.t_offset;
+      rg.jd_day = nullptr;
+      rg.jd_frac = nullptr;
+      rg.jd0 = 0;
+      rg.T = q.t_count;
+      rg.per_sat = 0;
+      rg.sat0 = q.sat_offset;
+      rg.r = static_cast<Out*>(a.r) + q.out_offset * 3;
+      rg.v = static_cast<Out*>(a.v) + q.out_offset * 3;
+      rg.status = a.status + q.out_offset;
+      for (int64_t j0 = first * kThreads; j0 < q.n; j0 += (int64_t)gridDim.x * kThreads)
+        deep_slice<Out>(a.rp, a.g, rg, j0, min(q.n, j0 + kThreads), 0, (int)q.t_count, s_sel,
+                        s_key, &s_n, &s_ph);
+    }
   }
 }
 
