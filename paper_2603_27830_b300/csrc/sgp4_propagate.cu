@@ -89,9 +89,10 @@ __device__ __forceinline__ void epoch_minutes(const RecordPtrs& rp, int64_t rec,
 // that met more than the queue's capacity of them rescans its own units for the mark
 // instead (one thread per unit, so a thread may then recompute several states in a row).
 // The batched kernel's tiles hold kFixCap entries; the single-problem kernel's queue
-// takes the dynamic shared memory that the time grid's split table leaves free (at least
-// kFixCap entries, 6,300 on a 100-time grid): a few blocks of the catalogue workload
-// queue close to 300 states, and their rescans had made the whole launch 55% longer.
+// takes the dynamic shared memory its launch asks for beyond the time grid's split table
+// (2,048 entries, or at least kFixCap on the longest split grids): a few blocks of the
+// catalogue workload queue close to 300 states, and their rescans past a 256-entry queue
+// had made the whole launch 55% longer.
 constexpr int kFixCap = 256;
 struct FixQueue {
   int64_t* idx;   // state index within the range, j * T + i
@@ -537,7 +538,9 @@ __global__ void __launch_bounds__(kThreads, kFP32 ? SGP4_MIN_BLOCKS_FP32 : SGP4_
   if (kFP32 && threadIdx.x == 0) {
     const int used = use_split ? (int)a.t_count : 0;
     s_fq.idx = reinterpret_cast<int64_t*>(s_split + used);
-    s_fq.cap = kSplitMaxT + kFixCap - used;
+    unsigned dyn_bytes;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+    s_fq.cap = (int)(dyn_bytes / sizeof(int64_t)) - used;
     s_fq.n = 0;
   }
   const int32_t jd0 = a.jd_day ? __ldg(a.jd_day) : 0;
@@ -879,16 +882,24 @@ template <bool kFP32, int kSpu, bool kPre = false, bool kJd = false, bool kCons 
 cudaError_t launch_spu(const PropArgs& a, cudaStream_t stream) {
   const int64_t total = a.rp.n * units_per_sat(a.t_count, kSpu);
   if (total == 0) return cudaSuccess;
-  // FP32: the split table and the guard-band queue share kFP32Dyn bytes of dynamic
-  // shared memory (an opt-in above 48 KB), whatever the grid length, so that the
-  // resident blocks per SM below hold for every launch.
+  // FP32: the split table and the guard-band queue share the dynamic shared memory (an
+  // opt-in above 48 KB): the grid's split times, then kFixQueueMin queue entries (the
+  // queue takes what the table leaves, within kFP32Dyn bytes in all).  The resident
+  // blocks per SM are found once with the largest size, so they hold for every launch.
+  // A launch asks only for what its grid needs: the rest of the SM's 256 KB of L1 and
+  // shared memory is then L1 cache, which a grid of one time per satellite (a 160-byte
+  // record row read per state) needs (1e6 satellites x 1 time: 61 -> 41 us).
   constexpr size_t kFP32Dyn = (size_t)(kSplitMaxT + kFixCap) * sizeof(int64_t);
+  constexpr int64_t kFixQueueMin = 2048;
   static_assert(sizeof(int64_t) == sizeof(float2), "queue entries reuse split slots");
-  const size_t dyn = kFP32 ? kFP32Dyn : 0;
+  const int64_t split_t = (!a.grid_per_sat && a.t_count <= kSplitMaxT) ? a.t_count : 0;
+  const size_t dyn = kFP32 ? std::min<size_t>(kFP32Dyn, (size_t)(split_t + kFixQueueMin) *
+                                                            sizeof(int64_t))
+                           : 0;
   static std::atomic<int> bps_dev[kMaxDevices];
   int bps = 0;
   const cudaError_t be = device_bps(bps_dev, propagate_kernel<kFP32, kSpu, kPre, kJd, kCons>,
-                                    dyn, kFP32, &bps);
+                                    kFP32 ? kFP32Dyn : 0, kFP32, &bps);
   if (be != cudaSuccess) return be;
   const int64_t tiles = (total + kThreads - 1) / kThreads;
   const int64_t grid = std::min<int64_t>(tiles, (int64_t)device_sm_count() * bps);
