@@ -154,8 +154,16 @@ __device__ __forceinline__ void jac_loop(const JacArgs& a, const SatShared<T>& s
   }
 }
 
+// Resident blocks per SM asked of the register allocator for the FP32 kernel: four, not
+// the six of the other FP32 sweeps.  Each thread's 6 x 7 Jacobian sits in local memory
+// (the seed loop writes its rows at a run-time index), and at six blocks that local
+// memory (768 threads x 168 B) no longer fitted the L1 left beside the blocks' shared
+// memory: sgp4_jacobian with covariance on 10,000 x 500 took 1.99 ms at six blocks,
+// 1.84 at four, 1.98 at three and 1.90 at two (CUDA events, A/B on one box).
+constexpr int kJacMinBlocksFP32 = 4;
+
 template <class T>
-__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kAdjMinBlocksFP32 : 1)
+__global__ void __launch_bounds__(kAdjThreads, sizeof(T) == 4 ? kJacMinBlocksFP32 : 1)
     jacobian_kernel(JacArgs a) {
   __shared__ T Ji[kNumAdj][7];
   __shared__ T C[7][7];
