@@ -119,8 +119,8 @@ def test_deep_space_catalogue_every_state(precision):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_mixed_catalogue(precision):
     """Near-Earth and deep-space records interleaved in one record set: each class
-    to its own bar, every status bit for bit (the FP32 launch leaves the deep-space
-    states to the FP64 deep-space kernel after it)."""
+    to its own bar, every status bit for bit (the propagation's blocks leave the
+    deep-space states to the deep-space pass, the same launch's last blocks)."""
     rng = np.random.default_rng(7)
     near = W.catalogue_elements(rng, 4000)
     deep = W.deep_space_elements(rng, 1000)
@@ -131,6 +131,27 @@ def test_mixed_catalogue(precision):
     day = rng.integers(2458000, 2462000, n).astype(np.int32)
     frac = rng.uniform(0.0, 1.0, n)
     t = np.linspace(0.0, 10080.0, 64)
+    r, v, st, ist = _propagate(el, t, day, frac, precision)
+    _compare(el, t, day, frac, precision, r, v, st, ist,
+             near_bar=(FP32_CATALOGUE_7D_KM, FP32_CATALOGUE_7D_KMS))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [(1, 5), (3, 1), (2500, 1), (40, 3000)])
+def test_deep_pass_launch_shapes(precision, shape):
+    """The deep-space pass at the launch shapes that size its share of the launch
+    differently: one satellite, a few, many satellites at one time each (one grid part
+    per work item), a long grid (many parts); deep-space and near-Earth records mixed."""
+    n, T = shape
+    rng = np.random.default_rng(100 + n)
+    deep = W.deep_space_elements(rng, n)
+    near = W.catalogue_elements(rng, n)
+    pick = rng.random(n) < 0.5
+    pick[0] = True                         # at least one deep-space record
+    el = np.where(pick[:, None], deep, near)
+    day = rng.integers(2458000, 2462000, n).astype(np.int32)
+    frac = rng.uniform(0.0, 1.0, n)
+    t = np.sort(rng.uniform(-1440.0, 10080.0, T))
     r, v, st, ist = _propagate(el, t, day, frac, precision)
     _compare(el, t, day, frac, precision, r, v, st, ist,
              near_bar=(FP32_CATALOGUE_7D_KM, FP32_CATALOGUE_7D_KMS))
