@@ -29,11 +29,12 @@ enum AdjField {
 
 constexpr int kAdjThreads = 128;
 constexpr int kAdjWarps = kAdjThreads / 32;
-// Resident blocks per SM asked of the register allocator for the FP32 sweeps.  Their
-// forward values take 260 B of shared memory per thread (33 KB per block), so six
-// blocks is the most an SM holds; on B300 six (80 registers, some spilled to L1) ran
-// 20% faster than two (255 registers, no spills) and 7% faster than four.
-constexpr int kAdjMinBlocksFP32 = 6;
+// Resident blocks per SM asked of the register allocator for the FP32 fit step (one
+// state per thread, its forward values in a 212-byte shared-memory slot per thread, 28 KB
+// per block).  On B300 (sgp4_fit_step, 10,000 x 500, CUDA events): five blocks (96
+// registers) 0.776 ms, six (80) 0.787, four (128) 0.780, three 0.853.  The packed adjoint
+// and the Jacobian kernel choose their own.
+constexpr int kAdjMinBlocksFP32 = 5;
 
 // Values of the forward pass of one state that the reverse sweep reads (names as in
 // the propagation: a, e, a_xN, a_yN, E, p_L, r, u and the short-period terms).  The
