@@ -110,12 +110,15 @@ __global__ void __launch_bounds__(kAdjThreads, 1) adjoint_prop_kernel64(AdjArgs 
 // count, so the 16 threads of a half-warp's 8-byte accesses hit distinct bank pairs).
 // Against the scalar FP32 sweep (one state per thread, 128 threads, 6 blocks per SM)
 // it issues 570 instead of 906 instructions per state; the fitting workload's
-// sgp4_adjoint (10,000 x 500) went 0.1925 -> 0.170 ms on B300.  Six blocks of 64 per SM
-// (168 registers) measured best: four 0.227 ms; eight, with the slot cut to 49 words so
-// that eight fit in shared memory, 0.186 (128 registers, their spills in the loop).
+// sgp4_adjoint (10,000 x 500) went 0.1925 -> 0.166 ms on B300.  The thread's 33 sums are
+// kept as floats (the pair's two adjoints added first) rather than as pairs: 33
+// registers fewer, so that eight blocks of 64 per SM fit in 128 registers each (the
+// 49-word slot lets eight fit in shared memory): 0.166 ms, against 0.170 for pairs of
+// sums at six blocks (168 registers), 0.186 for pairs at eight (spills in the loop) and
+// 0.227 at four.
 constexpr int kAdj2Threads = 64;
 #ifndef SGP4_ADJ2_MIN_BLOCKS
-#define SGP4_ADJ2_MIN_BLOCKS 6
+#define SGP4_ADJ2_MIN_BLOCKS 8
 #endif
 constexpr int kAdj2MinBlocks = SGP4_ADJ2_MIN_BLOCKS;
 constexpr int kAdjFixCap = 256;
@@ -239,9 +242,9 @@ __global__ void __launch_bounds__(kAdj2Threads, kAdj2MinBlocks) adjoint_prop_ker
   }
   const float* gr = static_cast<const float*>(a.grad_r);
   const float* gv = static_cast<const float*>(a.grad_v);
-  P2 acc[kNumAdj];
+  float acc[kNumAdj];
 #pragma unroll
-  for (int q = 0; q < kNumAdj; ++q) acc[q] = P2(0.0f);
+  for (int q = 0; q < kNumAdj; ++q) acc[q] = 0.0f;
   Fwd<P2>& f = sfwd[tid];
   const int64_t npair = (a.T + 1) / 2;
   double tn0 = 0.0, tn1 = 0.0;   // the times of the thread's next pair, loaded ahead
@@ -262,7 +265,7 @@ __global__ void __launch_bounds__(kAdj2Threads, kAdj2MinBlocks) adjoint_prop_ker
     adj_forward_times(a, sat, p, t0, t1, f, code);
     reload_barrier();
     if (usable(code[0]) && usable(code[1])) {
-      reverse(f, sat.k, g_r, g_v, [&](int q, P2 v) { acc[q] += v; });
+      reverse(f, sat.k, g_r, g_v, [&](int q, P2 v) { acc[q] += v.v.x + v.v.y; });
     } else {
       for (int l = 0; l < 2; ++l)
         if (code[l] == kRecomputeFP64 || usable(code[l]))
@@ -275,7 +278,7 @@ __global__ void __launch_bounds__(kAdj2Threads, kAdj2MinBlocks) adjoint_prop_ker
   // added in FP64.
   float* row = reinterpret_cast<float*>(&sfwd[tid]);
 #pragma unroll
-  for (int q = 0; q < kNumAdj; ++q) row[q] = acc[q].v.x + acc[q].v.y;
+  for (int q = 0; q < kNumAdj; ++q) row[q] = acc[q];
   __syncthreads();   // (also: every state queued)
   adj_fix_queued2(a, sat, &s_fq, row, j);
   __syncthreads();
